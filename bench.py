@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Throughput of the simulated-bifurcation solver on one GB300.
+
+One bench step = one pass of the whole SB hot path over the workload, inputs
+already resident in HBM: Philox initial state, S fused SB steps (CSR coupling
+product over R replicas + symplectic-Euler update + wall), FP64 QUBO energy of
+sgn(x) for every replica, arg-min and the best replica's selection.
+Metric: spin-updates/s = N * R * S / step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs the same workload on its own GPU with its own
+seed (independent replicas, no collective on the data path); the step time is
+the max over ranks and the value is the sum of the ranks' spin-updates.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SB spin-updates/s & time-to-target-energy: batched BF16 vs plain FP32, 1 GB300"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="event1000")
+    ap.add_argument("--variant", default="bsb", choices=["asb", "bsb", "dsb"])
+    ap.add_argument("--sb-steps", type=int, default=0, help="override S (0: workload's)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttt", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu, enabled=True):
+        self.proc = None
+        self.path = None
+        if not enabled:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(name, sb_steps):
+    from paper_2402_14718_gb300.workloads import WORKLOADS
+    w = dict(WORKLOADS[name])
+    if sb_steps:
+        w["steps"] = sb_steps
+    return w
+
+
+# ---------------------------------------------------------------- oracle (CPU) leg
+def oracle_sample(w, variant, target_s=15.0, seed=1):
+    """Time the FP64 oracle on a bounded sample of the workload: the full QUBO
+    and replica count, as many SB steps as fit in about ``target_s`` seconds."""
+    from oracle import events as oev, ising, qubo as oq, sb as osb
+    kw = dict(w["cuts"])
+    kw["five_hit_rule"] = bool(kw["five_hit_rule"])
+    ev = oev.generate(w["seed"], oev.EventParams(n_tracks=w["n_tracks"], noise_frac=w["noise_frac"]))
+    q = oq.build_qubo(ev, oq.BuildParams(**kw))
+    J, h, _ = ising.to_ising(q)
+    c0 = ising.c0_auto(J, q.n)
+    R, S = w["replicas"], w["steps"]
+    x, y = osb.init_state(seed, q.n, R)
+    sched = osb.linear_schedule(w["a0"], S)
+    v = {"asb": osb.ASB, "bsb": osb.BSB, "dsb": osb.DSB}[variant]
+    t0 = time.perf_counter()
+    k = 0
+    while k < S and (time.perf_counter() - t0) < target_s:
+        x, y = osb.step(J, h, x, y, float(sched[k]), w["a0"], c0, w["dt"], v)
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": q.n * R * k / dt, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} of {S} SB steps, N={q.n}, R={R}, FP64 NumPy/SciPy, one thread",
+            "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload(args.workload, args.sb_steps)
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        vals.append(oracle_sample(w, args.variant, target_s=8.0))
+    timed = vals[args.warmup:]
+    value = float(np.mean([t["value"] for t in timed]))
+    sec = float(np.mean([t["seconds"] for t in timed]))
+    cpu = dict(timed[0])
+    cpu["value"] = value
+    cpu.pop("seconds", None)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "spin-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "variant": args.variant, "replicas": w["replicas"],
+                       "sb_steps": w["steps"], "n_tracks": w["n_tracks"]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU leg
+def run_ours(args):
+    import torch
+    import paper_2402_14718_gb300 as sb
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    w = workload(args.workload, args.sb_steps)
+    R, S, a0, dt = w["replicas"], w["steps"], w["a0"], w["dt"]
+    prec = sb.SB_J_BF16 if w["jprec"] == "bf16" else sb.SB_J_FP32
+
+    # untimed: synthetic event and QUBO (host C++), as in the paper the QUBO build is not timed
+    ev = sb.sb_event_generate(w["seed"], sb.event_params(n_tracks=w["n_tracks"],
+                                                         noise_frac=w["noise_frac"]))
+    q = sb.sb_qubo_build(ev, sb.build_params(**w["cuts"]))
+    N, nnz = q.n, q.nnz
+    ctx = sb.sb_create(N, q.rowptr, q.col, q.val, q.lin, prec)
+    sched = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
+    d_E = torch.empty(R, dtype=torch.float64, device=dev)
+    d_bE = torch.empty(1, dtype=torch.float64, device=dev)
+    d_br = torch.empty(1, dtype=torch.int32, device=dev)
+    d_T = torch.empty(N, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    seed0 = 1000 * (rank + 1)
+
+    def one_step(seed, ev_marks=None):
+        if ev_marks:
+            ev_marks[0].record(stream)
+        sb.sb_run(ctx, args.variant, a0, 0.0, dt, 0, R, seed, None, stream)   # init
+        if ev_marks:
+            ev_marks[1].record(stream)
+        sb.sb_advance(ctx, args.variant, a0, 0.0, dt, S, sched, stream)       # S fused steps
+        if ev_marks:
+            ev_marks[2].record(stream)
+        sb.sb_readout_device(ctx, d_E, d_bE, d_br, d_T, stream)              # FP64 energy + arg-min
+        if ev_marks:
+            ev_marks[3].record(stream)
+
+    for i in range(args.warmup):
+        one_step(seed0 + i)
+    torch.cuda.synchronize(dev)
+
+    marks = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    clocks = Clocks(local, enabled=not args.no_clocks)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()                      # L2 flush between timed steps (outside the marks)
+        one_step(seed0 + args.warmup + i, marks[i])
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [m[0].elapsed_time(m[3]) for m in marks]
+    sweep_ms = [m[1].elapsed_time(m[2]) for m in marks]
+    ms = float(np.sum(step_ms)) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = N * R * S
+    value = units * ws / (ms * 1e-3)
+
+    # dominant kernel: the fused SB step (k_step), average launch over the timed region
+    kstep_s = float(np.mean(sweep_ms)) * 1e-3 / S
+    jbytes = 2 if prec == sb.SB_J_BF16 else 4
+    alg_bytes = 16 * N * R + nnz * (4 + jbytes) + (N + 1) * 4 + N * 4
+    hbm, src = peaks()
+    achieved = alg_bytes / kstep_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "kernel": "k_step",
+                "peak_source": src, "alg_bytes_per_launch": alg_bytes,
+                "kstep_us": kstep_s * 1e6}
+
+    # end to end through the public API with host buffers (pinned), every step:
+    # H2D of the QUBO, conversion, init, S steps, readout, D2H of the result
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+           (("rowptr", q.rowptr), ("col", q.col), ("val", q.val), ("lin", q.lin))}
+    T_host = torch.empty(N, dtype=torch.uint8).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in pin.values())
+    d2h = N + 8 + 4
+    e2e_steps = max(1, min(args.steps, 3))
+    from paper_2402_14718_gb300 import _lib
+    import ctypes
+
+    def e2e_once(seed):
+        h = ctypes.c_void_p()
+        _lib.check(_lib.lib.sb_create(N, nnz, pin["rowptr"].data_ptr(), pin["col"].data_ptr(),
+                                      pin["val"].data_ptr(), pin["lin"].data_ptr(), prec,
+                                      ctypes.byref(h)))
+        c2 = sb.Ctx(h.value)
+        sb.sb_run(c2, args.variant, a0, 0.0, dt, S, R, seed)
+        E = ctypes.c_double()
+        r = ctypes.c_int32()
+        _lib.check(_lib.lib.sb_best(c2.handle, T_host.data_ptr(), ctypes.byref(E), ctypes.byref(r)))
+        sb.sb_destroy(c2)
+        return E.value
+
+    e2e_once(7)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        e2e_once(100 + i)
+    torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": units * ws / e2e_s, "unit": "spin-updates/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s}
+
+    extra = {}
+    if rank == 0 and not args.no_ttt:
+        extra["ttt"] = time_to_target(sb, ctx, q, ev, w, args.variant, stream, sched, dev)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(w, args.variant)
+        cpu.pop("seconds", None)
+
+    launches_per_step = 2 + S + 4   # set_c0 + init, S x k_step, energy partial/reduce/argmin/best_T
+    line = {"metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_tracks": w["n_tracks"], "N": N, "nnz": nnz,
+                       "replicas": R, "sb_steps": S, "variant": args.variant,
+                       "J": w["jprec"], "state": "f32", "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas{ws}"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk, "wall_s_timed": t_wall}
+    line.update(extra)
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def time_to_target(sb, ctx, q, ev, w, variant, stream, sched, dev):
+    """TTT (section "Results"): energies of every replica each `every` steps on
+    one run; target = 99.9 % of the lowest energy known (the truth selection's
+    energy or the best found); TTT = min_k t(k) ln(0.01) / ln(1 - p_s(k))."""
+    import torch
+    R, S, a0, dt = w["replicas"], w["steps"], w["a0"], w["dt"]
+    every = 50
+    ev_a = ev.arrays()
+    part = ev_a["particle"]
+    truth = np.array([1 if part[a] == part[b] == part[c] >= 0 else 0 for a, b, c in q.trip],
+                     np.int8)
+    E_truth = float(sb.sb_energy(ctx, np.where(truth > 0, 1, -1).astype(np.int8)[:, None])[0, 0])
+    d_E = torch.empty(R, dtype=torch.float64, device=dev)
+    start = torch.cuda.Event(enable_timing=True)
+    marks = []
+    energies = []
+    sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)   # chunks of `every` steps: direct launches
+    sb.sb_run(ctx, variant, a0, 0.0, dt, 0, R, 4242, None, stream)
+    start.record(stream)
+    for k0 in range(0, S, every):
+        n = min(every, S - k0)
+        sb.sb_advance(ctx, variant, a0, 0.0, dt, n, sched[k0:k0 + n], stream)
+        sb.sb_readout_device(ctx, d_E, None, None, None, stream)
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        marks.append(e)
+        energies.append(d_E.clone())
+    torch.cuda.synchronize(dev)
+    sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 1)
+    times = [start.elapsed_time(m) * 1e-3 for m in marks]
+    Es = [e.cpu().numpy() for e in energies]
+    e_best = min(E_truth, min(float(e.min()) for e in Es))
+    target = e_best + 0.001 * abs(e_best)
+    best = math.inf
+    for t, e in zip(times, Es):
+        p = float(np.mean(e <= target))
+        if p >= 1.0:
+            best = min(best, t)
+        elif p > 0.0:
+            best = min(best, t * math.log(0.01) / math.log(1.0 - p))
+    T_best, E_b, _ = sb.sb_best(ctx)
+    sc = sb.sb_tracks(ev, q, T_best)
+    return {"seconds": None if best == math.inf else best, "target": target, "E_best": e_best,
+            "E_truth": E_truth, "E_final_best": float(E_b[0]), "checkpoint_every": every,
+            "efficiency": sc["efficiency"], "purity": sc["purity"],
+            "note": "one run of R replicas with a readout every 50 steps (the readouts are timed)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,253 @@
+/*
+ * sb.h -- C ABI of the GB300 simulated-bifurcation (SB) tracking library.
+ *
+ * The library solves the triplet QUBO of track reconstruction (Okawa, Zeng,
+ * Tao, Yung, arXiv:2402.14718) with ballistic / discrete / adiabatic
+ * simulated bifurcation on one GPU, and carries the host-side pieces that
+ * feed and score it: a synthetic barrel event generator, the triplet-QUBO
+ * builder and track assembly with efficiency / purity.
+ *
+ * Conventions (every entry point):
+ *  - a status code is returned; SB_OK = 0. On failure sb_last_error() gives a
+ *    thread-local message. No C++ exception crosses this boundary.
+ *  - inputs are copied; the caller keeps ownership of every buffer it passes.
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    global memory of the current device (e.g. a torch tensor's data_ptr()).
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream. Calls documented "asynchronous" only enqueue work on `stream`.
+ *  - CSR matrices hold both triangles of a symmetric matrix, columns strictly
+ *    ascending within a row, no diagonal entry, int32 indices.
+ *  - SB state is replica-minor: element (i, r) of an N x R array lives at
+ *    [i * R + r].
+ */
+#ifndef SB_H
+#define SB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SB_OK = 0,
+  SB_ERR_ARG = 1,      /* invalid argument (null pointer, size out of range) */
+  SB_ERR_CSR = 2,      /* malformed CSR: unsorted, out of range, diagonal, asymmetric */
+  SB_ERR_CUDA = 3,     /* a CUDA runtime call failed; see sb_last_error() */
+  SB_ERR_OOM = 4,      /* device allocation failed */
+  SB_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+  SB_ERR_STATE = 6     /* call out of order (e.g. readout before any run) */
+} sb_status;
+
+typedef enum { SB_ASB = 0, SB_BSB = 1, SB_DSB = 2 } sb_variant;
+typedef enum { SB_J_FP32 = 0, SB_J_BF16 = 1 } sb_jprec;
+
+/* Thread-local text of the last error raised on this thread ("" if none). */
+const char* sb_last_error(void);
+
+/* Library version string. */
+const char* sb_version(void);
+
+/* ======================================================================
+ * Host side: synthetic events, triplet QUBO, tracks. No GPU involved.
+ * ====================================================================== */
+
+/*
+ * Synthetic barrel event; stands in for the TrackML events of section
+ * "Dataset" (tt-bar + pile-up, barrel only, 10 layers, 2 T).
+ * Tracks: q = +-1, 1/pT ~ U[inv_pt_min, inv_pt_max] GeV^-1, eta ~ U(-eta_max,
+ * eta_max), phi0 ~ U[0, 2pi), z0 ~ N(0, z0_sigma); helix in B = bz tesla
+ * (Rc[mm] = 1000 pT / (0.3 bz)); one hit per cylinder radius, r*phi and z
+ * smeared by N(0, smear_rphi) and N(0, smear_z); floor(noise_frac * n_true +
+ * 0.5) uniform noise hits. Random numbers: Philox4x32-10 keyed by the seed.
+ * Hits are sorted by (layer, phi in [-pi, pi), generation index).
+ */
+typedef struct {
+  int32_t n_tracks;
+  int32_t n_layers;        /* <= 16; radii[0..n_layers-1] ascending, mm */
+  double radii[16];
+  double noise_frac;
+  double bz;               /* tesla */
+  double inv_pt_min, inv_pt_max;
+  double eta_max;
+  double z0_sigma;         /* mm */
+  double smear_rphi;       /* mm */
+  double smear_z;          /* mm */
+} sb_event_params;
+
+/* Fill `p` with the defaults: 100 tracks, 10 layers at 32..1000 mm, 10 % noise,
+ * 2 T, 1/pT in [0.1, 1], |eta| < 1, sigma_z0 = 5 mm, 0.1 mm smear. */
+void sb_event_params_default(sb_event_params* p);
+
+typedef struct sb_event sb_event;  /* opaque; owns its hit arrays */
+
+/* Generate one event. *out must be released with sb_event_destroy. */
+sb_status sb_event_generate(uint64_t seed, const sb_event_params* p, sb_event** out);
+int32_t sb_event_num_hits(const sb_event* ev);
+int32_t sb_event_num_true(const sb_event* ev);
+/* Copy hit arrays (each of sb_event_num_hits entries; any pointer may be NULL).
+ * particle = generating track index, -1 for a noise hit. */
+sb_status sb_event_hits(const sb_event* ev, int32_t* layer, double* r, double* phi,
+                        double* z, double* x, double* y, int32_t* particle);
+void sb_event_destroy(sb_event* ev);
+
+/*
+ * Triplet QUBO builder: sections "QUBO Formulation" (Eq. 13) and "QUBO
+ * Generation and Track Finding" (Eq. 16, 17, pruning).
+ *  doublets: consecutive layers, |wrap(dphi)| <= dphi_slope (r_out - r_in) +
+ *            dphi_margin / r_in, |z_in - r_in (z_out - z_in)/(r_out - r_in)| <= z0_max;
+ *  triplets: doublets sharing the middle hit, |kappa| <= kappa_max (signed
+ *            curvature of the circle through the 3 transverse points, mm^-1)
+ *            and |theta_bc - theta_ab| <= dtheta_max (Eq. 16);
+ *  quadruplets: (a,b,c),(b,c,d) with |kappa_t - kappa_u| <= dkappa_max (Eq. 17);
+ *  pruning: with five_hit_rule a quadruplet must have a consistent neighbour
+ *            on either side; triplets in no kept quadruplet are dropped;
+ *  weights: b = -1 consistent pair, +w_c conflict (shared hit, same or
+ *            adjacent start layer, not consistent), else 0;
+ *            a_i = w_q * (|kappa_i|/kappa_max + dtheta_i/dtheta_max) / 2.
+ * Triplets are indexed in lexicographic (hit a, hit b, hit c) order.
+ */
+typedef struct {
+  double dphi_slope, dphi_margin, z0_max;
+  double kappa_max, dtheta_max, dkappa_max;
+  double w_q, w_c;
+  int32_t five_hit_rule;
+} sb_build_params;
+
+void sb_build_params_default(sb_build_params* p);
+
+typedef struct sb_qubo sb_qubo;  /* opaque; owns its arrays */
+
+sb_status sb_qubo_build(const sb_event* ev, const sb_build_params* p, sb_qubo** out);
+sb_status sb_qubo_sizes(const sb_qubo* q, int32_t* n, int64_t* nnz);
+/* Copy out (host buffers; any may be NULL): rowptr[n+1], col[nnz], val[nnz]
+ * (b_ij), lin[n] (a_i), cls[nnz] (0 consistent, 1 conflict), quality[n],
+ * trip[3n] (hit ids a,b,c), kappa[n], dtheta[n]. */
+sb_status sb_qubo_arrays(const sb_qubo* q, int32_t* rowptr, int32_t* col, double* val,
+                         double* lin, int8_t* cls, double* quality, int32_t* trip,
+                         double* kappa, double* dtheta);
+void sb_qubo_destroy(sb_qubo* q);
+
+/*
+ * Track finding and scoring (last paragraph of "QUBO Generation and Track
+ * Finding"; Eq. 18-19). T[n] (host, 0/1) selects triplets; their doublets are
+ * merged, hits with more than one selected outgoing or incoming doublet lose
+ * them all, the rest is chained, candidates with < min_hits hits are dropped.
+ * Outputs (host, any may be NULL): n_tracks; track_ptr[n_tracks+1] and
+ * track_hits[] (capacity num_hits + 1 and num_hits suffice), tracks ordered by
+ * first hit; counts[3] = TP, FP, FN on doublets; eff_pur[2] = efficiency,
+ * purity (0 when a denominator is 0).
+ */
+sb_status sb_tracks(const sb_event* ev, const sb_qubo* q, const uint8_t* T, int32_t min_hits,
+                    int32_t* n_tracks, int32_t* track_ptr, int32_t* track_hits,
+                    int64_t* counts, double* eff_pur);
+
+/* ======================================================================
+ * Device side: the SB solver on one GPU.
+ * ====================================================================== */
+
+typedef struct sb_ctx sb_ctx;  /* opaque; owns every device buffer it allocates */
+
+/*
+ * sb_create -- QUBO (Eq. 13) -> Ising problem on the device.
+ * Host inputs: CSR (rowptr[n+1], col[nnz], qval[nnz] = b_ij) and qlin[n] = a_i.
+ * The CSR is validated on the host (SB_ERR_CSR). The arrays are copied to the
+ * device, where the conversion runs in FP64 (T = (1+s)/2):
+ *   J_ij = -b_ij / 4,  h_i = -(a_i/2 + sum_j b_ij / 4),
+ *   offset = sum_i a_i / 2 + sum_{i<j} b_ij / 4,
+ *   sigma_J = sqrt(sum_{i!=j} J_ij^2 / (n (n-1))),  c0_auto = 0.5 / (sqrt(n) sigma_J).
+ * J is stored as `prec` (FP32 or BF16) for the SB step and b, a stay in FP64
+ * for the energies. Synchronous. 1 <= n < 2^31 - 1, 0 <= nnz < 2^31.
+ */
+sb_status sb_create(int32_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                    const double* qval, const double* qlin, sb_jprec prec, sb_ctx** out);
+
+/*
+ * sb_create_batch -- many independent QUBOs (events) in one context, solved
+ * together by every later call. Host inputs: n_events, n_per_event[E],
+ * nnz_per_event[E] and the per-event CSRs concatenated (each rowptr of length
+ * n_e + 1 starting at 0, local column indices), qval and qlin concatenated.
+ * Each event keeps its own h, offset, sigma_J and c0. Synchronous.
+ */
+sb_status sb_create_batch(int32_t n_events, const int32_t* n_per_event,
+                          const int64_t* nnz_per_event, const int32_t* rowptr,
+                          const int32_t* col, const double* qval, const double* qlin,
+                          sb_jprec prec, sb_ctx** out);
+
+void sb_destroy(sb_ctx* ctx);
+
+/* Sizes and FP64 scalars of event `e` (0 for a single QUBO). Any pointer may be NULL. */
+sb_status sb_info(const sb_ctx* ctx, int32_t e, int32_t* n, int64_t* nnz, double* offset,
+                  double* sigma_j, double* c0_auto);
+int32_t sb_num_events(const sb_ctx* ctx);
+int32_t sb_total_rows(const sb_ctx* ctx);
+
+/*
+ * sb_run -- SB time evolution, section "Simulated Bifurcation":
+ *   aSB (Eq. 1-2), bSB (Eq. 5-8, wall at |x| > 1), dSB (Eq. 9-12, sgn(x_j) in
+ *   the coupling), symplectic Euler: y += dt (-(a0 - a_k) x [- x^3 for aSB]
+ *   + c0 (sum_j J_ij g(x_j) + h_i)); x += dt a0 y; wall (bSB, dSB):
+ *   |x| > 1 -> x = sgn(x), y = 0.
+ * Initial state: x, y ~ U(-0.01, 0.01) from Philox4x32-10, counter
+ * (row within event, replica, 3, event), key = seed.
+ * c0 <= 0 selects each event's c0_auto. a_sched: device FP32 array of `steps`
+ * values a_k, or NULL for the linear ramp a_k = a0 k / (steps - 1).
+ * Allocates the N x R state on first use (kept for later calls with the same
+ * R). 1 <= replicas <= 65535, 0 <= steps. Asynchronous on `stream`.
+ */
+sb_status sb_run(sb_ctx* ctx, sb_variant variant, double a0, double c0, double dt,
+                 int32_t steps, int32_t replicas, uint64_t seed, const float* a_sched,
+                 void* stream);
+
+/*
+ * sb_advance -- continue the current state for `steps` more steps; a_sched
+ * (device, `steps` values) is required. Used for checkpoint / resume.
+ * Asynchronous on `stream`.
+ */
+sb_status sb_advance(sb_ctx* ctx, sb_variant variant, double a0, double c0, double dt,
+                     int32_t steps, const float* a_sched, void* stream);
+
+/*
+ * sb_set_state / sb_get_state -- copy the N x R FP32 state (x, y) in or out
+ * (replica-minor). on_device = 0: host buffers; 1: device buffers. set_state
+ * fixes R = replicas (allocating if needed). Synchronous.
+ */
+sb_status sb_set_state(sb_ctx* ctx, const float* x, const float* y, int32_t replicas,
+                       int32_t on_device);
+sb_status sb_get_state(const sb_ctx* ctx, float* x, float* y, int32_t on_device);
+
+/*
+ * sb_energy -- QUBO energies O(T) of Eq. 13 in FP64 for R spin vectors.
+ * spins: host int8 [N x R] (replica-minor, +1 selects the triplet, anything
+ * else does not), or NULL to read sgn(x) of the current state (x > 0 -> T = 1).
+ * out_E: host double [E x R] (event-major). Synchronous.
+ */
+sb_status sb_energy(sb_ctx* ctx, const int8_t* spins, int32_t replicas, double* out_E);
+
+/*
+ * sb_best -- readout of the current state: FP64 QUBO energy of every replica
+ * of every event, arg-min over replicas (ties -> lowest replica index), and the
+ * best replica's 0/1 selection. Host outputs, any may be NULL:
+ * out_T[N] (all events' rows), out_E[E], out_replica[E]. Synchronous.
+ */
+sb_status sb_best(sb_ctx* ctx, uint8_t* out_T, double* out_E, int32_t* out_replica);
+
+/*
+ * sb_readout_device -- sb_best with device outputs, asynchronous on `stream`:
+ * d_E_all[E x R] (may be NULL), d_best_E[E], d_best_r[E], d_T[N] (may be NULL).
+ */
+sb_status sb_readout_device(sb_ctx* ctx, double* d_E_all, double* d_best_E, int32_t* d_best_r,
+                            uint8_t* d_T, void* stream);
+
+/*
+ * sb_set_option -- per-context switches.
+ *   SB_OPT_GRAPH (0): 1 (default) replays runs of >= 8 steps from a captured
+ *   CUDA graph; 0 launches one kernel per step directly on the stream.
+ */
+#define SB_OPT_GRAPH 0
+sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SB_H */

@@ -99,3 +99,35 @@ def hamiltonian(J, h, x, y, a, a0, c0, variant):
     if variant == ASB:
         pot = pot + 0.25 * np.sum(x ** 4, axis=0)
     return kin + pot
+
+
+def step_rows(J, h, x, y, rows, a_k, a0, c0, dt, variant):
+    """The step above for a subset of rows only (neighbours read from the full x);
+    returns the new (x, y) of those rows."""
+    rows = np.asarray(rows)
+    g = np.sign(x) if variant == DSB else x
+    f = J[rows] @ g
+    xr, yr = x[rows], y[rows]
+    force = -(a0 - a_k) * xr + c0 * (f + h[rows][:, None])
+    if variant == ASB:
+        force = force - xr ** 3
+    yr = yr + dt * force
+    xr = xr + dt * a0 * yr
+    if variant != ASB:
+        hit = np.abs(xr) > 1.0
+        xr = np.where(hit, np.sign(xr), xr)
+        yr = np.where(hit, 0.0, yr)
+    return xr, yr
+
+
+def prewall_x(J, h, x, y, a_k, a0, c0, dt, variant, rows=None):
+    """Position after the momentum and position update but before the wall
+    (used to recognise wall decisions that sit within rounding of |x| = 1)."""
+    if rows is None:
+        rows = np.arange(x.shape[0])
+    g = np.sign(x) if variant == DSB else x
+    xr, yr = x[rows], y[rows]
+    force = -(a0 - a_k) * xr + c0 * (J[rows] @ g + h[rows][:, None])
+    if variant == ASB:
+        force = force - xr ** 3
+    return xr + dt * a0 * (yr + dt * force)

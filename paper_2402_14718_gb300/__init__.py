@@ -1,0 +1,298 @@
+"""GB300 simulated-bifurcation solver for the triplet QUBO of track
+reconstruction (Okawa, Zeng, Tao, Yung, arXiv:2402.14718).
+
+Thin Python binding of the C ABI in include/sb.h: the functions keep the C
+names and only marshal arguments (numpy arrays for host buffers, torch CUDA
+tensors or raw integers for device buffers and streams). Every step of the
+solver runs in the library's CUDA kernels; there is no Python or CPU fallback.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (SB_ASB, SB_BSB, SB_DSB, SB_J_BF16, SB_J_FP32, SB_OPT_GRAPH, SbError, check,
+                   lib)
+
+__all__ = [
+    "SB_ASB", "SB_BSB", "SB_DSB", "SB_J_FP32", "SB_J_BF16", "SB_OPT_GRAPH", "SbError",
+    "event_params", "build_params", "sb_event_generate", "sb_qubo_build", "sb_tracks",
+    "sb_create", "sb_create_batch", "sb_destroy", "sb_info", "sb_run", "sb_advance",
+    "sb_set_state", "sb_get_state", "sb_energy", "sb_best", "sb_readout_device", "sb_set_option",
+    "sb_version", "LIB_PATH",
+]
+
+LIB_PATH = _lib.LIB_PATH
+VARIANTS = {"asb": SB_ASB, "bsb": SB_BSB, "dsb": SB_DSB}
+
+
+def _variant(v):
+    return VARIANTS[v.lower()] if isinstance(v, str) else int(v)
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev_ptr(t):
+    """Device pointer of a torch CUDA tensor, an int, or None."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def sb_version():
+    return lib.sb_version().decode()
+
+
+# ------------------------------------------------------------------ host side
+def event_params(**kw):
+    p = _lib.SbEventParams()
+    lib.sb_event_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "radii":
+            p.n_layers = len(v)
+            for i, r in enumerate(v):
+                p.radii[i] = r
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def build_params(**kw):
+    p = _lib.SbBuildParams()
+    lib.sb_build_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, int(v) if k == "five_hit_rule" else v)
+    return p
+
+
+class Event:
+    """Owns an sb_event handle; ``arrays()`` copies the hits out."""
+
+    def __init__(self, handle):
+        self._h = handle
+        self.n_hits = lib.sb_event_num_hits(handle)
+        self.n_true = lib.sb_event_num_true(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def arrays(self):
+        n = self.n_hits
+        out = {"layer": np.zeros(n, np.int32), "r": np.zeros(n), "phi": np.zeros(n),
+               "z": np.zeros(n), "x": np.zeros(n), "y": np.zeros(n),
+               "particle": np.zeros(n, np.int32)}
+        check(lib.sb_event_hits(self._h, *(out[k].ctypes.data_as(ctypes.c_void_p) for k in
+                                           ("layer", "r", "phi", "z", "x", "y", "particle"))))
+        return out
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib.sb_event_destroy(self._h)
+            self._h = None
+
+
+def sb_event_generate(seed, params=None):
+    h = ctypes.c_void_p()
+    p = params if params is not None else event_params()
+    check(lib.sb_event_generate(ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), ctypes.byref(p),
+                                ctypes.byref(h)))
+    return Event(h.value)
+
+
+class Qubo:
+    """Owns an sb_qubo handle; arrays are copied out at construction."""
+
+    def __init__(self, handle):
+        self._h = handle
+        n = ctypes.c_int32()
+        nnz = ctypes.c_int64()
+        check(lib.sb_qubo_sizes(handle, ctypes.byref(n), ctypes.byref(nnz)))
+        self.n, self.nnz = n.value, nnz.value
+        self.rowptr = np.zeros(self.n + 1, np.int32)
+        self.col = np.zeros(self.nnz, np.int32)
+        self.val = np.zeros(self.nnz)
+        self.lin = np.zeros(self.n)
+        self.cls = np.zeros(self.nnz, np.int8)
+        self.quality = np.zeros(self.n)
+        self.trip = np.zeros((self.n, 3), np.int32)
+        self.kappa = np.zeros(self.n)
+        self.dtheta = np.zeros(self.n)
+        check(lib.sb_qubo_arrays(handle, *(a.ctypes.data_as(ctypes.c_void_p) for a in (
+            self.rowptr, self.col, self.val, self.lin, self.cls, self.quality, self.trip,
+            self.kappa, self.dtheta))))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib.sb_qubo_destroy(self._h)
+            self._h = None
+
+
+def sb_qubo_build(event, params=None):
+    h = ctypes.c_void_p()
+    p = params if params is not None else build_params()
+    check(lib.sb_qubo_build(event.handle, ctypes.byref(p), ctypes.byref(h)))
+    return Qubo(h.value)
+
+
+def sb_tracks(event, qubo, T, min_hits=4):
+    T, pT = _host(T, np.uint8)
+    if T.shape[0] != qubo.n:
+        raise ValueError("T must have one entry per triplet")
+    nh = event.n_hits
+    ntr = ctypes.c_int32()
+    ptr = np.zeros(nh + 1, np.int32)
+    hits = np.zeros(max(nh, 1), np.int32)
+    counts = np.zeros(3, np.int64)
+    ep = np.zeros(2)
+    check(lib.sb_tracks(event.handle, qubo.handle, pT, int(min_hits), ctypes.byref(ntr),
+                        ptr.ctypes.data_as(ctypes.c_void_p), hits.ctypes.data_as(ctypes.c_void_p),
+                        counts.ctypes.data_as(ctypes.c_void_p), ep.ctypes.data_as(ctypes.c_void_p)))
+    tracks = [hits[ptr[k]:ptr[k + 1]].tolist() for k in range(ntr.value)]
+    return {"tracks": tracks, "tp": int(counts[0]), "fp": int(counts[1]), "fn": int(counts[2]),
+            "efficiency": float(ep[0]), "purity": float(ep[1])}
+
+
+# ------------------------------------------------------------------ device side
+class Ctx:
+    """Owns an sb_ctx handle (device memory is released by sb_destroy / GC)."""
+
+    def __init__(self, handle):
+        self._h = handle
+        self.n_events = lib.sb_num_events(handle)
+        self.n = lib.sb_total_rows(handle)
+        self.R = 0
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("context destroyed")
+        return self._h
+
+    def __del__(self):
+        sb_destroy(self)
+
+
+def sb_create(n, rowptr, col, qval, qlin, prec=SB_J_FP32):
+    rp, prp = _host(rowptr, np.int32)
+    c, pc = _host(col, np.int32)
+    v, pv = _host(qval, np.float64)
+    a, pa = _host(qlin, np.float64)
+    h = ctypes.c_void_p()
+    check(lib.sb_create(int(n), int(c.shape[0]), prp, pc, pv, pa, int(prec), ctypes.byref(h)))
+    return Ctx(h.value)
+
+
+def sb_create_batch(events, prec=SB_J_FP32):
+    """``events``: sequence of (rowptr, col, qval, qlin) per event (local indices)."""
+    ns = np.array([len(e[3]) for e in events], np.int32)
+    zs = np.array([len(e[1]) for e in events], np.int64)
+    rp, prp = _host(np.concatenate([np.asarray(e[0], np.int32) for e in events]), np.int32)
+    c, pc = _host(np.concatenate([np.asarray(e[1], np.int32) for e in events]), np.int32)
+    v, pv = _host(np.concatenate([np.asarray(e[2], np.float64) for e in events]), np.float64)
+    a, pa = _host(np.concatenate([np.asarray(e[3], np.float64) for e in events]), np.float64)
+    h = ctypes.c_void_p()
+    check(lib.sb_create_batch(len(events), ns.ctypes.data_as(ctypes.c_void_p),
+                              zs.ctypes.data_as(ctypes.c_void_p), prp, pc, pv, pa, int(prec),
+                              ctypes.byref(h)))
+    return Ctx(h.value)
+
+
+def sb_destroy(ctx):
+    if getattr(ctx, "_h", None):
+        lib.sb_destroy(ctx._h)
+        ctx._h = None
+
+
+def sb_info(ctx, e=0):
+    n = ctypes.c_int32()
+    nnz = ctypes.c_int64()
+    off, sig, c0 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    check(lib.sb_info(ctx.handle, int(e), ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(off),
+                      ctypes.byref(sig), ctypes.byref(c0)))
+    return {"n": n.value, "nnz": nnz.value, "offset": off.value, "sigma_j": sig.value,
+            "c0_auto": c0.value}
+
+
+def sb_run(ctx, variant, a0, c0, dt, steps, replicas, seed, a_sched=None, stream=None):
+    check(lib.sb_run(ctx.handle, _variant(variant), float(a0), float(c0), float(dt), int(steps),
+                     int(replicas), ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
+                     _dev_ptr(a_sched), _stream(stream)))
+    ctx.R = int(replicas)
+
+
+def sb_advance(ctx, variant, a0, c0, dt, steps, a_sched, stream=None):
+    check(lib.sb_advance(ctx.handle, _variant(variant), float(a0), float(c0), float(dt),
+                         int(steps), _dev_ptr(a_sched), _stream(stream)))
+
+
+def sb_set_state(ctx, x, y):
+    """``x``, ``y``: [N, R] float32, numpy (host) or torch CUDA tensors (device)."""
+    if isinstance(x, np.ndarray):
+        xs, px = _host(x, np.float32)
+        ys, py = _host(y, np.float32)
+        R = xs.shape[1] if xs.ndim == 2 else 1
+        check(lib.sb_set_state(ctx.handle, px, py, R, 0))
+    else:
+        R = x.shape[1] if x.dim() == 2 else 1
+        check(lib.sb_set_state(ctx.handle, _dev_ptr(x), _dev_ptr(y), R, 1))
+    ctx.R = int(R)
+
+
+def sb_get_state(ctx):
+    """Current (x, y) as host float32 arrays of shape [N, R]."""
+    x = np.zeros((ctx.n, ctx.R), np.float32)
+    y = np.zeros((ctx.n, ctx.R), np.float32)
+    check(lib.sb_get_state(ctx.handle, x.ctypes.data_as(ctypes.c_void_p),
+                           y.ctypes.data_as(ctypes.c_void_p), 0))
+    return x, y
+
+
+def sb_energy(ctx, spins=None, replicas=None):
+    """QUBO energies [E, R]; ``spins`` int8 [N, R] (+1 selects) or None for sgn(x)."""
+    if spins is not None:
+        s, ps = _host(spins, np.int8)
+        R = s.shape[1] if s.ndim == 2 else 1
+    else:
+        ps, R = None, int(replicas or ctx.R)
+    out = np.zeros((ctx.n_events, R))
+    check(lib.sb_energy(ctx.handle, ps, R, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def sb_best(ctx):
+    """(T [N] uint8 of the best replica per event, best energy [E], best replica [E])."""
+    T = np.zeros(ctx.n, np.uint8)
+    E = np.zeros(ctx.n_events)
+    r = np.zeros(ctx.n_events, np.int32)
+    check(lib.sb_best(ctx.handle, T.ctypes.data_as(ctypes.c_void_p),
+                      E.ctypes.data_as(ctypes.c_void_p), r.ctypes.data_as(ctypes.c_void_p)))
+    return T, E, r
+
+
+def sb_readout_device(ctx, d_E_all=None, d_best_E=None, d_best_r=None, d_T=None, stream=None):
+    check(lib.sb_readout_device(ctx.handle, _dev_ptr(d_E_all), _dev_ptr(d_best_E),
+                                _dev_ptr(d_best_r), _dev_ptr(d_T), _stream(stream)))
+
+
+def sb_set_option(ctx, key, value):
+    check(lib.sb_set_option(ctx.handle, int(key), int(value)))

@@ -1,0 +1,101 @@
+"""ctypes declarations of the C ABI in include/sb.h (argument marshalling only).
+
+Loading builds the in-tree library first if it is missing or older than its
+sources; if that fails the import fails: there is no fallback path.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+c_int32, c_int64, c_uint64, c_double = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+c_void_p, c_char_p = ctypes.c_void_p, ctypes.c_char_p
+P = ctypes.POINTER
+
+SB_OK, SB_ERR_ARG, SB_ERR_CSR, SB_ERR_CUDA, SB_ERR_OOM, SB_ERR_TIMEOUT, SB_ERR_STATE = range(7)
+SB_ASB, SB_BSB, SB_DSB = 0, 1, 2
+SB_J_FP32, SB_J_BF16 = 0, 1
+SB_OPT_GRAPH = 0
+
+
+class SbEventParams(ctypes.Structure):
+    _fields_ = [("n_tracks", c_int32), ("n_layers", c_int32), ("radii", c_double * 16),
+                ("noise_frac", c_double), ("bz", c_double), ("inv_pt_min", c_double),
+                ("inv_pt_max", c_double), ("eta_max", c_double), ("z0_sigma", c_double),
+                ("smear_rphi", c_double), ("smear_z", c_double)]
+
+
+class SbBuildParams(ctypes.Structure):
+    _fields_ = [("dphi_slope", c_double), ("dphi_margin", c_double), ("z0_max", c_double),
+                ("kappa_max", c_double), ("dtheta_max", c_double), ("dkappa_max", c_double),
+                ("w_q", c_double), ("w_c", c_double), ("five_hit_rule", c_int32)]
+
+
+class SbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sb status {code}: {msg}")
+        self.code = code
+
+
+_SIGS = {
+    "sb_last_error": (c_char_p, []),
+    "sb_version": (c_char_p, []),
+    "sb_event_params_default": (None, [P(SbEventParams)]),
+    "sb_event_generate": (c_int32, [c_uint64, P(SbEventParams), P(c_void_p)]),
+    "sb_event_num_hits": (c_int32, [c_void_p]),
+    "sb_event_num_true": (c_int32, [c_void_p]),
+    "sb_event_hits": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_void_p, c_void_p]),
+    "sb_event_destroy": (None, [c_void_p]),
+    "sb_build_params_default": (None, [P(SbBuildParams)]),
+    "sb_qubo_build": (c_int32, [c_void_p, P(SbBuildParams), P(c_void_p)]),
+    "sb_qubo_sizes": (c_int32, [c_void_p, P(c_int32), P(c_int64)]),
+    "sb_qubo_arrays": (c_int32, [c_void_p] + [c_void_p] * 9),
+    "sb_qubo_destroy": (None, [c_void_p]),
+    "sb_tracks": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, P(c_int32), c_void_p,
+                            c_void_p, c_void_p, c_void_p]),
+    "sb_create": (c_int32, [c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                            P(c_void_p)]),
+    "sb_create_batch": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                  c_void_p, c_int32, P(c_void_p)]),
+    "sb_destroy": (None, [c_void_p]),
+    "sb_info": (c_int32, [c_void_p, c_int32, P(c_int32), P(c_int64), P(c_double), P(c_double),
+                          P(c_double)]),
+    "sb_num_events": (c_int32, [c_void_p]),
+    "sb_total_rows": (c_int32, [c_void_p]),
+    "sb_run": (c_int32, [c_void_p, c_int32, c_double, c_double, c_double, c_int32, c_int32,
+                         c_uint64, c_void_p, c_void_p]),
+    "sb_advance": (c_int32, [c_void_p, c_int32, c_double, c_double, c_double, c_int32, c_void_p,
+                             c_void_p]),
+    "sb_set_state": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32]),
+    "sb_get_state": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
+    "sb_energy": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p]),
+    "sb_best": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sb_readout_device": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sb_set_option": (c_int32, [c_void_p, c_int32, c_int64]),
+}
+
+
+def _load():
+    path = _build.LIB
+    try:
+        _build.build()
+    except Exception as exc:  # a missing toolchain with a present library is fine
+        if not os.path.exists(path):
+            raise ImportError(f"libsbtrack.so is missing and could not be built: {exc}") from exc
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+LIB_PATH = _build.LIB
+
+
+def check(status):
+    if status != SB_OK:
+        raise SbError(status, lib.sb_last_error().decode(errors="replace"))
+    return status

@@ -1,0 +1,725 @@
+// C ABI of the SB solver: context life cycle, QUBO -> Ising set-up, SB runs
+// (one launch per step, replayed from a captured CUDA graph), FP64 readout.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sb.h"
+#include "device/kernels.cuh"
+
+namespace sbh {
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+}  // namespace sbh
+
+using sbh::set_error;
+
+namespace {
+
+const int kEnergyRowsMin = 64;
+
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  int variant = -1, steps = -1, R = -1, cur = -1, G = -1;
+  float a0 = 0.f, dt = 0.f;
+  const float* sched = nullptr;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    steps = -1;
+  }
+};
+
+}  // namespace
+
+struct sb_ctx {
+  int device = 0;
+  int32_t E = 1;
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int jbf16 = 0;
+  std::vector<int32_t> ev_row0;  // [E + 1]
+  std::vector<int64_t> ev_nnz;   // [E]
+  std::vector<double> offset, sigma, c0_auto;
+  // device: problem
+  int32_t* d_rowptr = nullptr;
+  int32_t* d_col = nullptr;
+  double* d_qval = nullptr;
+  double* d_qlin = nullptr;
+  void* d_J = nullptr;
+  double* d_h64 = nullptr;
+  float* d_h32 = nullptr;
+  int32_t* d_row_event = nullptr;  // only when E > 1
+  int32_t* d_ev_row0 = nullptr;
+  double* d_offset = nullptr;
+  double* d_sigma = nullptr;
+  double* d_c0auto = nullptr;
+  float* d_c0ev = nullptr;
+  // device: state
+  int32_t R = 0;
+  float* d_x[2] = {nullptr, nullptr};
+  float* d_y = nullptr;
+  int cur = 0;
+  bool have_state = false;
+  float* d_sched = nullptr;  // default linear schedule
+  int32_t sched_len = 0;
+  double sched_a0 = 0.0;
+  // readout (sized for eR replicas, independent of the state's R)
+  int32_t eR = 0;
+  int32_t energy_rows = 0, nblk = 0;
+  int32_t* d_blk_row = nullptr;
+  int32_t* d_ev_blk0 = nullptr;
+  double* d_partial = nullptr;
+  double* d_Eall = nullptr;
+  double* d_bestE = nullptr;
+  int32_t* d_bestr = nullptr;
+  uint8_t* d_T = nullptr;
+  int8_t* d_spins = nullptr;
+  int32_t spins_cap_R = 0;
+  // execution
+  cudaStream_t cap_stream = nullptr;
+  GraphCache graph;
+  int use_graph = 1;
+};
+
+namespace {
+
+#define SB_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));               \
+      return e_ == cudaErrorMemoryAllocation ? SB_ERR_OOM : SB_ERR_CUDA;           \
+    }                                                                              \
+  } while (0)
+
+template <typename T>
+sb_status dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return SB_ERR_OOM;
+  }
+  return SB_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+sb_status validate_csr(int32_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                       const double* val, const double* lin) {
+  if (rowptr[0] != 0 || (int64_t)rowptr[n] != nnz) {
+    set_error("CSR: rowptr[0] must be 0 and rowptr[n] must equal nnz");
+    return SB_ERR_CSR;
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    if (rowptr[i + 1] < rowptr[i]) {
+      set_error("CSR: rowptr decreases at row " + std::to_string(i));
+      return SB_ERR_CSR;
+    }
+    if (!std::isfinite(lin[i])) {
+      set_error("linear term is not finite at row " + std::to_string(i));
+      return SB_ERR_ARG;
+    }
+    for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      const int32_t j = col[p];
+      if (j < 0 || j >= n) {
+        set_error("CSR: column out of range in row " + std::to_string(i));
+        return SB_ERR_CSR;
+      }
+      if (j == i) {
+        set_error("CSR: diagonal entry in row " + std::to_string(i));
+        return SB_ERR_CSR;
+      }
+      if (p > rowptr[i] && col[p - 1] >= j) {
+        set_error("CSR: columns not strictly ascending in row " + std::to_string(i));
+        return SB_ERR_CSR;
+      }
+      if (!std::isfinite(val[p])) {
+        set_error("CSR: value not finite in row " + std::to_string(i));
+        return SB_ERR_ARG;
+      }
+    }
+  }
+  // symmetry: (i, j, v) needs (j, i, v)
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      const int32_t j = col[p];
+      const int32_t* b = col + rowptr[j];
+      const int32_t* e = col + rowptr[j + 1];
+      const int32_t* f = std::lower_bound(b, e, i);
+      if (f == e || *f != i || val[rowptr[j] + (f - b)] != val[p]) {
+        set_error("CSR: matrix is not symmetric at (" + std::to_string(i) + ", " +
+                  std::to_string(j) + ")");
+        return SB_ERR_CSR;
+      }
+    }
+  return SB_OK;
+}
+
+void free_readout(sb_ctx* c) {
+  dfree(c->d_partial);
+  dfree(c->d_Eall);
+  c->eR = 0;
+}
+
+void free_state(sb_ctx* c) {
+  dfree(c->d_x[0]);
+  dfree(c->d_x[1]);
+  dfree(c->d_y);
+  c->R = 0;
+  c->have_state = false;
+  c->graph.reset();
+}
+
+void free_all(sb_ctx* c) {
+  free_state(c);
+  free_readout(c);
+  dfree(c->d_rowptr);
+  dfree(c->d_col);
+  dfree(c->d_qval);
+  dfree(c->d_qlin);
+  if (c->d_J) cudaFree(c->d_J);
+  c->d_J = nullptr;
+  dfree(c->d_h64);
+  dfree(c->d_h32);
+  dfree(c->d_row_event);
+  dfree(c->d_ev_row0);
+  dfree(c->d_offset);
+  dfree(c->d_sigma);
+  dfree(c->d_c0auto);
+  dfree(c->d_c0ev);
+  dfree(c->d_sched);
+  dfree(c->d_blk_row);
+  dfree(c->d_ev_blk0);
+  dfree(c->d_bestE);
+  dfree(c->d_bestr);
+  dfree(c->d_T);
+  dfree(c->d_spins);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  c->cap_stream = nullptr;
+}
+
+// (Re)build the energy block table: blocks of `rows` rows that never straddle an event.
+sb_status ensure_energy_blocks(sb_ctx* c, int32_t rows) {
+  if (c->energy_rows == rows && c->d_blk_row) return SB_OK;
+  std::vector<int32_t> blk_row, ev_blk0;
+  for (int32_t e = 0; e < c->E; ++e) {
+    ev_blk0.push_back((int32_t)blk_row.size());
+    for (int32_t r = c->ev_row0[e]; r < c->ev_row0[e + 1]; r += rows) blk_row.push_back(r);
+  }
+  ev_blk0.push_back((int32_t)blk_row.size());
+  blk_row.push_back(c->n);
+  dfree(c->d_blk_row);
+  dfree(c->d_ev_blk0);
+  sb_status st = dalloc(&c->d_blk_row, blk_row.size());
+  if (st) return st;
+  st = dalloc(&c->d_ev_blk0, ev_blk0.size());
+  if (st) return st;
+  SB_CUDA(cudaMemcpy(c->d_blk_row, blk_row.data(), blk_row.size() * 4, cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(c->d_ev_blk0, ev_blk0.data(), ev_blk0.size() * 4, cudaMemcpyHostToDevice));
+  c->nblk = (int32_t)blk_row.size() - 1;
+  c->energy_rows = rows;
+  return SB_OK;
+}
+
+sb_status ensure_state(sb_ctx* c, int32_t R) {
+  if (c->R == R && c->d_y) return SB_OK;
+  free_state(c);
+  const size_t cnt = (size_t)c->n * R;
+  sb_status st;
+  if ((st = dalloc(&c->d_x[0], cnt)) || (st = dalloc(&c->d_x[1], cnt)) ||
+      (st = dalloc(&c->d_y, cnt)))
+    return st;
+  c->R = R;
+  c->cur = 0;
+  c->have_state = false;
+  return SB_OK;
+}
+
+sb_status ensure_readout(sb_ctx* c, int32_t R) {
+  const sbd::Tiling t = sbd::make_tiling(R);
+  const int32_t rows = std::max(kEnergyRowsMin, 256 / t.G);
+  if (c->eR == R && c->energy_rows == rows && c->d_partial && c->d_Eall) return SB_OK;
+  free_readout(c);
+  sb_status st = ensure_energy_blocks(c, rows);
+  if (st) return st;
+  if ((st = dalloc(&c->d_partial, (size_t)c->nblk * R)) ||
+      (st = dalloc(&c->d_Eall, (size_t)c->E * R)))
+    return st;
+  c->eR = R;
+  return SB_OK;
+}
+
+sb_status create_common(sb_ctx* c, const int32_t* rowptr, const int32_t* col, const double* qval,
+                        const double* qlin) {
+  SB_CUDA(cudaGetDevice(&c->device));
+  sb_status st;
+  const size_t n = (size_t)c->n, nnz = (size_t)c->nnz;
+  if ((st = dalloc(&c->d_rowptr, n + 1)) || (st = dalloc(&c->d_col, nnz)) ||
+      (st = dalloc(&c->d_qval, nnz)) || (st = dalloc(&c->d_qlin, n)) ||
+      (st = dalloc(&c->d_h64, n)) || (st = dalloc(&c->d_h32, n)) ||
+      (st = dalloc(&c->d_ev_row0, (size_t)c->E + 1)) || (st = dalloc(&c->d_offset, c->E)) ||
+      (st = dalloc(&c->d_sigma, c->E)) || (st = dalloc(&c->d_c0auto, c->E)) ||
+      (st = dalloc(&c->d_c0ev, c->E)) || (st = dalloc(&c->d_bestE, c->E)) ||
+      (st = dalloc(&c->d_bestr, c->E)) || (st = dalloc(&c->d_T, n)))
+    return st;
+  {
+    cudaError_t e = cudaMalloc(&c->d_J, std::max<size_t>(nnz, 1) * (c->jbf16 ? 2 : 4));
+    if (e != cudaSuccess) {
+      c->d_J = nullptr;
+      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      return SB_ERR_OOM;
+    }
+  }
+  SB_CUDA(cudaMemcpy(c->d_rowptr, rowptr, (n + 1) * 4, cudaMemcpyHostToDevice));
+  if (nnz) {
+    SB_CUDA(cudaMemcpy(c->d_col, col, nnz * 4, cudaMemcpyHostToDevice));
+    SB_CUDA(cudaMemcpy(c->d_qval, qval, nnz * 8, cudaMemcpyHostToDevice));
+  }
+  SB_CUDA(cudaMemcpy(c->d_qlin, qlin, n * 8, cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(c->d_ev_row0, c->ev_row0.data(), ((size_t)c->E + 1) * 4,
+                     cudaMemcpyHostToDevice));
+  if (c->E > 1) {
+    std::vector<int32_t> re(n);
+    for (int32_t e = 0; e < c->E; ++e)
+      for (int32_t i = c->ev_row0[e]; i < c->ev_row0[e + 1]; ++i) re[i] = e;
+    if ((st = dalloc(&c->d_row_event, n))) return st;
+    SB_CUDA(cudaMemcpy(c->d_row_event, re.data(), n * 4, cudaMemcpyHostToDevice));
+  }
+  double *row_off = nullptr, *row_sq = nullptr;
+  if ((st = dalloc(&row_off, n)) || (st = dalloc(&row_sq, n))) {
+    dfree(row_off);
+    dfree(row_sq);
+    return st;
+  }
+  cudaError_t e1 = sbd::launch_convert(c->d_rowptr, c->d_col, c->d_qval, c->d_qlin, c->n, c->d_J,
+                                       c->jbf16, c->d_h64, c->d_h32, row_off, row_sq, 0);
+  cudaError_t e2 = sbd::launch_event_stats(row_off, row_sq, c->d_ev_row0, c->E, c->d_offset,
+                                           c->d_sigma, c->d_c0auto, 0);
+  cudaError_t e3 = cudaDeviceSynchronize();
+  dfree(row_off);
+  dfree(row_sq);
+  SB_CUDA(e1);
+  SB_CUDA(e2);
+  SB_CUDA(e3);
+  c->offset.resize(c->E);
+  c->sigma.resize(c->E);
+  c->c0_auto.resize(c->E);
+  SB_CUDA(cudaMemcpy(c->offset.data(), c->d_offset, c->E * 8, cudaMemcpyDeviceToHost));
+  SB_CUDA(cudaMemcpy(c->sigma.data(), c->d_sigma, c->E * 8, cudaMemcpyDeviceToHost));
+  SB_CUDA(cudaMemcpy(c->c0_auto.data(), c->d_c0auto, c->E * 8, cudaMemcpyDeviceToHost));
+  SB_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  return SB_OK;
+}
+
+sb_status check_run_args(sb_ctx* c, sb_variant variant, double a0, double c0, double dt,
+                         int32_t steps) {
+  if (!c) {
+    set_error("null context");
+    return SB_ERR_ARG;
+  }
+  if (variant < SB_ASB || variant > SB_DSB) {
+    set_error("variant must be SB_ASB, SB_BSB or SB_DSB");
+    return SB_ERR_ARG;
+  }
+  if (!(a0 > 0.0) || !std::isfinite(a0) || !(dt > 0.0) || !std::isfinite(dt) ||
+      !std::isfinite(c0) || steps < 0) {
+    set_error("a0 and dt must be positive and finite, c0 finite, steps >= 0");
+    return SB_ERR_ARG;
+  }
+  return SB_OK;
+}
+
+// Enqueue `steps` SB steps reading x from c->d_x[c->cur]; flips c->cur.
+sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t steps,
+                        const float* sched, cudaStream_t stream) {
+  if (steps <= 0) return SB_OK;
+  const sbd::Tiling t = sbd::make_tiling(c->R);
+  sbd::StepArgs a;
+  a.rowptr = c->d_rowptr;
+  a.col = c->d_col;
+  a.J = c->d_J;
+  a.h = c->d_h32;
+  a.row_event = c->d_row_event;
+  a.c0_ev = c->d_c0ev;
+  a.sched = sched;
+  a.a0 = (float)a0;
+  a.dt = (float)dt;
+  a.dta0 = (float)(dt * a0);
+  a.y = c->d_y;
+  a.n = c->n;
+  a.R = c->R;
+  a.G = t.G;
+  const bool graph = c->use_graph && steps >= 8;
+  if (!graph) {
+    for (int32_t k = 0; k < steps; ++k) {
+      a.k = k;
+      a.xin = c->d_x[c->cur];
+      a.xout = c->d_x[c->cur ^ 1];
+      SB_CUDA(sbd::launch_step(variant, c->jbf16, t, a, stream));
+      c->cur ^= 1;
+    }
+    return SB_OK;
+  }
+  GraphCache& gc = c->graph;
+  if (!(gc.exec && gc.variant == variant && gc.steps == steps && gc.R == c->R &&
+        gc.cur == c->cur && gc.a0 == a.a0 && gc.dt == a.dt && gc.sched == sched && gc.G == t.G)) {
+    gc.reset();
+    cudaGraph_t g = nullptr;
+    SB_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int cur = c->cur;
+    cudaError_t err = cudaSuccess;
+    for (int32_t k = 0; k < steps && err == cudaSuccess; ++k) {
+      a.k = k;
+      a.xin = c->d_x[cur];
+      a.xout = c->d_x[cur ^ 1];
+      err = sbd::launch_step(variant, c->jbf16, t, a, c->cap_stream);
+      cur ^= 1;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    SB_CUDA(err);
+    SB_CUDA(e2);
+    cudaError_t e3 = cudaGraphInstantiate(&gc.exec, g, 0);
+    cudaGraphDestroy(g);
+    SB_CUDA(e3);
+    gc.variant = variant;
+    gc.steps = steps;
+    gc.R = c->R;
+    gc.cur = c->cur;
+    gc.a0 = a.a0;
+    gc.dt = a.dt;
+    gc.sched = sched;
+    gc.G = t.G;
+  }
+  SB_CUDA(cudaGraphLaunch(gc.exec, stream));
+  if (steps & 1) c->cur ^= 1;
+  return SB_OK;
+}
+
+// Energies of R replicas (from the current x, or from d_spins) into d_Eall, arg-min into
+// d_bestE / d_bestr.
+sb_status readout(sb_ctx* c, const int8_t* d_spins, int32_t R, cudaStream_t s) {
+  sb_status st = ensure_readout(c, R);
+  if (st) return st;
+  const sbd::Tiling t = sbd::make_tiling(R);
+  sbd::EnergyArgs a;
+  a.rowptr = c->d_rowptr;
+  a.col = c->d_col;
+  a.qval = c->d_qval;
+  a.qlin = c->d_qlin;
+  a.x = d_spins ? nullptr : c->d_x[c->cur];
+  a.spins = d_spins;
+  a.blk_row = c->d_blk_row;
+  a.nblk = c->nblk;
+  a.n = c->n;
+  a.R = R;
+  a.G = t.G;
+  a.partial = c->d_partial;
+  SB_CUDA(sbd::launch_energy_partial(t, a, s));
+  SB_CUDA(sbd::launch_energy_reduce(c->d_partial, c->d_ev_blk0, c->E, R, c->d_Eall, s));
+  SB_CUDA(sbd::launch_argmin(c->d_Eall, c->E, R, c->d_bestE, c->d_bestr, s));
+  return SB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sb_last_error(void) { return sbh::g_err.c_str(); }
+const char* sb_version(void) { return "sbtrack-gb300 0.1 (sm_103a)"; }
+
+sb_status sb_create(int32_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                    const double* qval, const double* qlin, sb_jprec prec, sb_ctx** out) {
+  if (!out) {
+    set_error("sb_create: null output pointer");
+    return SB_ERR_ARG;
+  }
+  int32_t ns[1] = {n};
+  int64_t zs[1] = {nnz};
+  return sb_create_batch(1, ns, zs, rowptr, col, qval, qlin, prec, out);
+}
+
+sb_status sb_create_batch(int32_t n_events, const int32_t* n_per_event,
+                          const int64_t* nnz_per_event, const int32_t* rowptr,
+                          const int32_t* col, const double* qval, const double* qlin,
+                          sb_jprec prec, sb_ctx** out) {
+  if (!out) {
+    set_error("sb_create_batch: null output pointer");
+    return SB_ERR_ARG;
+  }
+  *out = nullptr;
+  if (n_events < 1 || !n_per_event || !nnz_per_event || !rowptr || !qlin ||
+      (prec != SB_J_FP32 && prec != SB_J_BF16)) {
+    set_error("sb_create: invalid argument (event count, null pointer or precision)");
+    return SB_ERR_ARG;
+  }
+  int64_t ntot = 0, ztot = 0;
+  for (int32_t e = 0; e < n_events; ++e) {
+    if (n_per_event[e] < 1 || nnz_per_event[e] < 0) {
+      set_error("sb_create: every event needs n >= 1 and nnz >= 0");
+      return SB_ERR_ARG;
+    }
+    ntot += n_per_event[e];
+    ztot += nnz_per_event[e];
+  }
+  if (ntot >= 0x7FFFFFFFll || ztot >= 0x7FFFFFFFll) {
+    set_error("sb_create: total rows and nonzeros must stay below 2^31 - 1");
+    return SB_ERR_ARG;
+  }
+  if (ztot > 0 && (!col || !qval)) {
+    set_error("sb_create: null CSR arrays");
+    return SB_ERR_ARG;
+  }
+  // validate each event and build the global CSR (global column indices)
+  std::vector<int32_t> grp((size_t)ntot + 1), gcol((size_t)ztot);
+  std::vector<int32_t> ev_row0(n_events + 1);
+  int64_t rp_off = 0, z_off = 0, r_off = 0;
+  for (int32_t e = 0; e < n_events; ++e) {
+    const int32_t ne = n_per_event[e];
+    const int64_t ze = nnz_per_event[e];
+    const int32_t* rp = rowptr + rp_off;
+    sb_status st = validate_csr(ne, ze, rp, col + z_off, qval + z_off, qlin + r_off);
+    if (st) {
+      if (n_events > 1) set_error("event " + std::to_string(e) + ": " + sbh::g_err);
+      return st;
+    }
+    ev_row0[e] = (int32_t)r_off;
+    for (int32_t i = 0; i < ne; ++i) grp[r_off + i] = (int32_t)(z_off + rp[i]);
+    for (int64_t p = 0; p < ze; ++p) gcol[z_off + p] = (int32_t)(col[z_off + p] + r_off);
+    rp_off += ne + 1;
+    z_off += ze;
+    r_off += ne;
+  }
+  grp[ntot] = (int32_t)ztot;
+  ev_row0[n_events] = (int32_t)ntot;
+  sb_ctx* c = new (std::nothrow) sb_ctx;
+  if (!c) {
+    set_error("sb_create: host allocation failed");
+    return SB_ERR_OOM;
+  }
+  c->E = n_events;
+  c->n = (int32_t)ntot;
+  c->nnz = ztot;
+  c->jbf16 = prec == SB_J_BF16;
+  c->ev_row0 = ev_row0;
+  c->ev_nnz.assign(nnz_per_event, nnz_per_event + n_events);
+  sb_status st = create_common(c, grp.data(), gcol.data(), qval, qlin);
+  if (st) {
+    free_all(c);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return SB_OK;
+}
+
+void sb_destroy(sb_ctx* ctx) {
+  if (!ctx) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  free_all(ctx);
+  cudaSetDevice(prev);
+  delete ctx;
+}
+
+int32_t sb_num_events(const sb_ctx* ctx) { return ctx ? ctx->E : 0; }
+int32_t sb_total_rows(const sb_ctx* ctx) { return ctx ? ctx->n : 0; }
+
+sb_status sb_info(const sb_ctx* ctx, int32_t e, int32_t* n, int64_t* nnz, double* offset,
+                  double* sigma_j, double* c0_auto) {
+  if (!ctx || e < 0 || e >= ctx->E) {
+    set_error("sb_info: null context or event out of range");
+    return SB_ERR_ARG;
+  }
+  if (n) *n = ctx->ev_row0[e + 1] - ctx->ev_row0[e];
+  if (nnz) *nnz = ctx->ev_nnz[e];
+  if (offset) *offset = ctx->offset[e];
+  if (sigma_j) *sigma_j = ctx->sigma[e];
+  if (c0_auto) *c0_auto = ctx->c0_auto[e];
+  return SB_OK;
+}
+
+sb_status sb_run(sb_ctx* ctx, sb_variant variant, double a0, double c0, double dt,
+                 int32_t steps, int32_t replicas, uint64_t seed, const float* a_sched,
+                 void* stream) {
+  sb_status st = check_run_args(ctx, variant, a0, c0, dt, steps);
+  if (st) return st;
+  if (replicas < 1 || replicas > 65535) {
+    set_error("sb_run: replicas must be in [1, 65535]");
+    return SB_ERR_ARG;
+  }
+  if ((size_t)ctx->n * (size_t)replicas >= ((size_t)1 << 40)) {
+    set_error("sb_run: state too large");
+    return SB_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = ensure_state(ctx, replicas))) return st;
+  const float* sched = a_sched;
+  if (!sched && steps > 0) {
+    if (ctx->sched_len != steps || ctx->sched_a0 != a0) {
+      dfree(ctx->d_sched);
+      if ((st = dalloc(&ctx->d_sched, steps))) return st;
+      SB_CUDA(sbd::launch_linear_schedule(ctx->d_sched, steps, a0, s));
+      ctx->sched_len = steps;
+      ctx->sched_a0 = a0;
+    }
+    sched = ctx->d_sched;
+  }
+  SB_CUDA(sbd::launch_set_c0(ctx->d_c0ev, ctx->d_c0auto, c0, ctx->E, s));
+  ctx->cur = 0;
+  SB_CUDA(sbd::launch_init(ctx->d_x[0], ctx->d_y, ctx->d_row_event, ctx->d_ev_row0, ctx->n,
+                           ctx->R, seed, s));
+  ctx->have_state = true;
+  return enqueue_steps(ctx, variant, a0, dt, steps, sched, s);
+}
+
+sb_status sb_advance(sb_ctx* ctx, sb_variant variant, double a0, double c0, double dt,
+                     int32_t steps, const float* a_sched, void* stream) {
+  sb_status st = check_run_args(ctx, variant, a0, c0, dt, steps);
+  if (st) return st;
+  if (!ctx->have_state) {
+    set_error("sb_advance: no state (call sb_run or sb_set_state first)");
+    return SB_ERR_STATE;
+  }
+  if (steps > 0 && !a_sched) {
+    set_error("sb_advance: a_sched is required");
+    return SB_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  SB_CUDA(sbd::launch_set_c0(ctx->d_c0ev, ctx->d_c0auto, c0, ctx->E, s));
+  return enqueue_steps(ctx, variant, a0, dt, steps, a_sched, s);
+}
+
+sb_status sb_set_state(sb_ctx* ctx, const float* x, const float* y, int32_t replicas,
+                       int32_t on_device) {
+  if (!ctx || !x || !y || replicas < 1 || replicas > 65535) {
+    set_error("sb_set_state: invalid argument");
+    return SB_ERR_ARG;
+  }
+  sb_status st = ensure_state(ctx, replicas);
+  if (st) return st;
+  const size_t bytes = (size_t)ctx->n * replicas * 4;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  SB_CUDA(cudaDeviceSynchronize());
+  ctx->cur = 0;
+  SB_CUDA(cudaMemcpy(ctx->d_x[0], x, bytes, k));
+  SB_CUDA(cudaMemcpy(ctx->d_y, y, bytes, k));
+  ctx->have_state = true;
+  return SB_OK;
+}
+
+sb_status sb_get_state(const sb_ctx* ctx, float* x, float* y, int32_t on_device) {
+  if (!ctx || (!x && !y)) {
+    set_error("sb_get_state: invalid argument");
+    return SB_ERR_ARG;
+  }
+  if (!ctx->have_state) {
+    set_error("sb_get_state: no state");
+    return SB_ERR_STATE;
+  }
+  const size_t bytes = (size_t)ctx->n * ctx->R * 4;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  SB_CUDA(cudaDeviceSynchronize());
+  if (x) SB_CUDA(cudaMemcpy(x, ctx->d_x[ctx->cur], bytes, k));
+  if (y) SB_CUDA(cudaMemcpy(y, ctx->d_y, bytes, k));
+  return SB_OK;
+}
+
+sb_status sb_energy(sb_ctx* ctx, const int8_t* spins, int32_t replicas, double* out_E) {
+  if (!ctx || !out_E || replicas < 1 || replicas > 65535) {
+    set_error("sb_energy: invalid argument");
+    return SB_ERR_ARG;
+  }
+  sb_status st;
+  if (spins) {
+    if (ctx->spins_cap_R < replicas) {
+      dfree(ctx->d_spins);
+      if ((st = dalloc(&ctx->d_spins, (size_t)ctx->n * replicas))) return st;
+      ctx->spins_cap_R = replicas;
+    }
+    SB_CUDA(cudaMemcpy(ctx->d_spins, spins, (size_t)ctx->n * replicas, cudaMemcpyHostToDevice));
+  } else {
+    if (!ctx->have_state || ctx->R != replicas) {
+      set_error("sb_energy: no current state with that replica count");
+      return SB_ERR_STATE;
+    }
+  }
+  if ((st = readout(ctx, spins ? ctx->d_spins : nullptr, replicas, 0))) return st;
+  SB_CUDA(cudaDeviceSynchronize());
+  SB_CUDA(cudaMemcpy(out_E, ctx->d_Eall, (size_t)ctx->E * replicas * 8, cudaMemcpyDeviceToHost));
+  return SB_OK;
+}
+
+sb_status sb_readout_device(sb_ctx* ctx, double* d_E_all, double* d_best_E, int32_t* d_best_r,
+                            uint8_t* d_T, void* stream) {
+  if (!ctx) {
+    set_error("sb_readout_device: null context");
+    return SB_ERR_ARG;
+  }
+  if (!ctx->have_state) {
+    set_error("sb_readout_device: no state");
+    return SB_ERR_STATE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  sb_status st = readout(ctx, nullptr, ctx->R, s);
+  if (st) return st;
+  if (d_T)
+    SB_CUDA(sbd::launch_best_T(ctx->d_x[ctx->cur], ctx->d_row_event, ctx->d_bestr, ctx->n,
+                               ctx->R, d_T, s));
+  if (d_E_all)
+    SB_CUDA(cudaMemcpyAsync(d_E_all, ctx->d_Eall, (size_t)ctx->E * ctx->R * 8,
+                            cudaMemcpyDeviceToDevice, s));
+  if (d_best_E)
+    SB_CUDA(cudaMemcpyAsync(d_best_E, ctx->d_bestE, ctx->E * 8, cudaMemcpyDeviceToDevice, s));
+  if (d_best_r)
+    SB_CUDA(cudaMemcpyAsync(d_best_r, ctx->d_bestr, ctx->E * 4, cudaMemcpyDeviceToDevice, s));
+  return SB_OK;
+}
+
+sb_status sb_best(sb_ctx* ctx, uint8_t* out_T, double* out_E, int32_t* out_replica) {
+  if (!ctx) {
+    set_error("sb_best: null context");
+    return SB_ERR_ARG;
+  }
+  sb_status st = sb_readout_device(ctx, nullptr, nullptr, nullptr, out_T ? ctx->d_T : nullptr, 0);
+  if (st) return st;
+  SB_CUDA(cudaDeviceSynchronize());
+  if (out_T) SB_CUDA(cudaMemcpy(out_T, ctx->d_T, ctx->n, cudaMemcpyDeviceToHost));
+  if (out_E) SB_CUDA(cudaMemcpy(out_E, ctx->d_bestE, ctx->E * 8, cudaMemcpyDeviceToHost));
+  if (out_replica)
+    SB_CUDA(cudaMemcpy(out_replica, ctx->d_bestr, ctx->E * 4, cudaMemcpyDeviceToHost));
+  return SB_OK;
+}
+
+sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value) {
+  if (!ctx) {
+    set_error("sb_set_option: null context");
+    return SB_ERR_ARG;
+  }
+  switch (key) {
+    case 0:  // SB_OPT_GRAPH
+      ctx->use_graph = value != 0;
+      if (!ctx->use_graph) ctx->graph.reset();
+      return SB_OK;
+    default:
+      set_error("sb_set_option: unknown key");
+      return SB_ERR_ARG;
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,574 @@
+// Device kernels of the SB solver (sm_103a).
+//
+//  * k_convert / k_event_stats -- QUBO (Eq. 13) -> Ising in FP64.
+//  * k_init                    -- Philox4x32-10 initial state.
+//  * k_step                    -- one fused SB step: CSR coupling product over
+//                                 the replicas (Eq. 2 / 6 / 10), symplectic-Euler
+//                                 momentum and position update, inelastic wall.
+//  * k_energy_partial / k_energy_reduce / k_argmin / k_best_T -- FP64 QUBO
+//                                 energy of sgn(x), arg-min over replicas.
+//
+// State is replica-minor (element (i, r) at i * R + r): the R replicas of one
+// row are contiguous, so one group of threads reading row j of X for all its
+// replicas issues fully coalesced 16-byte loads.
+#include <cuda_bf16.h>
+#include <float.h>
+#include <limits.h>
+
+#include "../philox.h"
+#include "kernels.cuh"
+
+namespace sbd {
+
+Tiling make_tiling(int R) {
+  Tiling t;
+  t.V = (R % 4 == 0) ? 4 : 1;
+  t.C = R / t.V;
+  int G = 1;
+  while (G * 2 <= t.C && G < 32) G *= 2;
+  t.G = G;
+  const int per = (t.C + G - 1) / G;
+  t.NCH = per <= 1 ? 1 : (per <= 2 ? 2 : 4);
+  t.tiles = (t.C + G * t.NCH - 1) / (G * t.NCH);
+  return t;
+}
+
+namespace {
+
+constexpr int kBlock = 256;
+
+template <int V>
+struct Vec;
+template <>
+struct Vec<4> {
+  float v[4];
+  __device__ __forceinline__ void ldg(const float* p) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+  }
+  __device__ __forceinline__ void ld(const float* p) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+  }
+  __device__ __forceinline__ void st(float* p) const {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct Vec<1> {
+  float v[1];
+  __device__ __forceinline__ void ldg(const float* p) { v[0] = __ldg(p); }
+  __device__ __forceinline__ void ld(const float* p) { v[0] = *p; }
+  __device__ __forceinline__ void st(float* p) const { *p = v[0]; }
+};
+
+__device__ __forceinline__ float jval(const float* J, int p) { return __ldg(J + p); }
+__device__ __forceinline__ float jval(const __nv_bfloat16* J, int p) {
+  return __bfloat162float(J[p]);
+}
+
+__device__ __forceinline__ float sgnf(float x) { return (float)((x > 0.f) - (x < 0.f)); }
+
+// lanes of this thread's row group inside its warp
+__device__ __forceinline__ unsigned group_mask(int G) {
+  const int lane = threadIdx.x & 31;
+  return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+}
+
+// ---------------------------------------------------------------- SB step
+// One row per group of G threads; the group loads G (col, J) pairs of the row
+// at a time (coalesced) and broadcasts them with shuffles; every thread then
+// gathers its replica chunks of the neighbour rows with 16-byte loads, four
+// neighbours in flight at once.
+template <int V, int NCH, int VARIANT, typename JT>
+__global__ void __launch_bounds__(kBlock) k_step(const StepArgs a) {
+  const int G = a.G;
+  const int gid = threadIdx.x / G;
+  const int g = threadIdx.x - gid * G;
+  const int groups = blockDim.x / G;
+  const int row = blockIdx.x * groups + gid;
+  if (row >= a.n) return;  // whole group leaves together
+  const unsigned mask = group_mask(G);
+  const int R = a.R;
+  const int C = R / V;
+  const int ch0 = blockIdx.y * (G * NCH) + g;
+  const JT* J = static_cast<const JT*>(a.J);
+
+  float acc[NCH][V];
+#pragma unroll
+  for (int j = 0; j < NCH; ++j)
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[j][v] = 0.f;
+
+  const int p0 = __ldg(a.rowptr + row), p1 = __ldg(a.rowptr + row + 1);
+  for (int pb = p0; pb < p1; pb += G) {
+    const int cnt = min(G, p1 - pb);
+    int mc = 0;
+    float mv = 0.f;
+    if (g < cnt) {
+      mc = __ldg(a.col + pb + g);
+      mv = jval(J, pb + g);
+    }
+    int q = 0;
+    for (; q + 4 <= cnt; q += 4) {
+      int c[4];
+      float w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c[u] = __shfl_sync(mask, mc, q + u, G);
+        w[u] = __shfl_sync(mask, mv, q + u, G);
+      }
+      Vec<V> xv[4][NCH];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+          const int ch = ch0 + j * G;
+          if (ch < C) xv[u][j].ldg(a.xin + (size_t)c[u] * R + (size_t)ch * V);
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < NCH; ++j)
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const float xx = VARIANT == 2 ? sgnf(xv[u][j].v[v]) : xv[u][j].v[v];
+            acc[j][v] = fmaf(w[u], xx, acc[j][v]);
+          }
+    }
+    for (; q < cnt; ++q) {
+      const int c = __shfl_sync(mask, mc, q, G);
+      const float w = __shfl_sync(mask, mv, q, G);
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        const int ch = ch0 + j * G;
+        if (ch < C) {
+          Vec<V> xv;
+          xv.ldg(a.xin + (size_t)c * R + (size_t)ch * V);
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const float xx = VARIANT == 2 ? sgnf(xv.v[v]) : xv.v[v];
+            acc[j][v] = fmaf(w, xx, acc[j][v]);
+          }
+        }
+      }
+    }
+  }
+
+  // symplectic Euler: momentum with the old position, then position, then wall
+  const float pa = a.a0 - __ldg(a.sched + a.k);
+  const int e = a.row_event ? __ldg(a.row_event + row) : 0;
+  const float c0 = __ldg(a.c0_ev + e);
+  const float hi = __ldg(a.h + row);
+#pragma unroll
+  for (int j = 0; j < NCH; ++j) {
+    const int ch = ch0 + j * G;
+    if (ch >= C) continue;
+    const size_t idx = (size_t)row * R + (size_t)ch * V;
+    Vec<V> xv, yv;
+    xv.ldg(a.xin + idx);
+    yv.ld(a.y + idx);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      float x = xv.v[v], y = yv.v[v];
+      float force = -pa * x + c0 * (acc[j][v] + hi);
+      if (VARIANT == 0) force -= x * x * x;
+      y = y + a.dt * force;
+      x = x + a.dta0 * y;
+      if (VARIANT != 0 && fabsf(x) > 1.f) {
+        x = copysignf(1.f, x);
+        y = 0.f;
+      }
+      xv.v[v] = x;
+      yv.v[v] = y;
+    }
+    xv.st(a.xout + idx);
+    yv.st(a.y + idx);
+  }
+}
+
+template <int V, int NCH, int VARIANT>
+cudaError_t launch_step_t(int jbf16, const Tiling& t, const StepArgs& a, cudaStream_t s) {
+  const int groups = kBlock / t.G;
+  dim3 grid((a.n + groups - 1) / groups, t.tiles);
+  if (jbf16)
+    k_step<V, NCH, VARIANT, __nv_bfloat16><<<grid, kBlock, 0, s>>>(a);
+  else
+    k_step<V, NCH, VARIANT, float><<<grid, kBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int V, int NCH>
+cudaError_t launch_step_v(int variant, int jbf16, const Tiling& t, const StepArgs& a,
+                          cudaStream_t s) {
+  switch (variant) {
+    case 0: return launch_step_t<V, NCH, 0>(jbf16, t, a, s);
+    case 1: return launch_step_t<V, NCH, 1>(jbf16, t, a, s);
+    default: return launch_step_t<V, NCH, 2>(jbf16, t, a, s);
+  }
+}
+
+// ---------------------------------------------------------------- init / schedule
+__global__ void k_init(float* x, float* y, const int32_t* row_event, const int32_t* ev_row0,
+                       int32_t n, int32_t R, uint32_t k0, uint32_t k1) {
+  const size_t total = (size_t)n * R;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int32_t i = (int32_t)(idx / R), r = (int32_t)(idx - (size_t)i * R);
+    const int32_t e = row_event ? row_event[i] : 0;
+    const int32_t il = row_event ? i - ev_row0[e] : i;
+    const sbk::U32x4 w =
+        sbk::philox4x32_10((uint32_t)il, (uint32_t)r, sbk::kPurposeInit, (uint32_t)e, k0, k1);
+    x[idx] = sbk::init_value(w.v[0]);
+    y[idx] = sbk::init_value(w.v[1]);
+  }
+}
+
+__global__ void k_linear_schedule(float* sched, int32_t steps, double a0) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < steps; k += gridDim.x * blockDim.x)
+    sched[k] = steps > 1 ? (float)(a0 * (double)k / (double)(steps - 1)) : 0.f;
+}
+
+__global__ void k_set_c0(float* c0_ev, const double* c0_auto, double c0, int32_t E) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
+    c0_ev[e] = (float)(c0 > 0.0 ? c0 : c0_auto[e]);
+}
+
+// ---------------------------------------------------------------- QUBO -> Ising (FP64)
+__device__ __forceinline__ void store_j(float* J, int p, double v) { J[p] = (float)v; }
+__device__ __forceinline__ void store_j(__nv_bfloat16* J, int p, double v) {
+  J[p] = __double2bfloat16(v);
+}
+
+template <typename JT>
+__global__ void k_convert(const int32_t* rowptr, const int32_t* col, const double* qval,
+                          const double* qlin, int32_t n, JT* J, double* h64, float* h32,
+                          double* row_off, double* row_sq) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double s = 0.0, lo = 0.0, sq = 0.0;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      const double b = qval[p];
+      s += b;
+      const double jv = -b / 4.0;
+      store_j(J, p, jv);
+      sq += jv * jv;
+      if (col[p] < i) lo += b;
+    }
+    const double hv = -(qlin[i] / 2.0 + s / 4.0);
+    h64[i] = hv;
+    h32[i] = (float)hv;
+    row_off[i] = qlin[i] / 2.0 + lo / 4.0;
+    row_sq[i] = sq;
+  }
+}
+
+// one block per event: fixed-order tree reduction of the per-row terms
+__global__ void k_event_stats(const double* row_off, const double* row_sq,
+                              const int32_t* ev_row0, double* offset, double* sigma,
+                              double* c0_auto) {
+  __shared__ double so[kBlock], ss[kBlock];
+  const int e = blockIdx.x;
+  const int r0 = ev_row0[e], r1 = ev_row0[e + 1];
+  double a = 0.0, b = 0.0;
+  for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    a += row_off[i];
+    b += row_sq[i];
+  }
+  so[threadIdx.x] = a;
+  ss[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      so[threadIdx.x] += so[threadIdx.x + w];
+      ss[threadIdx.x] += ss[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double n = (double)(r1 - r0);
+    const double sg = n >= 2.0 ? sqrt(ss[0] / (n * (n - 1.0))) : 0.0;
+    offset[e] = so[0];
+    sigma[e] = sg;
+    c0_auto[e] = sg > 0.0 ? 0.5 / (sqrt(n) * sg) : 1.0;
+  }
+}
+
+// ---------------------------------------------------------------- FP64 energy
+template <int V>
+__device__ __forceinline__ void load_T(const EnergyArgs& a, size_t idx, double (&t)[V]) {
+  if (a.x) {
+    Vec<V> xv;
+    xv.ldg(a.x + idx);
+#pragma unroll
+    for (int v = 0; v < V; ++v) t[v] = xv.v[v] > 0.f ? 1.0 : 0.0;
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) t[v] = a.spins[idx + v] > 0 ? 1.0 : 0.0;
+  }
+}
+
+// Block b sums, for every replica, T_i (a_i + 1/2 sum_j b_ij T_j) over its rows
+// (Eq. 13 written with both CSR triangles), then reduces its groups in fixed order.
+template <int V, int NCH>
+__global__ void __launch_bounds__(kBlock) k_energy_partial(const EnergyArgs a) {
+  extern __shared__ double sm[];
+  const int G = a.G;
+  const int gid = threadIdx.x / G;
+  const int g = threadIdx.x - gid * G;
+  const int groups = blockDim.x / G;
+  const unsigned mask = group_mask(G);
+  const int R = a.R;
+  const int C = R / V;
+  const int tile_base = blockIdx.y * (G * NCH);
+  const int ch0 = tile_base + g;
+  const int b = blockIdx.x;
+  const int r0 = a.blk_row[b], r1 = a.blk_row[b + 1];
+  double acc[NCH][V];
+#pragma unroll
+  for (int j = 0; j < NCH; ++j)
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[j][v] = 0.0;
+  for (int row = r0 + gid; row < r1; row += groups) {
+    double inner[NCH][V];
+#pragma unroll
+    for (int j = 0; j < NCH; ++j)
+#pragma unroll
+      for (int v = 0; v < V; ++v) inner[j][v] = 0.0;
+    const int p0 = a.rowptr[row], p1 = a.rowptr[row + 1];
+    for (int pb = p0; pb < p1; pb += G) {
+      const int cnt = min(G, p1 - pb);
+      int mc = 0;
+      double mv = 0.0;
+      if (g < cnt) {
+        mc = a.col[pb + g];
+        mv = a.qval[pb + g];
+      }
+      for (int q = 0; q < cnt; ++q) {
+        const int c = __shfl_sync(mask, mc, q, G);
+        const double w = __shfl_sync(mask, mv, q, G);
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+          const int ch = ch0 + j * G;
+          if (ch < C) {
+            double t[V];
+            load_T<V>(a, (size_t)c * R + (size_t)ch * V, t);
+#pragma unroll
+            for (int v = 0; v < V; ++v) inner[j][v] += w * t[v];
+          }
+        }
+      }
+    }
+    const double ai = a.qlin[row];
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+      const int ch = ch0 + j * G;
+      if (ch < C) {
+        double t[V];
+        load_T<V>(a, (size_t)row * R + (size_t)ch * V, t);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[j][v] += t[v] * (ai + 0.5 * inner[j][v]);
+      }
+    }
+  }
+  const int W = G * NCH * V;
+#pragma unroll
+  for (int j = 0; j < NCH; ++j)
+#pragma unroll
+    for (int v = 0; v < V; ++v) sm[gid * W + (j * G + g) * V + v] = acc[j][v];
+  __syncthreads();
+  for (int t = threadIdx.x; t < W; t += blockDim.x) {
+    const int rep = tile_base * V + t;
+    if (rep >= R) continue;
+    double s = 0.0;
+    for (int k = 0; k < groups; ++k) s += sm[k * W + t];
+    a.partial[(size_t)b * R + rep] = s;
+  }
+}
+
+__global__ void k_energy_reduce(const double* partial, const int32_t* ev_blk0, int32_t R,
+                                double* out) {
+  const int e = blockIdx.y;
+  const int b0 = ev_blk0[e], b1 = ev_blk0[e + 1];
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = b0; b < b1; ++b) s += partial[(size_t)b * R + r];
+    out[(size_t)e * R + r] = s;
+  }
+}
+
+__device__ __forceinline__ bool better(double v, int r, double bv, int br) {
+  return v < bv || (v == bv && r < br);
+}
+
+// warp-shuffle arg-min over the replicas of one event
+__global__ void k_argmin(const double* E_all, int32_t R, double* best_E, int32_t* best_r) {
+  __shared__ double sv[32];
+  __shared__ int sr[32];
+  const int e = blockIdx.x;
+  double bv = DBL_MAX;
+  int br = INT_MAX;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    const double v = E_all[(size_t)e * R + r];
+    if (better(v, r, bv, br)) {
+      bv = v;
+      br = r;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+    const int orr = __shfl_down_sync(0xffffffffu, br, off);
+    if (better(ov, orr, bv, br)) {
+      bv = ov;
+      br = orr;
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sv[wid] = bv;
+    sr[wid] = br;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    bv = lane < nw ? sv[lane] : DBL_MAX;
+    br = lane < nw ? sr[lane] : INT_MAX;
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+      const int orr = __shfl_down_sync(0xffffffffu, br, off);
+      if (better(ov, orr, bv, br)) {
+        bv = ov;
+        br = orr;
+      }
+    }
+    if (lane == 0) {
+      best_E[e] = bv;
+      best_r[e] = br == INT_MAX ? 0 : br;
+    }
+  }
+}
+
+__global__ void k_best_T(const float* x, const int32_t* row_event, const int32_t* best_r,
+                         int32_t n, int32_t R, uint8_t* T) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int e = row_event ? row_event[i] : 0;
+    T[i] = x[(size_t)i * R + best_r[e]] > 0.f ? 1 : 0;
+  }
+}
+
+template <int V, int NCH>
+cudaError_t launch_energy_t(const Tiling& t, const EnergyArgs& a, cudaStream_t s) {
+  const int groups = kBlock / t.G;
+  const size_t smem = (size_t)groups * t.G * t.NCH * t.V * sizeof(double);
+  dim3 grid(a.nblk, t.tiles);
+  k_energy_partial<V, NCH><<<grid, kBlock, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+int grid_for(size_t work, int block) {
+  size_t g = (work + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs& a,
+                        cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  if (t.V == 4) {
+    if (t.NCH == 1) return launch_step_v<4, 1>(variant, jbf16, t, a, s);
+    if (t.NCH == 2) return launch_step_v<4, 2>(variant, jbf16, t, a, s);
+    return launch_step_v<4, 4>(variant, jbf16, t, a, s);
+  }
+  if (t.NCH == 1) return launch_step_v<1, 1>(variant, jbf16, t, a, s);
+  if (t.NCH == 2) return launch_step_v<1, 2>(variant, jbf16, t, a, s);
+  return launch_step_v<1, 4>(variant, jbf16, t, a, s);
+}
+
+cudaError_t launch_init(float* x, float* y, const int32_t* row_event, const int32_t* ev_row0,
+                        int32_t n, int32_t R, uint64_t seed, cudaStream_t s) {
+  const size_t total = (size_t)n * R;
+  if (!total) return cudaSuccess;
+  k_init<<<grid_for(total, kBlock), kBlock, 0, s>>>(x, y, row_event, ev_row0, n, R,
+                                                     (uint32_t)(seed & 0xFFFFFFFFu),
+                                                     (uint32_t)(seed >> 32));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_linear_schedule(float* sched, int32_t steps, double a0, cudaStream_t s) {
+  if (steps <= 0) return cudaSuccess;
+  k_linear_schedule<<<grid_for(steps, kBlock), kBlock, 0, s>>>(sched, steps, a0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_c0(float* c0_ev, const double* c0_auto, double c0, int32_t E,
+                          cudaStream_t s) {
+  k_set_c0<<<grid_for(E, kBlock), kBlock, 0, s>>>(c0_ev, c0_auto, c0, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const int32_t* rowptr, const int32_t* col, const double* qval,
+                           const double* qlin, int32_t n, void* J, int jbf16, double* h64,
+                           float* h32, double* row_off, double* row_sq, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = grid_for(n, kBlock);
+  if (jbf16)
+    k_convert<__nv_bfloat16><<<grid, kBlock, 0, s>>>(rowptr, col, qval, qlin, n,
+                                                     static_cast<__nv_bfloat16*>(J), h64, h32,
+                                                     row_off, row_sq);
+  else
+    k_convert<float><<<grid, kBlock, 0, s>>>(rowptr, col, qval, qlin, n, static_cast<float*>(J),
+                                             h64, h32, row_off, row_sq);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_event_stats(const double* row_off, const double* row_sq,
+                               const int32_t* ev_row0, int32_t E, double* offset,
+                               double* sigma, double* c0_auto, cudaStream_t s) {
+  if (E <= 0) return cudaSuccess;
+  k_event_stats<<<E, kBlock, 0, s>>>(row_off, row_sq, ev_row0, offset, sigma, c0_auto);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_partial(const Tiling& t, const EnergyArgs& a, cudaStream_t s) {
+  if (a.nblk <= 0) return cudaSuccess;
+  if (t.V == 4) {
+    if (t.NCH == 1) return launch_energy_t<4, 1>(t, a, s);
+    if (t.NCH == 2) return launch_energy_t<4, 2>(t, a, s);
+    return launch_energy_t<4, 4>(t, a, s);
+  }
+  if (t.NCH == 1) return launch_energy_t<1, 1>(t, a, s);
+  if (t.NCH == 2) return launch_energy_t<1, 2>(t, a, s);
+  return launch_energy_t<1, 4>(t, a, s);
+}
+
+cudaError_t launch_energy_reduce(const double* partial, const int32_t* ev_blk0, int32_t E,
+                                 int32_t R, double* E_out, cudaStream_t s) {
+  if (E <= 0 || R <= 0) return cudaSuccess;
+  dim3 grid((R + kBlock - 1) / kBlock, E);
+  k_energy_reduce<<<grid, kBlock, 0, s>>>(partial, ev_blk0, R, E_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_argmin(const double* E_all, int32_t E, int32_t R, double* best_E,
+                          int32_t* best_r, cudaStream_t s) {
+  if (E <= 0) return cudaSuccess;
+  k_argmin<<<E, kBlock, 0, s>>>(E_all, R, best_E, best_r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_best_T(const float* x, const int32_t* row_event, const int32_t* best_r,
+                          int32_t n, int32_t R, uint8_t* T, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_best_T<<<grid_for(n, kBlock), kBlock, 0, s>>>(x, row_event, best_r, n, R, T);
+  return cudaGetLastError();
+}
+
+}  // namespace sbd

@@ -1,0 +1,78 @@
+// Internal interface between the C ABI (api.cu) and the device kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sbd {
+
+// Replica tiling of the N x R state: each row is handled by a group of G
+// threads (G a power of two <= 32); a thread covers NCH chunks of V
+// consecutive replicas, chunks strided by G so a group reads contiguous bytes.
+struct Tiling {
+  int V;      // replicas per chunk: 4 (float4) or 1
+  int G;      // threads per row
+  int NCH;    // chunks per thread per replica tile: 1, 2 or 4
+  int tiles;  // replica tiles (grid.y)
+  int C;      // chunks per row = R / V
+};
+Tiling make_tiling(int R);
+
+struct StepArgs {
+  const int32_t* rowptr;
+  const int32_t* col;
+  const void* J;          // float or __nv_bfloat16, -b/4
+  const float* h;         // FP32 field
+  const int32_t* row_event;  // event of each row (NULL: single event)
+  const float* c0_ev;     // per-event c0
+  const float* sched;     // a_k, device
+  int32_t k;              // step index into sched
+  float a0, dt, dta0;     // dta0 = fp32(dt * a0)
+  const float* xin;
+  float* xout;
+  float* y;
+  int32_t n, R;
+  int32_t G;
+};
+
+cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs& a,
+                        cudaStream_t s);
+
+cudaError_t launch_init(float* x, float* y, const int32_t* row_event, const int32_t* ev_row0,
+                        int32_t n, int32_t R, uint64_t seed, cudaStream_t s);
+
+cudaError_t launch_linear_schedule(float* sched, int32_t steps, double a0, cudaStream_t s);
+
+cudaError_t launch_set_c0(float* c0_ev, const double* c0_auto, double c0, int32_t E,
+                          cudaStream_t s);
+
+// QUBO -> Ising in FP64 (per row), then per-event reductions.
+cudaError_t launch_convert(const int32_t* rowptr, const int32_t* col, const double* qval,
+                           const double* qlin, int32_t n, void* J, int jbf16, double* h64,
+                           float* h32, double* row_off, double* row_sq, cudaStream_t s);
+cudaError_t launch_event_stats(const double* row_off, const double* row_sq,
+                               const int32_t* ev_row0, int32_t E, double* offset,
+                               double* sigma, double* c0_auto, cudaStream_t s);
+
+struct EnergyArgs {
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* qval;
+  const double* qlin;
+  const float* x;          // state positions (T = x > 0), or NULL when spins given
+  const int8_t* spins;     // +1 selects; used when x == NULL
+  const int32_t* blk_row;  // row range of each partial block [nblk + 1]
+  int32_t nblk;
+  int32_t n, R, G;
+  double* partial;         // [nblk x R] scratch
+};
+cudaError_t launch_energy_partial(const Tiling& t, const EnergyArgs& a, cudaStream_t s);
+// E[e*R + r] = sum of the event's block partials, in block order.
+cudaError_t launch_energy_reduce(const double* partial, const int32_t* ev_blk0, int32_t E,
+                                 int32_t R, double* E_out, cudaStream_t s);
+// arg-min over replicas per event (ties -> lowest index).
+cudaError_t launch_argmin(const double* E_all, int32_t E, int32_t R, double* best_E,
+                          int32_t* best_r, cudaStream_t s);
+cudaError_t launch_best_T(const float* x, const int32_t* row_event, const int32_t* best_r,
+                          int32_t n, int32_t R, uint8_t* T, cudaStream_t s);
+
+}  // namespace sbd

@@ -1,0 +1,37 @@
+"""Named synthetic workloads (numbers only; no arithmetic of the method).
+
+Each entry fixes the event recipe (tracks, noise fraction, seed), the builder
+cuts and the SB run shape. The cut values are one family scaled by a looseness
+factor s: dphi_slope = 4e-4 s rad/mm, dphi_margin = 0.5 s mm, z0_max = 50 s mm,
+kappa_max = 8e-4 s mm^-1, dtheta_max = 0.1 s rad (s = 1 is the printed Eq. 16
+cut read in mm^-1), with the quadruplet curvature cut dkappa_max = 5e-4 mm^-1.
+s is chosen per workload so the QUBO size matches the workload's stated N.
+"""
+
+
+def _cuts(dphi_slope, dphi_margin, z0_max, kappa_max, dtheta_max, dkappa_max=5e-4):
+    return dict(dphi_slope=dphi_slope, dphi_margin=dphi_margin, z0_max=z0_max,
+                kappa_max=kappa_max, dtheta_max=dtheta_max, dkappa_max=dkappa_max,
+                w_q=1.0, w_c=1.0, five_hit_rule=1)
+
+
+# s = 8: 100 tracks -> N ~ 1.7k
+CUTS_S8 = _cuts(3.2e-3, 4.0, 400.0, 6.4e-3, 0.8)
+# s = 2.35: 1000 tracks -> N ~ 40k
+CUTS_S2_35 = _cuts(9.4e-4, 1.175, 117.5, 1.88e-3, 0.235)
+# s = 2.8: 500 tracks -> N ~ 10k
+CUTS_S2_8 = _cuts(1.12e-3, 1.4, 140.0, 2.24e-3, 0.28)
+# paper values of Eq. 16 / 17 read in mm^-1 (s = 1, dkappa = 1e-4)
+CUTS_PAPER = _cuts(4e-4, 0.5, 50.0, 8e-4, 0.1, 1e-4)
+
+WORKLOADS = {
+    # plain bSB / dSB on one small event, FP32 J, one replica
+    "event100": dict(n_tracks=100, noise_frac=0.1, seed=0, cuts=CUTS_S8,
+                     replicas=1, steps=2000, dt=0.5, a0=1.0, jprec="fp32"),
+    # replica-parallel run on one dense event, BF16 J
+    "event1000": dict(n_tracks=1000, noise_frac=0.1, seed=1000, cuts=CUTS_S2_35,
+                      replicas=256, steps=4000, dt=0.5, a0=1.0, jprec="bf16"),
+    # adjoint workload
+    "event500": dict(n_tracks=500, noise_frac=0.1, seed=3000, cuts=CUTS_S2_8,
+                     replicas=32, steps=1000, dt=0.5, a0=1.0, jprec="fp32"),
+}

@@ -1,0 +1,47 @@
+"""Helpers shared by the GPU parity tests (no arithmetic of the method)."""
+import functools
+
+import numpy as np
+
+import paper_2402_14718_gb300 as sb
+from paper_2402_14718_gb300.workloads import WORKLOADS
+from oracle import events as oev
+from oracle import qubo as oq
+
+
+def oracle_params(cuts):
+    kw = dict(cuts)
+    kw["five_hit_rule"] = bool(kw["five_hit_rule"])
+    return oq.BuildParams(**kw)
+
+
+@functools.lru_cache(maxsize=None)
+def workload_qubos(name):
+    """(product event, product qubo, oracle event, oracle qubo) of a named workload."""
+    w = WORKLOADS[name]
+    ev_c = sb.sb_event_generate(w["seed"], sb.event_params(n_tracks=w["n_tracks"],
+                                                            noise_frac=w["noise_frac"]))
+    qc = sb.sb_qubo_build(ev_c, sb.build_params(**w["cuts"]))
+    ev_o = oev.generate(w["seed"], oev.EventParams(n_tracks=w["n_tracks"],
+                                                  noise_frac=w["noise_frac"]))
+    qo = oq.build_qubo(ev_o, oracle_params(w["cuts"]))
+    return ev_c, qc, ev_o, qo
+
+
+def max_rel(a, ref):
+    """max |a - ref| / max |ref| (scale-normalised error of one state array)."""
+    scale = max(float(np.max(np.abs(ref))), 1e-30)
+    return float(np.max(np.abs(np.asarray(a, np.float64) - ref))) / scale
+
+
+def compare_step(xg, yg, xo, yo, xpre, tol=1e-5):
+    """One-step parity with wall near-ties excluded: where the oracle's pre-wall
+    |x| is within 1e-5 of 1 the two sides may take different wall decisions."""
+    tie = np.abs(np.abs(xpre) - 1.0) < 1e-5
+    keep = ~tie
+    assert tie.mean() < 1e-3
+    ex = max_rel(np.where(keep, xg, 0.0), np.where(keep, xo, 0.0))
+    ey = max_rel(np.where(keep, yg, 0.0), np.where(keep, yo, 0.0))
+    assert ex <= tol, ex
+    assert ey <= tol, ey
+    return ex, ey
