@@ -240,6 +240,42 @@ sb_status sb_readout_device(sb_ctx* ctx, double* d_E_all, double* d_best_E, int3
                             uint8_t* d_T, void* stream);
 
 /*
+ * sb_energy_noalloc -- the FP64 readout of sb_energy / sb_readout_device
+ * (QUBO energies of R replicas, arg-min over replicas with ties to the lowest
+ * index) for callers that cannot allocate device memory. The paper has no
+ * counterpart: it is an interface for embedding the solver in host frameworks
+ * that own every device allocation themselves (an online trigger or
+ * reconstruction framework running under a fixed memory budget, or a
+ * latency-bound loop where the implicit device synchronisation of cudaMalloc /
+ * cudaFree is not acceptable). It calls no cudaMalloc, cudaFree or allocating
+ * library routine, and needs no sb_ctx.
+ *
+ * Inputs (device pointers, one QUBO): the CSR of Eq. 13 as for sb_create
+ * (rowptr[n+1], col[nnz], qval[nnz] = b_ij; not validated here), qlin[n] = a_i,
+ * and exactly one of x (FP32 [n x R], T_i = 1 iff x > 0) or spins (int8
+ * [n x R], T_i = 1 iff spin > 0), both replica-minor.
+ * Outputs (device): E[R] (QUBO energies, FP64); best_E[1] and best_r[1] (both
+ * or neither). Asynchronous on `stream`.
+ *
+ * Scratch: a static device array of 8 MiB inside the library, held by every
+ * GPU that loads the library until the process exits. A call needs
+ * 8 * ceil(n / B) * R bytes of it plus a small row table (B = 64 rows when
+ * R >= 16, 128 or 256 for fewer replicas): e.g. n <= 261,000 rows at R = 256.
+ * Larger problems are rejected with SB_ERR_ARG and a message (use sb_energy or
+ * sb_readout_device, which allocate). The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. Every call on a device
+ * shares the one array and it keeps the last call's contents (each call
+ * writes every scratch entry it reads, so nothing needs clearing); calls that
+ * overlap on the GPU (other streams, other threads) race on it and must be
+ * serialised by the caller.
+ */
+sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col,
+                            const double* qval, const double* qlin, const float* x,
+                            const int8_t* spins, int32_t replicas, double* E, double* best_E,
+                            int32_t* best_r, void* stream);
+
+/*
  * sb_set_option -- per-context switches.
  *   SB_OPT_GRAPH (0): 1 (default) replays runs of >= 8 steps from a captured
  *   CUDA graph; 0 launches one kernel per step directly on the stream.

@@ -19,6 +19,7 @@ __all__ = [
     "event_params", "build_params", "sb_event_generate", "sb_qubo_build", "sb_tracks",
     "sb_create", "sb_create_batch", "sb_destroy", "sb_info", "sb_run", "sb_advance",
     "sb_set_state", "sb_get_state", "sb_energy", "sb_best", "sb_readout_device", "sb_set_option",
+    "sb_energy_noalloc",
     "sb_version", "LIB_PATH",
 ]
 
@@ -296,3 +297,13 @@ def sb_readout_device(ctx, d_E_all=None, d_best_E=None, d_best_r=None, d_T=None,
 
 def sb_set_option(ctx, key, value):
     check(lib.sb_set_option(ctx.handle, int(key), int(value)))
+
+
+def sb_energy_noalloc(n, d_rowptr, d_col, d_qval, d_qlin, d_x, d_spins, replicas, d_E,
+                      d_best_E=None, d_best_r=None, stream=None):
+    """Readout into caller-owned device buffers with the library's static scratch
+    (no device allocation); all array arguments are torch CUDA tensors or ints."""
+    check(lib.sb_energy_noalloc(int(n), _dev_ptr(d_rowptr), _dev_ptr(d_col), _dev_ptr(d_qval),
+                                _dev_ptr(d_qlin), _dev_ptr(d_x), _dev_ptr(d_spins), int(replicas),
+                                _dev_ptr(d_E), _dev_ptr(d_best_E), _dev_ptr(d_best_r),
+                                _stream(stream)))

@@ -73,6 +73,8 @@ _SIGS = {
     "sb_best": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "sb_readout_device": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sb_set_option": (c_int32, [c_void_p, c_int32, c_int64]),
+    "sb_energy_noalloc": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 

@@ -18,7 +18,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsbtrack.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-CU = ["api.cu", "device/kernels.cu"]
+CU = ["api.cu", "device/kernels.cu", "device/noalloc.cu"]
 CPP = ["host/events.cpp", "host/qubo.cpp", "host/tracks.cpp"]
 
 
