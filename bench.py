@@ -42,6 +42,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttt", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "untiled"],
+                    help="step kernel: auto (row-block tiled when R %% 32 == 0) or untiled")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="profiling driver: set up the workload, run this many SB steps with "
+                         "one direct launch each (no graph, no timing), exit")
     return ap.parse_args()
 
 
@@ -194,7 +199,16 @@ def run_ours(args):
     q = sb.sb_qubo_build(ev, sb.build_params(**w["cuts"]))
     N, nnz = q.n, q.nnz
     ctx = sb.sb_create(N, q.rowptr, q.col, q.val, q.lin, prec)
+    if args.kernel == "untiled":
+        sb.sb_set_option(ctx, sb.SB_OPT_TILED, 0)
     sched = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
+    if args.profile_steps:
+        sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
+        sb.sb_run(ctx, args.variant, a0, 0.0, dt, 0, R, 1, None, stream)
+        sb.sb_advance(ctx, args.variant, a0, 0.0, dt, min(args.profile_steps, S), sched, stream)
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"profile_steps": args.profile_steps, "N": N, "nnz": nnz, "R": R}))
+        return 0
     d_E = torch.empty(R, dtype=torch.float64, device=dev)
     d_bE = torch.empty(1, dtype=torch.float64, device=dev)
     d_br = torch.empty(1, dtype=torch.int32, device=dev)
@@ -296,7 +310,7 @@ def run_ours(args):
         cpu = oracle_sample(w, args.variant)
         cpu.pop("seconds", None)
 
-    launches_per_step = 2 + S + 4   # set_c0 + init, S x k_step, energy partial/reduce/argmin/best_T
+    launches_per_step = 3 + S + 4   # set_c0 + init + set_c0, S x step, energy partial/reduce/argmin/best_T
     line = {"metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

@@ -279,9 +279,32 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
  * sb_set_option -- per-context switches.
  *   SB_OPT_GRAPH (0): 1 (default) replays runs of >= 8 steps from a captured
  *   CUDA graph; 0 launches one kernel per step directly on the stream.
+ *   SB_OPT_TILED (1): 1 uses the row-block tiled step kernel (shared-memory
+ *   staging of each row block's neighbour union) when R is a multiple of 32;
+ *   0 (default) the untiled kernel. Both give bit-identical states (same FMA
+ *   order).
+ *   SB_OPT_STEP_RT (2): replica-tile width of the untiled kernel (4 x a power
+ *   of two, <= 128, dividing R; 0 = automatic).
+ *   SB_OPT_STEP_RPC (3): rows per CTA of the untiled kernel (0 = one row per
+ *   thread group); a CTA walks a contiguous row chunk so rows in flight share
+ *   neighbour rows in L1. Neither changes results.
  */
 #define SB_OPT_GRAPH 0
+#define SB_OPT_TILED 1
+#define SB_OPT_STEP_RT 2
+#define SB_OPT_STEP_RPC 3
 sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
+
+/*
+ * sb_autotune -- pick the step-kernel configuration (tiled or untiled kernel,
+ * replica-tile width, rows per CTA) for this context, variant and replica
+ * count by timing each candidate for `trial_steps` steps with CUDA events on
+ * `stream`, and set it on the context. Results do not depend on the choice.
+ * Outputs (host, may be NULL): out_cfg[3] = {tiled, tile width, rows per CTA},
+ * out_us_per_step = the best time. Synchronous; discards the current state.
+ */
+sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t trial_steps,
+                      int32_t* out_cfg, float* out_us_per_step, void* stream);
 
 #ifdef __cplusplus
 }

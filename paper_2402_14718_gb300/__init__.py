@@ -11,15 +11,16 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (SB_ASB, SB_BSB, SB_DSB, SB_J_BF16, SB_J_FP32, SB_OPT_GRAPH, SbError, check,
-                   lib)
+from ._lib import (SB_ASB, SB_BSB, SB_DSB, SB_J_BF16, SB_J_FP32, SB_OPT_GRAPH, SB_OPT_TILED,
+                   SbError, check, lib)
 
 __all__ = [
-    "SB_ASB", "SB_BSB", "SB_DSB", "SB_J_FP32", "SB_J_BF16", "SB_OPT_GRAPH", "SbError",
+    "SB_ASB", "SB_BSB", "SB_DSB", "SB_J_FP32", "SB_J_BF16", "SB_OPT_GRAPH", "SB_OPT_TILED",
+    "SbError",
     "event_params", "build_params", "sb_event_generate", "sb_qubo_build", "sb_tracks",
     "sb_create", "sb_create_batch", "sb_destroy", "sb_info", "sb_run", "sb_advance",
     "sb_set_state", "sb_get_state", "sb_energy", "sb_best", "sb_readout_device", "sb_set_option",
-    "sb_energy_noalloc",
+    "sb_energy_noalloc", "sb_autotune",
     "sb_version", "LIB_PATH",
 ]
 
@@ -307,3 +308,13 @@ def sb_energy_noalloc(n, d_rowptr, d_col, d_qval, d_qlin, d_x, d_spins, replicas
                                 _dev_ptr(d_qlin), _dev_ptr(d_x), _dev_ptr(d_spins), int(replicas),
                                 _dev_ptr(d_E), _dev_ptr(d_best_E), _dev_ptr(d_best_r),
                                 _stream(stream)))
+
+
+def sb_autotune(ctx, variant, replicas, trial_steps=50, stream=None):
+    """Time the step-kernel candidates and keep the fastest; returns
+    ({"tiled", "tile", "rows_per_cta"}, microseconds per step)."""
+    cfg = np.zeros(3, np.int32)
+    us = ctypes.c_float()
+    check(lib.sb_autotune(ctx.handle, _variant(variant), int(replicas), int(trial_steps),
+                          cfg.ctypes.data_as(ctypes.c_void_p), ctypes.byref(us), _stream(stream)))
+    return {"tiled": int(cfg[0]), "tile": int(cfg[1]), "rows_per_cta": int(cfg[2])}, us.value

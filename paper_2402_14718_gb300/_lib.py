@@ -16,6 +16,9 @@ SB_OK, SB_ERR_ARG, SB_ERR_CSR, SB_ERR_CUDA, SB_ERR_OOM, SB_ERR_TIMEOUT, SB_ERR_S
 SB_ASB, SB_BSB, SB_DSB = 0, 1, 2
 SB_J_FP32, SB_J_BF16 = 0, 1
 SB_OPT_GRAPH = 0
+SB_OPT_TILED = 1
+SB_OPT_STEP_RT = 2
+SB_OPT_STEP_RPC = 3
 
 
 class SbEventParams(ctypes.Structure):
@@ -73,6 +76,7 @@ _SIGS = {
     "sb_best": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "sb_readout_device": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sb_set_option": (c_int32, [c_void_p, c_int32, c_int64]),
+    "sb_autotune": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "sb_energy_noalloc": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
 }

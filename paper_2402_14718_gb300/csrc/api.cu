@@ -26,7 +26,7 @@ const int kEnergyRowsMin = 64;
 
 struct GraphCache {
   cudaGraphExec_t exec = nullptr;
-  int variant = -1, steps = -1, R = -1, cur = -1, G = -1;
+  int variant = -1, steps = -1, R = -1, cur = -1, G = -1, tiled = -1, rpc = -1, tiles = -1;
   float a0 = 0.f, dt = 0.f;
   const float* sched = nullptr;
   void reset() {
@@ -82,10 +82,21 @@ struct sb_ctx {
   uint8_t* d_T = nullptr;
   int8_t* d_spins = nullptr;
   int32_t spins_cap_R = 0;
+  // row-block tiling of the coupling product (k_step_tiled)
+  bool tiled_ok = false;
+  int32_t nb = 0;
+  int32_t* d_blk_row0 = nullptr;
+  int32_t* d_blk_u0 = nullptr;
+  int32_t* d_ucol = nullptr;
+  uint16_t* d_own = nullptr;
+  void* d_tz = nullptr;
   // execution
   cudaStream_t cap_stream = nullptr;
   GraphCache graph;
   int use_graph = 1;
+  int use_tiled = 0;
+  int step_rt = 0;    // replica-tile width of the untiled kernel (0: automatic)
+  int step_rpc = 0;   // rows per CTA of the untiled kernel (0: one row per group)
 };
 
 namespace {
@@ -208,6 +219,12 @@ void free_all(sb_ctx* c) {
   dfree(c->d_bestr);
   dfree(c->d_T);
   dfree(c->d_spins);
+  dfree(c->d_blk_row0);
+  dfree(c->d_blk_u0);
+  dfree(c->d_ucol);
+  dfree(c->d_own);
+  if (c->d_tz) cudaFree(c->d_tz);
+  c->d_tz = nullptr;
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->cap_stream = nullptr;
 }
@@ -260,6 +277,99 @@ sb_status ensure_readout(sb_ctx* c, int32_t R) {
       (st = dalloc(&c->d_Eall, (size_t)c->E * R)))
     return st;
   c->eR = R;
+  return SB_OK;
+}
+
+// Cut rows into blocks (in row order) whose union of neighbour rows plus own
+// rows stays within kTileUCap, nonzeros within kTileNzCap and rows within
+// kTileRowCap; record each nonzero's index inside its block's sorted union.
+struct TileHost {
+  bool ok = true;
+  std::vector<int32_t> row0, u0, ucol;
+  std::vector<uint16_t> own, lidx;
+};
+
+TileHost build_tiles(int32_t n, const int32_t* rp, const int32_t* col) {
+  TileHost t;
+  t.own.assign(n, 0);
+  t.lidx.assign((size_t)rp[n], 0);
+  std::vector<int32_t> mark(n, -1), cur, sorted;
+  int32_t row = 0;
+  while (row < n) {
+    const int32_t start = row;
+    cur.clear();
+    int64_t nz = 0;
+    while (row < n && row - start < sbd::kTileRowCap) {
+      int32_t add = mark[row] < 0 ? 1 : 0;
+      for (int32_t p = rp[row]; p < rp[row + 1]; ++p) add += mark[col[p]] < 0 ? 1 : 0;
+      const int64_t rnz = rp[row + 1] - rp[row];
+      if ((int64_t)cur.size() + add > sbd::kTileUCap || nz + rnz > sbd::kTileNzCap) {
+        if (row == start) {
+          t.ok = false;
+          return t;
+        }
+        break;
+      }
+      if (mark[row] < 0) {
+        mark[row] = (int32_t)cur.size();
+        cur.push_back(row);
+      }
+      for (int32_t p = rp[row]; p < rp[row + 1]; ++p)
+        if (mark[col[p]] < 0) {
+          mark[col[p]] = (int32_t)cur.size();
+          cur.push_back(col[p]);
+        }
+      nz += rnz;
+      ++row;
+    }
+    sorted = cur;
+    std::sort(sorted.begin(), sorted.end());
+    for (size_t k = 0; k < sorted.size(); ++k) mark[sorted[k]] = (int32_t)k;
+    for (int32_t i = start; i < row; ++i) {
+      t.own[i] = (uint16_t)mark[i];
+      for (int32_t p = rp[i]; p < rp[i + 1]; ++p) t.lidx[p] = (uint16_t)mark[col[p]];
+    }
+    t.row0.push_back(start);
+    t.u0.push_back((int32_t)t.ucol.size());
+    t.ucol.insert(t.ucol.end(), sorted.begin(), sorted.end());
+    for (int32_t v : cur) mark[v] = -1;
+  }
+  t.row0.push_back(n);
+  t.u0.push_back((int32_t)t.ucol.size());
+  return t;
+}
+
+sb_status setup_tiles(sb_ctx* c, const int32_t* rowptr, const int32_t* col) {
+  TileHost t = build_tiles(c->n, rowptr, col);
+  c->tiled_ok = false;
+  if (!t.ok) return SB_OK;  // a row too long for a block: the generic kernel serves every run
+  sb_status st;
+  const size_t nnz = (size_t)c->nnz;
+  uint16_t* d_lidx = nullptr;
+  if ((st = dalloc(&c->d_blk_row0, t.row0.size())) || (st = dalloc(&c->d_blk_u0, t.u0.size())) ||
+      (st = dalloc(&c->d_ucol, t.ucol.size())) || (st = dalloc(&c->d_own, (size_t)c->n)) ||
+      (st = dalloc(&d_lidx, nnz)))
+    return st;
+  cudaError_t e = cudaMalloc(&c->d_tz, std::max<size_t>(nnz, 1) * (c->jbf16 ? 4 : 8));
+  if (e != cudaSuccess) {
+    c->d_tz = nullptr;
+    dfree(d_lidx);
+    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return SB_ERR_OOM;
+  }
+  SB_CUDA(cudaMemcpy(c->d_blk_row0, t.row0.data(), t.row0.size() * 4, cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(c->d_blk_u0, t.u0.data(), t.u0.size() * 4, cudaMemcpyHostToDevice));
+  if (!t.ucol.empty())
+    SB_CUDA(cudaMemcpy(c->d_ucol, t.ucol.data(), t.ucol.size() * 4, cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(c->d_own, t.own.data(), (size_t)c->n * 2, cudaMemcpyHostToDevice));
+  if (nnz) SB_CUDA(cudaMemcpy(d_lidx, t.lidx.data(), nnz * 2, cudaMemcpyHostToDevice));
+  cudaError_t e1 = sbd::launch_pack_tz(c->d_J, c->jbf16, d_lidx, (int64_t)nnz, c->d_tz, 0);
+  cudaError_t e2 = cudaDeviceSynchronize();
+  dfree(d_lidx);
+  SB_CUDA(e1);
+  SB_CUDA(e2);
+  c->nb = (int32_t)t.row0.size() - 1;
+  c->tiled_ok = true;
   return SB_OK;
 }
 
@@ -321,6 +431,7 @@ sb_status create_common(sb_ctx* c, const int32_t* rowptr, const int32_t* col, co
   SB_CUDA(cudaMemcpy(c->offset.data(), c->d_offset, c->E * 8, cudaMemcpyDeviceToHost));
   SB_CUDA(cudaMemcpy(c->sigma.data(), c->d_sigma, c->E * 8, cudaMemcpyDeviceToHost));
   SB_CUDA(cudaMemcpy(c->c0_auto.data(), c->d_c0auto, c->E * 8, cudaMemcpyDeviceToHost));
+  if ((st = setup_tiles(c, rowptr, col))) return st;
   SB_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   return SB_OK;
 }
@@ -344,10 +455,15 @@ sb_status check_run_args(sb_ctx* c, sb_variant variant, double a0, double c0, do
 }
 
 // Enqueue `steps` SB steps reading x from c->d_x[c->cur]; flips c->cur.
+sbd::Tiling step_tiling(const sb_ctx* c) {
+  if (c->step_rt > 0 && c->R % c->step_rt == 0) return sbd::make_tiling_rt(c->R, c->step_rt);
+  return sbd::make_tiling(c->R);
+}
+
 sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t steps,
                         const float* sched, cudaStream_t stream) {
   if (steps <= 0) return SB_OK;
-  const sbd::Tiling t = sbd::make_tiling(c->R);
+  const sbd::Tiling t = step_tiling(c);
   sbd::StepArgs a;
   a.rowptr = c->d_rowptr;
   a.col = c->d_col;
@@ -363,30 +479,57 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   a.n = c->n;
   a.R = c->R;
   a.G = t.G;
+  a.rpc = std::max(256 / t.G, c->step_rpc);
+  const int tiled = (c->tiled_ok && c->use_tiled && c->R % sbd::kTileRT == 0) ? 1 : 0;
+  sbd::TiledArgs ta;
+  ta.blk_row0 = c->d_blk_row0;
+  ta.blk_u0 = c->d_blk_u0;
+  ta.ucol = c->d_ucol;
+  ta.own = c->d_own;
+  ta.rowptr = c->d_rowptr;
+  ta.tz = c->d_tz;
+  ta.h = c->d_h32;
+  ta.row_event = c->d_row_event;
+  ta.c0_ev = c->d_c0ev;
+  ta.sched = sched;
+  ta.a0 = a.a0;
+  ta.dt = a.dt;
+  ta.dta0 = a.dta0;
+  ta.y = c->d_y;
+  ta.n = c->n;
+  ta.R = c->R;
+  ta.nb = c->nb;
+  auto launch = [&](int32_t k, int cur, cudaStream_t st) -> cudaError_t {
+    if (tiled) {
+      ta.k = k;
+      ta.xin = c->d_x[cur];
+      ta.xout = c->d_x[cur ^ 1];
+      return sbd::launch_step_tiled(variant, c->jbf16, ta, st);
+    }
+    a.k = k;
+    a.xin = c->d_x[cur];
+    a.xout = c->d_x[cur ^ 1];
+    return sbd::launch_step(variant, c->jbf16, t, a, st);
+  };
   const bool graph = c->use_graph && steps >= 8;
   if (!graph) {
     for (int32_t k = 0; k < steps; ++k) {
-      a.k = k;
-      a.xin = c->d_x[c->cur];
-      a.xout = c->d_x[c->cur ^ 1];
-      SB_CUDA(sbd::launch_step(variant, c->jbf16, t, a, stream));
+      SB_CUDA(launch(k, c->cur, stream));
       c->cur ^= 1;
     }
     return SB_OK;
   }
   GraphCache& gc = c->graph;
   if (!(gc.exec && gc.variant == variant && gc.steps == steps && gc.R == c->R &&
-        gc.cur == c->cur && gc.a0 == a.a0 && gc.dt == a.dt && gc.sched == sched && gc.G == t.G)) {
+        gc.cur == c->cur && gc.a0 == a.a0 && gc.dt == a.dt && gc.sched == sched && gc.G == t.G &&
+        gc.tiled == tiled && gc.rpc == a.rpc && gc.tiles == t.tiles)) {
     gc.reset();
     cudaGraph_t g = nullptr;
     SB_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     int cur = c->cur;
     cudaError_t err = cudaSuccess;
     for (int32_t k = 0; k < steps && err == cudaSuccess; ++k) {
-      a.k = k;
-      a.xin = c->d_x[cur];
-      a.xout = c->d_x[cur ^ 1];
-      err = sbd::launch_step(variant, c->jbf16, t, a, c->cap_stream);
+      err = launch(k, cur, c->cap_stream);
       cur ^= 1;
     }
     cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
@@ -403,6 +546,9 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     gc.dt = a.dt;
     gc.sched = sched;
     gc.G = t.G;
+    gc.tiled = tiled;
+    gc.rpc = a.rpc;
+    gc.tiles = t.tiles;
   }
   SB_CUDA(cudaGraphLaunch(gc.exec, stream));
   if (steps & 1) c->cur ^= 1;
@@ -706,6 +852,74 @@ sb_status sb_best(sb_ctx* ctx, uint8_t* out_T, double* out_E, int32_t* out_repli
   return SB_OK;
 }
 
+sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t trial_steps,
+                      int32_t* out_cfg, float* out_us_per_step, void* stream) {
+  if (!ctx || replicas < 1 || replicas > 65535 || trial_steps < 1 || trial_steps > 100000) {
+    set_error("sb_autotune: invalid argument");
+    return SB_ERR_ARG;
+  }
+  sb_status st = check_run_args(ctx, variant, 1.0, 0.0, 0.5, trial_steps);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // candidates: (tiled, replica-tile width, rows per CTA); invalid ones are skipped
+  struct Cand {
+    int tiled, rt, rpc;
+  };
+  std::vector<Cand> cands = {{0, 0, 0}, {0, 0, 32}, {0, 128, 0}, {0, 64, 0}, {0, 32, 0}, {1, 0, 0}};
+  const int keep_graph = ctx->use_graph;
+  ctx->use_graph = 0;
+  if ((st = ensure_state(ctx, replicas))) return st;
+  float* sched = nullptr;
+  if ((st = dalloc(&sched, (size_t)trial_steps))) return st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float best_us = 3.0e38f;
+  int best = 0;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  if (err == cudaSuccess) err = sbd::launch_linear_schedule(sched, trial_steps, 1.0, s);
+  for (size_t k = 0; k < cands.size() && err == cudaSuccess; ++k) {
+    const Cand& c = cands[k];
+    if (c.tiled && !(ctx->tiled_ok && replicas % sbd::kTileRT == 0)) continue;
+    if (c.rt && (replicas % c.rt != 0)) continue;
+    ctx->use_tiled = c.tiled;
+    ctx->step_rt = c.rt;
+    ctx->step_rpc = c.rpc;
+    ctx->graph.reset();
+    if ((st = sb_run(ctx, variant, 1.0, 0.0, 0.5, 0, replicas, 12345, nullptr, stream))) break;
+    if ((st = enqueue_steps(ctx, variant, 1.0, 0.5, std::min(trial_steps, 4), sched, s))) break;
+    err = cudaEventRecord(e0, s);
+    if (err != cudaSuccess) break;
+    if ((st = enqueue_steps(ctx, variant, 1.0, 0.5, trial_steps, sched, s))) break;
+    err = cudaEventRecord(e1, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    const float us = ms * 1000.f / trial_steps;
+    if (err == cudaSuccess && us < best_us) {
+      best_us = us;
+      best = (int)k;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  dfree(sched);
+  ctx->use_graph = keep_graph;
+  ctx->have_state = false;
+  if (st) return st;
+  SB_CUDA(err);
+  ctx->use_tiled = cands[best].tiled;
+  ctx->step_rt = cands[best].rt;
+  ctx->step_rpc = cands[best].rpc;
+  ctx->graph.reset();
+  if (out_cfg) {
+    out_cfg[0] = cands[best].tiled;
+    out_cfg[1] = cands[best].rt;
+    out_cfg[2] = cands[best].rpc;
+  }
+  if (out_us_per_step) *out_us_per_step = best_us;
+  return SB_OK;
+}
+
 sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value) {
   if (!ctx) {
     set_error("sb_set_option: null context");
@@ -715,6 +929,27 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value) {
     case 0:  // SB_OPT_GRAPH
       ctx->use_graph = value != 0;
       if (!ctx->use_graph) ctx->graph.reset();
+      return SB_OK;
+    case 1:  // SB_OPT_TILED
+      ctx->use_tiled = value != 0;
+      ctx->graph.reset();
+      return SB_OK;
+    case 2:  // SB_OPT_STEP_RT
+      if (value != 0 && (value % 4 != 0 || value > 128 || value < 4 ||
+                         ((value / 4) & (value / 4 - 1)) != 0)) {
+        set_error("sb_set_option: SB_OPT_STEP_RT must be 0 or 4 * (a power of two <= 32)");
+        return SB_ERR_ARG;
+      }
+      ctx->step_rt = (int)value;
+      ctx->graph.reset();
+      return SB_OK;
+    case 3:  // SB_OPT_STEP_RPC
+      if (value < 0 || value > (1 << 20)) {
+        set_error("sb_set_option: SB_OPT_STEP_RPC out of range");
+        return SB_ERR_ARG;
+      }
+      ctx->step_rpc = (int)value;
+      ctx->graph.reset();
       return SB_OK;
     default:
       set_error("sb_set_option: unknown key");

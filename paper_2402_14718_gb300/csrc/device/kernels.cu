@@ -15,6 +15,8 @@
 #include <float.h>
 #include <limits.h>
 
+#include <algorithm>
+
 #include "../philox.h"
 #include "kernels.cuh"
 
@@ -30,6 +32,16 @@ Tiling make_tiling(int R) {
   const int per = (t.C + G - 1) / G;
   t.NCH = per <= 1 ? 1 : (per <= 2 ? 2 : 4);
   t.tiles = (t.C + G * t.NCH - 1) / (G * t.NCH);
+  return t;
+}
+
+Tiling make_tiling_rt(int R, int RT) {
+  Tiling t;
+  t.V = 4;
+  t.C = R / 4;
+  t.G = RT / 4;
+  t.NCH = 1;
+  t.tiles = R / RT;
   return t;
 }
 
@@ -92,13 +104,15 @@ __global__ void __launch_bounds__(kBlock) k_step(const StepArgs a) {
   const int gid = threadIdx.x / G;
   const int g = threadIdx.x - gid * G;
   const int groups = blockDim.x / G;
-  const int row = blockIdx.x * groups + gid;
-  if (row >= a.n) return;  // whole group leaves together
   const unsigned mask = group_mask(G);
   const int R = a.R;
   const int C = R / V;
   const int ch0 = blockIdx.y * (G * NCH) + g;
   const JT* J = static_cast<const JT*>(a.J);
+  const int row_end = min(a.n, (blockIdx.x + 1) * a.rpc);
+  // a CTA walks a contiguous chunk of rows, so rows in flight together share
+  // neighbour rows in L1; the group count is uniform, so a group leaves whole
+  for (int row = blockIdx.x * a.rpc + gid; row < row_end; row += groups) {
 
   float acc[NCH][V];
 #pragma unroll
@@ -191,12 +205,12 @@ __global__ void __launch_bounds__(kBlock) k_step(const StepArgs a) {
     xv.st(a.xout + idx);
     yv.st(a.y + idx);
   }
+  }
 }
 
 template <int V, int NCH, int VARIANT>
 cudaError_t launch_step_t(int jbf16, const Tiling& t, const StepArgs& a, cudaStream_t s) {
-  const int groups = kBlock / t.G;
-  dim3 grid((a.n + groups - 1) / groups, t.tiles);
+  dim3 grid((a.n + a.rpc - 1) / a.rpc, t.tiles);
   if (jbf16)
     k_step<V, NCH, VARIANT, __nv_bfloat16><<<grid, kBlock, 0, s>>>(a);
   else
@@ -212,6 +226,187 @@ cudaError_t launch_step_v(int variant, int jbf16, const Tiling& t, const StepArg
     case 1: return launch_step_t<V, NCH, 1>(jbf16, t, a, s);
     default: return launch_step_t<V, NCH, 2>(jbf16, t, a, s);
   }
+}
+
+// ---------------------------------------------------------------- tiled SB step
+// Packed per-nonzero word of the tiled kernel: the neighbour's local index in
+// the block's union and J. BF16 J: u32 = (index << 16) | bf16 bits (a BF16 value
+// widens to FP32 by a 16-bit shift). FP32 J: u64 = (index, f32 bits).
+template <typename JT>
+struct TzWord;
+template <>
+struct TzWord<__nv_bfloat16> {
+  typedef uint32_t T;
+  static __device__ __forceinline__ int idx(uint32_t w) { return (int)(w >> 16); }
+  static __device__ __forceinline__ float val(uint32_t w) { return __uint_as_float(w << 16); }
+};
+template <>
+struct TzWord<float> {
+  typedef uint2 T;
+  static __device__ __forceinline__ int idx(uint2 w) { return (int)w.x; }
+  static __device__ __forceinline__ float val(uint2 w) { return __uint_as_float(w.y); }
+};
+
+__device__ __forceinline__ void cp_async16(void* smem_ptr, const void* gptr) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_ptr);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gptr));
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* smem_ptr, const void* gptr) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_ptr);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gptr), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_prev() {  // all groups but the newest done
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+constexpr int kTiledThreads = 512;
+
+template <typename W>
+struct TiledStage {
+  static constexpr size_t kX = (size_t)kTileUCap * kTileRT * sizeof(float);
+  static constexpr size_t kBytes = kX + (size_t)kTileNzCap * sizeof(W);
+};
+
+// Issue the asynchronous copies of one (row block, replica tile) item into a
+// pipeline stage: the union rows of x (32 replicas = 128 bytes each) and the
+// block's packed (index, J) words. Row ids are read before any copy is issued.
+template <typename W>
+__device__ __forceinline__ void tiled_issue(const TiledArgs& a, long long item, int ntiles,
+                                            unsigned char* stage) {
+  const int b = (int)(item / ntiles);
+  const int r_base = (int)(item - (long long)b * ntiles) * kTileRT;
+  const int u0 = a.blk_u0[b], nu8 = (a.blk_u0[b + 1] - u0) * 8;
+  const int row0 = a.blk_row0[b];
+  const int z0 = a.rowptr[row0], nz = a.rowptr[a.blk_row0[b + 1]] - z0;
+  float4* Xs = reinterpret_cast<float4*>(stage);
+  W* Zs = reinterpret_cast<W*>(stage + TiledStage<W>::kX);
+  constexpr int PER = kTileUCap * 8 / kTiledThreads;
+  int uc[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int k = threadIdx.x + j * kTiledThreads;
+    uc[j] = k < nu8 ? __ldg(a.ucol + u0 + (k >> 3)) : 0;
+  }
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int k = threadIdx.x + j * kTiledThreads;
+    if (k < nu8) cp_async16(Xs + k, a.xin + (size_t)uc[j] * a.R + r_base + 4 * (k & 7));
+  }
+  const W* tz = static_cast<const W*>(a.tz) + z0;
+  for (int k = threadIdx.x; k < nz; k += kTiledThreads) cp_async_small<sizeof(W)>(Zs + k, tz + k);
+}
+
+// Persistent CTAs (one per SM) walk the (row block, replica tile) items with a
+// two-stage cp.async pipeline: the copies of the next item are in flight while
+// the current one is computed. Each item: 8 lanes own a row and 4 replicas
+// (float4), so every shared-memory read of a neighbour row serves 4 FMAs and a
+// warp reads 4 whole 128-byte rows at once. The FMA sequence per (row,
+// replica) is the CSR order, as in k_step (dSB applies sgn at use, as k_step).
+template <int VARIANT, typename JT>
+__global__ void __launch_bounds__(kTiledThreads, 1) k_step_tiled(const TiledArgs a) {
+  typedef typename TzWord<JT>::T W;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int ntiles = a.R / kTileRT;
+  const long long items = (long long)a.nb * ntiles;
+  long long it = blockIdx.x;
+  if (it >= items) return;
+  const int R = a.R;
+  const float pa = a.a0 - __ldg(a.sched + a.k);
+  const int slot = threadIdx.x >> 3, q = threadIdx.x & 7;
+  int stage = 0;
+  tiled_issue<W>(a, it, ntiles, smem);
+  cp_async_commit();
+  for (; it < items; it += gridDim.x) {
+    const long long nxt = it + gridDim.x;
+    if (nxt < items) tiled_issue<W>(a, nxt, ntiles, smem + (stage ^ 1) * TiledStage<W>::kBytes);
+    cp_async_commit();
+    cp_async_wait_prev();
+    __syncthreads();
+
+    unsigned char* st = smem + stage * TiledStage<W>::kBytes;
+    const float4* Xs = reinterpret_cast<const float4*>(st);
+    const W* Zs = reinterpret_cast<const W*>(st + TiledStage<W>::kX);
+    const int b = (int)(it / ntiles);
+    const int r_base = (int)(it - (long long)b * ntiles) * kTileRT;
+    const int row0 = a.blk_row0[b], row1 = a.blk_row0[b + 1];
+    const int z0 = a.rowptr[row0];
+    for (int row = row0 + slot; row < row1; row += kTiledThreads / 8) {
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      const int p0 = a.rowptr[row] - z0, p1 = a.rowptr[row + 1] - z0;
+#pragma unroll 4
+      for (int p = p0; p < p1; ++p) {
+        const W w = Zs[p];
+        const float j = TzWord<JT>::val(w);
+        float4 xv = Xs[TzWord<JT>::idx(w) * 8 + q];
+        if (VARIANT == 2) xv = make_float4(sgnf(xv.x), sgnf(xv.y), sgnf(xv.z), sgnf(xv.w));
+        acc.x = fmaf(j, xv.x, acc.x);
+        acc.y = fmaf(j, xv.y, acc.y);
+        acc.z = fmaf(j, xv.z, acc.z);
+        acc.w = fmaf(j, xv.w, acc.w);
+      }
+      const int e = a.row_event ? __ldg(a.row_event + row) : 0;
+      const float c0 = __ldg(a.c0_ev + e);
+      const float hi = __ldg(a.h + row);
+      const size_t idx = (size_t)row * R + r_base + 4 * q;
+      const float4 xo = Xs[(int)a.own[row] * 8 + q];
+      const float4 yo = *reinterpret_cast<const float4*>(a.y + idx);
+      float xs[4] = {xo.x, xo.y, xo.z, xo.w};
+      float ys[4] = {yo.x, yo.y, yo.z, yo.w};
+      const float fs[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        float x = xs[v], y = ys[v];
+        float force = -pa * x + c0 * (fs[v] + hi);
+        if (VARIANT == 0) force -= x * x * x;
+        y = y + a.dt * force;
+        x = x + a.dta0 * y;
+        if (VARIANT != 0 && fabsf(x) > 1.f) {
+          x = copysignf(1.f, x);
+          y = 0.f;
+        }
+        xs[v] = x;
+        ys[v] = y;
+      }
+      *reinterpret_cast<float4*>(a.xout + idx) = make_float4(xs[0], xs[1], xs[2], xs[3]);
+      *reinterpret_cast<float4*>(a.y + idx) = make_float4(ys[0], ys[1], ys[2], ys[3]);
+    }
+    __syncthreads();  // the stage is refilled by the next iteration's issue
+    stage ^= 1;
+  }
+}
+
+template <int VARIANT, typename JT>
+cudaError_t launch_tiled_t(const TiledArgs& a, cudaStream_t s) {
+  typedef typename TzWord<JT>::T W;
+  const size_t smem = 2 * TiledStage<W>::kBytes;
+  cudaError_t e = cudaFuncSetAttribute(k_step_tiled<VARIANT, JT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  const long long items = (long long)a.nb * (a.R / kTileRT);
+  const long long grid = std::min<long long>(items, (long long)sms);
+  k_step_tiled<VARIANT, JT><<<(unsigned)grid, kTiledThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+__global__ void k_pack_tz_bf16(const __nv_bfloat16* J, const uint16_t* lidx, int64_t nnz,
+                               uint32_t* tz) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+       p += (int64_t)gridDim.x * blockDim.x)
+    tz[p] = ((uint32_t)lidx[p] << 16) | (uint32_t)__bfloat16_as_ushort(J[p]);
+}
+
+__global__ void k_pack_tz_f32(const float* J, const uint16_t* lidx, int64_t nnz, uint2* tz) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+       p += (int64_t)gridDim.x * blockDim.x)
+    tz[p] = make_uint2((uint32_t)lidx[p], __float_as_uint(J[p]));
 }
 
 // ---------------------------------------------------------------- init / schedule
@@ -490,6 +685,31 @@ cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs&
   if (t.NCH == 1) return launch_step_v<1, 1>(variant, jbf16, t, a, s);
   if (t.NCH == 2) return launch_step_v<1, 2>(variant, jbf16, t, a, s);
   return launch_step_v<1, 4>(variant, jbf16, t, a, s);
+}
+
+cudaError_t launch_step_tiled(int variant, int jbf16, const TiledArgs& a, cudaStream_t s) {
+  if (a.nb <= 0) return cudaSuccess;
+  switch (variant * 2 + (jbf16 ? 1 : 0)) {
+    case 0: return launch_tiled_t<0, float>(a, s);
+    case 1: return launch_tiled_t<0, __nv_bfloat16>(a, s);
+    case 2: return launch_tiled_t<1, float>(a, s);
+    case 3: return launch_tiled_t<1, __nv_bfloat16>(a, s);
+    case 4: return launch_tiled_t<2, float>(a, s);
+    default: return launch_tiled_t<2, __nv_bfloat16>(a, s);
+  }
+}
+
+cudaError_t launch_pack_tz(const void* J, int jbf16, const uint16_t* lidx, int64_t nnz, void* tz,
+                           cudaStream_t s) {
+  if (nnz <= 0) return cudaSuccess;
+  const int grid = grid_for((size_t)nnz, kBlock);
+  if (jbf16)
+    k_pack_tz_bf16<<<grid, kBlock, 0, s>>>(static_cast<const __nv_bfloat16*>(J), lidx, nnz,
+                                           static_cast<uint32_t*>(tz));
+  else
+    k_pack_tz_f32<<<grid, kBlock, 0, s>>>(static_cast<const float*>(J), lidx, nnz,
+                                          static_cast<uint2*>(tz));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_init(float* x, float* y, const int32_t* row_event, const int32_t* ev_row0,

@@ -16,6 +16,9 @@ struct Tiling {
   int C;      // chunks per row = R / V
 };
 Tiling make_tiling(int R);
+// Tiling with a fixed replica-tile width RT (a multiple of 4 dividing R, RT <= 128):
+// V = 4, G = RT / 4 threads per row, one chunk per thread, R / RT tiles.
+Tiling make_tiling_rt(int R, int RT);
 
 struct StepArgs {
   const int32_t* rowptr;
@@ -32,10 +35,43 @@ struct StepArgs {
   float* y;
   int32_t n, R;
   int32_t G;
+  int32_t rpc;            // rows per CTA: a CTA walks rows [b * rpc, (b + 1) * rpc)
 };
 
 cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs& a,
                         cudaStream_t s);
+
+// Row-block tiling of the coupling product: rows are cut into blocks whose
+// union of neighbour rows ("ucol") fits kTileUCap; each CTA stages that union
+// for one 32-replica tile in shared memory and computes its block from there.
+constexpr int kTileRT = 32;        // replicas per tile
+constexpr int kTileUCap = 512;     // union rows per block (64 KB of FP32 x)
+constexpr int kTileNzCap = 4096;   // nonzeros per block
+constexpr int kTileRowCap = 256;   // rows per block
+
+struct TiledArgs {
+  const int32_t* blk_row0;   // [nb + 1] first row of each block
+  const int32_t* blk_u0;     // [nb + 1] offset of each block's union in ucol
+  const int32_t* ucol;       // union rows (global row ids), ascending within a block
+  const uint16_t* own;       // [n] local index of row i inside its block's union
+  const int32_t* rowptr;     // CSR row pointers (global)
+  const void* tz;            // per nonzero: packed (local index, J): u32 for BF16, u64 for FP32
+  const float* h;
+  const int32_t* row_event;
+  const float* c0_ev;
+  const float* sched;
+  int32_t k;
+  float a0, dt, dta0;
+  const float* xin;
+  float* xout;
+  float* y;
+  int32_t n, R, nb;
+};
+
+cudaError_t launch_step_tiled(int variant, int jbf16, const TiledArgs& a, cudaStream_t s);
+// tz[p] = packed (lidx[p], J[p]) (u32 for BF16 J, u64 for FP32 J)
+cudaError_t launch_pack_tz(const void* J, int jbf16, const uint16_t* lidx, int64_t nnz, void* tz,
+                           cudaStream_t s);
 
 cudaError_t launch_init(float* x, float* y, const int32_t* row_event, const int32_t* ev_row0,
                         int32_t n, int32_t R, uint64_t seed, cudaStream_t s);

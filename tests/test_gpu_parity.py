@@ -281,3 +281,69 @@ def test_batch_matches_oracle_per_event():
         T = (x1[sl] > 0).astype(np.int8)
         np.testing.assert_allclose(E[e], ising.qubo_energy(q, T), rtol=1e-12, atol=1e-12)
         row0 += q.n
+
+
+@pytest.mark.parametrize("variant", ["asb", "bsb", "dsb"])
+@pytest.mark.parametrize("prec", [sb.SB_J_FP32, sb.SB_J_BF16])
+@pytest.mark.parametrize("R", [32, 96, 256])
+def test_tiled_and_untiled_kernels_bit_identical(variant, prec, R):
+    """The row-block tiled step and the untiled step run the same FMA sequence
+    per (row, replica): their states must agree bit for bit."""
+    _, qc, _, _ = workload_qubos("event500")
+    dt = 0.1 if variant == "asb" else 0.5
+    out = []
+    for tiled in (1, 0):
+        ctx = _ctx(qc, prec)
+        sb.sb_set_option(ctx, sb.SB_OPT_TILED, tiled)
+        sb.sb_run(ctx, variant, 1.0, 0.0, dt, 25, R, seed=R)
+        out.append(sb.sb_get_state(ctx))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_batch_tiled_matches_single_events():
+    """A batch of two events with R = 32 (tiled kernel; row blocks may straddle
+    the event boundary) gives each event, from the same starting state, the
+    bit-identical trajectory of its own single-event context."""
+    qs = [workload_qubos("event100")[1], inputs.random_qubo(300, 9, seed=3)]
+    R, S = 32, 30
+    ctxb = sb.sb_create_batch([(q.rowptr, q.col, q.val, q.lin) for q in qs])
+    singles = [_ctx(q) for q in qs]
+    states = [inputs.random_state(q.n, R, 40 + k, 0.5) for k, q in enumerate(qs)]
+    sb.sb_set_state(ctxb, np.concatenate([s[0] for s in states]),
+                    np.concatenate([s[1] for s in states]))
+    sched = _sched(np.float32(np.linspace(0, 1, S)))
+    sb.sb_advance(ctxb, "dsb", 1.0, 0.0, 0.5, S, sched)
+    xb, yb = sb.sb_get_state(ctxb)
+    row0 = 0
+    for q, ctx, (x0, y0) in zip(qs, singles, states):
+        sb.sb_set_state(ctx, x0, y0)
+        sb.sb_advance(ctx, "dsb", 1.0, 0.0, 0.5, S, sched)
+        x, y = sb.sb_get_state(ctx)
+        assert np.array_equal(xb[row0:row0 + q.n], x) and np.array_equal(yb[row0:row0 + q.n], y)
+        row0 += q.n
+
+
+def test_autotune_keeps_results_and_picks_a_valid_config():
+    _, qc, _, _ = workload_qubos("event500")
+    ref = _ctx(qc, sb.SB_J_BF16)
+    sb.sb_run(ref, "bsb", 1.0, 0.0, 0.5, 20, 64, seed=5)
+    x_ref, y_ref = sb.sb_get_state(ref)
+    ctx = _ctx(qc, sb.SB_J_BF16)
+    cfg, us = sb.sb_autotune(ctx, "bsb", 64, trial_steps=10)
+    assert cfg["tiled"] in (0, 1) and us > 0
+    sb.sb_run(ctx, "bsb", 1.0, 0.0, 0.5, 20, 64, seed=5)
+    x, y = sb.sb_get_state(ctx)
+    assert np.array_equal(x, x_ref) and np.array_equal(y, y_ref)
+
+
+@pytest.mark.parametrize("rt,rpc", [(32, 0), (64, 96), (128, 40), (0, 512)])
+def test_step_tiling_options_bit_identical(rt, rpc):
+    _, qc, _, _ = workload_qubos("event500")
+    out = []
+    for opts in ((0, 0), (rt, rpc)):
+        ctx = _ctx(qc)
+        sb.sb_set_option(ctx, 2, opts[0])
+        sb.sb_set_option(ctx, 3, opts[1])
+        sb.sb_run(ctx, "dsb", 1.0, 0.0, 0.5, 15, 128, seed=2)
+        out.append(sb.sb_get_state(ctx))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
