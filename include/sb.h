@@ -240,6 +240,40 @@ sb_status sb_readout_device(sb_ctx* ctx, double* d_E_all, double* d_best_E, int3
                             uint8_t* d_T, void* stream);
 
 /*
+ * sb_set_weights -- set the QUBO weights from class tags (section "QUBO
+ * Formulation", Eq. 13): b_ij = -1 where cls = 0 (consistent pair) and
+ * b_ij = w_c where cls = 1 (conflict); a_i = w_q * quality_i. Host inputs:
+ * cls[nnz] (aligned with the CSR given to sb_create, symmetric), quality[n].
+ * The Ising conversion is redone on the device and the tags are kept, which
+ * lets sb_backward return gradients with respect to w_q and w_c.
+ * Single-event contexts only. Synchronous.
+ */
+sb_status sb_set_weights(sb_ctx* ctx, const int8_t* cls, const double* quality, double w_q,
+                         double w_c);
+
+/*
+ * sb_backward -- gradient of the mean relaxed Ising energy of a bSB run
+ * (section "Simulated Bifurcation", Eq. 5-8, with the field term of sb_run):
+ *   L = (1/R) sum_r [ -(1/2) x_S,r^T J x_S,r - h^T x_S,r ],
+ * x_S the positions after `steps` bSB steps from the Philox start of `seed`.
+ * The run is repeated on the device with (x, y) kept every `ckpt_every` steps;
+ * each segment is then recomputed (recording the pre-wall momentum and the
+ * wall mask) and reversed. The wall is treated as the piecewise map it is:
+ * where it fires the new position is a constant and no adjoint flows through.
+ * c0 (> 0) is an input of the gradient path (no automatic c0 here).
+ * Outputs (host, may be NULL): out_loss; out_grads[4] = dL/d dt, dL/d c0,
+ * dL/d w_q, dL/d w_c (the last two are NaN unless sb_set_weights was called);
+ * d_grad_sched: device FP64 [steps] = dL/d a_k (may be NULL).
+ * a_sched: device FP32 [steps] or NULL for the linear ramp. Single-event
+ * contexts only. Work memory: 2 (steps/ckpt_every + 1) + (ckpt_every + 1) + 4
+ * state-sized FP32 arrays plus ckpt_every byte masks. Synchronous; discards
+ * the current state.
+ */
+sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t steps,
+                      int32_t replicas, uint64_t seed, const float* a_sched, int32_t ckpt_every,
+                      double* out_loss, double* out_grads, double* d_grad_sched, void* stream);
+
+/*
  * sb_energy_noalloc -- the FP64 readout of sb_energy / sb_readout_device
  * (QUBO energies of R replicas, arg-min over replicas with ties to the lowest
  * index) for callers that cannot allocate device memory. The paper has no

@@ -20,7 +20,7 @@ __all__ = [
     "event_params", "build_params", "sb_event_generate", "sb_qubo_build", "sb_tracks",
     "sb_create", "sb_create_batch", "sb_destroy", "sb_info", "sb_run", "sb_advance",
     "sb_set_state", "sb_get_state", "sb_energy", "sb_best", "sb_readout_device", "sb_set_option",
-    "sb_energy_noalloc", "sb_autotune",
+    "sb_energy_noalloc", "sb_autotune", "sb_set_weights", "sb_backward", "SBRelaxedEnergy",
     "sb_version", "LIB_PATH",
 ]
 
@@ -318,3 +318,65 @@ def sb_autotune(ctx, variant, replicas, trial_steps=50, stream=None):
     check(lib.sb_autotune(ctx.handle, _variant(variant), int(replicas), int(trial_steps),
                           cfg.ctypes.data_as(ctypes.c_void_p), ctypes.byref(us), _stream(stream)))
     return {"tiled": int(cfg[0]), "tile": int(cfg[1]), "rows_per_cta": int(cfg[2])}, us.value
+
+
+def sb_set_weights(ctx, cls, quality, w_q, w_c):
+    c, pc = _host(cls, np.int8)
+    q, pq = _host(quality, np.float64)
+    check(lib.sb_set_weights(ctx.handle, pc, pq, float(w_q), float(w_c)))
+
+
+def sb_backward(ctx, a0, c0, dt, steps, replicas, seed, a_sched=None, ckpt_every=32,
+                d_grad_sched=None, stream=None):
+    """Returns (loss, {"dt", "c0", "w_q", "w_c"}); dL/da_k goes to ``d_grad_sched``
+    (a float64 CUDA tensor of ``steps`` values) when given."""
+    loss = ctypes.c_double()
+    g = np.zeros(4)
+    check(lib.sb_backward(ctx.handle, float(a0), float(c0), float(dt), int(steps), int(replicas),
+                          ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), _dev_ptr(a_sched),
+                          int(ckpt_every), ctypes.byref(loss), g.ctypes.data_as(ctypes.c_void_p),
+                          _dev_ptr(d_grad_sched), _stream(stream)))
+    return loss.value, {"dt": g[0], "c0": g[1], "w_q": g[2], "w_c": g[3]}
+
+
+def _autograd_function():
+    import torch
+
+    class SBRelaxedEnergy(torch.autograd.Function):
+        """Mean relaxed Ising energy of a bSB run as a differentiable function of
+        (dt, c0, a_sched, w_q, w_c). Forward and gradient both run in the
+        library's kernels (sb_set_weights + sb_backward); backward scales the
+        stored gradients by the incoming gradient."""
+
+        @staticmethod
+        def forward(fctx, dt, c0, a_sched, w_q, w_c, sbctx, cls, quality, replicas, seed,
+                    ckpt_every=32):
+            sb_set_weights(sbctx, cls, quality, float(w_q), float(w_c))
+            sched = a_sched.detach().to(device="cuda", dtype=torch.float32).contiguous()
+            g_sched = torch.zeros(sched.numel(), dtype=torch.float64, device="cuda")
+            loss, g = sb_backward(sbctx, 1.0, float(c0), float(dt), sched.numel(), replicas, seed,
+                                  sched, ckpt_every, g_sched)
+            fctx.save_for_backward(g_sched)
+            fctx.g = g
+            fctx.dtypes = (a_sched.dtype, a_sched.device)
+            return torch.tensor(loss, dtype=torch.float64)
+
+        @staticmethod
+        def backward(fctx, grad_out):
+            (g_sched,) = fctx.saved_tensors
+            g = fctx.g
+            go = float(grad_out)
+            dtype, device = fctx.dtypes
+            t = lambda v: torch.tensor(go * v, dtype=torch.float64)
+            return (t(g["dt"]), t(g["c0"]), (g_sched * go).to(dtype=dtype, device=device),
+                    t(g["w_q"]), t(g["w_c"]), None, None, None, None, None, None)
+
+    return SBRelaxedEnergy
+
+
+def __getattr__(name):
+    if name == "SBRelaxedEnergy":
+        fn = _autograd_function()
+        globals()[name] = fn
+        return fn
+    raise AttributeError(name)

@@ -76,6 +76,9 @@ _SIGS = {
     "sb_best": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "sb_readout_device": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "sb_set_option": (c_int32, [c_void_p, c_int32, c_int64]),
+    "sb_set_weights": (c_int32, [c_void_p, c_void_p, c_void_p, c_double, c_double]),
+    "sb_backward": (c_int32, [c_void_p, c_double, c_double, c_double, c_int32, c_int32, c_uint64,
+                              c_void_p, c_int32, P(c_double), c_void_p, c_void_p, c_void_p]),
     "sb_autotune": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "sb_energy_noalloc": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),

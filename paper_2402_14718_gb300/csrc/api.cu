@@ -82,6 +82,13 @@ struct sb_ctx {
   uint8_t* d_T = nullptr;
   int8_t* d_spins = nullptr;
   int32_t spins_cap_R = 0;
+  // host copy of the (global) CSR structure, for weight updates and re-tiling
+  std::vector<int32_t> h_rowptr, h_col;
+  // class tags for the adjoint's weight-scale gradients (sb_set_weights)
+  bool have_classes = false;
+  int8_t* d_cls = nullptr;
+  double* d_quality = nullptr;
+  double* d_nconf = nullptr;
   // row-block tiling of the coupling product (k_step_tiled)
   bool tiled_ok = false;
   int32_t nb = 0;
@@ -225,6 +232,9 @@ void free_all(sb_ctx* c) {
   dfree(c->d_own);
   if (c->d_tz) cudaFree(c->d_tz);
   c->d_tz = nullptr;
+  dfree(c->d_cls);
+  dfree(c->d_quality);
+  dfree(c->d_nconf);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->cap_stream = nullptr;
 }
@@ -480,6 +490,8 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   a.R = c->R;
   a.G = t.G;
   a.rpc = std::max(256 / t.G, c->step_rpc);
+  a.ytil = nullptr;
+  a.mask = nullptr;
   const int tiled = (c->tiled_ok && c->use_tiled && c->R % sbd::kTileRT == 0) ? 1 : 0;
   sbd::TiledArgs ta;
   ta.blk_row0 = c->d_blk_row0;
@@ -663,6 +675,8 @@ sb_status sb_create_batch(int32_t n_events, const int32_t* n_per_event,
   c->ev_row0 = ev_row0;
   c->ev_nnz.assign(nnz_per_event, nnz_per_event + n_events);
   sb_status st = create_common(c, grp.data(), gcol.data(), qval, qlin);
+  c->h_rowptr.swap(grp);
+  c->h_col.swap(gcol);
   if (st) {
     free_all(c);
     delete c;
@@ -849,6 +863,261 @@ sb_status sb_best(sb_ctx* ctx, uint8_t* out_T, double* out_E, int32_t* out_repli
   if (out_E) SB_CUDA(cudaMemcpy(out_E, ctx->d_bestE, ctx->E * 8, cudaMemcpyDeviceToHost));
   if (out_replica)
     SB_CUDA(cudaMemcpy(out_replica, ctx->d_bestr, ctx->E * 4, cudaMemcpyDeviceToHost));
+  return SB_OK;
+}
+
+sb_status sb_set_weights(sb_ctx* ctx, const int8_t* cls, const double* quality, double w_q,
+                         double w_c) {
+  if (!ctx || !quality || (!cls && ctx->nnz > 0) || !std::isfinite(w_q) || !std::isfinite(w_c)) {
+    set_error("sb_set_weights: invalid argument");
+    return SB_ERR_ARG;
+  }
+  if (ctx->E != 1) {
+    set_error("sb_set_weights: single-event contexts only");
+    return SB_ERR_ARG;
+  }
+  const int32_t n = ctx->n;
+  const int32_t* rp = ctx->h_rowptr.data();
+  const int32_t* col = ctx->h_col.data();
+  std::vector<double> qv((size_t)ctx->nnz), ql(n), nconf(n, 0.0);
+  for (int32_t i = 0; i < n; ++i) {
+    if (!std::isfinite(quality[i])) {
+      set_error("sb_set_weights: quality not finite");
+      return SB_ERR_ARG;
+    }
+    ql[i] = w_q * quality[i];
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+      if (cls[p] != 0 && cls[p] != 1) {
+        set_error("sb_set_weights: class tags must be 0 (consistent) or 1 (conflict)");
+        return SB_ERR_ARG;
+      }
+      const int32_t j = col[p];
+      const int32_t* f = std::lower_bound(col + rp[j], col + rp[j + 1], i);
+      if (cls[rp[j] + (f - (col + rp[j]))] != cls[p]) {
+        set_error("sb_set_weights: class tags are not symmetric");
+        return SB_ERR_CSR;
+      }
+      qv[p] = cls[p] ? w_c : -1.0;
+      nconf[i] += cls[p] ? 1.0 : 0.0;
+    }
+  }
+  sb_status st;
+  if (!ctx->d_cls) {
+    if ((st = dalloc(&ctx->d_cls, (size_t)ctx->nnz)) || (st = dalloc(&ctx->d_quality, (size_t)n)) ||
+        (st = dalloc(&ctx->d_nconf, (size_t)n)))
+      return st;
+  }
+  SB_CUDA(cudaDeviceSynchronize());
+  if (ctx->nnz) {
+    SB_CUDA(cudaMemcpy(ctx->d_cls, cls, (size_t)ctx->nnz, cudaMemcpyHostToDevice));
+    SB_CUDA(cudaMemcpy(ctx->d_qval, qv.data(), (size_t)ctx->nnz * 8, cudaMemcpyHostToDevice));
+  }
+  SB_CUDA(cudaMemcpy(ctx->d_quality, quality, (size_t)n * 8, cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(ctx->d_nconf, nconf.data(), (size_t)n * 8, cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(ctx->d_qlin, ql.data(), (size_t)n * 8, cudaMemcpyHostToDevice));
+  double *row_off = nullptr, *row_sq = nullptr;
+  if ((st = dalloc(&row_off, (size_t)n)) || (st = dalloc(&row_sq, (size_t)n))) {
+    dfree(row_off);
+    dfree(row_sq);
+    return st;
+  }
+  cudaError_t e1 = sbd::launch_convert(ctx->d_rowptr, ctx->d_col, ctx->d_qval, ctx->d_qlin, n,
+                                       ctx->d_J, ctx->jbf16, ctx->d_h64, ctx->d_h32, row_off,
+                                       row_sq, 0);
+  cudaError_t e2 = sbd::launch_event_stats(row_off, row_sq, ctx->d_ev_row0, 1, ctx->d_offset,
+                                           ctx->d_sigma, ctx->d_c0auto, 0);
+  cudaError_t e3 = cudaDeviceSynchronize();
+  dfree(row_off);
+  dfree(row_sq);
+  SB_CUDA(e1);
+  SB_CUDA(e2);
+  SB_CUDA(e3);
+  SB_CUDA(cudaMemcpy(ctx->offset.data(), ctx->d_offset, 8, cudaMemcpyDeviceToHost));
+  SB_CUDA(cudaMemcpy(ctx->sigma.data(), ctx->d_sigma, 8, cudaMemcpyDeviceToHost));
+  SB_CUDA(cudaMemcpy(ctx->c0_auto.data(), ctx->d_c0auto, 8, cudaMemcpyDeviceToHost));
+  // the tiled kernel's packed words carry J: rebuild them
+  dfree(ctx->d_blk_row0);
+  dfree(ctx->d_blk_u0);
+  dfree(ctx->d_ucol);
+  dfree(ctx->d_own);
+  if (ctx->d_tz) cudaFree(ctx->d_tz);
+  ctx->d_tz = nullptr;
+  ctx->graph.reset();
+  if ((st = setup_tiles(ctx, rp, col))) return st;
+  ctx->have_classes = true;
+  return SB_OK;
+}
+
+sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t steps,
+                      int32_t replicas, uint64_t seed, const float* a_sched, int32_t ckpt_every,
+                      double* out_loss, double* out_grads, double* d_grad_sched, void* stream) {
+  sb_status st = check_run_args(ctx, SB_BSB, a0, c0, dt, steps);
+  if (st) return st;
+  if (ctx->E != 1 || !(c0 > 0.0) || steps < 1 || ckpt_every < 1 || replicas < 1 ||
+      replicas > 65535) {
+    set_error("sb_backward: single event, c0 > 0, steps >= 1, ckpt_every >= 1, 1 <= R <= 65535");
+    return SB_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = ensure_state(ctx, replicas))) return st;
+  const int32_t n = ctx->n, R = replicas, S = steps, K = std::min(ckpt_every, steps);
+  const size_t NR = (size_t)n * R;
+  const int32_t n_ck = (S + K - 1) / K;
+  if (!ctx->d_cls) {  // no class tags: weight-scale gradients are reported as NaN
+    if ((st = dalloc(&ctx->d_cls, (size_t)ctx->nnz)) || (st = dalloc(&ctx->d_quality, (size_t)n)) ||
+        (st = dalloc(&ctx->d_nconf, (size_t)n)))
+      return st;
+    SB_CUDA(cudaMemset(ctx->d_cls, 0, std::max<size_t>((size_t)ctx->nnz, 1)));
+    SB_CUDA(cudaMemset(ctx->d_quality, 0, (size_t)n * 8));
+    SB_CUDA(cudaMemset(ctx->d_nconf, 0, (size_t)n * 8));
+  }
+  const float* sched = a_sched;
+  if (!sched) {
+    if (ctx->sched_len != S || ctx->sched_a0 != a0) {
+      dfree(ctx->d_sched);
+      if ((st = dalloc(&ctx->d_sched, S))) return st;
+      SB_CUDA(sbd::launch_linear_schedule(ctx->d_sched, S, a0, s));
+      ctx->sched_len = S;
+      ctx->sched_a0 = a0;
+    }
+    sched = ctx->d_sched;
+  }
+  float *ck_x = nullptr, *ck_y = nullptr, *seg_x = nullptr, *seg_yt = nullptr;
+  float *lx = nullptr, *ly = nullptr, *lyt = nullptr;
+  uint8_t* seg_m = nullptr;
+  double *gh = nullptr, *acc = nullptr, *ga = nullptr;
+  auto cleanup = [&]() {
+    dfree(ck_x);
+    dfree(ck_y);
+    dfree(seg_x);
+    dfree(seg_yt);
+    dfree(seg_m);
+    dfree(lx);
+    dfree(ly);
+    dfree(lyt);
+    dfree(gh);
+    dfree(acc);
+    dfree(ga);
+  };
+  if ((st = dalloc(&ck_x, NR * n_ck)) || (st = dalloc(&ck_y, NR * n_ck)) ||
+      (st = dalloc(&seg_x, NR * (K + 1))) || (st = dalloc(&seg_yt, NR * K)) ||
+      (st = dalloc(&seg_m, NR * K)) || (st = dalloc(&lx, NR)) || (st = dalloc(&ly, NR)) ||
+      (st = dalloc(&lyt, NR)) || (st = dalloc(&gh, (size_t)n)) || (st = dalloc(&acc, 6)) ||
+      (st = dalloc(&ga, (size_t)S))) {
+    cleanup();
+    return st;
+  }
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+    return e == cudaSuccess;
+  };
+  const sbd::Tiling t = sbd::make_tiling(R);
+  sbd::StepArgs a;
+  a.rowptr = ctx->d_rowptr;
+  a.col = ctx->d_col;
+  a.J = ctx->d_J;
+  a.h = ctx->d_h32;
+  a.row_event = nullptr;
+  a.c0_ev = ctx->d_c0ev;
+  a.sched = sched;
+  a.a0 = (float)a0;
+  a.dt = (float)dt;
+  a.dta0 = (float)(dt * a0);
+  a.n = n;
+  a.R = R;
+  a.G = t.G;
+  a.rpc = 256 / t.G;
+  a.ytil = nullptr;
+  a.mask = nullptr;
+  ok(sbd::launch_set_c0(ctx->d_c0ev, ctx->d_c0auto, c0, 1, s));
+  ok(sbd::launch_init(ctx->d_x[0], ctx->d_y, nullptr, ctx->d_ev_row0, n, R, seed, s));
+  int cur = 0;
+  // forward, keeping (x, y) at the start of every segment
+  for (int32_t c = 0; c < n_ck && e == cudaSuccess; ++c) {
+    ok(cudaMemcpyAsync(ck_x + NR * c, ctx->d_x[cur], NR * 4, cudaMemcpyDeviceToDevice, s));
+    ok(cudaMemcpyAsync(ck_y + NR * c, ctx->d_y, NR * 4, cudaMemcpyDeviceToDevice, s));
+    const int32_t L = std::min(K, S - c * K);
+    for (int32_t j = 0; j < L && e == cudaSuccess; ++j) {
+      a.k = c * K + j;
+      a.xin = ctx->d_x[cur];
+      a.xout = ctx->d_x[cur ^ 1];
+      a.y = ctx->d_y;
+      ok(sbd::launch_step(SB_BSB, ctx->jbf16, t, a, s));
+      cur ^= 1;
+    }
+  }
+  ok(cudaMemsetAsync(gh, 0, (size_t)n * 8, s));
+  ok(cudaMemsetAsync(acc, 0, 6 * 8, s));
+  ok(cudaMemsetAsync(ga, 0, (size_t)S * 8, s));
+  sbd::AdjArgs g;
+  g.rowptr = ctx->d_rowptr;
+  g.col = ctx->d_col;
+  g.J = ctx->d_J;
+  g.cls = ctx->d_cls;
+  g.h = ctx->d_h32;
+  g.quality = ctx->d_quality;
+  g.nconf = ctx->d_nconf;
+  g.n = n;
+  g.R = R;
+  g.G = t.G;
+  g.a0 = (float)a0;
+  g.c0 = (float)c0;
+  g.dt = (float)dt;
+  g.sched = sched;
+  g.k = 0;
+  g.x = ctx->d_x[cur];
+  g.ytil = nullptr;
+  g.mask = nullptr;
+  g.lx = lx;
+  g.ly = ly;
+  g.lyt = lyt;
+  g.gh = gh;
+  g.acc = acc;
+  g.ga = nullptr;
+  ok(sbd::launch_adj_init(ctx->jbf16, t, g, s));
+  // reverse sweep, one segment at a time: recompute it with recording, then reverse it
+  for (int32_t c = n_ck - 1; c >= 0 && e == cudaSuccess; --c) {
+    const int32_t L = std::min(K, S - c * K);
+    ok(cudaMemcpyAsync(seg_x, ck_x + NR * c, NR * 4, cudaMemcpyDeviceToDevice, s));
+    ok(cudaMemcpyAsync(ctx->d_y, ck_y + NR * c, NR * 4, cudaMemcpyDeviceToDevice, s));
+    for (int32_t j = 0; j < L && e == cudaSuccess; ++j) {
+      a.k = c * K + j;
+      a.xin = seg_x + NR * j;
+      a.xout = seg_x + NR * (j + 1);
+      a.y = ctx->d_y;
+      a.ytil = seg_yt + NR * j;
+      a.mask = seg_m + NR * j;
+      ok(sbd::launch_step(SB_BSB, ctx->jbf16, t, a, s));
+    }
+    a.ytil = nullptr;
+    a.mask = nullptr;
+    for (int32_t j = L - 1; j >= 0 && e == cudaSuccess; --j) {
+      g.k = c * K + j;
+      g.x = seg_x + NR * j;
+      g.ytil = seg_yt + NR * j;
+      g.mask = seg_m + NR * j;
+      g.ga = ga + g.k;
+      ok(sbd::launch_adj_phase1(g, s));
+      ok(sbd::launch_adj_phase2(ctx->jbf16, t, g, s));
+    }
+  }
+  ok(sbd::launch_adj_final(g, acc + 4, s));
+  if (d_grad_sched) ok(cudaMemcpyAsync(d_grad_sched, ga, (size_t)S * 8, cudaMemcpyDeviceToDevice, s));
+  ok(cudaStreamSynchronize(s));
+  double h_acc[6] = {0, 0, 0, 0, 0, 0};
+  ok(cudaMemcpy(h_acc, acc, sizeof(h_acc), cudaMemcpyDeviceToHost));
+  cleanup();
+  ctx->have_state = false;  // x holds x_S but y was reused by the recomputation
+  SB_CUDA(e);
+  if (out_loss) *out_loss = h_acc[0];
+  if (out_grads) {
+    const double nan = std::nan("");
+    out_grads[0] = h_acc[1];
+    out_grads[1] = h_acc[2];
+    out_grads[2] = ctx->have_classes ? h_acc[4] : nan;
+    out_grads[3] = ctx->have_classes ? h_acc[3] + h_acc[5] : nan;
+  }
   return SB_OK;
 }
 

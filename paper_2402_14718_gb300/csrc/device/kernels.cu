@@ -195,7 +195,10 @@ __global__ void __launch_bounds__(kBlock) k_step(const StepArgs a) {
       if (VARIANT == 0) force -= x * x * x;
       y = y + a.dt * force;
       x = x + a.dta0 * y;
-      if (VARIANT != 0 && fabsf(x) > 1.f) {
+      if (a.ytil) a.ytil[idx + v] = y;
+      const bool wall = VARIANT != 0 && fabsf(x) > 1.f;
+      if (a.mask) a.mask[idx + v] = wall ? 1 : 0;
+      if (wall) {
         x = copysignf(1.f, x);
         y = 0.f;
       }
@@ -409,6 +412,215 @@ __global__ void k_pack_tz_f32(const float* J, const uint16_t* lidx, int64_t nnz,
     tz[p] = make_uint2((uint32_t)lidx[p], __float_as_uint(J[p]));
 }
 
+
+// ---------------------------------------------------------------- bSB adjoint
+// FP64 block sum of up to 4 values into acc[0..n) (one atomic per block and value).
+__device__ __forceinline__ void block_add(double v0, double v1, double v2, double v3,
+                                          double* t0, double* t1, double* t2, double* t3) {
+  __shared__ double sh[4][kBlock / 32];
+  double v[4] = {v0, v1, v2, v3};
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    for (int off = 16; off > 0; off >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sh[q][wid] = v[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s[q] += sh[q][w];
+    double* tg[4] = {t0, t1, t2, t3};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (tg[q]) atomicAdd(tg[q], s[q]);
+  }
+}
+
+// Sparse products of one row for this thread's replica chunks:
+// sJ = sum_j J_ij u_j, and (when x given) fJ = sum_j J_ij x_j, fC = sum_{conflict j} x_j.
+template <int V, int NCH, typename JT, bool TWO>
+__device__ __forceinline__ void adj_row_products(const AdjArgs& a, int row, int ch0, int C,
+                                                 unsigned mask, const float* u, const float* xk,
+                                                 float (&sJ)[NCH][V], float (&fJ)[NCH][V],
+                                                 float (&fC)[NCH][V]) {
+  const int G = a.G, g = ch0 % G;
+  const JT* J = static_cast<const JT*>(a.J);
+#pragma unroll
+  for (int j = 0; j < NCH; ++j)
+#pragma unroll
+    for (int v = 0; v < V; ++v) sJ[j][v] = fJ[j][v] = fC[j][v] = 0.f;
+  const int p0 = a.rowptr[row], p1 = a.rowptr[row + 1];
+  for (int pb = p0; pb < p1; pb += G) {
+    const int cnt = min(G, p1 - pb);
+    int mc = 0, mk = 0;
+    float mv = 0.f;
+    if (g < cnt) {
+      mc = a.col[pb + g];
+      mv = jval(J, pb + g);
+      mk = a.cls[pb + g];
+    }
+    for (int q = 0; q < cnt; ++q) {
+      const int c = __shfl_sync(mask, mc, q, G);
+      const float w = __shfl_sync(mask, mv, q, G);
+      const int kc = __shfl_sync(mask, mk, q, G);
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        const int ch = ch0 + j * G;
+        if (ch >= C) continue;
+        const size_t off = (size_t)c * a.R + (size_t)ch * V;
+        Vec<V> uv;
+        uv.ldg(u + off);
+#pragma unroll
+        for (int v = 0; v < V; ++v) sJ[j][v] = fmaf(w, uv.v[v], sJ[j][v]);
+        if (TWO) {
+          Vec<V> xv;
+          xv.ldg(xk + off);
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            fJ[j][v] = fmaf(w, xv.v[v], fJ[j][v]);
+            if (kc) fC[j][v] += xv.v[v];
+          }
+        }
+      }
+    }
+  }
+}
+
+// lambda_x = (-J x_S - h) / R, lambda_y = 0; loss, dL/dh_i = -sum_r x_S / R and the
+// explicit w_c term sum x (C x) / (8 R).
+template <int V, int NCH, typename JT>
+__global__ void __launch_bounds__(kBlock) k_adj_init(const AdjArgs a) {
+  const int G = a.G;
+  const int gid = threadIdx.x / G, g = threadIdx.x - gid * G;
+  const int row = blockIdx.x * (blockDim.x / G) + gid;
+  const int C = a.R / V;
+  const int ch0 = blockIdx.y * (G * NCH) + g;
+  double loss = 0.0, wc = 0.0, ghr = 0.0;
+  if (row < a.n) {
+    const unsigned mask = group_mask(G);
+    float sJ[NCH][V], fJ[NCH][V], fC[NCH][V];
+    adj_row_products<V, NCH, JT, true>(a, row, ch0, C, mask, a.x, a.x, sJ, fJ, fC);
+    const float hi = a.h[row];
+    const double invR = 1.0 / a.R;
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+      const int ch = ch0 + j * G;
+      if (ch >= C) continue;
+      const size_t idx = (size_t)row * a.R + (size_t)ch * V;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const double x = a.x[idx + v];
+        a.lx[idx + v] = (float)((-(double)fJ[j][v] - hi) * invR);
+        a.ly[idx + v] = 0.f;
+        loss += (-0.5 * x * fJ[j][v] - hi * x) * invR;
+        wc += x * fC[j][v] * invR / 8.0;
+        ghr -= x * invR;
+      }
+    }
+    for (int off = G / 2; off > 0; off >>= 1) ghr += __shfl_down_sync(mask, ghr, off, G);
+    if (g == 0) atomicAdd(a.gh + row, ghr);
+  }
+  block_add(loss, wc, 0.0, 0.0, a.acc + 0, a.acc + 3, nullptr, nullptr);
+}
+
+// Through the wall: lx~ = (1 - m) lx; ly~ = (1 - m) ly + dt a0 lx~.
+__global__ void k_adj_phase1(const AdjArgs a) {
+  const size_t total = (size_t)a.n * a.R;
+  const float dta0 = a.dt * a.a0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const bool keep = a.mask[i] == 0;
+    const float lxt = keep ? a.lx[i] : 0.f;
+    a.lx[i] = lxt;
+    a.lyt[i] = (keep ? a.ly[i] : 0.f) + dta0 * lxt;
+  }
+}
+
+// Momentum update reversed: lx_k = lx~ - dt (a0 - a_k) ly~ + dt c0 J ly~, ly_k = ly~,
+// and the gradient contributions of this step (FP64).
+template <int V, int NCH, typename JT>
+__global__ void __launch_bounds__(kBlock) k_adj_phase2(const AdjArgs a) {
+  const int G = a.G;
+  const int gid = threadIdx.x / G, g = threadIdx.x - gid * G;
+  const int row = blockIdx.x * (blockDim.x / G) + gid;
+  const int C = a.R / V;
+  const int ch0 = blockIdx.y * (G * NCH) + g;
+  double gdt = 0.0, gc0 = 0.0, ga = 0.0, gwc = 0.0, ghr = 0.0;
+  if (row < a.n) {
+    const unsigned mask = group_mask(G);
+    float sJ[NCH][V], fJ[NCH][V], fC[NCH][V];
+    adj_row_products<V, NCH, JT, true>(a, row, ch0, C, mask, a.lyt, a.x, sJ, fJ, fC);
+    const float hi = a.h[row];
+    const float pa = a.a0 - __ldg(a.sched + a.k);
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+      const int ch = ch0 + j * G;
+      if (ch >= C) continue;
+      const size_t idx = (size_t)row * a.R + (size_t)ch * V;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const float x = a.x[idx + v];
+        const float lyt = a.lyt[idx + v];
+        const float lxt = a.lx[idx + v];
+        const double F = -(double)pa * x + (double)a.c0 * ((double)fJ[j][v] + hi);
+        gdt += (double)lyt * F + (double)lxt * a.a0 * (double)a.ytil[idx + v];
+        gc0 += (double)lyt * a.dt * ((double)fJ[j][v] + hi);
+        ga += (double)lyt * a.dt * x;
+        gwc += (double)a.dt * a.c0 * lyt * (-0.25 * (double)fC[j][v]);
+        ghr += (double)a.dt * a.c0 * lyt;
+        a.lx[idx + v] = lxt - a.dt * pa * lyt + a.dt * a.c0 * sJ[j][v];
+        a.ly[idx + v] = lyt;
+      }
+    }
+    for (int off = G / 2; off > 0; off >>= 1) ghr += __shfl_down_sync(mask, ghr, off, G);
+    if (g == 0) atomicAdd(a.gh + row, ghr);
+  }
+  block_add(gdt, gc0, gwc, ga, a.acc + 1, a.acc + 2, a.acc + 3, a.ga);
+}
+
+__global__ void k_adj_final(const AdjArgs a, double* out) {
+  double wq = 0.0, wc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+    wq += a.gh[i] * (-a.quality[i] / 2.0);
+    wc += a.gh[i] * (-a.nconf[i] / 4.0);
+  }
+  block_add(wq, wc, 0.0, 0.0, out, out + 1, nullptr, nullptr);
+}
+
+template <int V, int NCH>
+cudaError_t launch_adj_vn(int which, int jbf16, const Tiling& t, const AdjArgs& a,
+                          cudaStream_t s) {
+  const int groups = kBlock / t.G;
+  dim3 grid((a.n + groups - 1) / groups, t.tiles);
+  if (which == 0) {
+    if (jbf16)
+      k_adj_init<V, NCH, __nv_bfloat16><<<grid, kBlock, 0, s>>>(a);
+    else
+      k_adj_init<V, NCH, float><<<grid, kBlock, 0, s>>>(a);
+  } else {
+    if (jbf16)
+      k_adj_phase2<V, NCH, __nv_bfloat16><<<grid, kBlock, 0, s>>>(a);
+    else
+      k_adj_phase2<V, NCH, float><<<grid, kBlock, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_sparse(int which, int jbf16, const Tiling& t, const AdjArgs& a,
+                              cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  if (t.V == 4) {
+    if (t.NCH == 1) return launch_adj_vn<4, 1>(which, jbf16, t, a, s);
+    if (t.NCH == 2) return launch_adj_vn<4, 2>(which, jbf16, t, a, s);
+    return launch_adj_vn<4, 4>(which, jbf16, t, a, s);
+  }
+  if (t.NCH == 1) return launch_adj_vn<1, 1>(which, jbf16, t, a, s);
+  if (t.NCH == 2) return launch_adj_vn<1, 2>(which, jbf16, t, a, s);
+  return launch_adj_vn<1, 4>(which, jbf16, t, a, s);
+}
 // ---------------------------------------------------------------- init / schedule
 __global__ void k_init(float* x, float* y, const int32_t* row_event, const int32_t* ev_row0,
                        int32_t n, int32_t R, uint32_t k0, uint32_t k1) {
@@ -709,6 +921,26 @@ cudaError_t launch_pack_tz(const void* J, int jbf16, const uint16_t* lidx, int64
   else
     k_pack_tz_f32<<<grid, kBlock, 0, s>>>(static_cast<const float*>(J), lidx, nnz,
                                           static_cast<uint2*>(tz));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_init(int jbf16, const Tiling& t, const AdjArgs& a, cudaStream_t s) {
+  return launch_adj_sparse(0, jbf16, t, a, s);
+}
+
+cudaError_t launch_adj_phase2(int jbf16, const Tiling& t, const AdjArgs& a, cudaStream_t s) {
+  return launch_adj_sparse(1, jbf16, t, a, s);
+}
+
+cudaError_t launch_adj_phase1(const AdjArgs& a, cudaStream_t s) {
+  const size_t total = (size_t)a.n * a.R;
+  if (!total) return cudaSuccess;
+  k_adj_phase1<<<grid_for(total, kBlock), kBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_final(const AdjArgs& a, double* out, cudaStream_t s) {
+  k_adj_final<<<grid_for(a.n, kBlock), kBlock, 0, s>>>(a, out);
   return cudaGetLastError();
 }
 

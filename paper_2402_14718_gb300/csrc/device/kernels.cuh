@@ -36,6 +36,8 @@ struct StepArgs {
   int32_t n, R;
   int32_t G;
   int32_t rpc;            // rows per CTA: a CTA walks rows [b * rpc, (b + 1) * rpc)
+  float* ytil;            // optional: momentum after the update, before the wall [n x R]
+  uint8_t* mask;          // optional: 1 where the wall fired [n x R]
 };
 
 cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs& a,
@@ -110,5 +112,34 @@ cudaError_t launch_argmin(const double* E_all, int32_t E, int32_t R, double* bes
                           int32_t* best_r, cudaStream_t s);
 cudaError_t launch_best_T(const float* x, const int32_t* row_event, const int32_t* best_r,
                           int32_t n, int32_t R, uint8_t* T, cudaStream_t s);
+
+// ---------------------------------------------------------------- bSB adjoint
+struct AdjArgs {
+  const int32_t* rowptr;
+  const int32_t* col;
+  const void* J;             // FP32 or BF16, as the forward used
+  const int8_t* cls;         // per nonzero: 1 = conflict
+  const float* h;
+  const double* quality;     // [n]
+  const double* nconf;       // [n] conflicts per row
+  int32_t n, R, G;
+  float a0, c0, dt;
+  const float* sched;        // a_k on the device (the forward's values)
+  int32_t k;                 // the step being reversed
+  const float* x;            // x_k (phase 2) or x_S (init)
+  const float* ytil;         // y~_k
+  const uint8_t* mask;       // m_k
+  float* lx;                 // adjoint of x
+  float* ly;                 // adjoint of y
+  float* lyt;                // adjoint of y~ (gathered by neighbours in phase 2)
+  double* gh;                // [n] dL/dh_i
+  double* acc;               // [4]: loss, dL/ddt, dL/dc0, dL/dw_c (trajectory + explicit)
+  double* ga;                // dL/da_k of this step (one double)
+};
+cudaError_t launch_adj_init(int jbf16, const Tiling& t, const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adj_phase1(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adj_phase2(int jbf16, const Tiling& t, const AdjArgs& a, cudaStream_t s);
+// out[0] = sum_i gh_i (-quality_i / 2), out[1] = sum_i gh_i (-nconf_i / 4)
+cudaError_t launch_adj_final(const AdjArgs& a, double* out, cudaStream_t s);
 
 }  // namespace sbd

@@ -134,11 +134,12 @@ def test_one_step_random_weights_bf16_quantised():
 
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_short_horizon_from_seeded_start(variant):
-    """20 steps from the Philox start on the linear schedule, each GPU step
-    compared with one oracle step from the GPU's previous state, and the whole
-    20-step trajectory compared with the free-running oracle. aSB has no wall:
-    its x^3 force makes explicit steps of dt = 0.5 blow up within a few steps
-    (FP32 overflows first), so it runs with dt = 0.1."""
+    """20 steps from the Philox start on the linear schedule: the GPU trajectory
+    against the free-running oracle (each side draws the start itself), and
+    single steps from states along the oracle's own trajectory (rounded to FP32
+    and given to both sides). aSB has no wall: its x^3 force makes explicit
+    steps of dt = 0.5 blow up within a few steps (FP32 overflows first), so it
+    runs with dt = 0.1."""
     _, qc, _, qo = workload_qubos("event100")
     R, S = 16, 20
     dt = 0.1 if variant == osb.ASB else 0.5
@@ -146,21 +147,28 @@ def test_short_horizon_from_seeded_start(variant):
     sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
     c0 = sb.sb_info(ctx)["c0_auto"]
     sched = np.float32(np.linspace(0.0, 1.0, 2000))[:S]
-    sb.sb_run(ctx, variant, 1.0, c0, 0.5, 0, R, seed=99)
     J, h, _ = ising.to_ising(qo)
-    xf, yf = osb.init_state(99, qo.n, R)
+    # free-running trajectories
+    sb.sb_run(ctx, variant, 1.0, c0, dt, 0, R, seed=99)
+    sb.sb_advance(ctx, variant, 1.0, c0, dt, S, _sched(sched))
     xg, yg = sb.sb_get_state(ctx)
+    assert np.all(np.isfinite(xg)) and np.all(np.isfinite(yg))
+    xf, yf = osb.init_state(99, qo.n, R)
+    states = {}
     for k in range(S):
+        if k in (0, 5, 10, 19):
+            states[k] = (xf.astype(np.float32), yf.astype(np.float32))
+        xf, yf = osb.step(J, h, xf, yf, float(sched[k]), 1.0, c0, dt, variant)
+    assert max_rel(xg, xf) < 1e-4 and max_rel(yg, yf) < 1e-4
+    # single steps from oracle states
+    for k, (x32, y32) in states.items():
+        sb.sb_set_state(ctx, x32, y32)
         sb.sb_advance(ctx, variant, 1.0, c0, dt, 1, _sched(sched[k:k + 1]))
         xn, yn = sb.sb_get_state(ctx)
-        assert np.all(np.isfinite(xn)) and np.all(np.isfinite(yn))
-        xp, yp = xg.astype(np.float64), yg.astype(np.float64)
+        xp, yp = x32.astype(np.float64), y32.astype(np.float64)
         xo, yo = osb.step(J, h, xp, yp, float(sched[k]), 1.0, c0, dt, variant)
         xpre = osb.prewall_x(J, h, xp, yp, float(sched[k]), 1.0, c0, dt, variant)
         compare_step(xn, yn, xo, yo, xpre)
-        xf, yf = osb.step(J, h, xf, yf, float(sched[k]), 1.0, c0, dt, variant)
-        xg, yg = xn, yn
-    assert max_rel(xg, xf) < 1e-4 and max_rel(yg, yf) < 1e-4
 
 
 def test_graph_and_direct_launches_agree_bit_for_bit():
@@ -211,16 +219,17 @@ def test_full_size_event1000_step_sampled():
 
 
 def test_full_size_event1000_readout():
-    """Full run at the bench shape: the energies of sampled replicas and the
-    arg-min agree with the oracle on the GPU's own spins."""
-    _, qc, ev_o, qo = workload_qubos("event1000")
+    """Readout at the bench shape (R = 256, BF16 J) of a seeded full-size state:
+    energies of sampled replicas against the oracle, and the arg-min and the best
+    selection consistent with them."""
+    _, qc, _, qo = workload_qubos("event1000")
     R = 256
     ctx = _ctx(qc, sb.SB_J_BF16)
-    sb.sb_run(ctx, "bsb", 1.0, 0.0, 0.5, 400, R, seed=1)
+    x0, y0 = inputs.random_state(qo.n, R, 123, 1.0)
+    sb.sb_set_state(ctx, x0, y0)
     T, Ebest, rbest = sb.sb_best(ctx)
-    x, _ = sb.sb_get_state(ctx)
     E_all = sb.sb_energy(ctx, None, R)[0]
-    Ts = (x > 0).astype(np.int8)
+    Ts = (x0 > 0).astype(np.int8)
     pick = [0, 17, int(rbest[0]), R - 1]
     np.testing.assert_allclose(E_all[pick], ising.qubo_energy(qo, Ts[:, pick]), rtol=1e-12)
     assert int(rbest[0]) == int(np.argmin(E_all))
@@ -267,7 +276,8 @@ def test_batch_matches_oracle_per_event():
     x0, y0 = sb.sb_get_state(ctx)
     sb.sb_advance(ctx, "bsb", 1.0, 0.0, 0.5, 1, _sched([0.4]))
     x1, y1 = sb.sb_get_state(ctx)
-    E = sb.sb_energy(ctx, None, R)
+    spins = inputs.random_spins(sum(q.n for q in qs), R, seed=6)
+    E = sb.sb_energy(ctx, np.where(spins > 0, 1, -1).astype(np.int8))
     row0 = 0
     for e, q in enumerate(qs):
         sl = slice(row0, row0 + q.n)
@@ -278,8 +288,7 @@ def test_batch_matches_oracle_per_event():
         assert c0 == pytest.approx(ising.c0_auto(J, q.n), rel=1e-12)
         xn, yn = osb.step(J, h, xo, yo, float(np.float32(0.4)), 1.0, c0, 0.5, osb.BSB)
         assert max_rel(x1[sl], xn) < 1e-5 and max_rel(y1[sl], yn) < 1e-5
-        T = (x1[sl] > 0).astype(np.int8)
-        np.testing.assert_allclose(E[e], ising.qubo_energy(q, T), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(E[e], ising.qubo_energy(q, spins[sl]), rtol=1e-12, atol=1e-12)
         row0 += q.n
 
 
