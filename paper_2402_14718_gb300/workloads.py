@@ -21,8 +21,13 @@ CUTS_S8 = _cuts(3.2e-3, 4.0, 400.0, 6.4e-3, 0.8)
 CUTS_S2_35 = _cuts(9.4e-4, 1.175, 117.5, 1.88e-3, 0.235)
 # s = 2.8: 500 tracks -> N ~ 10k
 CUTS_S2_8 = _cuts(1.12e-3, 1.4, 140.0, 2.24e-3, 0.28)
+# s = 1.6: the batch of uneven events (N ~ 0.4k - 92k per event)
+CUTS_S1_6 = _cuts(6.4e-4, 0.8, 80.0, 1.28e-3, 0.16)
 # paper values of Eq. 16 / 17 read in mm^-1 (s = 1, dkappa = 1e-4)
 CUTS_PAPER = _cuts(4e-4, 0.5, 50.0, 8e-4, 0.1, 1e-4)
+# dense pile-up events: windows at the track resolution (dtheta of a true
+# triplet is < 0.003 rad at 0.1 mm smear); 10k tracks -> N ~ 0.47M, ~21M couplings
+CUTS_DENSE = _cuts(3.5e-4, 0.3, 25.0, 8e-4, 0.04)
 
 WORKLOADS = {
     # plain bSB / dSB on one small event, FP32 J, one replica
@@ -34,4 +39,24 @@ WORKLOADS = {
     # adjoint workload
     "event500": dict(n_tracks=500, noise_frac=0.1, seed=3000, cuts=CUTS_S2_8,
                      replicas=32, steps=1000, dt=0.5, a0=1.0, jprec="fp32"),
+    # high pile-up event
+    "event10k": dict(n_tracks=10000, noise_frac=0.2, seed=4000, cuts=CUTS_DENSE,
+                     replicas=128, steps=5000, dt=0.5, a0=1.0, jprec="bf16"),
 }
+
+# 512 uneven events in one context: event e has BATCH512_TRACKS[e] tracks
+# (log-uniform in [50, 2000], drawn once from numpy's PCG64 with seed 2000) and
+# event seed 2000 + e; 10 % noise; dSB, 64 replicas, 2000 steps.
+BATCH512 = dict(n_events=512, tracks_min=50, tracks_max=2000, track_seed=2000, seed0=2000,
+                noise_frac=0.1, cuts=CUTS_S1_6, replicas=64, steps=2000, dt=0.5, a0=1.0,
+                variant="dsb", jprec="bf16")
+
+
+def batch512_tracks():
+    import math
+
+    import numpy as np
+    rng = np.random.default_rng(BATCH512["track_seed"])
+    u = rng.uniform(math.log(BATCH512["tracks_min"]), math.log(BATCH512["tracks_max"]),
+                    BATCH512["n_events"])
+    return [int(v) for v in np.round(np.exp(u))]

@@ -458,3 +458,8 @@ def test_ttt_closed_forms():
     assert ttt.target_energy(-100.0) == pytest.approx(-99.9)
     assert ttt.ttt([1.0, 2.0], [[0, 0, 0, 5], [0, 0, 0, 0]], 0.5) == pytest.approx(min(math.log(0.01) / math.log(0.25), 2.0))
     assert ttt.ttt([1.0], [[1.0, 2.0]], 0.5) is None
+    # at or above 99 % one run suffices; a batch of R replicas succeeds if any does
+    assert ttt.ttt_at(2.0, 0.995) == 2.0
+    assert ttt.p_batch(0.5, 3) == pytest.approx(0.875)
+    assert ttt.ttt([1.0], [[0, 5, 5, 5]], 0.5, replicas_per_run=4) == pytest.approx(
+        math.log(0.01) / math.log(0.75 ** 4))
