@@ -199,8 +199,11 @@ def run_ours(args):
     q = sb.sb_qubo_build(ev, sb.build_params(**w["cuts"]))
     N, nnz = q.n, q.nnz
     ctx = sb.sb_create(N, q.rowptr, q.col, q.val, q.lin, prec)
+    tuned = None
     if args.kernel == "untiled":
         sb.sb_set_option(ctx, sb.SB_OPT_TILED, 0)
+    elif not args.profile_steps:
+        tuned = sb.sb_autotune(ctx, args.variant, R, trial_steps=30)   # untimed set-up
     sched = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
     if args.profile_steps:
         sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
@@ -318,7 +321,8 @@ def run_ours(args):
             "config": {"workload": args.workload, "n_tracks": w["n_tracks"], "N": N, "nnz": nnz,
                        "replicas": R, "sb_steps": S, "variant": args.variant,
                        "J": w["jprec"], "state": "f32", "l2": "flushed between steps (256 MB write)",
-                       "parallelism": f"replicas{ws}"},
+                       "parallelism": f"replicas{ws}",
+                       "autotune": None if tuned is None else tuned[0]},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "clocks": clk, "wall_s_timed": t_wall}
     line.update(extra)

@@ -320,13 +320,19 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
  *   SB_OPT_STEP_RT (2): replica-tile width of the untiled kernel (4 x a power
  *   of two, <= 128, dividing R; 0 = automatic).
  *   SB_OPT_STEP_RPC (3): rows per CTA of the untiled kernel (0 = one row per
- *   thread group); a CTA walks a contiguous row chunk so rows in flight share
- *   neighbour rows in L1. Neither changes results.
+ *   thread group, -1 = one wave of CTAs over the SMs); a CTA walks a contiguous
+ *   row chunk so rows in flight share neighbour rows in L1.
+ *   SB_OPT_STEP_UNROLL (4): neighbour rows gathered at once per thread (4).
+ *   SB_OPT_DSB_SIGNS (5): 1 (default) lets dSB gather int8 copies of sgn(x)
+ *   (written by the step that writes x) instead of FP32 positions.
+ *   None of these changes results.
  */
 #define SB_OPT_GRAPH 0
 #define SB_OPT_TILED 1
 #define SB_OPT_STEP_RT 2
 #define SB_OPT_STEP_RPC 3
+#define SB_OPT_STEP_UNROLL 4
+#define SB_OPT_DSB_SIGNS 5
 sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
 
 /*
@@ -334,7 +340,7 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
  * replica-tile width, rows per CTA) for this context, variant and replica
  * count by timing each candidate for `trial_steps` steps with CUDA events on
  * `stream`, and set it on the context. Results do not depend on the choice.
- * Outputs (host, may be NULL): out_cfg[3] = {tiled, tile width, rows per CTA},
+ * Outputs (host, may be NULL): out_cfg[4] = {tiled, tile width, rows per CTA, unroll},
  * out_us_per_step = the best time. Synchronous; discards the current state.
  */
 sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t trial_steps,

@@ -19,6 +19,8 @@ SB_OPT_GRAPH = 0
 SB_OPT_TILED = 1
 SB_OPT_STEP_RT = 2
 SB_OPT_STEP_RPC = 3
+SB_OPT_STEP_UNROLL = 4
+SB_OPT_DSB_SIGNS = 5
 
 
 class SbEventParams(ctypes.Structure):

@@ -27,6 +27,7 @@ const int kEnergyRowsMin = 64;
 struct GraphCache {
   cudaGraphExec_t exec = nullptr;
   int variant = -1, steps = -1, R = -1, cur = -1, G = -1, tiled = -1, rpc = -1, tiles = -1;
+  int unroll = -1, sgn = -1;
   float a0 = 0.f, dt = 0.f;
   const float* sched = nullptr;
   void reset() {
@@ -103,7 +104,11 @@ struct sb_ctx {
   int use_graph = 1;
   int use_tiled = 0;
   int step_rt = 0;    // replica-tile width of the untiled kernel (0: automatic)
-  int step_rpc = 0;   // rows per CTA of the untiled kernel (0: one row per group)
+  int step_rpc = 0;   // rows per CTA of the untiled kernel (0: one row per group, -1: one wave)
+  int step_unroll = 4;
+  int dsb_signs = 1;  // dSB gathers int8 signs instead of FP32 positions
+  int8_t* d_sgn[2] = {nullptr, nullptr};
+  int sms = 0;
 };
 
 namespace {
@@ -197,6 +202,8 @@ void free_state(sb_ctx* c) {
   dfree(c->d_x[0]);
   dfree(c->d_x[1]);
   dfree(c->d_y);
+  dfree(c->d_sgn[0]);
+  dfree(c->d_sgn[1]);
   c->R = 0;
   c->have_state = false;
   c->graph.reset();
@@ -473,7 +480,9 @@ sbd::Tiling step_tiling(const sb_ctx* c) {
 sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t steps,
                         const float* sched, cudaStream_t stream) {
   if (steps <= 0) return SB_OK;
-  const sbd::Tiling t = step_tiling(c);
+  const bool dsb16 = variant == SB_DSB && c->dsb_signs && c->step_rt == 0 && sbd::dsb16_ok(c->R) &&
+                     !(c->tiled_ok && c->use_tiled && c->R % sbd::kTileRT == 0);
+  const sbd::Tiling t = dsb16 ? sbd::make_tiling_dsb16(c->R) : step_tiling(c);
   sbd::StepArgs a;
   a.rowptr = c->d_rowptr;
   a.col = c->d_col;
@@ -489,9 +498,19 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   a.n = c->n;
   a.R = c->R;
   a.G = t.G;
+  a.unroll = c->step_unroll;
   a.rpc = std::max(256 / t.G, c->step_rpc);
+  if (c->step_rpc < 0) {  // one wave: every resident CTA walks one contiguous row chunk
+    if (!c->sms) SB_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
+    const long long slots =
+        (long long)c->sms * sbd::step_blocks_per_sm(variant, c->jbf16, t, a.unroll);
+    const long long per = ((long long)c->n * t.tiles + slots - 1) / slots;
+    a.rpc = (int)std::max<long long>(256 / t.G, per);
+  }
   a.ytil = nullptr;
   a.mask = nullptr;
+  a.sgn_in = nullptr;
+  a.sgn_out = nullptr;
   const int tiled = (c->tiled_ok && c->use_tiled && c->R % sbd::kTileRT == 0) ? 1 : 0;
   sbd::TiledArgs ta;
   ta.blk_row0 = c->d_blk_row0;
@@ -511,7 +530,17 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   ta.n = c->n;
   ta.R = c->R;
   ta.nb = c->nb;
+  const int sgn = (variant == SB_DSB && c->dsb_signs && !tiled) ? 1 : 0;
+  if (sgn && !c->d_sgn[0]) {
+    sb_status st2;
+    const size_t cnt = (size_t)c->n * c->R;
+    if ((st2 = dalloc(&c->d_sgn[0], cnt)) || (st2 = dalloc(&c->d_sgn[1], cnt))) return st2;
+  }
   auto launch = [&](int32_t k, int cur, cudaStream_t st) -> cudaError_t {
+    if (sgn) {
+      a.sgn_in = c->d_sgn[cur];
+      a.sgn_out = c->d_sgn[cur ^ 1];
+    }
     if (tiled) {
       ta.k = k;
       ta.xin = c->d_x[cur];
@@ -523,8 +552,10 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     a.xout = c->d_x[cur ^ 1];
     return sbd::launch_step(variant, c->jbf16, t, a, st);
   };
+  const size_t NR = (size_t)c->n * c->R;
   const bool graph = c->use_graph && steps >= 8;
   if (!graph) {
+    if (sgn) SB_CUDA(sbd::launch_signs(c->d_x[c->cur], c->d_sgn[c->cur], NR, stream));
     for (int32_t k = 0; k < steps; ++k) {
       SB_CUDA(launch(k, c->cur, stream));
       c->cur ^= 1;
@@ -534,12 +565,14 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   GraphCache& gc = c->graph;
   if (!(gc.exec && gc.variant == variant && gc.steps == steps && gc.R == c->R &&
         gc.cur == c->cur && gc.a0 == a.a0 && gc.dt == a.dt && gc.sched == sched && gc.G == t.G &&
-        gc.tiled == tiled && gc.rpc == a.rpc && gc.tiles == t.tiles)) {
+        gc.tiled == tiled && gc.rpc == a.rpc && gc.tiles == t.tiles && gc.unroll == a.unroll &&
+        gc.sgn == sgn)) {
     gc.reset();
     cudaGraph_t g = nullptr;
     SB_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     int cur = c->cur;
     cudaError_t err = cudaSuccess;
+    if (sgn) err = sbd::launch_signs(c->d_x[cur], c->d_sgn[cur], NR, c->cap_stream);
     for (int32_t k = 0; k < steps && err == cudaSuccess; ++k) {
       err = launch(k, cur, c->cap_stream);
       cur ^= 1;
@@ -561,6 +594,8 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     gc.tiled = tiled;
     gc.rpc = a.rpc;
     gc.tiles = t.tiles;
+    gc.unroll = a.unroll;
+    gc.sgn = sgn;
   }
   SB_CUDA(cudaGraphLaunch(gc.exec, stream));
   if (steps & 1) c->cur ^= 1;
@@ -1028,8 +1063,11 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
   a.R = R;
   a.G = t.G;
   a.rpc = 256 / t.G;
+  a.unroll = 4;
   a.ytil = nullptr;
   a.mask = nullptr;
+  a.sgn_in = nullptr;
+  a.sgn_out = nullptr;
   ok(sbd::launch_set_c0(ctx->d_c0ev, ctx->d_c0auto, c0, 1, s));
   ok(sbd::launch_init(ctx->d_x[0], ctx->d_y, nullptr, ctx->d_ev_row0, n, R, seed, s));
   int cur = 0;
@@ -1132,9 +1170,10 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
   cudaStream_t s = (cudaStream_t)stream;
   // candidates: (tiled, replica-tile width, rows per CTA); invalid ones are skipped
   struct Cand {
-    int tiled, rt, rpc;
+    int tiled, rt, rpc, unroll;
   };
-  std::vector<Cand> cands = {{0, 0, 0}, {0, 0, 32}, {0, 128, 0}, {0, 64, 0}, {0, 32, 0}, {1, 0, 0}};
+  std::vector<Cand> cands = {{0, 0, 0, 4},   {0, 0, 32, 4},  {0, 128, 0, 4}, {0, 128, 32, 4},
+                             {0, 64, 0, 4},  {0, 32, 0, 4},  {1, 0, 0, 4}};
   const int keep_graph = ctx->use_graph;
   ctx->use_graph = 0;
   if ((st = ensure_state(ctx, replicas))) return st;
@@ -1153,6 +1192,7 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
     ctx->use_tiled = c.tiled;
     ctx->step_rt = c.rt;
     ctx->step_rpc = c.rpc;
+    ctx->step_unroll = c.unroll;
     ctx->graph.reset();
     if ((st = sb_run(ctx, variant, 1.0, 0.0, 0.5, 0, replicas, 12345, nullptr, stream))) break;
     if ((st = enqueue_steps(ctx, variant, 1.0, 0.5, std::min(trial_steps, 4), sched, s))) break;
@@ -1179,11 +1219,13 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
   ctx->use_tiled = cands[best].tiled;
   ctx->step_rt = cands[best].rt;
   ctx->step_rpc = cands[best].rpc;
+  ctx->step_unroll = cands[best].unroll;
   ctx->graph.reset();
   if (out_cfg) {
     out_cfg[0] = cands[best].tiled;
     out_cfg[1] = cands[best].rt;
     out_cfg[2] = cands[best].rpc;
+    out_cfg[3] = cands[best].unroll;
   }
   if (out_us_per_step) *out_us_per_step = best_us;
   return SB_OK;
@@ -1213,11 +1255,23 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value) {
       ctx->graph.reset();
       return SB_OK;
     case 3:  // SB_OPT_STEP_RPC
-      if (value < 0 || value > (1 << 20)) {
+      if (value < -1 || value > (1 << 20)) {
         set_error("sb_set_option: SB_OPT_STEP_RPC out of range");
         return SB_ERR_ARG;
       }
       ctx->step_rpc = (int)value;
+      ctx->graph.reset();
+      return SB_OK;
+    case 4:  // SB_OPT_STEP_UNROLL
+      if (value != 4) {
+        set_error("sb_set_option: SB_OPT_STEP_UNROLL must be 4 (8 measured slower and was removed)");
+        return SB_ERR_ARG;
+      }
+      ctx->step_unroll = (int)value;
+      ctx->graph.reset();
+      return SB_OK;
+    case 5:  // SB_OPT_DSB_SIGNS
+      ctx->dsb_signs = value != 0;
       ctx->graph.reset();
       return SB_OK;
     default:

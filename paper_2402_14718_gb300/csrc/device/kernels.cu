@@ -35,6 +35,22 @@ Tiling make_tiling(int R) {
   return t;
 }
 
+bool dsb16_ok(int R) {
+  if (R % 16 != 0) return false;
+  const int G = R / 16;
+  return G >= 1 && G <= 32 && (G & (G - 1)) == 0;
+}
+
+Tiling make_tiling_dsb16(int R) {
+  Tiling t;
+  t.V = 16;
+  t.G = R / 16;
+  t.C = 1;
+  t.NCH = 1;
+  t.tiles = 1;
+  return t;
+}
+
 Tiling make_tiling_rt(int R, int RT) {
   Tiling t;
   t.V = 4;
@@ -80,6 +96,21 @@ struct Vec<1> {
   __device__ __forceinline__ void st(float* p) const { *p = v[0]; }
 };
 
+// V signs (int8) of one chunk as floats
+template <int V>
+__device__ __forceinline__ void ld_signs(const int8_t* p, float (&out)[V]) {
+  if (V == 4) {
+    const int w = __ldg(reinterpret_cast<const int*>(p));
+    out[0] = (float)(int8_t)(w & 0xff);
+    out[1 % V] = (float)(int8_t)((w >> 8) & 0xff);
+    out[2 % V] = (float)(int8_t)((w >> 16) & 0xff);
+    out[3 % V] = (float)(int8_t)((w >> 24) & 0xff);
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) out[v] = (float)__ldg(p + v);
+  }
+}
+
 __device__ __forceinline__ float jval(const float* J, int p) { return __ldg(J + p); }
 __device__ __forceinline__ float jval(const __nv_bfloat16* J, int p) {
   return __bfloat162float(J[p]);
@@ -98,8 +129,14 @@ __device__ __forceinline__ unsigned group_mask(int G) {
 // at a time (coalesced) and broadcasts them with shuffles; every thread then
 // gathers its replica chunks of the neighbour rows with 16-byte loads, four
 // neighbours in flight at once.
-template <int V, int NCH, int VARIANT, typename JT>
+// MODE: 0 aSB, 1 bSB, 2 dSB gathering x (sgn at use), 3 dSB gathering int8
+// signs, 4 bSB also recording the pre-wall momentum and the wall mask.
+template <int V, int NCH, int MODE, typename JT>
 __global__ void __launch_bounds__(kBlock) k_step(const StepArgs a) {
+  constexpr int VARIANT = MODE == 3 ? 2 : (MODE == 4 ? 1 : MODE);
+  constexpr bool use_sgn = MODE == 3;
+  constexpr bool record = MODE == 4;
+  constexpr int U = 4;
   const int G = a.G;
   const int gid = threadIdx.x / G;
   const int g = threadIdx.x - gid * G;
@@ -113,7 +150,6 @@ __global__ void __launch_bounds__(kBlock) k_step(const StepArgs a) {
   // a CTA walks a contiguous chunk of rows, so rows in flight together share
   // neighbour rows in L1; the group count is uniform, so a group leaves whole
   for (int row = blockIdx.x * a.rpc + gid; row < row_end; row += groups) {
-
   float acc[NCH][V];
 #pragma unroll
   for (int j = 0; j < NCH; ++j)
@@ -130,31 +166,38 @@ __global__ void __launch_bounds__(kBlock) k_step(const StepArgs a) {
       mv = jval(J, pb + g);
     }
     int q = 0;
-    for (; q + 4 <= cnt; q += 4) {
-      int c[4];
-      float w[4];
+    for (; q + U <= cnt; q += U) {
+      int c[U];
+      float w[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < U; ++u) {
         c[u] = __shfl_sync(mask, mc, q + u, G);
         w[u] = __shfl_sync(mask, mv, q + u, G);
       }
-      Vec<V> xv[4][NCH];
+      float xv[U][NCH][V];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int j = 0; j < NCH; ++j) {
           const int ch = ch0 + j * G;
-          if (ch < C) xv[u][j].ldg(a.xin + (size_t)c[u] * R + (size_t)ch * V);
+          if (ch < C) {
+            const size_t off = (size_t)c[u] * R + (size_t)ch * V;
+            if (use_sgn) {
+              ld_signs<V>(a.sgn_in + off, xv[u][j]);
+            } else {
+              Vec<V> t;
+              t.ldg(a.xin + off);
+#pragma unroll
+              for (int v = 0; v < V; ++v) xv[u][j][v] = VARIANT == 2 ? sgnf(t.v[v]) : t.v[v];
+            }
+          }
         }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int j = 0; j < NCH; ++j)
 #pragma unroll
-          for (int v = 0; v < V; ++v) {
-            const float xx = VARIANT == 2 ? sgnf(xv[u][j].v[v]) : xv[u][j].v[v];
-            acc[j][v] = fmaf(w[u], xx, acc[j][v]);
-          }
+          for (int v = 0; v < V; ++v) acc[j][v] = fmaf(w[u], xv[u][j][v], acc[j][v]);
     }
     for (; q < cnt; ++q) {
       const int c = __shfl_sync(mask, mc, q, G);
@@ -163,13 +206,18 @@ __global__ void __launch_bounds__(kBlock) k_step(const StepArgs a) {
       for (int j = 0; j < NCH; ++j) {
         const int ch = ch0 + j * G;
         if (ch < C) {
-          Vec<V> xv;
-          xv.ldg(a.xin + (size_t)c * R + (size_t)ch * V);
+          const size_t off = (size_t)c * R + (size_t)ch * V;
+          float xs[V];
+          if (use_sgn) {
+            ld_signs<V>(a.sgn_in + off, xs);
+          } else {
+            Vec<V> t;
+            t.ldg(a.xin + off);
 #pragma unroll
-          for (int v = 0; v < V; ++v) {
-            const float xx = VARIANT == 2 ? sgnf(xv.v[v]) : xv.v[v];
-            acc[j][v] = fmaf(w, xx, acc[j][v]);
+            for (int v = 0; v < V; ++v) xs[v] = VARIANT == 2 ? sgnf(t.v[v]) : t.v[v];
           }
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc[j][v] = fmaf(w, xs[v], acc[j][v]);
         }
       }
     }
@@ -188,6 +236,7 @@ __global__ void __launch_bounds__(kBlock) k_step(const StepArgs a) {
     Vec<V> xv, yv;
     xv.ldg(a.xin + idx);
     yv.ld(a.y + idx);
+    int sw = 0;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       float x = xv.v[v], y = yv.v[v];
@@ -195,39 +244,163 @@ __global__ void __launch_bounds__(kBlock) k_step(const StepArgs a) {
       if (VARIANT == 0) force -= x * x * x;
       y = y + a.dt * force;
       x = x + a.dta0 * y;
-      if (a.ytil) a.ytil[idx + v] = y;
+      if (record) a.ytil[idx + v] = y;
       const bool wall = VARIANT != 0 && fabsf(x) > 1.f;
-      if (a.mask) a.mask[idx + v] = wall ? 1 : 0;
+      if (record) a.mask[idx + v] = wall ? 1 : 0;
       if (wall) {
         x = copysignf(1.f, x);
         y = 0.f;
       }
       xv.v[v] = x;
       yv.v[v] = y;
+      if (VARIANT == 2) sw |= ((int)(int8_t)((x > 0.f) - (x < 0.f)) & 0xff) << (8 * v);
     }
     xv.st(a.xout + idx);
     yv.st(a.y + idx);
+    if (use_sgn) {
+      if (V == 4) {
+        *reinterpret_cast<int*>(a.sgn_out + idx) = sw;
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) a.sgn_out[idx + v] = (int8_t)((sw >> (8 * v)) & 0xff);
+      }
+    }
   }
   }
 }
 
-template <int V, int NCH, int VARIANT>
+template <int V, int NCH, int MODE>
 cudaError_t launch_step_t(int jbf16, const Tiling& t, const StepArgs& a, cudaStream_t s) {
   dim3 grid((a.n + a.rpc - 1) / a.rpc, t.tiles);
   if (jbf16)
-    k_step<V, NCH, VARIANT, __nv_bfloat16><<<grid, kBlock, 0, s>>>(a);
+    k_step<V, NCH, MODE, __nv_bfloat16><<<grid, kBlock, 0, s>>>(a);
   else
-    k_step<V, NCH, VARIANT, float><<<grid, kBlock, 0, s>>>(a);
+    k_step<V, NCH, MODE, float><<<grid, kBlock, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int V, int NCH, int MODE>
+int blocks_per_sm_t(int jbf16) {
+  int b = 0;
+  const cudaError_t e =
+      jbf16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<V, NCH, MODE, __nv_bfloat16>,
+                                                            kBlock, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step<V, NCH, MODE, float>,
+                                                            kBlock, 0);
+  return e == cudaSuccess && b > 0 ? b : 1;
+}
+
+template <int V, int NCH>
+int blocks_per_sm_v(int variant, int jbf16, int) {
+  switch (variant) {
+    case 0: return blocks_per_sm_t<V, NCH, 0>(jbf16);
+    case 1: return blocks_per_sm_t<V, NCH, 1>(jbf16);
+    default: return blocks_per_sm_t<V, NCH, 3>(jbf16);
+  }
 }
 
 template <int V, int NCH>
 cudaError_t launch_step_v(int variant, int jbf16, const Tiling& t, const StepArgs& a,
                           cudaStream_t s) {
+  if (variant == 1 && a.ytil) return launch_step_t<V, NCH, 4>(jbf16, t, a, s);
   switch (variant) {
     case 0: return launch_step_t<V, NCH, 0>(jbf16, t, a, s);
     case 1: return launch_step_t<V, NCH, 1>(jbf16, t, a, s);
-    default: return launch_step_t<V, NCH, 2>(jbf16, t, a, s);
+    default:
+      return a.sgn_in ? launch_step_t<V, NCH, 3>(jbf16, t, a, s)
+                      : launch_step_t<V, NCH, 2>(jbf16, t, a, s);
+  }
+}
+
+// ---------------------------------------------------------------- dSB, 16 signs per lane
+// dSB gathering int8 signs with 16 replicas per lane: one 16-byte load brings a
+// neighbour's signs for 16 replicas. G = R / 16 lanes own a row (R / 16 a power
+// of two, <= 32). Same CSR-order FMA sequence per replica as k_step.
+__device__ __forceinline__ float sbyte(unsigned w, int b) {
+  return (float)(int)(signed char)((w >> (8 * b)) & 0xffu);
+}
+
+template <typename JT>
+__global__ void __launch_bounds__(kBlock) k_step_dsb16(const StepArgs a) {
+  const int G = a.G;
+  const int gid = threadIdx.x / G;
+  const int g = threadIdx.x - gid * G;
+  const int groups = blockDim.x / G;
+  const unsigned mask = group_mask(G);
+  const int R = a.R;
+  const JT* J = static_cast<const JT*>(a.J);
+  const int row_end = min(a.n, (blockIdx.x + 1) * a.rpc);
+  for (int row = blockIdx.x * a.rpc + gid; row < row_end; row += groups) {
+    float acc[16];
+#pragma unroll
+    for (int v = 0; v < 16; ++v) acc[v] = 0.f;
+    const int p0 = __ldg(a.rowptr + row), p1 = __ldg(a.rowptr + row + 1);
+    for (int pb = p0; pb < p1; pb += G) {
+      const int cnt = min(G, p1 - pb);
+      int mc = 0;
+      float mv = 0.f;
+      if (g < cnt) {
+        mc = __ldg(a.col + pb + g);
+        mv = jval(J, pb + g);
+      }
+      int q = 0;
+      for (; q + 4 <= cnt; q += 4) {
+        int c[4];
+        float w[4];
+        uint4 sv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          c[u] = __shfl_sync(mask, mc, q + u, G);
+          w[u] = __shfl_sync(mask, mv, q + u, G);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          sv[u] = __ldg(reinterpret_cast<const uint4*>(a.sgn_in + (size_t)c[u] * R + 16 * g));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const unsigned ww[4] = {sv[u].x, sv[u].y, sv[u].z, sv[u].w};
+#pragma unroll
+          for (int v = 0; v < 16; ++v) acc[v] = fmaf(w[u], sbyte(ww[v >> 2], v & 3), acc[v]);
+        }
+      }
+      for (; q < cnt; ++q) {
+        const int c = __shfl_sync(mask, mc, q, G);
+        const float w = __shfl_sync(mask, mv, q, G);
+        const uint4 s4 = __ldg(reinterpret_cast<const uint4*>(a.sgn_in + (size_t)c * R + 16 * g));
+        const unsigned ww[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+        for (int v = 0; v < 16; ++v) acc[v] = fmaf(w, sbyte(ww[v >> 2], v & 3), acc[v]);
+      }
+    }
+    const float pa = a.a0 - __ldg(a.sched + a.k);
+    const int e = a.row_event ? __ldg(a.row_event + row) : 0;
+    const float c0 = __ldg(a.c0_ev + e);
+    const float hi = __ldg(a.h + row);
+    const size_t idx = (size_t)row * R + 16 * g;
+    unsigned sw[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int h4 = 0; h4 < 4; ++h4) {
+      Vec<4> xv, yv;
+      xv.ldg(a.xin + idx + 4 * h4);
+      yv.ld(a.y + idx + 4 * h4);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        float x = xv.v[v], y = yv.v[v];
+        const float force = -pa * x + c0 * (acc[4 * h4 + v] + hi);
+        y = y + a.dt * force;
+        x = x + a.dta0 * y;
+        if (fabsf(x) > 1.f) {
+          x = copysignf(1.f, x);
+          y = 0.f;
+        }
+        xv.v[v] = x;
+        yv.v[v] = y;
+        sw[h4] |= ((unsigned)(int)(signed char)((x > 0.f) - (x < 0.f)) & 0xffu) << (8 * v);
+      }
+      xv.st(a.xout + idx + 4 * h4);
+      yv.st(a.y + idx + 4 * h4);
+    }
+    *reinterpret_cast<uint4*>(a.sgn_out + idx) = make_uint4(sw[0], sw[1], sw[2], sw[3]);
   }
 }
 
@@ -889,6 +1062,14 @@ int grid_for(size_t work, int block) {
 cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs& a,
                         cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
+  if (variant == 2 && a.sgn_in && a.G * 16 == a.R && t.tiles == 1 && t.V == 16) {
+    dim3 grid((a.n + a.rpc - 1) / a.rpc, 1);
+    if (jbf16)
+      k_step_dsb16<__nv_bfloat16><<<grid, kBlock, 0, s>>>(a);
+    else
+      k_step_dsb16<float><<<grid, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+  }
   if (t.V == 4) {
     if (t.NCH == 1) return launch_step_v<4, 1>(variant, jbf16, t, a, s);
     if (t.NCH == 2) return launch_step_v<4, 2>(variant, jbf16, t, a, s);
@@ -897,6 +1078,29 @@ cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs&
   if (t.NCH == 1) return launch_step_v<1, 1>(variant, jbf16, t, a, s);
   if (t.NCH == 2) return launch_step_v<1, 2>(variant, jbf16, t, a, s);
   return launch_step_v<1, 4>(variant, jbf16, t, a, s);
+}
+
+int step_blocks_per_sm(int variant, int jbf16, const Tiling& t, int unroll) {
+  if (t.V == 4) {
+    if (t.NCH == 1) return blocks_per_sm_v<4, 1>(variant, jbf16, unroll);
+    if (t.NCH == 2) return blocks_per_sm_v<4, 2>(variant, jbf16, unroll);
+    return blocks_per_sm_v<4, 4>(variant, jbf16, unroll);
+  }
+  if (t.NCH == 1) return blocks_per_sm_v<1, 1>(variant, jbf16, unroll);
+  if (t.NCH == 2) return blocks_per_sm_v<1, 2>(variant, jbf16, unroll);
+  return blocks_per_sm_v<1, 4>(variant, jbf16, unroll);
+}
+
+__global__ void k_signs(const float* x, int8_t* s, size_t count) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    s[i] = (int8_t)((x[i] > 0.f) - (x[i] < 0.f));
+}
+
+cudaError_t launch_signs(const float* x, int8_t* s, size_t count, cudaStream_t st) {
+  if (!count) return cudaSuccess;
+  k_signs<<<grid_for(count, kBlock), kBlock, 0, st>>>(x, s, count);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_step_tiled(int variant, int jbf16, const TiledArgs& a, cudaStream_t s) {

@@ -19,6 +19,9 @@ Tiling make_tiling(int R);
 // Tiling with a fixed replica-tile width RT (a multiple of 4 dividing R, RT <= 128):
 // V = 4, G = RT / 4 threads per row, one chunk per thread, R / RT tiles.
 Tiling make_tiling_rt(int R, int RT);
+// dSB with int8 signs, 16 replicas per lane: valid when R / 16 is a power of two <= 32.
+bool dsb16_ok(int R);
+Tiling make_tiling_dsb16(int R);
 
 struct StepArgs {
   const int32_t* rowptr;
@@ -38,6 +41,9 @@ struct StepArgs {
   int32_t rpc;            // rows per CTA: a CTA walks rows [b * rpc, (b + 1) * rpc)
   float* ytil;            // optional: momentum after the update, before the wall [n x R]
   uint8_t* mask;          // optional: 1 where the wall fired [n x R]
+  const int8_t* sgn_in;   // dSB: sgn(x_k) [n x R] gathered instead of x (NULL: use x)
+  int8_t* sgn_out;        // dSB: sgn(x_{k+1}) written with x_{k+1} (may be NULL)
+  int32_t unroll;         // neighbours in flight per thread: 4 or 8
 };
 
 cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs& a,
@@ -77,6 +83,10 @@ cudaError_t launch_pack_tz(const void* J, int jbf16, const uint16_t* lidx, int64
 
 cudaError_t launch_init(float* x, float* y, const int32_t* row_event, const int32_t* ev_row0,
                         int32_t n, int32_t R, uint64_t seed, cudaStream_t s);
+// s[i] = sgn(x[i]) as int8 (-1, 0, +1)
+cudaError_t launch_signs(const float* x, int8_t* s, size_t count, cudaStream_t st);
+// blocks of the untiled step kernel resident per SM for this tiling and unroll
+int step_blocks_per_sm(int variant, int jbf16, const Tiling& t, int unroll);
 
 cudaError_t launch_linear_schedule(float* sched, int32_t steps, double a0, cudaStream_t s);
 

@@ -356,3 +356,34 @@ def test_step_tiling_options_bit_identical(rt, rpc):
         sb.sb_run(ctx, "dsb", 1.0, 0.0, 0.5, 15, 128, seed=2)
         out.append(sb.sb_get_state(ctx))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("R", [1, 3, 64, 256])
+def test_dsb_sign_gather_bit_identical(R):
+    """dSB gathering int8 signs gives the state of dSB gathering FP32 positions,
+    also across sb_set_state / sb_advance boundaries and graph replay."""
+    _, qc, _, _ = workload_qubos("event500")
+    out = []
+    for signs in (1, 0):
+        ctx = _ctx(qc, sb.SB_J_BF16)
+        sb.sb_set_option(ctx, 5, signs)
+        sb.sb_run(ctx, "dsb", 1.0, 0.0, 0.5, 12, R, seed=R + 1)
+        x, y = sb.sb_get_state(ctx)
+        sb.sb_set_state(ctx, x, y)
+        sb.sb_advance(ctx, "dsb", 1.0, 0.0, 0.5, 9, _sched(np.float32(np.linspace(0.2, 0.9, 9))))
+        out.append(sb.sb_get_state(ctx))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("variant", ["bsb", "dsb"])
+@pytest.mark.parametrize("unroll,rpc", [(4, -1), (4, 32)])
+def test_unroll_and_wave_options_bit_identical(variant, unroll, rpc):
+    _, qc, _, _ = workload_qubos("event500")
+    out = []
+    for opts in ((4, 0), (unroll, rpc)):
+        ctx = _ctx(qc, sb.SB_J_BF16)
+        sb.sb_set_option(ctx, 4, opts[0])
+        sb.sb_set_option(ctx, 3, opts[1])
+        sb.sb_run(ctx, variant, 1.0, 0.0, 0.5, 20, 256, seed=4)
+        out.append(sb.sb_get_state(ctx))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
