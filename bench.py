@@ -57,6 +57,27 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed(rank, base=1000):
+    """Each rank runs independent replicas: its own Philox seed."""
+    return base * (rank + 1)
+
+
+def reduce_step_ms(ms, world_size, dist=None, device=None):
+    """Max of the per-rank step times (the slowest rank sets the job's time);
+    the only collective, outside the data path."""
+    if world_size <= 1 or dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world_size, ms):
+    """Whole-job spin-updates/s: every rank's units over the slowest rank's time."""
+    return units_per_rank * world_size / (ms * 1e-3)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -217,7 +238,7 @@ def run_ours(args):
     d_br = torch.empty(1, dtype=torch.int32, device=dev)
     d_T = torch.empty(N, dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
-    seed0 = 1000 * (rank + 1)
+    seed0 = rank_seed(rank)
 
     def one_step(seed, ev_marks=None):
         if ev_marks:
@@ -252,13 +273,9 @@ def run_ours(args):
     clk = clocks.stop()
     step_ms = [m[0].elapsed_time(m[3]) for m in marks]
     sweep_ms = [m[1].elapsed_time(m[2]) for m in marks]
-    ms = float(np.sum(step_ms)) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_step_ms(float(np.sum(step_ms)) / args.steps, ws, dist if ws > 1 else None, dev)
     units = N * R * S
-    value = units * ws / (ms * 1e-3)
+    value = job_value(units, ws, ms)
 
     # dominant kernel: the fused SB step (k_step), average launch over the timed region
     kstep_s = float(np.mean(sweep_ms)) * 1e-3 / S
@@ -302,7 +319,8 @@ def run_ours(args):
         e2e_once(100 + i)
     torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": units * ws / e2e_s, "unit": "spin-updates/s", "h2d_bytes_per_step": h2d,
+    e2e_s = reduce_step_ms(e2e_s * 1e3, ws, dist if ws > 1 else None, dev) * 1e-3
+    e2e = {"value": job_value(units, ws, e2e_s * 1e3), "unit": "spin-updates/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s}
 
     extra = {}

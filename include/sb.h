@@ -105,6 +105,13 @@ void sb_event_destroy(sb_event* ev);
  *  weights: b = -1 consistent pair, +w_c conflict (shared hit, same or
  *            adjacent start layer, not consistent), else 0;
  *            a_i = w_q * (|kappa_i|/kappa_max + dtheta_i/dtheta_max) / 2.
+ *  coupling_mode = 1 (paper Eq. 14, 17): consistent pairs carry b = -S_ij,
+ *            S_ij = 1 - (|kappa_i - kappa_j| + max(dtheta_i, dtheta_j)) / 2 (no
+ *            holes), and a quadruplet also needs S_ij > s_min.
+ *  bias_mode = 1 (paper Eq. 15, decaying-exponential reading): quality_i =
+ *            alpha (1 - exp(-|d0|/gamma)) + beta (1 - exp(-|z0|/lambda)), d0 the
+ *            closest approach of the triplet's circle to the beam line, z0 the
+ *            r = 0 intercept of its a-c line in r-z (mm).
  * Triplets are indexed in lexicographic (hit a, hit b, hit c) order.
  */
 typedef struct {
@@ -112,6 +119,10 @@ typedef struct {
   double kappa_max, dtheta_max, dkappa_max;
   double w_q, w_c;
   int32_t five_hit_rule;
+  int32_t coupling_mode;   /* 0: -1 for consistent pairs; 1: -S_ij (Eq. 14) */
+  int32_t bias_mode;       /* 0: curvature/angle quality; 1: Eq. 15 */
+  double s_min;            /* Eq. 17 cut on S_ij (0.2) */
+  double alpha, beta, gamma, lambda;  /* Eq. 15 (0.5, 0.2, 1.0, 0.5) */
 } sb_build_params;
 
 void sb_build_params_default(sb_build_params* p);

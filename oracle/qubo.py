@@ -24,8 +24,16 @@ Steps, in the paper's order:
    cannot both lie on one track), b_ij = 0 otherwise (no shared hit, or only
    the junction hit of (a,b,c),(c,d,e));
    a_i = w_q * quality_i, quality_i = (|kappa_i|/kappa_max +
-   dtheta_i/dtheta_max) / 2 (reading of the bias weight as a triplet quality;
-   the displaced-vertex form of Eq. 15 is a separate builder option).
+   dtheta_i/dtheta_max) / 2 (reading of the bias weight as a triplet quality).
+
+Paper-exact options:
+* coupling_mode = 1: consistent pairs carry b_ij = -S_ij of Eq. 14,
+  S_ij = (1 - (|kappa_i - kappa_j| + max(dtheta_i, dtheta_j)) / 2) / (1 + H_i + H_j)^2
+  (H = 0: no holes are built), and a quadruplet also needs S_ij > s_min (Eq. 17);
+* bias_mode = 1: quality_i follows Eq. 15 read with a decaying exponential,
+  alpha (1 - exp(-|d0|/gamma)) + beta (1 - exp(-|z0|/lambda)), where d0 is the
+  transverse distance of closest approach of the triplet's circle to the beam
+  line and z0 the z of the triplet's r-z line at r = 0.
 
 Triplet index order: lexicographic in (hit a, hit b, hit c).
 Output CSR holds both triangles, ascending columns, no diagonal.
@@ -52,6 +60,13 @@ class BuildParams:
     w_q: float = 1.0               # bias weight scale
     w_c: float = 1.0               # conflict weight scale
     five_hit_rule: bool = True
+    coupling_mode: int = 0         # 0: b = -1 for consistent pairs; 1: b = -S_ij (Eq. 14)
+    bias_mode: int = 0             # 0: curvature/angle quality; 1: Eq. 15 (d0, z0)
+    s_min: float = 0.2             # Eq. 17 cut on S_ij (coupling_mode 1)
+    alpha: float = 0.5             # Eq. 15 parameters
+    beta: float = 0.2
+    gamma: float = 1.0
+    lam: float = 0.5
 
 
 @dataclass
@@ -108,6 +123,29 @@ def curvature(xa, ya, xb, yb, xc, yc):
     return 2.0 * cross / (d1 * d2 * d3)
 
 
+def impact_parameters(xa, ya, za, ra, xb, yb, xc, yc, zc, rc):
+    """(d0, z0) of a triplet: closest approach of the circle through the three
+    transverse points to the origin, and the r = 0 intercept of the a-c line in r-z."""
+    d = 2.0 * (xa * (yb - yc) + xb * (yc - ya) + xc * (ya - yb))
+    z0 = za - ra * (zc - za) / (rc - ra)
+    if d == 0.0:
+        lx = xc - xa
+        ly = yc - ya
+        return abs(xa * yc - xc * ya) / math.sqrt(lx * lx + ly * ly), z0
+    sa = xa * xa + ya * ya
+    sb_ = xb * xb + yb * yb
+    sc = xc * xc + yc * yc
+    ux = (sa * (yb - yc) + sb_ * (yc - ya) + sc * (ya - yb)) / d
+    uy = (sa * (xc - xb) + sb_ * (xa - xc) + sc * (xb - xa)) / d
+    rad = math.sqrt((xa - ux) * (xa - ux) + (ya - uy) * (ya - uy))
+    return abs(math.sqrt(ux * ux + uy * uy) - rad), z0
+
+
+def pair_consistency(t, u):
+    """S_ij of Eq. 14 with no holes: 1 - (|kappa_t - kappa_u| + max(dtheta_t, dtheta_u)) / 2."""
+    return 1.0 - 0.5 * (abs(t[3] - u[3]) + max(t[4], u[4]))
+
+
 def build_triplets(ev, doublets, p: BuildParams):
     """Triplets passing Eq. 16; list of (a, b, c, kappa, dtheta) sorted by (a, b, c)."""
     theta = {}
@@ -156,6 +194,8 @@ def classify_pairs(ev, trip, p: BuildParams):
                 ok = abs(u[3] - t[3]) <= p.dkappa_max
             else:
                 ok = False
+            if ok and p.coupling_mode == 1:
+                ok = pair_consistency(t, u) > p.s_min
             pairs[(i, j)] = CLASS_CONSISTENT if ok else CLASS_CONFLICT
     return pairs
 
@@ -190,7 +230,10 @@ def build_qubo(ev, p: BuildParams = BuildParams()):
     rows = [[] for _ in range(n)]
     for (i, j), c in pairs.items():
         if i in new_index and j in new_index:
-            v = -1.0 if c == CLASS_CONSISTENT else p.w_c
+            if c == CLASS_CONSISTENT:
+                v = -pair_consistency(trip[i], trip[j]) if p.coupling_mode == 1 else -1.0
+            else:
+                v = p.w_c
             rows[new_index[i]].append((new_index[j], v, c))
     rowptr = np.zeros(n + 1, dtype=np.int32)
     col, val, cls = [], [], []
@@ -208,7 +251,13 @@ def build_qubo(ev, p: BuildParams = BuildParams()):
     tri = np.zeros((n, 3), dtype=np.int32)
     for k, old in enumerate(keep):
         a, b, c, kk, dd = trip[old]
-        quality[k] = 0.5 * (abs(kk) / p.kappa_max + dd / p.dtheta_max)
+        if p.bias_mode == 1:
+            d0, z0 = impact_parameters(ev.x[a], ev.y[a], ev.z[a], ev.r[a], ev.x[b], ev.y[b],
+                                       ev.x[c], ev.y[c], ev.z[c], ev.r[c])
+            quality[k] = (p.alpha * (1.0 - math.exp(-abs(d0) / p.gamma)) +
+                          p.beta * (1.0 - math.exp(-abs(z0) / p.lam)))
+        else:
+            quality[k] = 0.5 * (abs(kk) / p.kappa_max + dd / p.dtheta_max)
         lin[k] = p.w_q * quality[k]
         kap[k] = kk
         dth[k] = dd

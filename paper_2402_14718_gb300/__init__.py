@@ -78,7 +78,7 @@ def build_params(**kw):
     p = _lib.SbBuildParams()
     lib.sb_build_params_default(ctypes.byref(p))
     for k, v in kw.items():
-        setattr(p, k, int(v) if k == "five_hit_rule" else v)
+        setattr(p, k, int(v) if k in ("five_hit_rule", "coupling_mode", "bias_mode") else v)
     return p
 
 

@@ -33,7 +33,10 @@ class SbEventParams(ctypes.Structure):
 class SbBuildParams(ctypes.Structure):
     _fields_ = [("dphi_slope", c_double), ("dphi_margin", c_double), ("z0_max", c_double),
                 ("kappa_max", c_double), ("dtheta_max", c_double), ("dkappa_max", c_double),
-                ("w_q", c_double), ("w_c", c_double), ("five_hit_rule", c_int32)]
+                ("w_q", c_double), ("w_c", c_double), ("five_hit_rule", c_int32),
+                ("coupling_mode", c_int32), ("bias_mode", c_int32), ("s_min", c_double),
+                ("alpha", c_double), ("beta", c_double), ("gamma", c_double),
+                ("lam", c_double)]
 
 
 class SbError(RuntimeError):

@@ -27,6 +27,11 @@ struct Triplet {
   double kappa, dtheta;
 };
 
+// S_ij of Eq. 14 without holes
+double pair_consistency(const Triplet& t, const Triplet& u) {
+  return 1.0 - 0.5 * (fabs(t.kappa - u.kappa) + std::max(t.dtheta, u.dtheta));
+}
+
 // Signed curvature of the circle through three transverse points:
 // 2 * cross(b - a, c - b) / (|b - a| |c - b| |c - a|); > 0 counter-clockwise.
 double curvature(double xa, double ya, double xb, double yb, double xc, double yc) {
@@ -41,6 +46,27 @@ double curvature(double xa, double ya, double xb, double yb, double xc, double y
   double d2 = sqrt(dx2 * dx2 + dy2 * dy2);
   double d3 = sqrt(dx3 * dx3 + dy3 * dy3);
   return 2.0 * cross / (d1 * d2 * d3);
+}
+
+// (d0, z0) of a triplet: closest approach of the circle through the three
+// transverse points to the origin, and the r = 0 intercept of the a-c line in r-z.
+void impact_parameters(double xa, double ya, double za, double ra, double xb, double yb,
+                       double xc, double yc, double zc, double rc, double* d0, double* z0) {
+  double d = 2.0 * (xa * (yb - yc) + xb * (yc - ya) + xc * (ya - yb));
+  *z0 = za - ra * (zc - za) / (rc - ra);
+  if (d == 0.0) {
+    double lx = xc - xa;
+    double ly = yc - ya;
+    *d0 = fabs(xa * yc - xc * ya) / sqrt(lx * lx + ly * ly);
+    return;
+  }
+  double sa = xa * xa + ya * ya;
+  double sb = xb * xb + yb * yb;
+  double sc = xc * xc + yc * yc;
+  double ux = (sa * (yb - yc) + sb * (yc - ya) + sc * (ya - yb)) / d;
+  double uy = (sa * (xc - xb) + sb * (xa - xc) + sc * (xb - xa)) / d;
+  double rad = sqrt((xa - ux) * (xa - ux) + (ya - uy) * (ya - uy));
+  *d0 = fabs(sqrt(ux * ux + uy * uy) - rad);
 }
 
 enum : int8_t { kConsistent = 0, kConflict = 1 };
@@ -58,11 +84,23 @@ extern "C" void sb_build_params_default(sb_build_params* p) {
   p->w_q = 1.0;
   p->w_c = 1.0;
   p->five_hit_rule = 1;
+  p->coupling_mode = 0;
+  p->bias_mode = 0;
+  p->s_min = 0.2;
+  p->alpha = 0.5;
+  p->beta = 0.2;
+  p->gamma = 1.0;
+  p->lambda = 0.5;
 }
 
 extern "C" sb_status sb_qubo_build(const sb_event* ev, const sb_build_params* p, sb_qubo** out) {
   if (!ev || !p || !out) {
     sbh::set_error("sb_qubo_build: null argument");
+    return SB_ERR_ARG;
+  }
+  if ((p->coupling_mode != 0 && p->coupling_mode != 1) || (p->bias_mode != 0 && p->bias_mode != 1) ||
+      (p->bias_mode == 1 && !(p->gamma > 0.0 && p->lambda > 0.0))) {
+    sbh::set_error("sb_qubo_build: coupling_mode / bias_mode must be 0 or 1, gamma and lambda > 0");
     return SB_ERR_ARG;
   }
   *out = nullptr;
@@ -150,6 +188,7 @@ extern "C" sb_status sb_qubo_build(const sb_event* ev, const sb_build_params* p,
         ok = fabs(u.kappa - t.kappa) <= p->dkappa_max;
       else
         ok = false;
+      if (ok && p->coupling_mode == 1) ok = pair_consistency(t, u) > p->s_min;
       pairs.push_back(Pair{i, j, ok ? kConsistent : kConflict});
     }
   }
@@ -178,7 +217,10 @@ extern "C" sb_status sb_qubo_build(const sb_event* ev, const sb_build_params* p,
     const int32_t ni = new_index[pr.i], nj = new_index[pr.j];
     if (ni < 0 || nj < 0) continue;
     q->col.push_back(nj);
-    q->val.push_back(pr.cls == kConsistent ? -1.0 : p->w_c);
+    double v = p->w_c;
+    if (pr.cls == kConsistent)
+      v = p->coupling_mode == 1 ? -pair_consistency(trip[pr.i], trip[pr.j]) : -1.0;
+    q->val.push_back(v);
     q->cls.push_back(pr.cls);
     q->rowptr[ni + 1]++;
   }
@@ -192,7 +234,15 @@ extern "C" sb_status sb_qubo_build(const sb_event* ev, const sb_build_params* p,
     const int32_t k = new_index[i];
     if (k < 0) continue;
     const Triplet& t = trip[i];
-    q->quality[k] = 0.5 * (fabs(t.kappa) / p->kappa_max + t.dtheta / p->dtheta_max);
+    if (p->bias_mode == 1) {
+      double d0, z0;
+      impact_parameters(ev->x[t.a], ev->y[t.a], ev->z[t.a], ev->r[t.a], ev->x[t.b], ev->y[t.b],
+                        ev->x[t.c], ev->y[t.c], ev->z[t.c], ev->r[t.c], &d0, &z0);
+      q->quality[k] = p->alpha * (1.0 - exp(-fabs(d0) / p->gamma)) +
+                      p->beta * (1.0 - exp(-fabs(z0) / p->lambda));
+    } else {
+      q->quality[k] = 0.5 * (fabs(t.kappa) / p->kappa_max + t.dtheta / p->dtheta_max);
+    }
     q->lin[k] = p->w_q * q->quality[k];
     q->kappa[k] = t.kappa;
     q->dtheta[k] = t.dtheta;

@@ -387,3 +387,39 @@ def test_unroll_and_wave_options_bit_identical(variant, unroll, rpc):
         sb.sb_run(ctx, variant, 1.0, 0.0, 0.5, 20, 256, seed=4)
         out.append(sb.sb_get_state(ctx))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+# ------------------------------------------------------------------ paper-exact weights (Eq. 14, 15)
+def _paper_qubos():
+    from paper_2402_14718_gb300.workloads import CUTS_S8
+    from oracle import events as oev, qubo as oq
+    kw = dict(CUTS_S8, coupling_mode=1, bias_mode=1)
+    ev_c = sb.sb_event_generate(0, sb.event_params(n_tracks=100))
+    qc = sb.sb_qubo_build(ev_c, sb.build_params(**kw))
+    kw["five_hit_rule"] = True
+    qo = oq.build_qubo(oev.generate(0, oev.EventParams(n_tracks=100)), oq.BuildParams(**kw))
+    return qc, qo
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("prec", [sb.SB_J_FP32, sb.SB_J_BF16])
+def test_paper_weights_one_step(variant, prec):
+    qc, qo = _paper_qubos()
+    _one_step_case(qc, qo, prec, variant, 32, seed=13 + variant, a_k=0.45, scale=0.9)
+
+
+def test_paper_weights_bf16_quantisation_effect():
+    """-S_ij / 4 is not exact in BF16 (8 significant bits): the J error is at
+    most 2^-9 relative, and over a full 2000-step bSB run the median final
+    energy of 64 replicas moves by less than 0.5 %."""
+    qc, _ = _paper_qubos()
+    J = -qc.val / 4.0
+    Jb = _bf16_round(J)
+    rel = np.max(np.abs(Jb - J) / np.abs(J))
+    assert 0.0 < rel <= 2.0 ** -9
+    med = []
+    for prec in (sb.SB_J_FP32, sb.SB_J_BF16):
+        ctx = _ctx(qc, prec)
+        sb.sb_run(ctx, "bsb", 1.0, 0.0, 0.5, 2000, 64, seed=77)
+        med.append(float(np.median(sb.sb_energy(ctx, None, 64)[0])))
+    assert abs(med[1] - med[0]) <= 0.005 * abs(med[0])

@@ -83,3 +83,16 @@ def test_tracks_and_scores_bit_exact(frac):
         assert rc["tracks"] == tr
         assert (rc["tp"], rc["fp"], rc["fn"]) == (tp, fp, fn)
         assert rc["efficiency"] == eff and rc["purity"] == pur
+
+
+@pytest.mark.parametrize("cm,bm", [(1, 0), (0, 1), (1, 1)])
+def test_paper_weights_bit_exact(cm, bm):
+    ev_c, ev_o = _both_events(0, 100, 0.1)
+    kw = dict(CUTS_S8, coupling_mode=cm, bias_mode=bm)
+    qc = sb.sb_qubo_build(ev_c, sb.build_params(**kw))
+    kw["five_hit_rule"] = True
+    qo = oq.build_qubo(ev_o, oq.BuildParams(**kw))
+    _cmp_qubo(qc, qo)
+    if cm:
+        cons = qc.val[qc.cls == 0]
+        assert np.all((cons < -0.2) & (cons >= -1.0)) and len(np.unique(cons)) > 10

@@ -463,3 +463,46 @@ def test_ttt_closed_forms():
     assert ttt.p_batch(0.5, 3) == pytest.approx(0.875)
     assert ttt.ttt([1.0], [[0, 5, 5, 5]], 0.5, replicas_per_run=4) == pytest.approx(
         math.log(0.01) / math.log(0.75 ** 4))
+
+
+# ---------------------------------------------------------------- paper-exact weights
+def test_impact_parameters_closed_forms():
+    """Points on a circle of radius R centred at (X, 0): closest approach to the
+    origin |X - R|; a straight r-z line through (r, z) pairs meets r = 0 at its
+    intercept; collinear transverse points fall back to the point-line distance."""
+    R, X = 800.0, 803.25
+    pts = [(X + R * math.cos(t), R * math.sin(t)) for t in (2.9, 3.0, 3.1)]
+    zs = [(r, 2.5 + 0.75 * r) for r in (32.0, 72.0, 116.0)]
+    d0, z0 = qubo.impact_parameters(pts[0][0], pts[0][1], zs[0][1], zs[0][0], pts[1][0], pts[1][1],
+                                    pts[2][0], pts[2][1], zs[2][1], zs[2][0])
+    assert d0 == pytest.approx(abs(X - R), abs=1e-9)
+    assert z0 == pytest.approx(2.5, abs=1e-12)
+    d0, _ = qubo.impact_parameters(1.0, 3.0, 0.0, 1.0, 2.0, 3.0, 5.0, 3.0, 1.0, 2.0)
+    assert d0 == pytest.approx(3.0, abs=1e-15)
+
+
+def test_pair_consistency_matches_eq14_by_hand():
+    t = (0, 1, 2, 2.0e-4, 0.03)
+    u = (1, 2, 3, 1.5e-4, 0.01)
+    assert qubo.pair_consistency(t, u) == pytest.approx(1.0 - 0.5 * (5e-5 + 0.03), abs=1e-15)
+
+
+def test_paper_weights_on_clean_tracks():
+    """Clean isolated tracks from the origin: consistent couplings are -S_ij
+    (close to -1, inside (-1, -1 + dtheta_max/2]); the Eq. 15 bias sits near its
+    z0 term, d0 being ~0 for tracks from the beam line."""
+    seed, ev = _separated_seed(4, 0.6)
+    p = qubo.BuildParams(dphi_slope=1.5e-3, dphi_margin=1.0, z0_max=100, kappa_max=2e-3,
+                         dtheta_max=0.2, dkappa_max=5e-4, coupling_mode=1, bias_mode=1)
+    q = qubo.build_qubo(ev, p)
+    assert q.n == 32
+    assert np.all((q.val < -0.9) & (q.val >= -1.0))
+    for i in range(q.n):
+        a, _, c = q.trip[i]
+        qq, pt, eta, phi0, z0, rc = ev.truth[ev.particle[a]]
+        # the straight r-z line through the truth helix at r_a and r_c, read at r = 0
+        za = z0 + math.sinh(eta) * 2 * rc * math.asin(ev.r[a] / (2 * rc))
+        zc = z0 + math.sinh(eta) * 2 * rc * math.asin(ev.r[c] / (2 * rc))
+        z_line = za - ev.r[a] * (zc - za) / (ev.r[c] - ev.r[a])
+        expect = 0.2 * (1.0 - math.exp(-abs(z_line) / 0.5))   # d0 = 0 for tracks from the origin
+        assert q.quality[i] == pytest.approx(expect, abs=1e-6)
