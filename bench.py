@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttt", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--study", default="", choices=["", "paper-sizes", "c0-scan", "schedule"],
+                    help="experiments (not bench lines): energy traces and 50-shot statistics "
+                         "at the paper's QUBO sizes, the c0 scan, schedule learning by the adjoint")
     ap.add_argument("--kernel", default="auto", choices=["auto", "untiled"],
                     help="step kernel: auto (row-block tiled when R %% 32 == 0) or untiled")
     ap.add_argument("--profile-steps", type=int, default=0,
@@ -438,6 +441,17 @@ def time_to_target(sb, ctx, q, ev, w, variant, stream, sched, dev, plain_runs=16
     plain_ok = float(np.mean([v <= target for v in plain_E]))
     times_plain = [t_plain_run * min(S, (k + 1) * every) / S for k in range(len(times))]
     ttt_p, kp = _ttt_from(times_plain, p_reps, 1)
+    # the library's own form at one replica: BF16 J, graph replay
+    sb.sb_run(ctx, variant, a0, 0.0, dt, S, 1, 1, None, stream)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for i in range(4):
+        sb.sb_run(ctx, variant, a0, 0.0, dt, S, 1, 100 + i, None, stream)
+        sb.sb_readout_device(ctx, d_E[:1], None, None, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_r1 = e0.elapsed_time(e1) * 1e-3 / 4
+    ttt_1, k1 = _ttt_from([t_r1 * min(S, (k + 1) * every) / S for k in range(len(times))], p_reps, 1)
     return {"target": target, "E_best": e_best, "E_reference_run": e_ref, "E_truth": E_truth,
             "gap_to_truth": (e_best - E_truth) / abs(E_truth),
             "E_final_best": float(E_b[0]), "checkpoint_every": every,
@@ -448,7 +462,10 @@ def time_to_target(sb, ctx, q, ev, w, variant, stream, sched, dev, plain_runs=16
                            "run_seconds": t_plain_run, "replicas_per_run": 1,
                            "runs_timed": plain_runs, "plain_runs_at_target": plain_ok,
                            "spin_updates_per_s": q.n * S / t_plain_run},
+            "bf16_graph_r1": {"seconds": ttt_1, "run_seconds": t_r1, "replicas_per_run": 1},
             "speedup_batched_vs_plain": (ttt_p / ttt_b) if (ttt_b and ttt_p) else None,
+            "speedup_best_vs_plain": (ttt_p / min(v for v in (ttt_b, ttt_1) if v))
+            if (ttt_p and (ttt_b or ttt_1)) else None,
             "efficiency": sc["efficiency"], "purity": sc["purity"],
             "note": "batched: one run of R replicas with a readout every 50 steps (timed)"}
 
@@ -558,8 +575,113 @@ def run_batch(args):
     return 0
 
 
+def _qubo_energy_trace(sb, ctx, variant, a0, c0, dt, S, R, seed, every, stream, dev):
+    """Energies of all R shots every `every` steps and the time to each checkpoint."""
+    import torch
+    sched = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
+    d_E = torch.empty(R, dtype=torch.float64, device=dev)
+    sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
+    sb.sb_run(ctx, variant, a0, c0, dt, 0, R, seed, None, stream)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    marks, Es = [], []
+    for k0 in range(0, S, every):
+        n = min(every, S - k0)
+        sb.sb_advance(ctx, variant, a0, c0, dt, n, sched[k0:k0 + n], stream)
+        sb.sb_readout_device(ctx, d_E, None, None, None, stream)
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        marks.append(e)
+        Es.append(d_E.clone())
+    torch.cuda.synchronize(dev)
+    return [t0.elapsed_time(m) * 1e-3 for m in marks], [e.cpu().numpy() for e in Es]
+
+
+def run_study(args):
+    import torch
+    import paper_2402_14718_gb300 as sb
+    from paper_2402_14718_gb300.workloads import CUTS_DENSE, PAPER_SIZES, WORKLOADS
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream(dev)
+    if args.study == "paper-sizes":
+        # section "Results": a0 = dt = 1, fixed c0, 50 shots; bSB and dSB
+        S, R, every = (args.sb_steps or 2000), 50, 20
+        for p in PAPER_SIZES:
+            ev = sb.sb_event_generate(p["seed"], sb.event_params(n_tracks=p["n_tracks"]))
+            q = sb.sb_qubo_build(ev, sb.build_params(**CUTS_DENSE))
+            ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_BF16)
+            off = sb.sb_info(ctx)["offset"]
+            for variant in ("bsb", "dsb"):
+                times, Es = _qubo_energy_trace(sb, ctx, variant, 1.0, 0.0, 1.0, S, R, 1, every,
+                                               stream, dev)
+                fin = Es[-1]
+                T, Eb, _ = sb.sb_best(ctx)
+                sc = sb.sb_tracks(ev, q, T)
+                pick = [int(v) for v in np.linspace(0, len(Es) - 1, 12)]
+                print(json.dumps({
+                    "study": "paper-sizes", "paper_N": p["paper_N"], "N": q.n, "nnz": q.nnz,
+                    "tracks": p["n_tracks"], "variant": variant, "shots": R, "steps": S,
+                    "a0": 1.0, "dt": 1.0, "c0": "auto",
+                    "final_ising_min": float(fin.min() - off), "final_ising_mean": float(fin.mean() - off),
+                    "final_ising_std": float(fin.std()), "final_ising_max": float(fin.max() - off),
+                    "run_seconds": times[-1],
+                    "trace": [{"t": times[i], "step": int((i + 1) * every), "mean": float(Es[i].mean() - off),
+                               "min": float(Es[i].min() - off), "max": float(Es[i].max() - off)}
+                              for i in pick],
+                    "efficiency": sc["efficiency"], "purity": sc["purity"]}), flush=True)
+        return 0
+    if args.study == "c0-scan":
+        # section "Results": fixed c0 versus a scan
+        w = WORKLOADS["event1000"]
+        ev = sb.sb_event_generate(w["seed"], sb.event_params(n_tracks=w["n_tracks"],
+                                                             noise_frac=w["noise_frac"]))
+        q = sb.sb_qubo_build(ev, sb.build_params(**w["cuts"]))
+        ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_BF16)
+        c0a = sb.sb_info(ctx)["c0_auto"]
+        S, R = 2000, 64
+        for f in (0.25, 0.5, 1.0, 2.0, 4.0):
+            sb.sb_run(ctx, "bsb", 1.0, c0a * f, 0.5, S, R, 3, None, stream)
+            E = sb.sb_energy(ctx, None, R)[0]
+            T, _, _ = sb.sb_best(ctx)
+            sc = sb.sb_tracks(ev, q, T)
+            print(json.dumps({"study": "c0-scan", "c0": c0a * f, "c0_over_auto": f,
+                              "median_E": float(np.median(E)), "min_E": float(E.min()),
+                              "efficiency": sc["efficiency"], "purity": sc["purity"]}), flush=True)
+        return 0
+    if args.study == "schedule":
+        # a(t) learned by gradient descent on the mean relaxed energy (sb_backward)
+        w = WORKLOADS["event500"]
+        ev = sb.sb_event_generate(w["seed"], sb.event_params(n_tracks=w["n_tracks"],
+                                                             noise_frac=w["noise_frac"]))
+        q = sb.sb_qubo_build(ev, sb.build_params(**w["cuts"]))
+        ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_FP32)
+        sb.sb_set_weights(ctx, q.cls, q.quality, 1.0, 1.0)
+        # the relaxed energy at the last step is piecewise constant in a(t) once every
+        # spin sits on a wall (long bSB runs): learn on a horizon that ends mid-bifurcation
+        S, R, c0 = (args.sb_steps or 60), w["replicas"], sb.sb_info(ctx)["c0_auto"]
+        a = torch.tensor(np.array([0.5 * k / (S - 1) for k in range(S)], np.float32), device=dev)
+        g = torch.zeros(S, dtype=torch.float64, device=dev)
+        for it in range(args.steps):
+            loss, grads = sb.sb_backward(ctx, 1.0, c0, 0.5, S, R, 11, a, 32, g)
+            sb.sb_run(ctx, "bsb", 1.0, c0, 0.5, S, R, 11, a, stream)
+            E = sb.sb_energy(ctx, None, R)[0]
+            x, _ = sb.sb_get_state(ctx)
+            print(json.dumps({"study": "schedule", "iter": it, "steps": S, "relaxed_loss": loss,
+                              "fraction_on_walls": float(np.mean(np.abs(x) == 1.0)),
+                              "median_qubo_E": float(np.median(E)), "min_qubo_E": float(E.min()),
+                              "grad_inf": float(g.abs().max()), "dL_ddt": grads["dt"],
+                              "dL_dc0": grads["c0"]}), flush=True)
+            step = 0.05 * g / max(float(g.abs().max()), 1e-30)
+            a = torch.clamp(a - step.to(torch.float32), 0.0, 1.0).contiguous()
+        return 0
+    return 0
+
+
 def main():
     args = parse()
+    if args.study:
+        return run_study(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch512":

@@ -60,3 +60,14 @@ def batch512_tracks():
     u = rng.uniform(math.log(BATCH512["tracks_min"]), math.log(BATCH512["tracks_max"]),
                     BATCH512["n_events"])
     return [int(v) for v in np.round(np.exp(u))]
+
+
+# Events whose QUBO sizes match the four examples of the paper's Fig. 2 / Fig. 4
+# (778, 10,295, 67,570, 109,498 triplets): every synthetic track crosses all ten
+# layers, so the sizes are matched by track count under the dense-event cuts.
+PAPER_SIZES = [
+    dict(paper_N=778, n_tracks=95, seed=5095),
+    dict(paper_N=10295, n_tracks=1064, seed=6064),
+    dict(paper_N=67570, n_tracks=4133, seed=9133),
+    dict(paper_N=109498, n_tracks=5406, seed=10406),
+]

@@ -409,14 +409,14 @@ def test_paper_weights_one_step(variant, prec):
 
 
 def test_paper_weights_bf16_quantisation_effect():
-    """-S_ij / 4 is not exact in BF16 (8 significant bits): the J error is at
-    most 2^-9 relative, and over a full 2000-step bSB run the median final
-    energy of 64 replicas moves by less than 0.5 %."""
+    """-S_ij / 4 is not exact in BF16 (8 significant bits, round to nearest): the
+    J error is at most 2^-8 relative, and over a full 2000-step bSB run the
+    median final energy of 64 replicas moves by less than 0.5 %."""
     qc, _ = _paper_qubos()
     J = -qc.val / 4.0
     Jb = _bf16_round(J)
     rel = np.max(np.abs(Jb - J) / np.abs(J))
-    assert 0.0 < rel <= 2.0 ** -9
+    assert 0.0 < rel <= 2.0 ** -8
     med = []
     for prec in (sb.SB_J_FP32, sb.SB_J_BF16):
         ctx = _ctx(qc, prec)
