@@ -530,7 +530,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   ta.n = c->n;
   ta.R = c->R;
   ta.nb = c->nb;
-  const int sgn = (variant == SB_DSB && c->dsb_signs && !tiled) ? 1 : 0;
+  const int sgn = (variant == SB_DSB && c->dsb_signs && !tiled && c->R % 4 == 0) ? 1 : 0;
   if (sgn && !c->d_sgn[0]) {
     sb_status st2;
     const size_t cnt = (size_t)c->n * c->R;

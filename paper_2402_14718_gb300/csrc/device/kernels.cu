@@ -312,6 +312,56 @@ cudaError_t launch_step_v(int variant, int jbf16, const Tiling& t, const StepArg
   }
 }
 
+// ---------------------------------------------------------------- one replica
+// R = 1: one thread per row; eight (col, J) pairs and eight neighbour values
+// are loaded before the FMAs, so a row's gathers overlap instead of forming a
+// chain of dependent L2 round trips. Same CSR-order FMA sequence as k_step.
+template <int MODE, typename JT>
+__global__ void __launch_bounds__(kBlock) k_step_r1(const StepArgs a) {
+  constexpr int VARIANT = MODE == 4 ? 1 : MODE;
+  constexpr bool record = MODE == 4;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= a.n) return;
+  const JT* J = static_cast<const JT*>(a.J);
+  const int p0 = __ldg(a.rowptr + row), p1 = __ldg(a.rowptr + row + 1);
+  float acc = 0.f;
+  int p = p0;
+  for (; p + 8 <= p1; p += 8) {
+    int c[8];
+    float w[8], xv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      c[u] = __ldg(a.col + p + u);
+      w[u] = jval(J, p + u);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) xv[u] = __ldg(a.xin + c[u]);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc = fmaf(w[u], VARIANT == 2 ? sgnf(xv[u]) : xv[u], acc);
+  }
+  for (; p < p1; ++p) {
+    const float xv = __ldg(a.xin + __ldg(a.col + p));
+    acc = fmaf(jval(J, p), VARIANT == 2 ? sgnf(xv) : xv, acc);
+  }
+  const float pa = a.a0 - __ldg(a.sched + a.k);
+  const int e = a.row_event ? __ldg(a.row_event + row) : 0;
+  const float c0 = __ldg(a.c0_ev + e);
+  float x = __ldg(a.xin + row), y = a.y[row];
+  float force = -pa * x + c0 * (acc + __ldg(a.h + row));
+  if (VARIANT == 0) force -= x * x * x;
+  y = y + a.dt * force;
+  x = x + a.dta0 * y;
+  if (record) a.ytil[row] = y;
+  const bool wall = VARIANT != 0 && fabsf(x) > 1.f;
+  if (record) a.mask[row] = wall ? 1 : 0;
+  if (wall) {
+    x = copysignf(1.f, x);
+    y = 0.f;
+  }
+  a.xout[row] = x;
+  a.y[row] = y;
+}
+
 // ---------------------------------------------------------------- dSB, 16 signs per lane
 // dSB gathering int8 signs with 16 replicas per lane: one 16-byte load brings a
 // neighbour's signs for 16 replicas. G = R / 16 lanes own a row (R / 16 a power
@@ -1062,6 +1112,21 @@ int grid_for(size_t work, int block) {
 cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs& a,
                         cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
+  if (a.R == 1 && !a.sgn_in && a.rpc == 256 / t.G) {
+    const int grid = (a.n + kBlock - 1) / kBlock;
+    const int mode = (variant == 1 && a.ytil) ? 4 : variant;
+#define SB_R1(M)                                                        \
+  (jbf16 ? (k_step_r1<M, __nv_bfloat16><<<grid, kBlock, 0, s>>>(a), 0) \
+         : (k_step_r1<M, float><<<grid, kBlock, 0, s>>>(a), 0))
+    switch (mode) {
+      case 0: SB_R1(0); break;
+      case 1: SB_R1(1); break;
+      case 2: SB_R1(2); break;
+      default: SB_R1(4); break;
+    }
+#undef SB_R1
+    return cudaGetLastError();
+  }
   if (variant == 2 && a.sgn_in && a.G * 16 == a.R && t.tiles == 1 && t.V == 16) {
     dim3 grid((a.n + a.rpc - 1) / a.rpc, 1);
     if (jbf16)

@@ -423,3 +423,19 @@ def test_paper_weights_bf16_quantisation_effect():
         sb.sb_run(ctx, "bsb", 1.0, 0.0, 0.5, 2000, 64, seed=77)
         med.append(float(np.median(sb.sb_energy(ctx, None, 64)[0])))
     assert abs(med[1] - med[0]) <= 0.005 * abs(med[0])
+
+
+
+@pytest.mark.parametrize("variant", ["asb", "bsb", "dsb"])
+def test_single_replica_kernel_bit_identical(variant):
+    """R = 1 runs on a dedicated one-thread-per-row kernel; forcing the generic
+    kernel (rows-per-CTA override) gives the same state bit for bit."""
+    _, qc, _, _ = workload_qubos("event500")
+    dt = 0.1 if variant == "asb" else 0.5
+    out = []
+    for rpc in (0, 300):
+        ctx = _ctx(qc)
+        sb.sb_set_option(ctx, 3, rpc)
+        sb.sb_run(ctx, variant, 1.0, 0.0, dt, 40, 1, seed=9)
+        out.append(sb.sb_get_state(ctx))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
