@@ -336,6 +336,9 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
  *   SB_OPT_STEP_UNROLL (4): neighbour rows gathered at once per thread (4).
  *   SB_OPT_DSB_SIGNS (5): 1 (default) lets dSB gather int8 copies of sgn(x)
  *   (written by the step that writes x) instead of FP32 positions.
+ *   SB_OPT_REPLICA_GROUPS (6): run the replicas as this many groups one after
+ *   another, each for all steps (R / groups replicas per group, a multiple of 4
+ *   with R / (4 groups) a power of two <= 32), so a group's state stays in L2.
  *   None of these changes results.
  */
 #define SB_OPT_GRAPH 0
@@ -344,6 +347,7 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
 #define SB_OPT_STEP_RPC 3
 #define SB_OPT_STEP_UNROLL 4
 #define SB_OPT_DSB_SIGNS 5
+#define SB_OPT_REPLICA_GROUPS 6
 sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
 
 /*
@@ -351,7 +355,8 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
  * replica-tile width, rows per CTA) for this context, variant and replica
  * count by timing each candidate for `trial_steps` steps with CUDA events on
  * `stream`, and set it on the context. Results do not depend on the choice.
- * Outputs (host, may be NULL): out_cfg[4] = {tiled, tile width, rows per CTA, unroll},
+ * Outputs (host, may be NULL): out_cfg[5] = {tiled, tile width, rows per CTA, unroll,
+ * replica groups},
  * out_us_per_step = the best time. Synchronous; discards the current state.
  */
 sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t trial_steps,

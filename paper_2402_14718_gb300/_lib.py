@@ -21,6 +21,7 @@ SB_OPT_STEP_RT = 2
 SB_OPT_STEP_RPC = 3
 SB_OPT_STEP_UNROLL = 4
 SB_OPT_DSB_SIGNS = 5
+SB_OPT_REPLICA_GROUPS = 6
 
 
 class SbEventParams(ctypes.Structure):

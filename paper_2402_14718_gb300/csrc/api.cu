@@ -27,7 +27,7 @@ const int kEnergyRowsMin = 64;
 struct GraphCache {
   cudaGraphExec_t exec = nullptr;
   int variant = -1, steps = -1, R = -1, cur = -1, G = -1, tiled = -1, rpc = -1, tiles = -1;
-  int unroll = -1, sgn = -1;
+  int unroll = -1, sgn = -1, groups = -1;
   float a0 = 0.f, dt = 0.f;
   const float* sched = nullptr;
   void reset() {
@@ -107,6 +107,7 @@ struct sb_ctx {
   int step_rpc = 0;   // rows per CTA of the untiled kernel (0: one row per group, -1: one wave)
   int step_unroll = 4;
   int dsb_signs = 1;  // dSB gathers int8 signs instead of FP32 positions
+  int groups = 1;     // replica groups run one after another (each for all steps)
   int8_t* d_sgn[2] = {nullptr, nullptr};
   int sms = 0;
 };
@@ -473,6 +474,10 @@ sb_status check_run_args(sb_ctx* c, sb_variant variant, double a0, double c0, do
 
 // Enqueue `steps` SB steps reading x from c->d_x[c->cur]; flips c->cur.
 sbd::Tiling step_tiling(const sb_ctx* c) {
+  if (c->groups > 1 && c->R % (4 * c->groups) == 0) {
+    const int rt = c->R / c->groups;
+    if (rt <= 128 && ((rt / 4) & (rt / 4 - 1)) == 0) return sbd::make_tiling_rt(c->R, rt);
+  }
   if (c->step_rt > 0 && c->R % c->step_rt == 0) return sbd::make_tiling_rt(c->R, c->step_rt);
   return sbd::make_tiling(c->R);
 }
@@ -480,7 +485,8 @@ sbd::Tiling step_tiling(const sb_ctx* c) {
 sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t steps,
                         const float* sched, cudaStream_t stream) {
   if (steps <= 0) return SB_OK;
-  const bool dsb16 = variant == SB_DSB && c->dsb_signs && c->step_rt == 0 && sbd::dsb16_ok(c->R) &&
+  const bool dsb16 = variant == SB_DSB && c->dsb_signs && c->step_rt == 0 && c->groups == 1 &&
+                     sbd::dsb16_ok(c->R) &&
                      !(c->tiled_ok && c->use_tiled && c->R % sbd::kTileRT == 0);
   const sbd::Tiling t = dsb16 ? sbd::make_tiling_dsb16(c->R) : step_tiling(c);
   sbd::StepArgs a;
@@ -499,6 +505,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   a.R = c->R;
   a.G = t.G;
   a.unroll = c->step_unroll;
+  a.tile0 = 0;
   a.rpc = std::max(256 / t.G, c->step_rpc);
   if (c->step_rpc < 0) {  // one wave: every resident CTA walks one contiguous row chunk
     if (!c->sms) SB_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
@@ -553,30 +560,47 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     return sbd::launch_step(variant, c->jbf16, t, a, st);
   };
   const size_t NR = (size_t)c->n * c->R;
+  const int ngroups = (!tiled && !dsb16 && c->groups > 1 && t.tiles == c->groups) ? c->groups : 1;
+  sbd::Tiling tg = t;
+  if (ngroups > 1) tg.tiles = 1;
+  // all steps for replica group g (tiles g), then the next group: each group's
+  // working set stays in L2 for the whole run; parity ends the same for all
+  auto launch_all = [&](int cur0, cudaStream_t st) -> cudaError_t {
+    cudaError_t err = cudaSuccess;
+    if (sgn) err = sbd::launch_signs(c->d_x[cur0], c->d_sgn[cur0], NR, st);
+    for (int grp = 0; grp < ngroups && err == cudaSuccess; ++grp) {
+      int cur = cur0;
+      a.tile0 = ngroups > 1 ? grp : 0;
+      for (int32_t k = 0; k < steps && err == cudaSuccess; ++k) {
+        if (ngroups > 1) {
+          a.k = k;
+          a.xin = c->d_x[cur];
+          a.xout = c->d_x[cur ^ 1];
+          err = sbd::launch_step(variant, c->jbf16, tg, a, st);
+        } else {
+          err = launch(k, cur, st);
+        }
+        cur ^= 1;
+      }
+    }
+    a.tile0 = 0;
+    return err;
+  };
   const bool graph = c->use_graph && steps >= 8;
   if (!graph) {
-    if (sgn) SB_CUDA(sbd::launch_signs(c->d_x[c->cur], c->d_sgn[c->cur], NR, stream));
-    for (int32_t k = 0; k < steps; ++k) {
-      SB_CUDA(launch(k, c->cur, stream));
-      c->cur ^= 1;
-    }
+    SB_CUDA(launch_all(c->cur, stream));
+    if (steps & 1) c->cur ^= 1;
     return SB_OK;
   }
   GraphCache& gc = c->graph;
   if (!(gc.exec && gc.variant == variant && gc.steps == steps && gc.R == c->R &&
         gc.cur == c->cur && gc.a0 == a.a0 && gc.dt == a.dt && gc.sched == sched && gc.G == t.G &&
         gc.tiled == tiled && gc.rpc == a.rpc && gc.tiles == t.tiles && gc.unroll == a.unroll &&
-        gc.sgn == sgn)) {
+        gc.sgn == sgn && gc.groups == ngroups)) {
     gc.reset();
     cudaGraph_t g = nullptr;
     SB_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    int cur = c->cur;
-    cudaError_t err = cudaSuccess;
-    if (sgn) err = sbd::launch_signs(c->d_x[cur], c->d_sgn[cur], NR, c->cap_stream);
-    for (int32_t k = 0; k < steps && err == cudaSuccess; ++k) {
-      err = launch(k, cur, c->cap_stream);
-      cur ^= 1;
-    }
+    cudaError_t err = launch_all(c->cur, c->cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
     SB_CUDA(err);
     SB_CUDA(e2);
@@ -596,6 +620,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     gc.tiles = t.tiles;
     gc.unroll = a.unroll;
     gc.sgn = sgn;
+    gc.groups = ngroups;
   }
   SB_CUDA(cudaGraphLaunch(gc.exec, stream));
   if (steps & 1) c->cur ^= 1;
@@ -1064,6 +1089,7 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
   a.G = t.G;
   a.rpc = 256 / t.G;
   a.unroll = 4;
+  a.tile0 = 0;
   a.ytil = nullptr;
   a.mask = nullptr;
   a.sgn_in = nullptr;
@@ -1170,10 +1196,12 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
   cudaStream_t s = (cudaStream_t)stream;
   // candidates: (tiled, replica-tile width, rows per CTA); invalid ones are skipped
   struct Cand {
-    int tiled, rt, rpc, unroll;
+    int tiled, rt, rpc, unroll, groups;
   };
-  std::vector<Cand> cands = {{0, 0, 0, 4},   {0, 0, 32, 4},  {0, 128, 0, 4}, {0, 128, 32, 4},
-                             {0, 64, 0, 4},  {0, 32, 0, 4},  {1, 0, 0, 4}};
+  std::vector<Cand> cands = {{0, 0, 0, 4, 1},  {0, 0, 32, 4, 1}, {0, 128, 0, 4, 1},
+                             {0, 128, 32, 4, 1}, {0, 64, 0, 4, 1}, {0, 32, 0, 4, 1},
+                             {0, 0, 0, 4, 2},  {0, 0, 32, 4, 2}, {0, 0, 0, 4, 4},
+                             {1, 0, 0, 4, 1}};
   const int keep_graph = ctx->use_graph;
   ctx->use_graph = 0;
   if ((st = ensure_state(ctx, replicas))) return st;
@@ -1189,10 +1217,15 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
     const Cand& c = cands[k];
     if (c.tiled && !(ctx->tiled_ok && replicas % sbd::kTileRT == 0)) continue;
     if (c.rt && (replicas % c.rt != 0)) continue;
+    if (c.groups > 1) {
+      const int rt = replicas / c.groups;
+      if (replicas % (4 * c.groups) != 0 || rt > 128 || ((rt / 4) & (rt / 4 - 1)) != 0) continue;
+    }
     ctx->use_tiled = c.tiled;
     ctx->step_rt = c.rt;
     ctx->step_rpc = c.rpc;
     ctx->step_unroll = c.unroll;
+    ctx->groups = c.groups;
     ctx->graph.reset();
     if ((st = sb_run(ctx, variant, 1.0, 0.0, 0.5, 0, replicas, 12345, nullptr, stream))) break;
     if ((st = enqueue_steps(ctx, variant, 1.0, 0.5, std::min(trial_steps, 4), sched, s))) break;
@@ -1220,12 +1253,14 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
   ctx->step_rt = cands[best].rt;
   ctx->step_rpc = cands[best].rpc;
   ctx->step_unroll = cands[best].unroll;
+  ctx->groups = cands[best].groups;
   ctx->graph.reset();
   if (out_cfg) {
     out_cfg[0] = cands[best].tiled;
     out_cfg[1] = cands[best].rt;
     out_cfg[2] = cands[best].rpc;
     out_cfg[3] = cands[best].unroll;
+    out_cfg[4] = cands[best].groups;
   }
   if (out_us_per_step) *out_us_per_step = best_us;
   return SB_OK;
@@ -1272,6 +1307,14 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value) {
       return SB_OK;
     case 5:  // SB_OPT_DSB_SIGNS
       ctx->dsb_signs = value != 0;
+      ctx->graph.reset();
+      return SB_OK;
+    case 6:  // SB_OPT_REPLICA_GROUPS
+      if (value < 1 || value > 64) {
+        set_error("sb_set_option: SB_OPT_REPLICA_GROUPS must be in [1, 64]");
+        return SB_ERR_ARG;
+      }
+      ctx->groups = (int)value;
       ctx->graph.reset();
       return SB_OK;
     default:

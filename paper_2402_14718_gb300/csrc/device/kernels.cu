@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kBlock) k_step(const StepArgs a) {
   const unsigned mask = group_mask(G);
   const int R = a.R;
   const int C = R / V;
-  const int ch0 = blockIdx.y * (G * NCH) + g;
+  const int ch0 = (blockIdx.y + a.tile0) * (G * NCH) + g;
   const JT* J = static_cast<const JT*>(a.J);
   const int row_end = min(a.n, (blockIdx.x + 1) * a.rpc);
   // a CTA walks a contiguous chunk of rows, so rows in flight together share

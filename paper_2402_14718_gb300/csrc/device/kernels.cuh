@@ -43,7 +43,8 @@ struct StepArgs {
   uint8_t* mask;          // optional: 1 where the wall fired [n x R]
   const int8_t* sgn_in;   // dSB: sgn(x_k) [n x R] gathered instead of x (NULL: use x)
   int8_t* sgn_out;        // dSB: sgn(x_{k+1}) written with x_{k+1} (may be NULL)
-  int32_t unroll;         // neighbours in flight per thread: 4 or 8
+  int32_t unroll;         // neighbours in flight per thread (4)
+  int32_t tile0;          // first replica tile of this launch (sequential replica groups)
 };
 
 cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs& a,

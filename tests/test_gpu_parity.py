@@ -439,3 +439,17 @@ def test_single_replica_kernel_bit_identical(variant):
         sb.sb_run(ctx, variant, 1.0, 0.0, dt, 40, 1, seed=9)
         out.append(sb.sb_get_state(ctx))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+
+@pytest.mark.parametrize("variant", ["bsb", "dsb"])
+@pytest.mark.parametrize("groups,R", [(2, 256), (4, 256), (2, 64)])
+def test_sequential_replica_groups_bit_identical(variant, groups, R):
+    _, qc, _, _ = workload_qubos("event500")
+    out = []
+    for g in (1, groups):
+        ctx = _ctx(qc, sb.SB_J_BF16)
+        sb.sb_set_option(ctx, 6, g)
+        sb.sb_run(ctx, variant, 1.0, 0.0, 0.5, 21, R, seed=3)
+        out.append(sb.sb_get_state(ctx))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
