@@ -1,0 +1,102 @@
+"""Error paths of the device API (status codes, no GPU fault): out-of-order
+calls, invalid arguments and allocation failure are reported, and the context
+stays usable afterwards."""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2402_14718_gb300 as sb
+from paper_2402_14718_gb300 import _lib
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _small():
+    q = inputs.random_qubo(40, 4, seed=1)
+    return q, sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin)
+
+
+def test_calls_out_of_order_and_bad_arguments():
+    q, ctx = _small()
+    with pytest.raises(sb.SbError) as ei:
+        sb.sb_advance(ctx, "bsb", 1.0, 0.0, 0.5, 3, torch.zeros(3, device="cuda"))
+    assert ei.value.code == _lib.SB_ERR_STATE
+    with pytest.raises(sb.SbError) as ei:
+        sb.sb_best(ctx)
+    assert ei.value.code == _lib.SB_ERR_STATE
+    for bad in (dict(replicas=0), dict(replicas=70000), dict(dt=-1.0), dict(a0=0.0),
+                dict(steps=-1), dict(dt=float("nan"))):
+        kw = dict(variant="bsb", a0=1.0, c0=0.0, dt=0.5, steps=5, replicas=4, seed=1)
+        kw.update(bad)
+        with pytest.raises(sb.SbError) as ei:
+            sb.sb_run(ctx, kw["variant"], kw["a0"], kw["c0"], kw["dt"], kw["steps"], kw["replicas"],
+                      kw["seed"])
+        assert ei.value.code == _lib.SB_ERR_ARG
+    with pytest.raises(sb.SbError):
+        sb.sb_run(ctx, 7, 1.0, 0.0, 0.5, 5, 4, 1)
+    with pytest.raises(sb.SbError):
+        sb.sb_set_option(ctx, 99, 1)
+    with pytest.raises(sb.SbError):
+        sb.sb_info(ctx, 1)
+    # still usable
+    sb.sb_run(ctx, "bsb", 1.0, 0.0, 0.5, 10, 4, 1)
+    assert sb.sb_energy(ctx, None, 4).shape == (1, 4)
+
+
+def test_backward_and_weights_argument_errors():
+    q, ctx = _small()
+    with pytest.raises(sb.SbError):
+        sb.sb_backward(ctx, 1.0, 0.0, 0.5, 10, 4, 1)          # c0 must be > 0
+    with pytest.raises(sb.SbError):
+        sb.sb_backward(ctx, 1.0, 0.3, 0.5, 10, 4, 1, ckpt_every=0)
+    asym = np.zeros(len(q.col), np.int8)
+    asym[0] = 1
+    with pytest.raises(sb.SbError) as ei:
+        sb.sb_set_weights(ctx, asym, np.zeros(q.n), 1.0, 1.0)
+    assert ei.value.code == _lib.SB_ERR_CSR
+    batch = sb.sb_create_batch([(q.rowptr, q.col, q.val, q.lin)] * 2)
+    with pytest.raises(sb.SbError):
+        sb.sb_backward(batch, 1.0, 0.3, 0.5, 10, 4, 1)
+    loss, g = sb.sb_backward(ctx, 1.0, 0.3, 0.5, 10, 4, 1)   # no class tags: NaN for w
+    assert np.isfinite(loss) and np.isfinite(g["dt"]) and np.isnan(g["w_q"]) and np.isnan(g["w_c"])
+
+
+def test_allocation_failure_is_reported():
+    """A state array larger than the whole device: the first cudaMalloc fails
+    (nothing is held), SB_ERR_OOM comes back, and the context still runs."""
+    n = 1_200_000
+    ctx = sb.sb_create(n, np.zeros(n + 1, np.int32), np.zeros(0, np.int32), np.zeros(0),
+                       np.linspace(-1.0, 1.0, n))
+    free, total = torch.cuda.mem_get_info()
+    R = 65535   # one x array alone: 1.2M x 65535 x 4 B = 315 GB
+    if 4 * n * R <= total:
+        pytest.skip("device holds the oversized array")
+    with pytest.raises(sb.SbError) as ei:
+        sb.sb_run(ctx, "bsb", 1.0, 0.0, 0.5, 1, R, 1)
+    assert ei.value.code in (_lib.SB_ERR_OOM, _lib.SB_ERR_CUDA)
+    sb.sb_run(ctx, "bsb", 1.0, 0.0, 0.5, 3, 8, 1)
+    assert sb.sb_energy(ctx, None, 8).shape == (1, 8)
+
+
+def test_degenerate_sizes():
+    # one variable, no couplings: runs, the wall is reached, energy is a or 0
+    ctx = sb.sb_create(1, np.array([0, 0]), np.zeros(0), np.zeros(0), np.array([-0.7]))
+    sb.sb_run(ctx, "bsb", 1.0, 1.0, 0.5, 200, 3, 5)
+    x, _ = sb.sb_get_state(ctx)
+    assert np.all(np.abs(x) == 1.0)
+    E = sb.sb_energy(ctx, None, 3)[0]
+    assert set(E.tolist()) <= {-0.7, 0.0}
+    # zero steps is a valid run (initial state only)
+    sb.sb_run(ctx, "dsb", 1.0, 1.0, 0.5, 0, 5, 5)
+    x0, _ = sb.sb_get_state(ctx)
+    assert np.all(np.abs(x0) <= 0.01)
+    # a large replica count on a small problem
+    q = inputs.random_qubo(64, 5, seed=4)
+    ctx2 = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_BF16)
+    sb.sb_run(ctx2, "bsb", 1.0, 0.0, 0.5, 20, 65535, 1)
+    T, E, r = sb.sb_best(ctx2)
+    assert 0 <= r[0] < 65535 and np.isfinite(E[0])
