@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttt", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--study", default="", choices=["", "paper-sizes", "c0-scan", "schedule"],
+    ap.add_argument("--study", default="",
+                    choices=["", "paper-sizes", "c0-scan", "schedule", "build"],
                     help="experiments (not bench lines): energy traces and 50-shot statistics "
                          "at the paper's QUBO sizes, the c0 scan, schedule learning by the adjoint")
     ap.add_argument("--kernel", default="auto", choices=["auto", "untiled"],
@@ -630,6 +631,25 @@ def run_study(args):
                                "min": float(Es[i].min() - off), "max": float(Es[i].max() - off)}
                               for i in pick],
                     "efficiency": sc["efficiency"], "purity": sc["purity"]}), flush=True)
+        return 0
+    if args.study == "build":
+        # QUBO construction time (left out of the paper's timings): host C++ vs GPU
+        for name in ("event1000", "event10k"):
+            w = WORKLOADS[name]
+            ev = sb.sb_event_generate(w["seed"], sb.event_params(n_tracks=w["n_tracks"],
+                                                                 noise_frac=w["noise_frac"]))
+            p = sb.build_params(**w["cuts"])
+            t0 = time.perf_counter()
+            qh = sb.sb_qubo_build(ev, p)
+            t_host = time.perf_counter() - t0
+            sb.sb_qubo_build_device(ev, p)                     # warm-up
+            t0 = time.perf_counter()
+            qd, ms = sb.sb_qubo_build_device(ev, p)
+            t_dev = time.perf_counter() - t0
+            print(json.dumps({"study": "build", "workload": name, "N": qh.n, "nnz": qh.nnz,
+                              "host_s": t_host, "device_kernels_ms": ms, "device_call_s": t_dev,
+                              "same_structure": bool(qd.n == qh.n and np.array_equal(qd.col, qh.col))}),
+                  flush=True)
         return 0
     if args.study == "c0-scan":
         # section "Results": fixed c0 versus a scan

@@ -140,6 +140,19 @@ sb_status sb_qubo_arrays(const sb_qubo* q, int32_t* rowptr, int32_t* col, double
 void sb_qubo_destroy(sb_qubo* q);
 
 /*
+ * sb_qubo_build_device -- the builder above run on the current GPU (hits
+ * uploaded from the host event; count / scan / write passes over doublets,
+ * triplets, hit incidences and triplet pairs). The result is the same sb_qubo
+ * as sb_qubo_build: identical structure (triplets, rows, columns, classes) and
+ * identical values except where they pass through atan2 (segment angles) or exp
+ * (Eq. 15 bias), whose device results may differ from the host's in the last
+ * place. out_device_ms (may be NULL): device time of the build, CUDA events on
+ * `stream`. Synchronous.
+ */
+sb_status sb_qubo_build_device(const sb_event* ev, const sb_build_params* p, sb_qubo** out,
+                               double* out_device_ms, void* stream);
+
+/*
  * Track finding and scoring (last paragraph of "QUBO Generation and Track
  * Finding"; Eq. 18-19). T[n] (host, 0/1) selects triplets; their doublets are
  * merged, hits with more than one selected outgoing or incoming doublet lose

@@ -18,6 +18,7 @@ __all__ = [
     "SB_ASB", "SB_BSB", "SB_DSB", "SB_J_FP32", "SB_J_BF16", "SB_OPT_GRAPH", "SB_OPT_TILED",
     "SbError",
     "event_params", "build_params", "sb_event_generate", "sb_qubo_build", "sb_tracks",
+    "sb_qubo_build_device",
     "sb_create", "sb_create_batch", "sb_destroy", "sb_info", "sb_run", "sb_advance",
     "sb_set_state", "sb_get_state", "sb_energy", "sb_best", "sb_readout_device", "sb_set_option",
     "sb_energy_noalloc", "sb_autotune", "sb_set_weights", "sb_backward", "SBRelaxedEnergy",
@@ -154,6 +155,16 @@ def sb_qubo_build(event, params=None):
     p = params if params is not None else build_params()
     check(lib.sb_qubo_build(event.handle, ctypes.byref(p), ctypes.byref(h)))
     return Qubo(h.value)
+
+
+def sb_qubo_build_device(event, params=None, stream=None):
+    """Build on the GPU; returns (Qubo, device milliseconds)."""
+    h = ctypes.c_void_p()
+    ms = ctypes.c_double()
+    p = params if params is not None else build_params()
+    check(lib.sb_qubo_build_device(event.handle, ctypes.byref(p), ctypes.byref(h), ctypes.byref(ms),
+                                   _stream(stream)))
+    return Qubo(h.value), ms.value
 
 
 def sb_tracks(event, qubo, T, min_hits=4):

@@ -61,6 +61,8 @@ _SIGS = {
     "sb_qubo_sizes": (c_int32, [c_void_p, P(c_int32), P(c_int64)]),
     "sb_qubo_arrays": (c_int32, [c_void_p] + [c_void_p] * 9),
     "sb_qubo_destroy": (None, [c_void_p]),
+    "sb_qubo_build_device": (c_int32, [c_void_p, P(SbBuildParams), P(c_void_p), P(c_double),
+                                       c_void_p]),
     "sb_tracks": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, P(c_int32), c_void_p,
                             c_void_p, c_void_p, c_void_p]),
     "sb_create": (c_int32, [c_int32, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,

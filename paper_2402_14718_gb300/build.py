@@ -18,7 +18,9 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsbtrack.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-CU = ["api.cu", "device/kernels.cu", "device/noalloc.cu"]
+CU = ["api.cu", "device/kernels.cu", "device/noalloc.cu", "device/build.cu"]
+# FP64 builder kernels: one IEEE operation per written operation, as on the host
+CU_FLAGS = {"device/build.cu": ["-fmad=false"]}
 CPP = ["host/events.cpp", "host/qubo.cpp", "host/tracks.cpp"]
 
 
@@ -64,7 +66,7 @@ def build(verbose=False, force=False, ptxas_verbose=False):
         objs.append(obj)
         if force or _stale(obj, [src] + deps):
             cmd = [nvcc, ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-                   "-c", src, "-o", obj]
+                   "--extended-lambda"] + CU_FLAGS.get(f, []) + ["-c", src, "-o", obj]
             if ptxas_verbose:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append(cmd)
