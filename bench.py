@@ -82,6 +82,23 @@ def job_value(units_per_rank, world_size, ms):
     return units_per_rank * world_size / (ms * 1e-3)
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step-kernel
+# launch from the ncu capture summarised in profiles/k_step_event1000_ncu.md,
+# valid only for the kernel sources that were captured (sha256 prefix of
+# kernels.cu + kernels.cuh); any other source reports null.
+MEASURED_TRAFFIC = {("event1000", "bsb", "14e9279fcb6b4ecf"): 126945792}
+
+
+def kernel_source_hash():
+    import hashlib
+    d = os.path.join(ROOT, "paper_2402_14718_gb300", "csrc", "device")
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "kernels.cuh"):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -288,7 +305,9 @@ def run_ours(args):
     hbm, src = peaks()
     achieved = alg_bytes / kstep_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "kernel": "k_step",
+                "frac": achieved / hbm,
+                "traffic": MEASURED_TRAFFIC.get((args.workload, args.variant, kernel_source_hash())),
+                "kernel": "k_step",
                 "peak_source": src, "alg_bytes_per_launch": alg_bytes,
                 "kstep_us": kstep_s * 1e6}
 

@@ -114,10 +114,13 @@ struct sb_ctx {
 
 namespace {
 
+// On failure the error is reported and CUDA's last-error slot is cleared, so a
+// non-sticky failure (e.g. an allocation) does not resurface at the next launch.
 #define SB_CUDA(call)                                                              \
   do {                                                                             \
     cudaError_t e_ = (call);                                                       \
     if (e_ != cudaSuccess) {                                                       \
+      cudaGetLastError();                                                          \
       set_error(std::string(#call) + ": " + cudaGetErrorString(e_));               \
       return e_ == cudaErrorMemoryAllocation ? SB_ERR_OOM : SB_ERR_CUDA;           \
     }                                                                              \
@@ -129,6 +132,7 @@ sb_status dalloc(T** p, size_t count) {
   if (count == 0) count = 1;
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
   if (e != cudaSuccess) {
+    cudaGetLastError();  // clear the non-sticky allocation error
     *p = nullptr;
     set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
     return SB_ERR_OOM;
@@ -370,6 +374,7 @@ sb_status setup_tiles(sb_ctx* c, const int32_t* rowptr, const int32_t* col) {
     return st;
   cudaError_t e = cudaMalloc(&c->d_tz, std::max<size_t>(nnz, 1) * (c->jbf16 ? 4 : 8));
   if (e != cudaSuccess) {
+    cudaGetLastError();
     c->d_tz = nullptr;
     dfree(d_lidx);
     set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
@@ -407,6 +412,7 @@ sb_status create_common(sb_ctx* c, const int32_t* rowptr, const int32_t* col, co
   {
     cudaError_t e = cudaMalloc(&c->d_J, std::max<size_t>(nnz, 1) * (c->jbf16 ? 2 : 4));
     if (e != cudaSuccess) {
+      cudaGetLastError();
       c->d_J = nullptr;
       set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
       return SB_ERR_OOM;

@@ -497,7 +497,10 @@ struct Pool {
     if (err != cudaSuccess) return nullptr;
     void* p = nullptr;
     err = cudaMalloc(&p, (size_t)std::max<long long>(count, 1) * sizeof(T));
-    if (err != cudaSuccess) return nullptr;
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
     ptrs.push_back(p);
     return static_cast<T*>(p);
   }
@@ -534,6 +537,7 @@ extern "C" sb_status sb_qubo_build_device(const sb_event* ev, const sb_build_par
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   auto fail = [&](cudaError_t e) {
+    cudaGetLastError();  // clear a non-sticky error (allocation) before returning
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     sbh::set_error(std::string("sb_qubo_build_device: ") + cudaGetErrorString(e));

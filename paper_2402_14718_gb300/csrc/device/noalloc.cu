@@ -128,6 +128,7 @@ extern "C" sb_status sb_energy_noalloc(int32_t n, const int32_t* d_rowptr, const
   if (e == cudaSuccess) e = sbd::launch_energy_reduce(partial, ev_blk0, 1, replicas, d_E, cs);
   if (e == cudaSuccess && d_best_E) e = sbd::launch_argmin(d_E, 1, replicas, d_best_E, d_best_r, cs);
   if (e != cudaSuccess) {
+    cudaGetLastError();
     sbh::set_error(std::string("sb_energy_noalloc: ") + cudaGetErrorString(e));
     return SB_ERR_CUDA;
   }
