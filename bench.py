@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--no-ttt", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--study", default="",
-                    choices=["", "paper-sizes", "c0-scan", "schedule", "build"],
+                    choices=["", "paper-sizes", "c0-scan", "schedule", "build", "adjoint"],
                     help="experiments (not bench lines): energy traces and 50-shot statistics "
                          "at the paper's QUBO sizes, the c0 scan, schedule learning by the adjoint")
     ap.add_argument("--kernel", default="auto", choices=["auto", "untiled"],
@@ -454,6 +454,8 @@ def time_to_target(sb, ctx, q, ev, w, variant, stream, sched, dev, plain_runs=16
     torch.cuda.synchronize(dev)
     t_plain_run = e0.elapsed_time(e1) * 1e-3 / plain_runs
     plain_E = [float(f.item()) for f in finals]
+    Tp, _, _ = sb.sb_best(ctxp)
+    scp = sb.sb_tracks(ev, q, Tp)
     e_best = min(e_ref, min(float(e.min()) for e in Es), min(plain_E))
     target = e_best + 0.001 * abs(e_best)
     p_reps = [float(np.mean(e <= target)) for e in Es]
@@ -481,6 +483,7 @@ def time_to_target(sb, ctx, q, ev, w, variant, stream, sched, dev, plain_runs=16
             "plain_fp32": {"seconds": ttt_p, "at_step": None if kp is None else (kp + 1) * every,
                            "run_seconds": t_plain_run, "replicas_per_run": 1,
                            "runs_timed": plain_runs, "plain_runs_at_target": plain_ok,
+                           "efficiency_last_run": scp["efficiency"], "purity_last_run": scp["purity"],
                            "spin_updates_per_s": q.n * S / t_plain_run},
             "bf16_graph_r1": {"seconds": ttt_1, "run_seconds": t_r1, "replicas_per_run": 1},
             "speedup_batched_vs_plain": (ttt_p / ttt_b) if (ttt_b and ttt_p) else None,
@@ -650,6 +653,32 @@ def run_study(args):
                                "min": float(Es[i].min() - off), "max": float(Es[i].max() - off)}
                               for i in pick],
                     "efficiency": sc["efficiency"], "purity": sc["purity"]}), flush=True)
+        return 0
+    if args.study == "adjoint":
+        # 500-track workload: bSB forward vs sb_backward (checkpoint every 32 steps)
+        w = WORKLOADS["event500"]
+        ev = sb.sb_event_generate(w["seed"], sb.event_params(n_tracks=w["n_tracks"],
+                                                             noise_frac=w["noise_frac"]))
+        q = sb.sb_qubo_build(ev, sb.build_params(**w["cuts"]))
+        ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_FP32)
+        sb.sb_set_weights(ctx, q.cls, q.quality, 1.0, 1.0)
+        S, R, c0 = w["steps"], w["replicas"], sb.sb_info(ctx)["c0_auto"]
+        sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)   # both directions launch one kernel per step
+        sb.sb_run(ctx, "bsb", 1.0, c0, 0.5, S, R, 1, None, stream)
+        sb.sb_backward(ctx, 1.0, c0, 0.5, S, R, 1, None, 32)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            sb.sb_run(ctx, "bsb", 1.0, c0, 0.5, S, R, 1, None, stream)
+        torch.cuda.synchronize(dev)
+        t_fwd = (time.perf_counter() - t0) / 3
+        t0 = time.perf_counter()
+        for _ in range(3):
+            loss, g = sb.sb_backward(ctx, 1.0, c0, 0.5, S, R, 1, None, 32)
+        t_bwd = (time.perf_counter() - t0) / 3
+        print(json.dumps({"study": "adjoint", "N": q.n, "R": R, "steps": S, "ckpt_every": 32,
+                          "forward_s": t_fwd, "backward_s": t_bwd, "backward_over_forward": t_bwd / t_fwd,
+                          "loss": loss, "grads": g}), flush=True)
         return 0
     if args.study == "build":
         # QUBO construction time (left out of the paper's timings): host C++ vs GPU

@@ -361,6 +361,10 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
 #define SB_OPT_STEP_UNROLL 4
 #define SB_OPT_DSB_SIGNS 5
 #define SB_OPT_REPLICA_GROUPS 6
+/* SB_OPT_L2_PERSIST (7): 1 marks each step's source positions as L2-persisting
+ * (stream access-policy window; the persisting L2 set-aside of this process's
+ * context is raised to the device maximum). Does not change results. */
+#define SB_OPT_L2_PERSIST 7
 sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
 
 /*

@@ -22,6 +22,7 @@ SB_OPT_STEP_RPC = 3
 SB_OPT_STEP_UNROLL = 4
 SB_OPT_DSB_SIGNS = 5
 SB_OPT_REPLICA_GROUPS = 6
+SB_OPT_L2_PERSIST = 7
 
 
 class SbEventParams(ctypes.Structure):

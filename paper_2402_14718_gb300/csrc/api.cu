@@ -108,6 +108,7 @@ struct sb_ctx {
   int step_unroll = 4;
   int dsb_signs = 1;  // dSB gathers int8 signs instead of FP32 positions
   int groups = 1;     // replica groups run one after another (each for all steps)
+  int l2_persist = 0; // mark each step's source x as L2-persisting (access-policy window)
   int8_t* d_sgn[2] = {nullptr, nullptr};
   int sms = 0;
 };
@@ -549,7 +550,25 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     const size_t cnt = (size_t)c->n * c->R;
     if ((st2 = dalloc(&c->d_sgn[0], cnt)) || (st2 = dalloc(&c->d_sgn[1], cnt))) return st2;
   }
+  size_t win_max = 0;
+  if (c->l2_persist) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxAccessPolicyWindowSize, c->device) == cudaSuccess)
+      win_max = (size_t)v;
+  }
+  auto set_window = [&](const void* base, cudaStream_t st) -> cudaError_t {
+    if (!c->l2_persist || !win_max) return cudaSuccess;
+    cudaStreamAttrValue v = {};
+    v.accessPolicyWindow.base_ptr = const_cast<void*>(base);
+    v.accessPolicyWindow.num_bytes = std::min(win_max, (size_t)c->n * c->R * sizeof(float));
+    v.accessPolicyWindow.hitRatio = 1.0f;
+    v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    return cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &v);
+  };
   auto launch = [&](int32_t k, int cur, cudaStream_t st) -> cudaError_t {
+    cudaError_t ew = set_window(c->d_x[cur], st);
+    if (ew != cudaSuccess) return ew;
     if (sgn) {
       a.sgn_in = c->d_sgn[cur];
       a.sgn_out = c->d_sgn[cur ^ 1];
@@ -596,6 +615,11 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   if (!graph) {
     SB_CUDA(launch_all(c->cur, stream));
     if (steps & 1) c->cur ^= 1;
+    if (c->l2_persist && win_max) {  // leave the caller's stream without our window
+      cudaStreamAttrValue v = {};
+      v.accessPolicyWindow.num_bytes = 0;
+      SB_CUDA(cudaStreamSetAttribute(stream, cudaStreamAttributeAccessPolicyWindow, &v));
+    }
     return SB_OK;
   }
   GraphCache& gc = c->graph;
@@ -1313,6 +1337,18 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value) {
       return SB_OK;
     case 5:  // SB_OPT_DSB_SIGNS
       ctx->dsb_signs = value != 0;
+      ctx->graph.reset();
+      return SB_OK;
+    case 7:  // SB_OPT_L2_PERSIST
+      if (value) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxPersistingL2CacheSize, ctx->device) ==
+                cudaSuccess &&
+            v > 0) {
+          SB_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)v));
+        }
+      }
+      ctx->l2_persist = value != 0;
       ctx->graph.reset();
       return SB_OK;
     case 6:  // SB_OPT_REPLICA_GROUPS

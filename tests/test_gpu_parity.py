@@ -453,3 +453,18 @@ def test_sequential_replica_groups_bit_identical(variant, groups, R):
         sb.sb_run(ctx, variant, 1.0, 0.0, 0.5, 21, R, seed=3)
         out.append(sb.sb_get_state(ctx))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+
+def test_l2_persist_option_bit_identical():
+    _, qc, _, _ = workload_qubos("event500")
+    out = []
+    for l2 in (0, 1):
+        for graph in (0, 1):
+            ctx = _ctx(qc, sb.SB_J_BF16)
+            sb.sb_set_option(ctx, 7, l2)
+            sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, graph)
+            sb.sb_run(ctx, "bsb", 1.0, 0.0, 0.5, 16, 64, seed=6)
+            out.append(sb.sb_get_state(ctx))
+    for o in out[1:]:
+        assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])
