@@ -289,7 +289,7 @@ sb_status sb_set_weights(sb_ctx* ctx, const int8_t* cls, const double* quality, 
  * dL/d w_q, dL/d w_c (the last two are NaN unless sb_set_weights was called);
  * d_grad_sched: device FP64 [steps] = dL/d a_k (may be NULL).
  * a_sched: device FP32 [steps] or NULL for the linear ramp. Single-event
- * contexts only. Work memory: 2 (steps/ckpt_every + 1) + (ckpt_every + 1) + 4
+ * contexts only. Work memory: 2 (steps/ckpt_every + 1) + 2 ckpt_every + 4
  * state-sized FP32 arrays plus ckpt_every byte masks. Synchronous; discards
  * the current state.
  */
@@ -372,8 +372,8 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
  * replica-tile width, rows per CTA) for this context, variant and replica
  * count by timing each candidate for `trial_steps` steps with CUDA events on
  * `stream`, and set it on the context. Results do not depend on the choice.
- * Outputs (host, may be NULL): out_cfg[5] = {tiled, tile width, rows per CTA, unroll,
- * replica groups},
+ * Outputs (host, may be NULL): out_cfg[6] = {tiled, tile width, rows per CTA, unroll,
+ * replica groups, L2 persist},
  * out_us_per_step = the best time. Synchronous; discards the current state.
  */
 sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t trial_steps,

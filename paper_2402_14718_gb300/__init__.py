@@ -324,12 +324,12 @@ def sb_energy_noalloc(n, d_rowptr, d_col, d_qval, d_qlin, d_x, d_spins, replicas
 def sb_autotune(ctx, variant, replicas, trial_steps=50, stream=None):
     """Time the step-kernel candidates and keep the fastest; returns
     ({"tiled", "tile", "rows_per_cta"}, microseconds per step)."""
-    cfg = np.zeros(5, np.int32)
+    cfg = np.zeros(6, np.int32)
     us = ctypes.c_float()
     check(lib.sb_autotune(ctx.handle, _variant(variant), int(replicas), int(trial_steps),
                           cfg.ctypes.data_as(ctypes.c_void_p), ctypes.byref(us), _stream(stream)))
     return {"tiled": int(cfg[0]), "tile": int(cfg[1]), "rows_per_cta": int(cfg[2]),
-            "unroll": int(cfg[3]), "groups": int(cfg[4])}, us.value
+            "unroll": int(cfg[3]), "groups": int(cfg[4]), "l2_persist": int(cfg[5])}, us.value
 
 
 def sb_set_weights(ctx, cls, quality, w_q, w_c):

@@ -514,6 +514,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   a.unroll = c->step_unroll;
   a.tile0 = 0;
   a.rpc = std::max(256 / t.G, c->step_rpc);
+  a.frec = nullptr;
   if (c->step_rpc < 0) {  // one wave: every resident CTA walks one contiguous row chunk
     if (!c->sms) SB_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
     const long long slots =
@@ -1072,7 +1073,7 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
     }
     sched = ctx->d_sched;
   }
-  float *ck_x = nullptr, *ck_y = nullptr, *seg_x = nullptr, *seg_yt = nullptr;
+  float *ck_x = nullptr, *ck_y = nullptr, *seg_x = nullptr, *seg_yt = nullptr, *seg_f = nullptr;
   float *lx = nullptr, *ly = nullptr, *lyt = nullptr;
   uint8_t* seg_m = nullptr;
   double *gh = nullptr, *acc = nullptr, *ga = nullptr;
@@ -1081,6 +1082,7 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
     dfree(ck_y);
     dfree(seg_x);
     dfree(seg_yt);
+    dfree(seg_f);
     dfree(seg_m);
     dfree(lx);
     dfree(ly);
@@ -1091,6 +1093,7 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
   };
   if ((st = dalloc(&ck_x, NR * n_ck)) || (st = dalloc(&ck_y, NR * n_ck)) ||
       (st = dalloc(&seg_x, NR * (K + 1))) || (st = dalloc(&seg_yt, NR * K)) ||
+      (st = dalloc(&seg_f, NR * K)) ||
       (st = dalloc(&seg_m, NR * K)) || (st = dalloc(&lx, NR)) || (st = dalloc(&ly, NR)) ||
       (st = dalloc(&lyt, NR)) || (st = dalloc(&gh, (size_t)n)) || (st = dalloc(&acc, 6)) ||
       (st = dalloc(&ga, (size_t)S))) {
@@ -1122,6 +1125,7 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
   a.tile0 = 0;
   a.ytil = nullptr;
   a.mask = nullptr;
+  a.frec = nullptr;
   a.sgn_in = nullptr;
   a.sgn_out = nullptr;
   ok(sbd::launch_set_c0(ctx->d_c0ev, ctx->d_c0auto, c0, 1, s));
@@ -1163,6 +1167,7 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
   g.x = ctx->d_x[cur];
   g.ytil = nullptr;
   g.mask = nullptr;
+  g.frec = nullptr;
   g.lx = lx;
   g.ly = ly;
   g.lyt = lyt;
@@ -1182,15 +1187,18 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
       a.y = ctx->d_y;
       a.ytil = seg_yt + NR * j;
       a.mask = seg_m + NR * j;
+      a.frec = seg_f + NR * j;
       ok(sbd::launch_step(SB_BSB, ctx->jbf16, t, a, s));
     }
     a.ytil = nullptr;
     a.mask = nullptr;
+    a.frec = nullptr;
     for (int32_t j = L - 1; j >= 0 && e == cudaSuccess; --j) {
       g.k = c * K + j;
       g.x = seg_x + NR * j;
       g.ytil = seg_yt + NR * j;
       g.mask = seg_m + NR * j;
+      g.frec = seg_f + NR * j;
       g.ga = ga + g.k;
       ok(sbd::launch_adj_phase1(g, s));
       ok(sbd::launch_adj_phase2(ctx->jbf16, t, g, s));
@@ -1215,6 +1223,8 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
   return SB_OK;
 }
 
+sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
+
 sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t trial_steps,
                       int32_t* out_cfg, float* out_us_per_step, void* stream) {
   if (!ctx || replicas < 1 || replicas > 65535 || trial_steps < 1 || trial_steps > 100000) {
@@ -1226,12 +1236,12 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
   cudaStream_t s = (cudaStream_t)stream;
   // candidates: (tiled, replica-tile width, rows per CTA); invalid ones are skipped
   struct Cand {
-    int tiled, rt, rpc, unroll, groups;
+    int tiled, rt, rpc, unroll, groups, l2;
   };
-  std::vector<Cand> cands = {{0, 0, 0, 4, 1},  {0, 0, 32, 4, 1}, {0, 128, 0, 4, 1},
-                             {0, 128, 32, 4, 1}, {0, 64, 0, 4, 1}, {0, 32, 0, 4, 1},
-                             {0, 0, 0, 4, 2},  {0, 0, 32, 4, 2}, {0, 0, 0, 4, 4},
-                             {1, 0, 0, 4, 1}};
+  std::vector<Cand> cands = {{0, 0, 0, 4, 1, 0},   {0, 0, 32, 4, 1, 0}, {0, 0, 0, 4, 1, 1},
+                             {0, 0, 32, 4, 1, 1},  {0, 128, 0, 4, 1, 0}, {0, 128, 32, 4, 1, 0},
+                             {0, 64, 0, 4, 1, 0},  {0, 32, 0, 4, 1, 0}, {0, 0, 0, 4, 2, 0},
+                             {0, 0, 32, 4, 2, 0},  {0, 0, 0, 4, 4, 0},  {1, 0, 0, 4, 1, 0}};
   const int keep_graph = ctx->use_graph;
   ctx->use_graph = 0;
   if ((st = ensure_state(ctx, replicas))) return st;
@@ -1256,6 +1266,10 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
     ctx->step_rpc = c.rpc;
     ctx->step_unroll = c.unroll;
     ctx->groups = c.groups;
+    if (c.l2 && !ctx->l2_persist) {
+      if ((st = sb_set_option(ctx, 7, 1))) break;
+    }
+    ctx->l2_persist = c.l2;
     ctx->graph.reset();
     if ((st = sb_run(ctx, variant, 1.0, 0.0, 0.5, 0, replicas, 12345, nullptr, stream))) break;
     if ((st = enqueue_steps(ctx, variant, 1.0, 0.5, std::min(trial_steps, 4), sched, s))) break;
@@ -1284,6 +1298,7 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
   ctx->step_rpc = cands[best].rpc;
   ctx->step_unroll = cands[best].unroll;
   ctx->groups = cands[best].groups;
+  ctx->l2_persist = cands[best].l2;
   ctx->graph.reset();
   if (out_cfg) {
     out_cfg[0] = cands[best].tiled;
@@ -1291,6 +1306,7 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
     out_cfg[2] = cands[best].rpc;
     out_cfg[3] = cands[best].unroll;
     out_cfg[4] = cands[best].groups;
+    out_cfg[5] = cands[best].l2;
   }
   if (out_us_per_step) *out_us_per_step = best_us;
   return SB_OK;

@@ -244,7 +244,10 @@ __global__ void __launch_bounds__(kBlock) k_step(const StepArgs a) {
       if (VARIANT == 0) force -= x * x * x;
       y = y + a.dt * force;
       x = x + a.dta0 * y;
-      if (record) a.ytil[idx + v] = y;
+      if (record) {
+        a.ytil[idx + v] = y;
+        a.frec[idx + v] = acc[j][v];
+      }
       const bool wall = VARIANT != 0 && fabsf(x) > 1.f;
       if (record) a.mask[idx + v] = wall ? 1 : 0;
       if (wall) {
@@ -351,7 +354,10 @@ __global__ void __launch_bounds__(kBlock) k_step_r1(const StepArgs a) {
   if (VARIANT == 0) force -= x * x * x;
   y = y + a.dt * force;
   x = x + a.dta0 * y;
-  if (record) a.ytil[row] = y;
+  if (record) {
+    a.ytil[row] = y;
+    a.frec[row] = acc;
+  }
   const bool wall = VARIANT != 0 && fabsf(x) > 1.f;
   if (record) a.mask[row] = wall ? 1 : 0;
   if (wall) {
@@ -763,7 +769,10 @@ __global__ void k_adj_phase1(const AdjArgs a) {
 }
 
 // Momentum update reversed: lx_k = lx~ - dt (a0 - a_k) ly~ + dt c0 J ly~, ly_k = ly~,
-// and the gradient contributions of this step (FP64).
+// and the gradient contributions of this step (FP64). One gather of ly~ gives
+// both J ly~ and C ly~ (conflict entries only); J x_k comes recorded from the
+// forward recomputation, and sum ly~ (C x_k) = sum x_k (C ly~) since C is
+// symmetric.
 template <int V, int NCH, typename JT>
 __global__ void __launch_bounds__(kBlock) k_adj_phase2(const AdjArgs a) {
   const int G = a.G;
@@ -774,8 +783,40 @@ __global__ void __launch_bounds__(kBlock) k_adj_phase2(const AdjArgs a) {
   double gdt = 0.0, gc0 = 0.0, ga = 0.0, gwc = 0.0, ghr = 0.0;
   if (row < a.n) {
     const unsigned mask = group_mask(G);
-    float sJ[NCH][V], fJ[NCH][V], fC[NCH][V];
-    adj_row_products<V, NCH, JT, true>(a, row, ch0, C, mask, a.lyt, a.x, sJ, fJ, fC);
+    const JT* J = static_cast<const JT*>(a.J);
+    float sJ[NCH][V], sC[NCH][V];
+#pragma unroll
+    for (int j = 0; j < NCH; ++j)
+#pragma unroll
+      for (int v = 0; v < V; ++v) sJ[j][v] = sC[j][v] = 0.f;
+    const int p0 = a.rowptr[row], p1 = a.rowptr[row + 1];
+    for (int pb = p0; pb < p1; pb += G) {
+      const int cnt = min(G, p1 - pb);
+      int mc = 0, mk = 0;
+      float mv = 0.f;
+      if (g < cnt) {
+        mc = a.col[pb + g];
+        mv = jval(J, pb + g);
+        mk = a.cls[pb + g];
+      }
+      for (int q = 0; q < cnt; ++q) {
+        const int c = __shfl_sync(mask, mc, q, G);
+        const float w = __shfl_sync(mask, mv, q, G);
+        const int kc = __shfl_sync(mask, mk, q, G);
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+          const int ch = ch0 + j * G;
+          if (ch >= C) continue;
+          Vec<V> uv;
+          uv.ldg(a.lyt + (size_t)c * a.R + (size_t)ch * V);
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            sJ[j][v] = fmaf(w, uv.v[v], sJ[j][v]);
+            if (kc) sC[j][v] += uv.v[v];
+          }
+        }
+      }
+    }
     const float hi = a.h[row];
     const float pa = a.a0 - __ldg(a.sched + a.k);
 #pragma unroll
@@ -788,11 +829,12 @@ __global__ void __launch_bounds__(kBlock) k_adj_phase2(const AdjArgs a) {
         const float x = a.x[idx + v];
         const float lyt = a.lyt[idx + v];
         const float lxt = a.lx[idx + v];
-        const double F = -(double)pa * x + (double)a.c0 * ((double)fJ[j][v] + hi);
+        const double f = a.frec[idx + v];
+        const double F = -(double)pa * x + (double)a.c0 * (f + hi);
         gdt += (double)lyt * F + (double)lxt * a.a0 * (double)a.ytil[idx + v];
-        gc0 += (double)lyt * a.dt * ((double)fJ[j][v] + hi);
+        gc0 += (double)lyt * a.dt * (f + hi);
         ga += (double)lyt * a.dt * x;
-        gwc += (double)a.dt * a.c0 * lyt * (-0.25 * (double)fC[j][v]);
+        gwc += (double)a.dt * a.c0 * (double)x * (-0.25 * (double)sC[j][v]);
         ghr += (double)a.dt * a.c0 * lyt;
         a.lx[idx + v] = lxt - a.dt * pa * lyt + a.dt * a.c0 * sJ[j][v];
         a.ly[idx + v] = lyt;

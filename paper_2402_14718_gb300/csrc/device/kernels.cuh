@@ -41,6 +41,7 @@ struct StepArgs {
   int32_t rpc;            // rows per CTA: a CTA walks rows [b * rpc, (b + 1) * rpc)
   float* ytil;            // optional: momentum after the update, before the wall [n x R]
   uint8_t* mask;          // optional: 1 where the wall fired [n x R]
+  float* frec;            // optional (with ytil): the coupling sum J g(x) [n x R]
   const int8_t* sgn_in;   // dSB: sgn(x_k) [n x R] gathered instead of x (NULL: use x)
   int8_t* sgn_out;        // dSB: sgn(x_{k+1}) written with x_{k+1} (may be NULL)
   int32_t unroll;         // neighbours in flight per thread (4)
@@ -140,6 +141,7 @@ struct AdjArgs {
   const float* x;            // x_k (phase 2) or x_S (init)
   const float* ytil;         // y~_k
   const uint8_t* mask;       // m_k
+  const float* frec;         // J x_k recorded by the forward recomputation
   float* lx;                 // adjoint of x
   float* ly;                 // adjoint of y
   float* lyt;                // adjoint of y~ (gathered by neighbours in phase 2)
