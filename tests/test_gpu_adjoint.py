@@ -78,7 +78,8 @@ def test_checkpoint_interval_does_not_change_gradients():
         if ref is None:
             ref = (loss, g)
             continue
-        assert loss == ref[0]
+        # FP64 block sums are combined with atomics: order-dependent in the last place
+        assert loss == pytest.approx(ref[0], rel=1e-13)
         for k in ("dt", "c0", "w_q", "w_c"):
             assert g[k] == pytest.approx(ref[1][k], rel=1e-9, abs=1e-12)
         np.testing.assert_allclose(g["sched"], ref[1]["sched"], rtol=1e-9, atol=1e-12)
