@@ -55,7 +55,9 @@ def _deps():
 
 
 def build(verbose=False, force=False, ptxas_verbose=False):
+    """Compile what is stale; SB_EXTRA_NVCC (environment) appends nvcc flags."""
     os.makedirs(BUILD, exist_ok=True)
+    extra = os.environ.get("SB_EXTRA_NVCC", "").split()
     deps = _deps()
     nvcc = _nvcc()
     jobs = []
@@ -66,7 +68,7 @@ def build(verbose=False, force=False, ptxas_verbose=False):
         objs.append(obj)
         if force or _stale(obj, [src] + deps):
             cmd = [nvcc, ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-                   "--extended-lambda"] + CU_FLAGS.get(f, []) + ["-c", src, "-o", obj]
+                   "--extended-lambda"] + CU_FLAGS.get(f, []) + extra + ["-c", src, "-o", obj]
             if ptxas_verbose:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append(cmd)

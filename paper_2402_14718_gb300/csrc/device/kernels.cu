@@ -131,8 +131,11 @@ __device__ __forceinline__ unsigned group_mask(int G) {
 // neighbours in flight at once.
 // MODE: 0 aSB, 1 bSB, 2 dSB gathering x (sgn at use), 3 dSB gathering int8
 // signs, 4 bSB also recording the pre-wall momentum and the wall mask.
+#ifndef SB_STEP_MIN_BLOCKS
+#define SB_STEP_MIN_BLOCKS 1
+#endif
 template <int V, int NCH, int MODE, typename JT>
-__global__ void __launch_bounds__(kBlock) k_step(const StepArgs a) {
+__global__ void __launch_bounds__(kBlock, SB_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
   constexpr int VARIANT = MODE == 3 ? 2 : (MODE == 4 ? 1 : MODE);
   constexpr bool use_sgn = MODE == 3;
   constexpr bool record = MODE == 4;
