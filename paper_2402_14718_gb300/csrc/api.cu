@@ -41,6 +41,7 @@ struct GraphCache {
 
 struct sb_ctx {
   int device = 0;
+  bool tiles_built = false;  // block tables of the tiled kernel are built on first use
   int32_t E = 1;
   int32_t n = 0;
   int64_t nnz = 0;
@@ -397,6 +398,15 @@ sb_status setup_tiles(sb_ctx* c, const int32_t* rowptr, const int32_t* col) {
   return SB_OK;
 }
 
+// Build the tiled kernel's block tables the first time the tiled kernel is wanted.
+sb_status ensure_tiles(sb_ctx* c) {
+  if (c->tiles_built) return SB_OK;
+  sb_status st = setup_tiles(c, c->h_rowptr.data(), c->h_col.data());
+  if (st) return st;
+  c->tiles_built = true;
+  return SB_OK;
+}
+
 sb_status create_common(sb_ctx* c, const int32_t* rowptr, const int32_t* col, const double* qval,
                         const double* qlin) {
   SB_CUDA(cudaGetDevice(&c->device));
@@ -456,7 +466,6 @@ sb_status create_common(sb_ctx* c, const int32_t* rowptr, const int32_t* col, co
   SB_CUDA(cudaMemcpy(c->offset.data(), c->d_offset, c->E * 8, cudaMemcpyDeviceToHost));
   SB_CUDA(cudaMemcpy(c->sigma.data(), c->d_sigma, c->E * 8, cudaMemcpyDeviceToHost));
   SB_CUDA(cudaMemcpy(c->c0_auto.data(), c->d_c0auto, c->E * 8, cudaMemcpyDeviceToHost));
-  if ((st = setup_tiles(c, rowptr, col))) return st;
   SB_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   return SB_OK;
 }
@@ -492,6 +501,10 @@ sbd::Tiling step_tiling(const sb_ctx* c) {
 sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t steps,
                         const float* sched, cudaStream_t stream) {
   if (steps <= 0) return SB_OK;
+  if (c->use_tiled && c->R % sbd::kTileRT == 0) {
+    sb_status st0 = ensure_tiles(c);
+    if (st0) return st0;
+  }
   const bool dsb16 = variant == SB_DSB && c->dsb_signs && c->step_rt == 0 && c->groups == 1 &&
                      sbd::dsb16_ok(c->R) &&
                      !(c->tiled_ok && c->use_tiled && c->R % sbd::kTileRT == 0);
@@ -1034,7 +1047,7 @@ sb_status sb_set_weights(sb_ctx* ctx, const int8_t* cls, const double* quality, 
   if (ctx->d_tz) cudaFree(ctx->d_tz);
   ctx->d_tz = nullptr;
   ctx->graph.reset();
-  if ((st = setup_tiles(ctx, rp, col))) return st;
+  if (ctx->tiles_built && (st = setup_tiles(ctx, rp, col))) return st;
   ctx->have_classes = true;
   return SB_OK;
 }
@@ -1255,7 +1268,11 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
   if (err == cudaSuccess) err = sbd::launch_linear_schedule(sched, trial_steps, 1.0, s);
   for (size_t k = 0; k < cands.size() && err == cudaSuccess; ++k) {
     const Cand& c = cands[k];
-    if (c.tiled && !(ctx->tiled_ok && replicas % sbd::kTileRT == 0)) continue;
+    if (c.tiled) {
+      if (replicas % sbd::kTileRT != 0) continue;
+      if ((st = ensure_tiles(ctx))) break;
+      if (!ctx->tiled_ok) continue;
+    }
     if (c.rt && (replicas % c.rt != 0)) continue;
     if (c.groups > 1) {
       const int rt = replicas / c.groups;
