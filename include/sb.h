@@ -19,6 +19,9 @@
  *    ascending within a row, no diagonal entry, int32 indices.
  *  - SB state is replica-minor: element (i, r) of an N x R array lives at
  *    [i * R + r].
+ *  - A context belongs to the device that was current when it was created;
+ *    call it with that device current. A context is not thread-safe: calls on
+ *    one context must not overlap; different contexts are independent.
  */
 #ifndef SB_H
 #define SB_H
@@ -198,6 +201,8 @@ sb_status sb_create_batch(int32_t n_events, const int32_t* n_per_event,
                           const int32_t* col, const double* qval, const double* qlin,
                           sb_jprec prec, sb_ctx** out);
 
+/* Release every device buffer of the context (waits for the device first).
+ * NULL is accepted. */
 void sb_destroy(sb_ctx* ctx);
 
 /* Sizes and FP64 scalars of event `e` (0 for a single QUBO). Any pointer may be NULL. */
