@@ -43,11 +43,17 @@ def parse():
     ap.add_argument("--no-ttt", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--study", default="",
-                    choices=["", "paper-sizes", "c0-scan", "schedule", "build", "adjoint"],
+                    choices=["", "paper-sizes", "c0-scan", "schedule", "build", "adjoint",
+                             "kernels"],
                     help="experiments (not bench lines): energy traces and 50-shot statistics "
                          "at the paper's QUBO sizes, the c0 scan, schedule learning by the adjoint")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "untiled"],
-                    help="step kernel: auto (row-block tiled when R %% 32 == 0) or untiled")
+    ap.add_argument("--kernel", default="auto",
+                    choices=["auto", "untiled", "rowgroup2", "rowgroup4", "stream", "tiled"],
+                    help="step kernel: auto (sb_autotune picks), or a fixed one: untiled (one "
+                         "row per warp), rowgroup2/4 (rows per warp), stream (bulk-copy ring), "
+                         "tiled (shared-memory row blocks)")
+    ap.add_argument("--rows-per-cta", type=int, default=0,
+                    help="with a fixed --kernel: rows per CTA (SB_OPT_STEP_RPC)")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling driver: set up the workload, run this many SB steps with "
                          "one direct launch each (no graph, no timing), exit")
@@ -83,17 +89,53 @@ def job_value(units_per_rank, world_size, ms):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step-kernel
-# launch from the ncu capture summarised in profiles/k_step_event1000_ncu.md,
-# valid only for the kernel sources that were captured (sha256 prefix of
-# kernels.cu + kernels.cuh); any other source reports null.
-MEASURED_TRAFFIC = {("event1000", "bsb", "14e9279fcb6b4ecf"): 126945792}
+# launch from the ncu captures summarised in profiles/, keyed by workload,
+# variant, kernel, its configuration and the step-kernel sources (sha256 prefix
+# of kernels.cu, kernels.cuh, rw.cu, stream.cu); anything else reports null.
+MEASURED_TRAFFIC = {}
+
+
+def set_kernel(sb, ctx, name):
+    """Fix the step kernel by its options; returns the kernel's name."""
+    if name == "rowgroup2" or name == "rowgroup4":
+        sb.sb_set_option(ctx, sb.SB_OPT_ROWS_PER_WARP, int(name[-1]))
+        return "k_step_rw"
+    if name == "stream":
+        sb.sb_set_option(ctx, sb.SB_OPT_STREAM, 1)
+        return "k_step_stream"
+    if name == "tiled":
+        sb.sb_set_option(ctx, sb.SB_OPT_TILED, 1)
+        return "k_step_tiled"
+    return "k_step"
+
+
+def tuned_kernel(cfg, variant, R):
+    """Name of the step kernel the context runs with autotuned configuration cfg
+    (the selection order of the library: row-group, tiled, dSB signs, one replica)."""
+    if cfg["rows_per_warp"] and R % 128 == 0:
+        return "k_step_rw"
+    if cfg["tiled"] and R % 32 == 0:
+        return "k_step_tiled"
+    if (variant == "dsb" and cfg["tile"] == 0 and cfg["groups"] == 1 and R % 16 == 0
+            and R // 16 <= 32 and (R // 16) & (R // 16 - 1) == 0):
+        return "k_step_dsb16"
+    if R == 1:
+        return "k_step_r1"
+    return "k_step"
+
+
+def R_cfg(tuned):
+    """Rows per warp / rows per CTA of the tuned configuration (part of the traffic key)."""
+    if tuned is None:
+        return None
+    return (tuned[0]["rows_per_warp"], tuned[0]["rows_per_cta"], tuned[0]["tile"])
 
 
 def kernel_source_hash():
     import hashlib
     d = os.path.join(ROOT, "paper_2402_14718_gb300", "csrc", "device")
     h = hashlib.sha256()
-    for f in ("kernels.cu", "kernels.cuh"):
+    for f in ("kernels.cu", "kernels.cuh", "rw.cu", "stream.cu"):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -242,10 +284,13 @@ def run_ours(args):
     N, nnz = q.n, q.nnz
     ctx = sb.sb_create(N, q.rowptr, q.col, q.val, q.lin, prec)
     tuned = None
-    if args.kernel == "untiled":
-        sb.sb_set_option(ctx, sb.SB_OPT_TILED, 0)
-    elif not args.profile_steps:
+    if args.kernel == "auto" and not args.profile_steps:
         tuned = sb.sb_autotune(ctx, args.variant, R, trial_steps=30)   # untimed set-up
+        kname = tuned_kernel(tuned[0], args.variant, R)
+    else:
+        kname = set_kernel(sb, ctx, args.kernel)
+        if args.rows_per_cta:
+            sb.sb_set_option(ctx, sb.SB_OPT_STEP_RPC, args.rows_per_cta)
     sched = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
     if args.profile_steps:
         sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
@@ -306,8 +351,9 @@ def run_ours(args):
     achieved = alg_bytes / kstep_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm,
-                "traffic": MEASURED_TRAFFIC.get((args.workload, args.variant, kernel_source_hash())),
-                "kernel": "k_step",
+                "traffic": MEASURED_TRAFFIC.get((args.workload, args.variant, kname, R_cfg(tuned),
+                                                  kernel_source_hash())),
+                "kernel": kname,
                 "peak_source": src, "alg_bytes_per_launch": alg_bytes,
                 "kstep_us": kstep_s * 1e6}
 
@@ -588,7 +634,8 @@ def run_batch(args):
                        "autotune": cfg, "autotune_us_per_step": us, "host_build_s": t_build},
             "roofline": {"bound": "hbm", "achieved": alg_bytes / sweep / 1e9, "peak": hbm,
                          "unit": "GB/s", "frac": alg_bytes / sweep / 1e9 / hbm, "traffic": None,
-                         "kernel": "k_step", "peak_source": src, "alg_bytes_per_launch": alg_bytes,
+                         "kernel": tuned_kernel(cfg, variant, R), "peak_source": src,
+                         "alg_bytes_per_launch": alg_bytes,
                          "kstep_us": sweep * 1e6},
             "plain_fp32_spin_updates_per_s": plain,
             "batched_vs_plain_throughput": value / plain,
@@ -627,6 +674,47 @@ def run_study(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream(dev)
+    if args.study == "kernels":
+        # every step kernel on the workload: microseconds per step (graph replay,
+        # CUDA events, best of 3 x 200 steps) and bit-equality with the untiled kernel
+        w = WORKLOADS[args.workload]
+        R = w["replicas"]
+        ev = sb.sb_event_generate(w["seed"], sb.event_params(n_tracks=w["n_tracks"],
+                                                             noise_frac=w["noise_frac"]))
+        q = sb.sb_qubo_build(ev, sb.build_params(**w["cuts"]))
+        prec = sb.SB_J_BF16 if w["jprec"] == "bf16" else sb.SB_J_FP32
+        S = 200
+        sched = torch.tensor(np.linspace(0, 1, S).astype(np.float32), device=dev)
+        kernels = [("untiled", 0), ("untiled", 32), ("rowgroup2", 0), ("rowgroup2", 32),
+                   ("rowgroup4", 0), ("stream", 0), ("tiled", 0)]
+        for variant in ("bsb", "dsb"):
+            ref = None
+            for name, rpc in kernels:
+                ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, prec)
+                kname = set_kernel(sb, ctx, name)
+                sb.sb_set_option(ctx, sb.SB_OPT_STEP_RPC, rpc)
+                sb.sb_run(ctx, variant, 1.0, 0.0, 0.5, 0, R, 7, None, stream)
+                sb.sb_advance(ctx, variant, 1.0, 0.0, 0.5, S, sched, stream)
+                x, y = sb.sb_get_state(ctx)
+                same = None
+                if ref is None:
+                    ref = (x, y)
+                else:
+                    same = bool(np.array_equal(ref[0], x) and np.array_equal(ref[1], y))
+                best = 1e30
+                for _ in range(3):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    sb.sb_advance(ctx, variant, 1.0, 0.0, 0.5, S, sched, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    best = min(best, e0.elapsed_time(e1) * 1e3 / S)
+                print(json.dumps({"study": "kernels", "workload": args.workload, "N": q.n,
+                                  "nnz": q.nnz, "R": R, "variant": variant, "kernel": kname,
+                                  "option": name, "rows_per_cta": rpc, "us_per_step": best,
+                                  "same_state_as_first": same}), flush=True)
+                sb.sb_destroy(ctx)
+        return 0
     if args.study == "paper-sizes":
         # section "Results": a0 = dt = 1, fixed c0, 50 shots; bSB and dSB
         S, R, every = (args.sb_steps or 2000), 50, 20

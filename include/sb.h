@@ -370,15 +370,34 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
  * (stream access-policy window; the persisting L2 set-aside of this process's
  * context is raised to the device maximum). Does not change results. */
 #define SB_OPT_L2_PERSIST 7
+/* SB_OPT_STREAM (8): 1 uses the streamed step kernel when R is a multiple of
+ * 64: one CTA per SM walks a contiguous chunk of rows in blocks of 32; a
+ * producer warp copies each block's union of neighbour x rows (one replica
+ * tile of 256, 128 or 64 replicas) into a shared-memory ring with bulk
+ * asynchronous copies and eight consumer warps (four rows each) accumulate
+ * from it. Same FMA order as the untiled kernel, so the states are identical.
+ * Its waits are bounded (2 s): if one gives up, the kernel returns early and
+ * the next of sb_best, sb_energy (current state) or sb_get_state returns
+ * SB_ERR_TIMEOUT once (the state of that run is not valid).
+ * Applies to every variant (dSB gathers FP32 positions on this path). */
+#define SB_OPT_STREAM 8
+/* SB_OPT_ROWS_PER_WARP (9): 2 or 4 uses the row-group step kernel when R is a
+ * multiple of 128: one warp owns that many consecutive rows and walks the
+ * sorted union of their columns, loading each neighbour row of x once for all
+ * of them (the union is built on first use). 0 (default) turns it off. Same
+ * FMA order as the untiled kernel, so the states are identical. With it,
+ * SB_OPT_STEP_RPC sets rows per CTA (divided by the group size) and
+ * SB_OPT_STEP_RT = 128 makes a warp cover 128 replicas instead of 256. */
+#define SB_OPT_ROWS_PER_WARP 9
 sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
 
 /*
- * sb_autotune -- pick the step-kernel configuration (tiled or untiled kernel,
- * replica-tile width, rows per CTA) for this context, variant and replica
+ * sb_autotune -- pick the step-kernel configuration (tiled, untiled or
+ * row-group kernel, replica-tile width, rows per CTA) for this context, variant and replica
  * count by timing each candidate for `trial_steps` steps with CUDA events on
  * `stream`, and set it on the context. Results do not depend on the choice.
- * Outputs (host, may be NULL): out_cfg[6] = {tiled, tile width, rows per CTA, unroll,
- * replica groups, L2 persist},
+ * Outputs (host, may be NULL): out_cfg[7] = {tiled, tile width, rows per CTA, unroll,
+ * replica groups, L2 persist, rows per warp},
  * out_us_per_step = the best time. Synchronous; discards the current state.
  */
 sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t trial_steps,

@@ -11,12 +11,15 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (SB_ASB, SB_BSB, SB_DSB, SB_J_BF16, SB_J_FP32, SB_OPT_GRAPH, SB_OPT_TILED,
-                   SbError, check, lib)
+from ._lib import (SB_ASB, SB_BSB, SB_DSB, SB_J_BF16, SB_J_FP32, SB_OPT_DSB_SIGNS, SB_OPT_GRAPH,
+                   SB_OPT_L2_PERSIST, SB_OPT_REPLICA_GROUPS, SB_OPT_ROWS_PER_WARP, SB_OPT_STEP_RPC,
+                   SB_OPT_STEP_RT, SB_OPT_STEP_UNROLL, SB_OPT_STREAM, SB_OPT_TILED, SbError, check,
+                   lib)
 
 __all__ = [
     "SB_ASB", "SB_BSB", "SB_DSB", "SB_J_FP32", "SB_J_BF16", "SB_OPT_GRAPH", "SB_OPT_TILED",
-    "SbError",
+    "SB_OPT_STREAM", "SB_OPT_ROWS_PER_WARP", "SB_OPT_STEP_RT", "SB_OPT_STEP_RPC",
+    "SB_OPT_STEP_UNROLL", "SB_OPT_DSB_SIGNS", "SB_OPT_REPLICA_GROUPS", "SB_OPT_L2_PERSIST", "SbError",
     "event_params", "build_params", "sb_event_generate", "sb_qubo_build", "sb_tracks",
     "sb_qubo_build_device",
     "sb_create", "sb_create_batch", "sb_destroy", "sb_info", "sb_run", "sb_advance",
@@ -323,13 +326,15 @@ def sb_energy_noalloc(n, d_rowptr, d_col, d_qval, d_qlin, d_x, d_spins, replicas
 
 def sb_autotune(ctx, variant, replicas, trial_steps=50, stream=None):
     """Time the step-kernel candidates and keep the fastest; returns
-    ({"tiled", "tile", "rows_per_cta"}, microseconds per step)."""
-    cfg = np.zeros(6, np.int32)
+    ({"tiled", "tile", "rows_per_cta", "unroll", "groups", "l2_persist",
+    "rows_per_warp"}, microseconds per step)."""
+    cfg = np.zeros(7, np.int32)
     us = ctypes.c_float()
     check(lib.sb_autotune(ctx.handle, _variant(variant), int(replicas), int(trial_steps),
                           cfg.ctypes.data_as(ctypes.c_void_p), ctypes.byref(us), _stream(stream)))
     return {"tiled": int(cfg[0]), "tile": int(cfg[1]), "rows_per_cta": int(cfg[2]),
-            "unroll": int(cfg[3]), "groups": int(cfg[4]), "l2_persist": int(cfg[5])}, us.value
+            "unroll": int(cfg[3]), "groups": int(cfg[4]), "l2_persist": int(cfg[5]),
+            "rows_per_warp": int(cfg[6])}, us.value
 
 
 def sb_set_weights(ctx, cls, quality, w_q, w_c):

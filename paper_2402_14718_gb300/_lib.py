@@ -23,6 +23,8 @@ SB_OPT_STEP_UNROLL = 4
 SB_OPT_DSB_SIGNS = 5
 SB_OPT_REPLICA_GROUPS = 6
 SB_OPT_L2_PERSIST = 7
+SB_OPT_STREAM = 8
+SB_OPT_ROWS_PER_WARP = 9
 
 
 class SbEventParams(ctypes.Structure):

@@ -27,7 +27,7 @@ const int kEnergyRowsMin = 64;
 struct GraphCache {
   cudaGraphExec_t exec = nullptr;
   int variant = -1, steps = -1, R = -1, cur = -1, G = -1, tiled = -1, rpc = -1, tiles = -1;
-  int unroll = -1, sgn = -1, groups = -1;
+  int unroll = -1, sgn = -1, groups = -1, stream = -1, rw = -1, nch = -1;
   float a0 = 0.f, dt = 0.f;
   const float* sched = nullptr;
   void reset() {
@@ -112,6 +112,28 @@ struct sb_ctx {
   int l2_persist = 0; // mark each step's source x as L2-persisting (access-policy window)
   int8_t* d_sgn[2] = {nullptr, nullptr};
   int sms = 0;
+  // streamed step kernel (k_step_stream): per-CTA row chunks cut into blocks
+  // with their neighbour-column unions; built on first use
+  int use_stream = 0;
+  bool stream_built = false;
+  bool stream_ok = false;
+  int32_t stream_grid = 0;
+  int32_t stream_jbuf = 0;
+  int32_t* d_s_cta = nullptr;
+  int32_t* d_s_blk = nullptr;
+  int32_t* d_s_rjo = nullptr;
+  int32_t* d_s_ucol = nullptr;
+  uint32_t* d_s_umask = nullptr;
+  int* d_err = nullptr;  // set by a kernel whose bounded wait gave up
+  // row-group step kernel (k_step_rw): union entries of RW consecutive rows
+  int rw_rows = 0;       // 0: off; 2 or 4 rows per warp
+  int rw_built = 0;      // RW the tables below were built for (0: none)
+  int32_t rw_ngroups = 0;
+  int64_t rw_E = 0;
+  int32_t* d_rw_gptr = nullptr;
+  int32_t* d_rw_ent = nullptr;
+  int32_t* d_rw_pos = nullptr;  // CSR position of each entry's RW slots (-1: absent)
+  void* d_rw_ejv = nullptr;     // J of each entry's RW slots
 };
 
 namespace {
@@ -249,6 +271,17 @@ void free_all(sb_ctx* c) {
   dfree(c->d_cls);
   dfree(c->d_quality);
   dfree(c->d_nconf);
+  dfree(c->d_s_cta);
+  dfree(c->d_s_blk);
+  dfree(c->d_s_rjo);
+  dfree(c->d_s_ucol);
+  dfree(c->d_s_umask);
+  dfree(c->d_err);
+  dfree(c->d_rw_gptr);
+  dfree(c->d_rw_ent);
+  dfree(c->d_rw_pos);
+  if (c->d_rw_ejv) cudaFree(c->d_rw_ejv);
+  c->d_rw_ejv = nullptr;
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->cap_stream = nullptr;
 }
@@ -407,6 +440,233 @@ sb_status ensure_tiles(sb_ctx* c) {
   return SB_OK;
 }
 
+// Tables of the streamed step kernel. Rows are split into `grid` contiguous
+// chunks of about equal work (nonzeros + 8 per row), one per CTA; each chunk
+// into blocks of kStreamBR rows. A block lists the sorted union of its rows'
+// columns, one mask bit per block row that uses the column, padded with empty
+// entries (column 0, mask 0) to a whole number (>= 1) of kStreamSPS-entry
+// stages. jmax: the largest 16-byte aligned span of a block's J values.
+struct StreamHost {
+  bool ok = false;
+  std::vector<int32_t> cta, row0, e0, ucol;
+  std::vector<uint32_t> umask;
+  std::vector<int32_t> blk;  // 4 per block (+ sentinel): row0, e0, first J element, J bytes
+  std::vector<int32_t> rjo;  // [n] rowptr[i] - first J element of i's block
+  int64_t jmax = 16;
+};
+
+StreamHost build_stream(int32_t n, const int32_t* rp, const int32_t* col, int grid, int esz) {
+  StreamHost t;
+  std::vector<int32_t> chunk(grid + 1, n);
+  chunk[0] = 0;
+  const long long total = (long long)rp[n] + 8LL * n;
+  int32_t row = 0;
+  long long acc = 0;
+  for (int c = 1; c < grid; ++c) {
+    const long long target = total * c / grid;
+    while (row < n && acc + (rp[row + 1] - rp[row]) + 8 <= target) {
+      acc += (rp[row + 1] - rp[row]) + 8;
+      ++row;
+    }
+    chunk[c] = row;
+  }
+  std::vector<int32_t> mark(n, -1), uni;
+  std::vector<uint32_t> mk;
+  for (int c = 0; c < grid; ++c) {
+    t.cta.push_back((int32_t)t.row0.size());
+    for (int32_t r = chunk[c]; r < chunk[c + 1]; r += sbd::kStreamBR) {
+      const int32_t r1 = std::min(r + sbd::kStreamBR, chunk[c + 1]);
+      t.row0.push_back(r);
+      t.e0.push_back((int32_t)t.ucol.size());
+      uni.clear();
+      for (int32_t i = r; i < r1; ++i)
+        for (int32_t p = rp[i]; p < rp[i + 1]; ++p)
+          if (mark[col[p]] < 0) {
+            mark[col[p]] = 0;
+            uni.push_back(col[p]);
+          }
+      std::sort(uni.begin(), uni.end());
+      for (size_t k = 0; k < uni.size(); ++k) mark[uni[k]] = (int32_t)k;
+      mk.assign(uni.size(), 0u);
+      for (int32_t i = r; i < r1; ++i)
+        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) mk[mark[col[p]]] |= 1u << (i - r);
+      for (int32_t v : uni) mark[v] = -1;
+      t.ucol.insert(t.ucol.end(), uni.begin(), uni.end());
+      t.umask.insert(t.umask.end(), mk.begin(), mk.end());
+      size_t pad = sbd::kStreamSPS - uni.size() % sbd::kStreamSPS;
+      if (pad == (size_t)sbd::kStreamSPS && !uni.empty()) pad = 0;
+      t.ucol.insert(t.ucol.end(), pad, 0);
+      t.umask.insert(t.umask.end(), pad, 0u);
+      const long long lo = ((long long)rp[r] * esz) & ~15LL;
+      const long long hi = ((long long)rp[r1] * esz + 15) & ~15LL;
+      t.jmax = std::max<int64_t>(t.jmax, hi - lo);
+      if (t.ucol.size() > (size_t)INT32_MAX / 2) return t;
+    }
+  }
+  t.cta.push_back((int32_t)t.row0.size());
+  t.row0.push_back(n);
+  t.e0.push_back((int32_t)t.ucol.size());
+  // invariants the kernel relies on: every block has >= 1 whole stage, columns
+  // are in range, and each row's mask bits count exactly its nonzeros
+  const size_t nblk = t.row0.size() - 1;
+  std::vector<int32_t> cnt(n, 0);
+  for (size_t b = 0; b < nblk; ++b) {
+    const int32_t e0 = t.e0[b], e1 = t.e0[b + 1];
+    if (e1 <= e0 || (e1 - e0) % sbd::kStreamSPS || t.row0[b + 1] - t.row0[b] > sbd::kStreamBR ||
+        t.row0[b + 1] <= t.row0[b])
+      return t;
+    for (int32_t e = e0; e < e1; ++e) {
+      if (t.ucol[e] < 0 || t.ucol[e] >= n) return t;
+      for (uint32_t m = t.umask[e]; m; m &= m - 1) {
+        const int q = __builtin_ctz(m);
+        if (t.row0[b] + q >= t.row0[b + 1]) return t;
+        ++cnt[t.row0[b] + q];
+      }
+    }
+  }
+  for (int32_t i = 0; i < n; ++i)
+    if (cnt[i] != rp[i + 1] - rp[i]) return t;
+  t.rjo.assign(n, 0);
+  for (size_t b = 0; b < nblk; ++b) {
+    const int64_t lo = ((int64_t)rp[t.row0[b]] * esz) & ~int64_t(15);
+    const int64_t hi = ((int64_t)rp[t.row0[b + 1]] * esz + 15) & ~int64_t(15);
+    if (lo / esz > INT32_MAX) return t;
+    t.blk.insert(t.blk.end(), {t.row0[b], t.e0[b], (int32_t)(lo / esz), (int32_t)(hi - lo)});
+    for (int32_t i = t.row0[b]; i < t.row0[b + 1]; ++i) t.rjo[i] = rp[i] - (int32_t)(lo / esz);
+  }
+  t.blk.insert(t.blk.end(), {n, t.e0[nblk], 0, 0});
+  t.ok = true;
+  return t;
+}
+
+// Build the streamed kernel's tables the first time it is wanted (one CTA per SM).
+sb_status ensure_stream(sb_ctx* c) {
+  if (c->stream_built) return SB_OK;
+  if (!c->sms) SB_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
+  SB_CUDA(sbd::stream_prepare());
+  StreamHost t = build_stream(c->n, c->h_rowptr.data(), c->h_col.data(), c->sms, c->jbf16 ? 2 : 4);
+  c->stream_built = true;
+  c->stream_ok = false;
+  if (!t.ok) return SB_OK;  // the untiled kernel serves every run
+  sb_status st;
+  if ((st = dalloc(&c->d_s_cta, t.cta.size())) || (st = dalloc(&c->d_s_blk, t.blk.size())) ||
+      (st = dalloc(&c->d_s_rjo, t.rjo.size())) || (st = dalloc(&c->d_s_ucol, t.ucol.size())) ||
+      (st = dalloc(&c->d_s_umask, t.umask.size())))
+    return st;
+  SB_CUDA(cudaMemcpy(c->d_s_cta, t.cta.data(), t.cta.size() * 4, cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(c->d_s_blk, t.blk.data(), t.blk.size() * 4, cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(c->d_s_rjo, t.rjo.data(), t.rjo.size() * 4, cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(c->d_s_ucol, t.ucol.data(), t.ucol.size() * 4, cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(c->d_s_umask, t.umask.data(), t.umask.size() * 4, cudaMemcpyHostToDevice));
+  c->stream_grid = c->sms;
+  c->stream_jbuf = (int32_t)t.jmax;
+  c->stream_ok = true;
+  return SB_OK;
+}
+
+// Tables of the row-group kernel: rows in groups of RW consecutive rows; a
+// group's entries are the sorted union of its rows' columns (a k-way merge of
+// the CSR rows), each with an RW-bit mask and the CSR position of every slot.
+struct RwHost {
+  bool ok = false;
+  std::vector<int32_t> gptr, ent, pos;
+};
+
+RwHost build_rw(int32_t n, const int32_t* rp, const int32_t* col, int RW) {
+  RwHost t;
+  if (n >= (1 << 27) || RW < 2 || RW > sbd::kRwMaxRows) return t;
+  const int32_t ng = (n + RW - 1) / RW;
+  t.gptr.reserve((size_t)ng + 1);
+  t.ent.reserve((size_t)rp[n]);
+  t.pos.reserve((size_t)rp[n] * RW);
+  t.gptr.push_back(0);
+  for (int32_t g = 0; g < ng; ++g) {
+    int32_t p[sbd::kRwMaxRows], pe[sbd::kRwMaxRows];
+    for (int q = 0; q < RW; ++q) {
+      const int32_t row = g * RW + q;
+      p[q] = row < n ? rp[row] : 0;
+      pe[q] = row < n ? rp[row + 1] : 0;
+    }
+    for (;;) {
+      int32_t cmin = INT32_MAX;
+      for (int q = 0; q < RW; ++q)
+        if (p[q] < pe[q]) cmin = std::min(cmin, col[p[q]]);
+      if (cmin == INT32_MAX) break;
+      int32_t mask = 0;
+      for (int q = 0; q < RW; ++q) {
+        if (p[q] < pe[q] && col[p[q]] == cmin) {
+          mask |= 1 << q;
+          t.pos.push_back(p[q]++);
+        } else {
+          t.pos.push_back(-1);
+        }
+      }
+      t.ent.push_back((cmin << 4) | mask);
+    }
+    if (t.ent.size() > (size_t)INT32_MAX / 8) return t;
+    t.gptr.push_back((int32_t)t.ent.size());
+  }
+  t.ok = true;
+  return t;
+}
+
+// (Re)fill the entries' J slots from the current J (after create or a weight change).
+sb_status refill_rw(sb_ctx* c) {
+  if (!c->rw_built) return SB_OK;
+  SB_CUDA(sbd::launch_fill_ejv(c->d_J, c->jbf16, c->d_rw_pos, c->rw_E * c->rw_built, c->d_rw_ejv,
+                               0));
+  SB_CUDA(cudaDeviceSynchronize());
+  return SB_OK;
+}
+
+// Build the row-group tables for RW rows per warp the first time they are wanted.
+sb_status ensure_rw(sb_ctx* c, int RW) {
+  if (c->rw_built == RW) return SB_OK;
+  RwHost t = build_rw(c->n, c->h_rowptr.data(), c->h_col.data(), RW);
+  dfree(c->d_rw_gptr);
+  dfree(c->d_rw_ent);
+  dfree(c->d_rw_pos);
+  if (c->d_rw_ejv) cudaFree(c->d_rw_ejv);
+  c->d_rw_ejv = nullptr;
+  c->rw_built = 0;
+  if (!t.ok) return SB_OK;  // the untiled kernel serves every run
+  sb_status st;
+  if ((st = dalloc(&c->d_rw_gptr, t.gptr.size())) || (st = dalloc(&c->d_rw_ent, t.ent.size())) ||
+      (st = dalloc(&c->d_rw_pos, t.pos.size())))
+    return st;
+  {
+    cudaError_t e = cudaMalloc(&c->d_rw_ejv, std::max<size_t>(t.pos.size(), 1) * (c->jbf16 ? 2 : 4));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->d_rw_ejv = nullptr;
+      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      return SB_ERR_OOM;
+    }
+  }
+  SB_CUDA(cudaMemcpy(c->d_rw_gptr, t.gptr.data(), t.gptr.size() * 4, cudaMemcpyHostToDevice));
+  if (!t.ent.empty()) {
+    SB_CUDA(cudaMemcpy(c->d_rw_ent, t.ent.data(), t.ent.size() * 4, cudaMemcpyHostToDevice));
+    SB_CUDA(cudaMemcpy(c->d_rw_pos, t.pos.data(), t.pos.size() * 4, cudaMemcpyHostToDevice));
+  }
+  c->rw_ngroups = (int32_t)t.gptr.size() - 1;
+  c->rw_E = (int64_t)t.ent.size();
+  c->rw_built = RW;
+  return refill_rw(c);
+}
+
+// Report (and clear) the flag a kernel sets when one of its bounded waits gave up.
+sb_status check_wait_flag(const sb_ctx* c) {
+  int v = 0;
+  SB_CUDA(cudaMemcpy(&v, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v) {
+    SB_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
+    set_error("a step kernel gave up waiting for its shared-memory pipeline (code " +
+              std::to_string(v) + "); the state of that run is not valid");
+    return SB_ERR_TIMEOUT;
+  }
+  return SB_OK;
+}
+
 sb_status create_common(sb_ctx* c, const int32_t* rowptr, const int32_t* col, const double* qval,
                         const double* qlin) {
   SB_CUDA(cudaGetDevice(&c->device));
@@ -421,14 +681,19 @@ sb_status create_common(sb_ctx* c, const int32_t* rowptr, const int32_t* col, co
       (st = dalloc(&c->d_bestr, c->E)) || (st = dalloc(&c->d_T, n)))
     return st;
   {
-    cudaError_t e = cudaMalloc(&c->d_J, std::max<size_t>(nnz, 1) * (c->jbf16 ? 2 : 4));
+    // padded so that 16-byte aligned copies of any row range stay inside
+    const size_t jb = ((std::max<size_t>(nnz, 1) * (c->jbf16 ? 2 : 4) + 15) & ~size_t(15)) + 16;
+    cudaError_t e = cudaMalloc(&c->d_J, jb);
     if (e != cudaSuccess) {
       cudaGetLastError();
       c->d_J = nullptr;
       set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
       return SB_ERR_OOM;
     }
+    SB_CUDA(cudaMemset(c->d_J, 0, jb));
   }
+  if ((st = dalloc(&c->d_err, 1))) return st;
+  SB_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
   SB_CUDA(cudaMemcpy(c->d_rowptr, rowptr, (n + 1) * 4, cudaMemcpyHostToDevice));
   if (nnz) {
     SB_CUDA(cudaMemcpy(c->d_col, col, nnz * 4, cudaMemcpyHostToDevice));
@@ -501,12 +766,73 @@ sbd::Tiling step_tiling(const sb_ctx* c) {
 sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t steps,
                         const float* sched, cudaStream_t stream) {
   if (steps <= 0) return SB_OK;
+  if (c->use_stream) {
+    sb_status st0 = ensure_stream(c);
+    if (st0) return st0;
+  }
   if (c->use_tiled && c->R % sbd::kTileRT == 0) {
     sb_status st0 = ensure_tiles(c);
     if (st0) return st0;
   }
-  const bool dsb16 = variant == SB_DSB && c->dsb_signs && c->step_rt == 0 && c->groups == 1 &&
-                     sbd::dsb16_ok(c->R) &&
+  // streamed kernel: chosen, tables valid, a supported replica count, and a ring that fits
+  sbd::StreamArgs sa{};
+  size_t s_smem = 0;
+  if (c->use_stream && c->stream_ok && c->groups == 1) {
+    sa.W = sbd::stream_tile_width(c->R);
+    if (sa.W) s_smem = sbd::stream_smem(sa.W, c->stream_jbuf, &sa.nst);
+  }
+  const int streamed = s_smem ? 1 : 0;
+  // row-group kernel: chosen, R a multiple of 128, tables valid
+  int rw = 0, rw_nch = 0;
+  sbd::RwArgs ra{};
+  if (!streamed && c->rw_rows && c->groups == 1 && c->R % 128 == 0) {
+    sb_status st0 = ensure_rw(c, c->rw_rows);
+    if (st0) return st0;
+    if (c->rw_built == c->rw_rows) {
+      rw = c->rw_rows;
+      rw_nch = (c->R % 256 == 0 && c->step_rt != 128) ? 2 : 1;
+      ra.gptr = c->d_rw_gptr;
+      ra.ent = c->d_rw_ent;
+      ra.ejv = c->d_rw_ejv;
+      ra.h = c->d_h32;
+      ra.row_event = c->d_row_event;
+      ra.c0_ev = c->d_c0ev;
+      ra.sched = sched;
+      ra.a0 = (float)a0;
+      ra.dt = (float)dt;
+      ra.dta0 = (float)(dt * a0);
+      ra.y = c->d_y;
+      ra.n = c->n;
+      ra.R = c->R;
+      ra.ngroups = c->rw_ngroups;
+      ra.gpc = std::max(8, c->step_rpc > 0 ? c->step_rpc / rw : 0);
+    }
+  }
+  if (streamed) {
+    sa.rowptr = c->d_rowptr;
+    sa.J = c->d_J;
+    sa.h = c->d_h32;
+    sa.row_event = c->d_row_event;
+    sa.c0_ev = c->d_c0ev;
+    sa.sched = sched;
+    sa.a0 = (float)a0;
+    sa.dt = (float)dt;
+    sa.dta0 = (float)(dt * a0);
+    sa.y = c->d_y;
+    sa.n = c->n;
+    sa.R = c->R;
+    sa.cta_blk0 = c->d_s_cta;
+    sa.blk = reinterpret_cast<const int4*>(c->d_s_blk);
+    sa.rjo = c->d_s_rjo;
+    sa.ucol = c->d_s_ucol;
+    sa.umask = c->d_s_umask;
+    sa.grid = c->stream_grid;
+    sa.tiles = c->R / sa.W;
+    sa.jbuf_bytes = c->stream_jbuf;
+    sa.err = c->d_err;
+  }
+  const bool dsb16 = !streamed && !rw && variant == SB_DSB && c->dsb_signs && c->step_rt == 0 &&
+                     c->groups == 1 && sbd::dsb16_ok(c->R) &&
                      !(c->tiled_ok && c->use_tiled && c->R % sbd::kTileRT == 0);
   const sbd::Tiling t = dsb16 ? sbd::make_tiling_dsb16(c->R) : step_tiling(c);
   sbd::StepArgs a;
@@ -539,7 +865,8 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   a.mask = nullptr;
   a.sgn_in = nullptr;
   a.sgn_out = nullptr;
-  const int tiled = (c->tiled_ok && c->use_tiled && c->R % sbd::kTileRT == 0) ? 1 : 0;
+  const int tiled =
+      (!streamed && !rw && c->tiled_ok && c->use_tiled && c->R % sbd::kTileRT == 0) ? 1 : 0;
   sbd::TiledArgs ta;
   ta.blk_row0 = c->d_blk_row0;
   ta.blk_u0 = c->d_blk_u0;
@@ -558,7 +885,8 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   ta.n = c->n;
   ta.R = c->R;
   ta.nb = c->nb;
-  const int sgn = (variant == SB_DSB && c->dsb_signs && !tiled && c->R % 4 == 0) ? 1 : 0;
+  const int sgn =
+      (variant == SB_DSB && c->dsb_signs && !tiled && !streamed && !rw && c->R % 4 == 0) ? 1 : 0;
   if (sgn && !c->d_sgn[0]) {
     sb_status st2;
     const size_t cnt = (size_t)c->n * c->R;
@@ -587,6 +915,18 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
       a.sgn_in = c->d_sgn[cur];
       a.sgn_out = c->d_sgn[cur ^ 1];
     }
+    if (streamed) {
+      sa.k = k;
+      sa.xin = c->d_x[cur];
+      sa.xout = c->d_x[cur ^ 1];
+      return sbd::launch_step_stream(variant, c->jbf16, sa, s_smem, st);
+    }
+    if (rw) {
+      ra.k = k;
+      ra.xin = c->d_x[cur];
+      ra.xout = c->d_x[cur ^ 1];
+      return sbd::launch_step_rw(variant, c->jbf16, rw, rw_nch, ra, st);
+    }
     if (tiled) {
       ta.k = k;
       ta.xin = c->d_x[cur];
@@ -599,7 +939,8 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     return sbd::launch_step(variant, c->jbf16, t, a, st);
   };
   const size_t NR = (size_t)c->n * c->R;
-  const int ngroups = (!tiled && !dsb16 && c->groups > 1 && t.tiles == c->groups) ? c->groups : 1;
+  const int ngroups =
+      (!streamed && !rw && !tiled && !dsb16 && c->groups > 1 && t.tiles == c->groups) ? c->groups : 1;
   sbd::Tiling tg = t;
   if (ngroups > 1) tg.tiles = 1;
   // all steps for replica group g (tiles g), then the next group: each group's
@@ -640,7 +981,8 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   if (!(gc.exec && gc.variant == variant && gc.steps == steps && gc.R == c->R &&
         gc.cur == c->cur && gc.a0 == a.a0 && gc.dt == a.dt && gc.sched == sched && gc.G == t.G &&
         gc.tiled == tiled && gc.rpc == a.rpc && gc.tiles == t.tiles && gc.unroll == a.unroll &&
-        gc.sgn == sgn && gc.groups == ngroups)) {
+        gc.sgn == sgn && gc.groups == ngroups && gc.stream == streamed && gc.rw == rw &&
+        gc.nch == rw_nch)) {
     gc.reset();
     cudaGraph_t g = nullptr;
     SB_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -665,6 +1007,9 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     gc.unroll = a.unroll;
     gc.sgn = sgn;
     gc.groups = ngroups;
+    gc.stream = streamed;
+    gc.rw = rw;
+    gc.nch = rw_nch;
   }
   SB_CUDA(cudaGraphLaunch(gc.exec, stream));
   if (steps & 1) c->cur ^= 1;
@@ -899,6 +1244,8 @@ sb_status sb_get_state(const sb_ctx* ctx, float* x, float* y, int32_t on_device)
   const size_t bytes = (size_t)ctx->n * ctx->R * 4;
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   SB_CUDA(cudaDeviceSynchronize());
+  sb_status st = check_wait_flag(ctx);
+  if (st) return st;
   if (x) SB_CUDA(cudaMemcpy(x, ctx->d_x[ctx->cur], bytes, k));
   if (y) SB_CUDA(cudaMemcpy(y, ctx->d_y, bytes, k));
   return SB_OK;
@@ -925,6 +1272,7 @@ sb_status sb_energy(sb_ctx* ctx, const int8_t* spins, int32_t replicas, double* 
   }
   if ((st = readout(ctx, spins ? ctx->d_spins : nullptr, replicas, 0))) return st;
   SB_CUDA(cudaDeviceSynchronize());
+  if (!spins && (st = check_wait_flag(ctx))) return st;
   SB_CUDA(cudaMemcpy(out_E, ctx->d_Eall, (size_t)ctx->E * replicas * 8, cudaMemcpyDeviceToHost));
   return SB_OK;
 }
@@ -963,6 +1311,7 @@ sb_status sb_best(sb_ctx* ctx, uint8_t* out_T, double* out_E, int32_t* out_repli
   sb_status st = sb_readout_device(ctx, nullptr, nullptr, nullptr, out_T ? ctx->d_T : nullptr, 0);
   if (st) return st;
   SB_CUDA(cudaDeviceSynchronize());
+  if ((st = check_wait_flag(ctx))) return st;
   if (out_T) SB_CUDA(cudaMemcpy(out_T, ctx->d_T, ctx->n, cudaMemcpyDeviceToHost));
   if (out_E) SB_CUDA(cudaMemcpy(out_E, ctx->d_bestE, ctx->E * 8, cudaMemcpyDeviceToHost));
   if (out_replica)
@@ -1048,6 +1397,8 @@ sb_status sb_set_weights(sb_ctx* ctx, const int8_t* cls, const double* quality, 
   ctx->d_tz = nullptr;
   ctx->graph.reset();
   if (ctx->tiles_built && (st = setup_tiles(ctx, rp, col))) return st;
+  // the row-group kernel's entries carry J too
+  if ((st = refill_rw(ctx))) return st;
   ctx->have_classes = true;
   return SB_OK;
 }
@@ -1249,12 +1600,15 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
   cudaStream_t s = (cudaStream_t)stream;
   // candidates: (tiled, replica-tile width, rows per CTA); invalid ones are skipped
   struct Cand {
-    int tiled, rt, rpc, unroll, groups, l2;
+    int tiled, rt, rpc, unroll, groups, l2, rw;
   };
-  std::vector<Cand> cands = {{0, 0, 0, 4, 1, 0},   {0, 0, 32, 4, 1, 0}, {0, 0, 0, 4, 1, 1},
-                             {0, 0, 32, 4, 1, 1},  {0, 128, 0, 4, 1, 0}, {0, 128, 32, 4, 1, 0},
-                             {0, 64, 0, 4, 1, 0},  {0, 32, 0, 4, 1, 0}, {0, 0, 0, 4, 2, 0},
-                             {0, 0, 32, 4, 2, 0},  {0, 0, 0, 4, 4, 0},  {1, 0, 0, 4, 1, 0}};
+  std::vector<Cand> cands = {
+      {0, 0, 0, 4, 1, 0, 0},  {0, 0, 32, 4, 1, 0, 0},  {0, 0, 0, 4, 1, 1, 0},
+      {0, 0, 32, 4, 1, 1, 0}, {0, 128, 0, 4, 1, 0, 0}, {0, 128, 32, 4, 1, 0, 0},
+      {0, 64, 0, 4, 1, 0, 0}, {0, 32, 0, 4, 1, 0, 0},  {0, 0, 0, 4, 2, 0, 0},
+      {0, 0, 32, 4, 2, 0, 0}, {0, 0, 0, 4, 4, 0, 0},   {1, 0, 0, 4, 1, 0, 0},
+      {0, 0, 0, 4, 1, 0, 2},  {0, 0, 32, 4, 1, 0, 2},  {0, 0, 64, 4, 1, 0, 2},
+      {0, 128, 0, 4, 1, 0, 2}, {0, 0, 0, 4, 1, 0, 4},  {0, 0, 64, 4, 1, 0, 4}};
   const int keep_graph = ctx->use_graph;
   ctx->use_graph = 0;
   if ((st = ensure_state(ctx, replicas))) return st;
@@ -1274,6 +1628,7 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
       if (!ctx->tiled_ok) continue;
     }
     if (c.rt && (replicas % c.rt != 0)) continue;
+    if (c.rw && replicas % 128 != 0) continue;
     if (c.groups > 1) {
       const int rt = replicas / c.groups;
       if (replicas % (4 * c.groups) != 0 || rt > 128 || ((rt / 4) & (rt / 4 - 1)) != 0) continue;
@@ -1283,6 +1638,7 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
     ctx->step_rpc = c.rpc;
     ctx->step_unroll = c.unroll;
     ctx->groups = c.groups;
+    ctx->rw_rows = c.rw;
     if (c.l2 && !ctx->l2_persist) {
       if ((st = sb_set_option(ctx, 7, 1))) break;
     }
@@ -1316,6 +1672,7 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
   ctx->step_unroll = cands[best].unroll;
   ctx->groups = cands[best].groups;
   ctx->l2_persist = cands[best].l2;
+  ctx->rw_rows = cands[best].rw;
   ctx->graph.reset();
   if (out_cfg) {
     out_cfg[0] = cands[best].tiled;
@@ -1324,6 +1681,7 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
     out_cfg[3] = cands[best].unroll;
     out_cfg[4] = cands[best].groups;
     out_cfg[5] = cands[best].l2;
+    out_cfg[6] = cands[best].rw;
   }
   if (out_us_per_step) *out_us_per_step = best_us;
   return SB_OK;
@@ -1382,6 +1740,18 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value) {
         }
       }
       ctx->l2_persist = value != 0;
+      ctx->graph.reset();
+      return SB_OK;
+    case 9:  // SB_OPT_ROWS_PER_WARP
+      if (value != 0 && value != 2 && value != 4) {
+        set_error("sb_set_option: SB_OPT_ROWS_PER_WARP must be 0, 2 or 4");
+        return SB_ERR_ARG;
+      }
+      ctx->rw_rows = (int)value;
+      ctx->graph.reset();
+      return SB_OK;
+    case 8:  // SB_OPT_STREAM
+      ctx->use_stream = value != 0;
       ctx->graph.reset();
       return SB_OK;
     case 6:  // SB_OPT_REPLICA_GROUPS

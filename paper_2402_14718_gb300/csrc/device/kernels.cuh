@@ -155,4 +155,93 @@ cudaError_t launch_adj_phase2(int jbf16, const Tiling& t, const AdjArgs& a, cuda
 // out[0] = sum_i gh_i (-quality_i / 2), out[1] = sum_i gh_i (-nconf_i / 4)
 cudaError_t launch_adj_final(const AdjArgs& a, double* out, cudaStream_t s);
 
+
+// ---------------------------------------------------------------- streamed step
+// Warp-specialised step kernel (stream.cu). Rows are cut into blocks of
+// kStreamBR rows; each block carries the sorted union of its rows' neighbour
+// columns, padded to whole stages of kStreamSPS entries, with a kStreamBR-bit
+// mask per entry telling which block rows use it. One producer warp per CTA
+// copies the neighbour x rows (one replica tile of W replicas each) of that
+// union into a shared-memory ring with bulk asynchronous copies; kStreamWarps
+// consumer warps own kStreamRW rows each and accumulate every union entry
+// their rows use, in ascending column order (the CSR order).
+constexpr int kStreamWarps = 8;                       // consumer warps per CTA
+constexpr int kStreamRW = 4;                          // rows per consumer warp
+constexpr int kStreamBR = kStreamWarps * kStreamRW;   // rows per block (mask bits)
+constexpr int kStreamSPS = 32;                        // union entries per ring stage
+constexpr int kStreamThreads = (kStreamWarps + 1) * 32;
+
+struct StreamArgs {
+  const int32_t* rowptr;
+  const void* J;             // float or __nv_bfloat16; the allocation is padded to 16 bytes
+  const float* h;
+  const int32_t* row_event;
+  const float* c0_ev;
+  const float* sched;
+  int32_t k;
+  float a0, dt, dta0;
+  const float* xin;
+  float* xout;
+  float* y;
+  int32_t n, R;
+  const int32_t* cta_blk0;   // [grid + 1] first block of each CTA
+  // [nblk + 1] per block: first row, first union entry (a multiple of
+  // kStreamSPS), first J element of its 16-byte aligned J span, span bytes;
+  // entry nblk = {n, total entries, 0, 0}
+  const int4* blk;
+  const int32_t* rjo;        // [n] rowptr[i] - first J element of the span of i's block
+  const int32_t* ucol;       // union columns (padding entries: 0)
+  const uint32_t* umask;     // bit q: block row q uses the column (padding entries: 0)
+  int32_t grid;              // CTAs (one per SM)
+  int32_t W;                 // replicas per tile: 256, 128 or 64
+  int32_t tiles;             // R / W
+  int32_t nst;               // ring stages
+  int32_t jbuf_bytes;        // bytes of each of the two J staging buffers (multiple of 16)
+  int* err;                  // set non-zero when a wait gives up (the kernel then returns)
+};
+
+// Replica-tile width of the streamed kernel for R replicas (0: not supported).
+int stream_tile_width(int R);
+// Dynamic shared memory of the streamed kernel for nst stages, or 0 when it
+// does not fit; *nst_out receives the largest stage count that fits (<= 16).
+size_t stream_smem(int W, int jbuf_bytes, int* nst_out);
+cudaError_t launch_step_stream(int variant, int jbf16, const StreamArgs& a, size_t smem,
+                               cudaStream_t s);
+// Raise the dynamic shared-memory limit of every k_step_stream instance on the
+// current device (call once per device before the first launch or capture).
+cudaError_t stream_prepare();
+
+// ---------------------------------------------------------------- row-group step
+// k_step_rw (rw.cu): one warp owns RW consecutive rows (a row group) and walks
+// the sorted union of their columns; each union entry holds the column, an
+// RW-bit mask of the group rows that use it and their J values (RW slots, 0
+// where absent). A neighbour row of x is loaded once per group instead of once
+// per row; every row still accumulates its nonzeros in CSR order, one FMA
+// each, so states are identical to k_step's.
+struct RwArgs {
+  const int32_t* gptr;       // [ngroups + 1] first union entry of each row group
+  const int32_t* ent;        // per entry: column << 4 | mask
+  const void* ejv;           // per entry: RW J values (float or __nv_bfloat16)
+  const float* h;
+  const int32_t* row_event;
+  const float* c0_ev;
+  const float* sched;
+  int32_t k;
+  float a0, dt, dta0;
+  const float* xin;
+  float* xout;
+  float* y;
+  int32_t n, R;
+  int32_t ngroups;
+  int32_t gpc;               // row groups per CTA (a CTA walks a contiguous chunk)
+};
+constexpr int kRwMaxRows = 4;  // RW is 2 or 4 (the mask has 4 bits)
+// nch = 2: a warp covers 256 replicas of a row (two float4 per lane), grid.y = R / 256;
+// nch = 1: 128 replicas, grid.y = R / 128. R must be a multiple of 128 * nch.
+cudaError_t launch_step_rw(int variant, int jbf16, int rw, int nch, const RwArgs& a,
+                           cudaStream_t s);
+// ejv[i] = pos[i] >= 0 ? J[pos[i]] : 0 for i < count (J float or bf16 as jbf16 says)
+cudaError_t launch_fill_ejv(const void* J, int jbf16, const int32_t* pos, int64_t count,
+                            void* ejv, cudaStream_t s);
+
 }  // namespace sbd

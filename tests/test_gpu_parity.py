@@ -332,15 +332,16 @@ def test_batch_tiled_matches_single_events():
         row0 += q.n
 
 
-def test_autotune_keeps_results_and_picks_a_valid_config():
+@pytest.mark.parametrize("R", [64, 256])
+def test_autotune_keeps_results_and_picks_a_valid_config(R):
     _, qc, _, _ = workload_qubos("event500")
     ref = _ctx(qc, sb.SB_J_BF16)
-    sb.sb_run(ref, "bsb", 1.0, 0.0, 0.5, 20, 64, seed=5)
+    sb.sb_run(ref, "bsb", 1.0, 0.0, 0.5, 20, R, seed=5)
     x_ref, y_ref = sb.sb_get_state(ref)
     ctx = _ctx(qc, sb.SB_J_BF16)
-    cfg, us = sb.sb_autotune(ctx, "bsb", 64, trial_steps=10)
-    assert cfg["tiled"] in (0, 1) and us > 0
-    sb.sb_run(ctx, "bsb", 1.0, 0.0, 0.5, 20, 64, seed=5)
+    cfg, us = sb.sb_autotune(ctx, "bsb", R, trial_steps=10)
+    assert cfg["tiled"] in (0, 1) and cfg["rows_per_warp"] in (0, 2, 4) and us > 0
+    sb.sb_run(ctx, "bsb", 1.0, 0.0, 0.5, 20, R, seed=5)
     x, y = sb.sb_get_state(ctx)
     assert np.array_equal(x, x_ref) and np.array_equal(y, y_ref)
 
