@@ -382,9 +382,10 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
  * Applies to every variant (dSB gathers FP32 positions on this path). */
 #define SB_OPT_STREAM 8
 /* SB_OPT_ROWS_PER_WARP (9): 2 or 4 uses the row-group step kernel when R is a
- * multiple of 128: one warp owns that many consecutive rows and walks the
- * sorted union of their columns, loading each neighbour row of x once for all
- * of them (the union is built on first use). 0 (default) turns it off. Same
+ * multiple of 128: one warp owns a group of that many rows (grouped on the
+ * host, on first use, so that they share neighbours) and walks the sorted
+ * union of their columns, loading each neighbour row of x once for all of
+ * them. 0 (default) turns it off. Same
  * FMA order as the untiled kernel, so the states are identical. With it,
  * SB_OPT_STEP_RPC sets rows per CTA (divided by the group size) and
  * SB_OPT_STEP_RT = 128 makes a warp cover 128 replicas instead of 256. */

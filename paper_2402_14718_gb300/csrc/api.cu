@@ -125,12 +125,13 @@ struct sb_ctx {
   int32_t* d_s_ucol = nullptr;
   uint32_t* d_s_umask = nullptr;
   int* d_err = nullptr;  // set by a kernel whose bounded wait gave up
-  // row-group step kernel (k_step_rw): union entries of RW consecutive rows
+  // row-group step kernel (k_step_rw): groups of RW rows and their union entries
   int rw_rows = 0;       // 0: off; 2 or 4 rows per warp
   int rw_built = 0;      // RW the tables below were built for (0: none)
   int32_t rw_ngroups = 0;
   int64_t rw_E = 0;
   int32_t* d_rw_gptr = nullptr;
+  int32_t* d_rw_rows = nullptr;  // rows of each group (-1: empty slot)
   int32_t* d_rw_ent = nullptr;
   int32_t* d_rw_pos = nullptr;  // CSR position of each entry's RW slots (-1: absent)
   void* d_rw_ejv = nullptr;     // J of each entry's RW slots
@@ -278,6 +279,7 @@ void free_all(sb_ctx* c) {
   dfree(c->d_s_umask);
   dfree(c->d_err);
   dfree(c->d_rw_gptr);
+  dfree(c->d_rw_rows);
   dfree(c->d_rw_ent);
   dfree(c->d_rw_pos);
   if (c->d_rw_ejv) cudaFree(c->d_rw_ejv);
@@ -564,18 +566,51 @@ sb_status ensure_stream(sb_ctx* c) {
   return SB_OK;
 }
 
-// Tables of the row-group kernel: rows in groups of RW consecutive rows; a
-// group's entries are the sorted union of its rows' columns (a k-way merge of
-// the CSR rows), each with an RW-bit mask and the CSR position of every slot.
+// Tables of the row-group kernel. Groups of RW rows are formed greedily in row
+// order: the first row not yet placed anchors a group, which then takes, one
+// at a time, the unplaced candidate (a neighbour of the anchor or one of the
+// next 7 rows) adding the fewest new columns to the group's union. A group's
+// entries are the sorted union of its rows' columns (a k-way merge of the CSR
+// rows), each with an RW-bit mask and the CSR position of every slot.
 struct RwHost {
   bool ok = false;
-  std::vector<int32_t> gptr, ent, pos;
+  std::vector<int32_t> gptr, rows, ent, pos;
 };
 
 RwHost build_rw(int32_t n, const int32_t* rp, const int32_t* col, int RW) {
   RwHost t;
   if (n >= (1 << 27) || RW < 2 || RW > sbd::kRwMaxRows) return t;
-  const int32_t ng = (n + RW - 1) / RW;
+  // greedy grouping
+  std::vector<char> placed(n, 0);
+  std::vector<int32_t> stamp(n, -1);
+  int32_t ng = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    if (placed[i]) continue;
+    placed[i] = 1;
+    const size_t g0 = t.rows.size();
+    t.rows.push_back(i);
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) stamp[col[p]] = ng;
+    for (int k = 1; k < RW; ++k) {
+      int32_t best = -1, best_add = INT32_MAX;
+      auto consider = [&](int32_t j) {
+        if (placed[j]) return;
+        int32_t add = 0;
+        for (int32_t p = rp[j]; p < rp[j + 1] && add < best_add; ++p) add += stamp[col[p]] != ng;
+        if (add < best_add) {
+          best_add = add;
+          best = j;
+        }
+      };
+      for (int32_t p = rp[i]; p < rp[i + 1] && best_add > 0; ++p) consider(col[p]);
+      for (int32_t j = i + 1; j < std::min(n, i + 8) && best_add > 0; ++j) consider(j);
+      if (best < 0) break;
+      placed[best] = 1;
+      t.rows.push_back(best);
+      for (int32_t p = rp[best]; p < rp[best + 1]; ++p) stamp[col[p]] = ng;
+    }
+    t.rows.resize(g0 + RW, -1);
+    ++ng;
+  }
   t.gptr.reserve((size_t)ng + 1);
   t.ent.reserve((size_t)rp[n]);
   t.pos.reserve((size_t)rp[n] * RW);
@@ -583,9 +618,9 @@ RwHost build_rw(int32_t n, const int32_t* rp, const int32_t* col, int RW) {
   for (int32_t g = 0; g < ng; ++g) {
     int32_t p[sbd::kRwMaxRows], pe[sbd::kRwMaxRows];
     for (int q = 0; q < RW; ++q) {
-      const int32_t row = g * RW + q;
-      p[q] = row < n ? rp[row] : 0;
-      pe[q] = row < n ? rp[row + 1] : 0;
+      const int32_t row = t.rows[(size_t)g * RW + q];
+      p[q] = row >= 0 ? rp[row] : 0;
+      pe[q] = row >= 0 ? rp[row + 1] : 0;
     }
     for (;;) {
       int32_t cmin = INT32_MAX;
@@ -624,6 +659,7 @@ sb_status ensure_rw(sb_ctx* c, int RW) {
   if (c->rw_built == RW) return SB_OK;
   RwHost t = build_rw(c->n, c->h_rowptr.data(), c->h_col.data(), RW);
   dfree(c->d_rw_gptr);
+  dfree(c->d_rw_rows);
   dfree(c->d_rw_ent);
   dfree(c->d_rw_pos);
   if (c->d_rw_ejv) cudaFree(c->d_rw_ejv);
@@ -631,8 +667,8 @@ sb_status ensure_rw(sb_ctx* c, int RW) {
   c->rw_built = 0;
   if (!t.ok) return SB_OK;  // the untiled kernel serves every run
   sb_status st;
-  if ((st = dalloc(&c->d_rw_gptr, t.gptr.size())) || (st = dalloc(&c->d_rw_ent, t.ent.size())) ||
-      (st = dalloc(&c->d_rw_pos, t.pos.size())))
+  if ((st = dalloc(&c->d_rw_gptr, t.gptr.size())) || (st = dalloc(&c->d_rw_rows, t.rows.size())) ||
+      (st = dalloc(&c->d_rw_ent, t.ent.size())) || (st = dalloc(&c->d_rw_pos, t.pos.size())))
     return st;
   {
     cudaError_t e = cudaMalloc(&c->d_rw_ejv, std::max<size_t>(t.pos.size(), 1) * (c->jbf16 ? 2 : 4));
@@ -644,6 +680,7 @@ sb_status ensure_rw(sb_ctx* c, int RW) {
     }
   }
   SB_CUDA(cudaMemcpy(c->d_rw_gptr, t.gptr.data(), t.gptr.size() * 4, cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(c->d_rw_rows, t.rows.data(), t.rows.size() * 4, cudaMemcpyHostToDevice));
   if (!t.ent.empty()) {
     SB_CUDA(cudaMemcpy(c->d_rw_ent, t.ent.data(), t.ent.size() * 4, cudaMemcpyHostToDevice));
     SB_CUDA(cudaMemcpy(c->d_rw_pos, t.pos.data(), t.pos.size() * 4, cudaMemcpyHostToDevice));
@@ -792,6 +829,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
       rw = c->rw_rows;
       rw_nch = (c->R % 256 == 0 && c->step_rt != 128) ? 2 : 1;
       ra.gptr = c->d_rw_gptr;
+      ra.grows = c->d_rw_rows;
       ra.ent = c->d_rw_ent;
       ra.ejv = c->d_rw_ejv;
       ra.h = c->d_h32;

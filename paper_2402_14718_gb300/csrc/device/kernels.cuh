@@ -212,14 +212,15 @@ cudaError_t launch_step_stream(int variant, int jbf16, const StreamArgs& a, size
 cudaError_t stream_prepare();
 
 // ---------------------------------------------------------------- row-group step
-// k_step_rw (rw.cu): one warp owns RW consecutive rows (a row group) and walks
-// the sorted union of their columns; each union entry holds the column, an
+// k_step_rw (rw.cu): one warp owns a group of RW rows that share many
+// neighbours and walks the sorted union of their columns; each union entry holds the column, an
 // RW-bit mask of the group rows that use it and their J values (RW slots, 0
 // where absent). A neighbour row of x is loaded once per group instead of once
 // per row; every row still accumulates its nonzeros in CSR order, one FMA
 // each, so states are identical to k_step's.
 struct RwArgs {
   const int32_t* gptr;       // [ngroups + 1] first union entry of each row group
+  const int32_t* grows;      // [ngroups x RW] rows of each group (-1: empty slot)
   const int32_t* ent;        // per entry: column << 4 | mask
   const void* ejv;           // per entry: RW J values (float or __nv_bfloat16)
   const float* h;

@@ -1,7 +1,8 @@
 // k_step_rw: one SB step (coupling product of Eq. 2 / 6 / 10, symplectic
 // Euler update, inelastic wall) computed by row groups.
 //
-// A warp owns RW consecutive rows and walks the sorted union of their columns.
+// A warp owns a group of RW rows (chosen on the host to share neighbours) and
+// walks the sorted union of their columns.
 // Each union entry carries the column, an RW-bit mask of the group rows that
 // use it, and those rows' J values. The warp loads the neighbour row of x (its
 // 128 * NCH replicas, 16-byte loads) once per entry and applies it to every
@@ -20,6 +21,17 @@ namespace sbd {
 namespace {
 
 constexpr int kRwBlock = 256;
+// union entries in flight per warp (x rows loaded before their FMAs) and the
+// launch-bounds residency hint; defaults measured best on the 1000-track event
+#ifndef SB_RW_UB_NCH2
+#define SB_RW_UB_NCH2 2
+#endif
+#ifndef SB_RW_UB_NCH1
+#define SB_RW_UB_NCH1 4
+#endif
+#ifndef SB_RW_MINB
+#define SB_RW_MINB 1
+#endif
 
 // RW J values of one entry, read by one lane and broadcast by shuffles.
 template <int RW, typename JT>
@@ -97,13 +109,16 @@ struct JPack<2, float> {
 __device__ __forceinline__ float sgnf(float x) { return (float)((x > 0.f) - (x < 0.f)); }
 
 template <int RW, int NCH, int VARIANT, typename JT>
-__global__ void __launch_bounds__(kRwBlock) k_step_rw(const RwArgs a) {
+__global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a) {
   using P = JPack<RW, JT>;
-  constexpr int UB = NCH == 2 ? 4 : 8;  // union entries whose x rows are in flight at once
+  constexpr int UB = NCH == 2 ? SB_RW_UB_NCH2 : SB_RW_UB_NCH1;
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   const int R = a.R;
   const size_t rep0 = (size_t)blockIdx.y * (128 * NCH) + 4 * lane;  // this lane's first replica
+  // byte address of (row 0, this lane's replicas); a neighbour row adds col * 4R bytes
+  const char* xl = reinterpret_cast<const char*>(a.xin + rep0);
+  const unsigned rb = 4u * (unsigned)R;
   const int g_end = min(a.ngroups, (blockIdx.x + 1) * a.gpc);
   const float pa = a.a0 - __ldg(a.sched + a.k);
   for (int grp = blockIdx.x * a.gpc + wid; grp < g_end; grp += kRwBlock / 32) {
@@ -115,7 +130,8 @@ __global__ void __launch_bounds__(kRwBlock) k_step_rw(const RwArgs a) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[q][j][v] = 0.f;
     const int e0 = __ldg(a.gptr + grp), e1 = __ldg(a.gptr + grp + 1);
-    // union entries 32 at a time, one per lane; the next 32 are loaded ahead
+    // union entries 32 at a time, one per lane (lanes past the end hold column
+    // 0 with an empty mask); the next 32 are loaded ahead
     int pk = 0;
     P jp;
     jp.zero();
@@ -138,15 +154,13 @@ __global__ void __launch_bounds__(kRwBlock) k_step_rw(const RwArgs a) {
         float xv[UB][NCH][4];
 #pragma unroll
         for (int u = 0; u < UB; ++u) {
-          const int src = q0 + u < cnt ? q0 + u : 0;
-          const int v = __shfl_sync(0xffffffffu, pk, src);
-          w[u] = jp.shfl(src);
-          m[u] = q0 + u < cnt ? (uint32_t)(v & 15) : 0u;
-          const size_t base = (size_t)(v >> 4) * R + rep0;
+          const unsigned v = (unsigned)__shfl_sync(0xffffffffu, pk, q0 + u);
+          w[u] = jp.shfl(q0 + u);
+          m[u] = v & 15u;
+          const float4* px = reinterpret_cast<const float4*>(xl + (size_t)(v >> 4) * rb);
 #pragma unroll
           for (int j = 0; j < NCH; ++j) {
-            float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (m[u]) t = __ldg(reinterpret_cast<const float4*>(a.xin + base + 128 * j));
+            const float4 t = __ldg(px + 32 * j);
             xv[u][j][0] = t.x;
             xv[u][j][1] = t.y;
             xv[u][j][2] = t.z;
@@ -179,8 +193,8 @@ __global__ void __launch_bounds__(kRwBlock) k_step_rw(const RwArgs a) {
     // symplectic Euler: momentum with the old position, then position, then wall
 #pragma unroll
     for (int q = 0; q < RW; ++q) {
-      const int row = grp * RW + q;
-      if (row >= a.n) continue;
+      const int row = __ldg(a.grows + (size_t)grp * RW + q);
+      if (row < 0) continue;
       const int ev = a.row_event ? __ldg(a.row_event + row) : 0;
       const float c0 = __ldg(a.c0_ev + ev);
       const float hi = __ldg(a.h + row);

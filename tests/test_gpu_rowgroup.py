@@ -1,5 +1,5 @@
-"""Row-group step kernel (SB_OPT_ROWS_PER_WARP): a warp owns 2 or 4
-consecutive rows and loads each union column once for all of them.
+"""Row-group step kernel (SB_OPT_ROWS_PER_WARP): a warp owns a group of 2 or
+4 rows that share neighbours and loads each union column once for all of them.
 
 Each (row, replica) still takes one FMA per nonzero in CSR order, so the
 states must equal the untiled kernel's bit for bit; one step is also checked
