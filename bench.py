@@ -89,10 +89,13 @@ def job_value(units_per_rank, world_size, ms):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step-kernel
-# launch from the ncu captures summarised in profiles/, keyed by workload,
-# variant, kernel, its configuration and the step-kernel sources (sha256 prefix
-# of kernels.cu, kernels.cuh, rw.cu, stream.cu); anything else reports null.
-MEASURED_TRAFFIC = {}
+# launch, from an ncu capture of that launch (third step, direct launch), keyed
+# by workload, variant, kernel, its configuration (rows per warp, rows per CTA,
+# replica tile) and the step-kernel sources (sha256 prefix of kernels.cu,
+# kernels.cuh, rw.cu, stream.cu); any other combination reports null.
+MEASURED_TRAFFIC = {
+    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "8359cb6d4e693882"): 89570560 + 33273600,
+}
 
 
 def set_kernel(sb, ctx, name):

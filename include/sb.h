@@ -368,7 +368,9 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
 #define SB_OPT_REPLICA_GROUPS 6
 /* SB_OPT_L2_PERSIST (7): 1 marks each step's source positions as L2-persisting
  * (stream access-policy window; the persisting L2 set-aside of this process's
- * context is raised to the device maximum). Does not change results. */
+ * context is raised to the device maximum). 0 (or sb_destroy) returns every
+ * persisting line to normal and puts the set-aside back. Does not change
+ * results. */
 #define SB_OPT_L2_PERSIST 7
 /* SB_OPT_STREAM (8): 1 uses the streamed step kernel when R is a multiple of
  * 64: one CTA per SM walks a contiguous chunk of rows in blocks of 32; a

@@ -110,6 +110,8 @@ struct sb_ctx {
   int dsb_signs = 1;  // dSB gathers int8 signs instead of FP32 positions
   int groups = 1;     // replica groups run one after another (each for all steps)
   int l2_persist = 0; // mark each step's source x as L2-persisting (access-policy window)
+  bool l2_raised = false;  // this context raised the persisting-L2 set-aside
+  size_t l2_saved = 0;     // the set-aside before it did
   int8_t* d_sgn[2] = {nullptr, nullptr};
   int sms = 0;
   // streamed step kernel (k_step_stream): per-CTA row chunks cut into blocks
@@ -691,6 +693,32 @@ sb_status ensure_rw(sb_ctx* c, int RW) {
   return refill_rw(c);
 }
 
+// The persisting-L2 set-aside belongs to the process's CUDA context. It is
+// raised to the device maximum while a context marks x as persisting, and put
+// back (with every persisting line returned to normal) when it stops, so that
+// later runs get the whole L2.
+sb_status l2_persist_on(sb_ctx* c) {
+  if (c->l2_raised) return SB_OK;
+  size_t old = 0;
+  SB_CUDA(cudaDeviceGetLimit(&old, cudaLimitPersistingL2CacheSize));
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxPersistingL2CacheSize, c->device) == cudaSuccess &&
+      v > 0)
+    SB_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)v));
+  c->l2_saved = old;
+  c->l2_raised = true;
+  return SB_OK;
+}
+
+sb_status l2_persist_off(sb_ctx* c) {
+  if (!c->l2_raised) return SB_OK;
+  SB_CUDA(cudaDeviceSynchronize());
+  SB_CUDA(cudaCtxResetPersistingL2Cache());
+  SB_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, c->l2_saved));
+  c->l2_raised = false;
+  return SB_OK;
+}
+
 // Report (and clear) the flag a kernel sets when one of its bounded waits gave up.
 sb_status check_wait_flag(const sb_ctx* c) {
   int v = 0;
@@ -1179,6 +1207,7 @@ void sb_destroy(sb_ctx* ctx) {
   cudaGetDevice(&prev);
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  if (ctx->l2_raised) l2_persist_off(ctx);
   free_all(ctx);
   cudaSetDevice(prev);
   delete ctx;
@@ -1677,9 +1706,7 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
     ctx->step_unroll = c.unroll;
     ctx->groups = c.groups;
     ctx->rw_rows = c.rw;
-    if (c.l2 && !ctx->l2_persist) {
-      if ((st = sb_set_option(ctx, 7, 1))) break;
-    }
+    if ((st = c.l2 ? l2_persist_on(ctx) : l2_persist_off(ctx))) break;
     ctx->l2_persist = c.l2;
     ctx->graph.reset();
     if ((st = sb_run(ctx, variant, 1.0, 0.0, 0.5, 0, replicas, 12345, nullptr, stream))) break;
@@ -1710,6 +1737,7 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
   ctx->step_unroll = cands[best].unroll;
   ctx->groups = cands[best].groups;
   ctx->l2_persist = cands[best].l2;
+  if ((st = ctx->l2_persist ? l2_persist_on(ctx) : l2_persist_off(ctx))) return st;
   ctx->rw_rows = cands[best].rw;
   ctx->graph.reset();
   if (out_cfg) {
@@ -1768,18 +1796,13 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value) {
       ctx->dsb_signs = value != 0;
       ctx->graph.reset();
       return SB_OK;
-    case 7:  // SB_OPT_L2_PERSIST
-      if (value) {
-        int v = 0;
-        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxPersistingL2CacheSize, ctx->device) ==
-                cudaSuccess &&
-            v > 0) {
-          SB_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)v));
-        }
-      }
+    case 7: {  // SB_OPT_L2_PERSIST
+      const sb_status st = value ? l2_persist_on(ctx) : l2_persist_off(ctx);
+      if (st) return st;
       ctx->l2_persist = value != 0;
       ctx->graph.reset();
       return SB_OK;
+    }
     case 9:  // SB_OPT_ROWS_PER_WARP
       if (value != 0 && value != 2 && value != 4) {
         set_error("sb_set_option: SB_OPT_ROWS_PER_WARP must be 0, 2 or 4");
