@@ -112,7 +112,7 @@ struct sb_ctx {
   int l2_persist = 0; // mark each step's source x as L2-persisting (access-policy window)
   bool l2_raised = false;  // this context raised the persisting-L2 set-aside
   size_t l2_saved = 0;     // the set-aside before it did
-  int8_t* d_sgn[2] = {nullptr, nullptr};
+  uint8_t* d_sgn[2] = {nullptr, nullptr};  // dSB signs, biased by 128
   int sms = 0;
   // streamed step kernel (k_step_stream): per-CTA row chunks cut into blocks
   // with their neighbour-column unions; built on first use
@@ -952,7 +952,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   ta.R = c->R;
   ta.nb = c->nb;
   const int sgn =
-      (variant == SB_DSB && c->dsb_signs && !tiled && !streamed && !rw && c->R % 4 == 0) ? 1 : 0;
+      (variant == SB_DSB && c->dsb_signs && !tiled && !streamed && c->R % 4 == 0) ? 1 : 0;
   if (sgn && !c->d_sgn[0]) {
     sb_status st2;
     const size_t cnt = (size_t)c->n * c->R;
@@ -991,6 +991,8 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
       ra.k = k;
       ra.xin = c->d_x[cur];
       ra.xout = c->d_x[cur ^ 1];
+      ra.sgn_in = sgn ? c->d_sgn[cur] : nullptr;
+      ra.sgn_out = sgn ? c->d_sgn[cur ^ 1] : nullptr;
       return sbd::launch_step_rw(variant, c->jbf16, rw, rw_nch, ra, st);
     }
     if (tiled) {

@@ -19,6 +19,7 @@
 
 #include "../philox.h"
 #include "kernels.cuh"
+#include "signs.cuh"
 
 namespace sbd {
 
@@ -96,18 +97,16 @@ struct Vec<1> {
   __device__ __forceinline__ void st(float* p) const { *p = v[0]; }
 };
 
-// V signs (int8) of one chunk as floats
+// V signs (biased bytes) of one chunk as floats
 template <int V>
-__device__ __forceinline__ void ld_signs(const int8_t* p, float (&out)[V]) {
+__device__ __forceinline__ void ld_signs(const uint8_t* p, float (&out)[V]) {
   if (V == 4) {
-    const int w = __ldg(reinterpret_cast<const int*>(p));
-    out[0] = (float)(int8_t)(w & 0xff);
-    out[1 % V] = (float)(int8_t)((w >> 8) & 0xff);
-    out[2 % V] = (float)(int8_t)((w >> 16) & 0xff);
-    out[3 % V] = (float)(int8_t)((w >> 24) & 0xff);
+    const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(p));
+#pragma unroll
+    for (int v = 0; v < V; ++v) out[v] = sign_of_byte(w, v);
   } else {
 #pragma unroll
-    for (int v = 0; v < V; ++v) out[v] = (float)__ldg(p + v);
+    for (int v = 0; v < V; ++v) out[v] = sign_of_byte(__ldg(p + v), 0);
   }
 }
 
@@ -116,7 +115,6 @@ __device__ __forceinline__ float jval(const __nv_bfloat16* J, int p) {
   return __bfloat162float(J[p]);
 }
 
-__device__ __forceinline__ float sgnf(float x) { return (float)((x > 0.f) - (x < 0.f)); }
 
 // lanes of this thread's row group inside its warp
 __device__ __forceinline__ unsigned group_mask(int G) {
@@ -239,7 +237,7 @@ __global__ void __launch_bounds__(kBlock, SB_STEP_MIN_BLOCKS) k_step(const StepA
     Vec<V> xv, yv;
     xv.ldg(a.xin + idx);
     yv.ld(a.y + idx);
-    int sw = 0;
+    uint32_t sw = 0;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       float x = xv.v[v], y = yv.v[v];
@@ -259,16 +257,16 @@ __global__ void __launch_bounds__(kBlock, SB_STEP_MIN_BLOCKS) k_step(const StepA
       }
       xv.v[v] = x;
       yv.v[v] = y;
-      if (VARIANT == 2) sw |= ((int)(int8_t)((x > 0.f) - (x < 0.f)) & 0xff) << (8 * v);
+      if (VARIANT == 2) sw |= sign_byte(x) << (8 * v);
     }
     xv.st(a.xout + idx);
     yv.st(a.y + idx);
     if (use_sgn) {
       if (V == 4) {
-        *reinterpret_cast<int*>(a.sgn_out + idx) = sw;
+        *reinterpret_cast<uint32_t*>(a.sgn_out + idx) = sw;
       } else {
 #pragma unroll
-        for (int v = 0; v < V; ++v) a.sgn_out[idx + v] = (int8_t)((sw >> (8 * v)) & 0xff);
+        for (int v = 0; v < V; ++v) a.sgn_out[idx + v] = (uint8_t)((sw >> (8 * v)) & 0xff);
       }
     }
   }
@@ -375,9 +373,6 @@ __global__ void __launch_bounds__(kBlock) k_step_r1(const StepArgs a) {
 // dSB gathering int8 signs with 16 replicas per lane: one 16-byte load brings a
 // neighbour's signs for 16 replicas. G = R / 16 lanes own a row (R / 16 a power
 // of two, <= 32). Same CSR-order FMA sequence per replica as k_step.
-__device__ __forceinline__ float sbyte(unsigned w, int b) {
-  return (float)(int)(signed char)((w >> (8 * b)) & 0xffu);
-}
 
 template <typename JT>
 __global__ void __launch_bounds__(kBlock) k_step_dsb16(const StepArgs a) {
@@ -419,7 +414,7 @@ __global__ void __launch_bounds__(kBlock) k_step_dsb16(const StepArgs a) {
         for (int u = 0; u < 4; ++u) {
           const unsigned ww[4] = {sv[u].x, sv[u].y, sv[u].z, sv[u].w};
 #pragma unroll
-          for (int v = 0; v < 16; ++v) acc[v] = fmaf(w[u], sbyte(ww[v >> 2], v & 3), acc[v]);
+          for (int v = 0; v < 16; ++v) acc[v] = fmaf(w[u], sign_of_byte(ww[v >> 2], v & 3), acc[v]);
         }
       }
       for (; q < cnt; ++q) {
@@ -428,7 +423,7 @@ __global__ void __launch_bounds__(kBlock) k_step_dsb16(const StepArgs a) {
         const uint4 s4 = __ldg(reinterpret_cast<const uint4*>(a.sgn_in + (size_t)c * R + 16 * g));
         const unsigned ww[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-        for (int v = 0; v < 16; ++v) acc[v] = fmaf(w, sbyte(ww[v >> 2], v & 3), acc[v]);
+        for (int v = 0; v < 16; ++v) acc[v] = fmaf(w, sign_of_byte(ww[v >> 2], v & 3), acc[v]);
       }
     }
     const float pa = a.a0 - __ldg(a.sched + a.k);
@@ -454,7 +449,7 @@ __global__ void __launch_bounds__(kBlock) k_step_dsb16(const StepArgs a) {
         }
         xv.v[v] = x;
         yv.v[v] = y;
-        sw[h4] |= ((unsigned)(int)(signed char)((x > 0.f) - (x < 0.f)) & 0xffu) << (8 * v);
+        sw[h4] |= sign_byte(x) << (8 * v);
       }
       xv.st(a.xout + idx + 4 * h4);
       yv.st(a.y + idx + 4 * h4);
@@ -1201,13 +1196,13 @@ int step_blocks_per_sm(int variant, int jbf16, const Tiling& t, int unroll) {
   return blocks_per_sm_v<1, 4>(variant, jbf16, unroll);
 }
 
-__global__ void k_signs(const float* x, int8_t* s, size_t count) {
+__global__ void k_signs(const float* x, uint8_t* s, size_t count) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (size_t)gridDim.x * blockDim.x)
-    s[i] = (int8_t)((x[i] > 0.f) - (x[i] < 0.f));
+    s[i] = (uint8_t)sign_byte(x[i]);
 }
 
-cudaError_t launch_signs(const float* x, int8_t* s, size_t count, cudaStream_t st) {
+cudaError_t launch_signs(const float* x, uint8_t* s, size_t count, cudaStream_t st) {
   if (!count) return cudaSuccess;
   k_signs<<<grid_for(count, kBlock), kBlock, 0, st>>>(x, s, count);
   return cudaGetLastError();

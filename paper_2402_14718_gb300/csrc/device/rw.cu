@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "kernels.cuh"
+#include "signs.cuh"
 
 namespace sbd {
 namespace {
@@ -106,10 +107,13 @@ struct JPack<2, float> {
   __device__ __forceinline__ void zero() { v = make_float2(0.f, 0.f); }
 };
 
-__device__ __forceinline__ float sgnf(float x) { return (float)((x > 0.f) - (x < 0.f)); }
 
-template <int RW, int NCH, int VARIANT, typename JT>
+// MODE: 0 aSB, 1 bSB, 2 dSB gathering x (sgn at use), 3 dSB gathering the
+// biased sign bytes written by the previous step (4 bytes per lane chunk)
+template <int RW, int NCH, int MODE, typename JT>
 __global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a) {
+  constexpr int VARIANT = MODE == 3 ? 2 : MODE;
+  constexpr bool use_sgn = MODE == 3;
   using P = JPack<RW, JT>;
   constexpr int UB = NCH == 2 ? SB_RW_UB_NCH2 : SB_RW_UB_NCH1;
   const int lane = threadIdx.x & 31;
@@ -117,8 +121,9 @@ __global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a
   const int R = a.R;
   const size_t rep0 = (size_t)blockIdx.y * (128 * NCH) + 4 * lane;  // this lane's first replica
   // byte address of (row 0, this lane's replicas); a neighbour row adds col * 4R bytes
-  const char* xl = reinterpret_cast<const char*>(a.xin + rep0);
-  const unsigned rb = 4u * (unsigned)R;
+  const char* xl = use_sgn ? reinterpret_cast<const char*>(a.sgn_in + rep0)
+                           : reinterpret_cast<const char*>(a.xin + rep0);
+  const unsigned rb = (use_sgn ? 1u : 4u) * (unsigned)R;
   const int g_end = min(a.ngroups, (blockIdx.x + 1) * a.gpc);
   const float pa = a.a0 - __ldg(a.sched + a.k);
   for (int grp = blockIdx.x * a.gpc + wid; grp < g_end; grp += kRwBlock / 32) {
@@ -157,19 +162,29 @@ __global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a
           const unsigned v = (unsigned)__shfl_sync(0xffffffffu, pk, q0 + u);
           w[u] = jp.shfl(q0 + u);
           m[u] = v & 15u;
-          const float4* px = reinterpret_cast<const float4*>(xl + (size_t)(v >> 4) * rb);
+          if (use_sgn) {
+            const uint32_t* ps = reinterpret_cast<const uint32_t*>(xl + (size_t)(v >> 4) * rb);
 #pragma unroll
-          for (int j = 0; j < NCH; ++j) {
-            const float4 t = __ldg(px + 32 * j);
-            xv[u][j][0] = t.x;
-            xv[u][j][1] = t.y;
-            xv[u][j][2] = t.z;
-            xv[u][j][3] = t.w;
+            for (int j = 0; j < NCH; ++j) {
+              const uint32_t t = __ldg(ps + 32 * j);
+#pragma unroll
+              for (int k = 0; k < 4; ++k) xv[u][j][k] = sign_of_byte(t, k);
+            }
+          } else {
+            const float4* px = reinterpret_cast<const float4*>(xl + (size_t)(v >> 4) * rb);
+#pragma unroll
+            for (int j = 0; j < NCH; ++j) {
+              const float4 t = __ldg(px + 32 * j);
+              xv[u][j][0] = t.x;
+              xv[u][j][1] = t.y;
+              xv[u][j][2] = t.z;
+              xv[u][j][3] = t.w;
+            }
           }
         }
 #pragma unroll
         for (int u = 0; u < UB; ++u) {
-          if (VARIANT == 2) {
+          if (MODE == 2) {
 #pragma unroll
             for (int j = 0; j < NCH; ++j)
 #pragma unroll
@@ -204,6 +219,7 @@ __global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a
         const float4 xo = __ldg(reinterpret_cast<const float4*>(a.xin + idx));
         const float4 yo = *reinterpret_cast<const float4*>(a.y + idx);
         float xs[4] = {xo.x, xo.y, xo.z, xo.w}, ys[4] = {yo.x, yo.y, yo.z, yo.w};
+        uint32_t sw = 0u;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           float x = xs[v], y = ys[v];
@@ -217,7 +233,9 @@ __global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a
           }
           xs[v] = x;
           ys[v] = y;
+          if (use_sgn) sw |= sign_byte(x) << (8 * v);
         }
+        if (use_sgn) *reinterpret_cast<uint32_t*>(a.sgn_out + idx) = sw;
         *reinterpret_cast<float4*>(a.xout + idx) = make_float4(xs[0], xs[1], xs[2], xs[3]);
         *reinterpret_cast<float4*>(a.y + idx) = make_float4(ys[0], ys[1], ys[2], ys[3]);
       }
@@ -231,7 +249,12 @@ cudaError_t launch_t(int variant, const RwArgs& a, cudaStream_t s) {
   switch (variant) {
     case 0: k_step_rw<RW, NCH, 0, JT><<<grid, kRwBlock, 0, s>>>(a); break;
     case 1: k_step_rw<RW, NCH, 1, JT><<<grid, kRwBlock, 0, s>>>(a); break;
-    default: k_step_rw<RW, NCH, 2, JT><<<grid, kRwBlock, 0, s>>>(a); break;
+    default:
+      if (a.sgn_in)
+        k_step_rw<RW, NCH, 3, JT><<<grid, kRwBlock, 0, s>>>(a);
+      else
+        k_step_rw<RW, NCH, 2, JT><<<grid, kRwBlock, 0, s>>>(a);
+      break;
   }
   return cudaGetLastError();
 }

@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
+#include "signs.cuh"
 
 namespace sbd {
 namespace {
@@ -152,7 +153,6 @@ __device__ __forceinline__ float jget(const float* J, int i) { return J[i]; }
 __device__ __forceinline__ float jget(const __nv_bfloat16* J, int i) {
   return __bfloat162float(J[i]);
 }
-__device__ __forceinline__ float sgnf(float x) { return (float)((x > 0.f) - (x < 0.f)); }
 
 template <int PER, int VARIANT, typename JT>
 __global__ void __launch_bounds__(kStreamThreads, 1) k_step_stream(const StreamArgs a) {

@@ -143,3 +143,37 @@ def test_rowgroup_full_size_event1000():
     _, qc, _, _ = workload_qubos("event1000")
     for rw in (2, 4):
         _same(qc, sb.SB_J_BF16, "bsb", 256, 8, rw, rpc=32)
+
+
+@pytest.mark.parametrize("rw", [0, 2, 4])
+@pytest.mark.parametrize("signs", [1, 0])
+def test_dsb_exact_zero_and_wall_positions_against_oracle(rw, signs):
+    """dSB uses sgn(x) with sgn(0) = 0. A state with exact zeros, exact +-1
+    (walls) and ordinary values, one step, every dSB gather form (stored sign
+    bytes or FP32 x, row groups or not) against the oracle, and the forms
+    against each other bit for bit."""
+    _, qc, _, qo = workload_qubos("event100")
+    R = 128
+    x0, y0 = inputs.random_state(qo.n, R, 77, 0.9)
+    rng = np.random.default_rng(5)
+    pick = rng.random(x0.shape)
+    x0[pick < 0.2] = 0.0
+    x0[(pick >= 0.2) & (pick < 0.4)] = 1.0
+    x0[(pick >= 0.4) & (pick < 0.5)] = -1.0
+    outs = []
+    for form in ((rw, signs), (0, 0)):
+        ctx = sb.sb_create(qc.n, qc.rowptr, qc.col, qc.val, qc.lin, sb.SB_J_FP32)
+        sb.sb_set_option(ctx, sb.SB_OPT_ROWS_PER_WARP, form[0])
+        sb.sb_set_option(ctx, sb.SB_OPT_DSB_SIGNS, form[1])
+        sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
+        c0 = sb.sb_info(ctx)["c0_auto"]
+        sb.sb_set_state(ctx, x0, y0)
+        sb.sb_advance(ctx, "dsb", 1.0, c0, 0.5, 1, _sched([0.3]))
+        outs.append(sb.sb_get_state(ctx))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    J, h, _ = _oracle_J(qo, sb.SB_J_FP32)
+    a32 = float(np.float32(0.3))
+    x64, y64 = x0.astype(np.float64), y0.astype(np.float64)
+    xo, yo = osb.step(J, h, x64, y64, a32, 1.0, c0, 0.5, osb.DSB)
+    xpre = osb.prewall_x(J, h, x64, y64, a32, 1.0, c0, 0.5, osb.DSB)
+    compare_step(outs[0][0], outs[0][1], xo, yo, xpre)
