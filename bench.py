@@ -98,8 +98,14 @@ MEASURED_TRAFFIC = {
 }
 
 
-def set_kernel(sb, ctx, name):
-    """Fix the step kernel by its options; returns the kernel's name."""
+def set_kernel(sb, ctx, name, variant="bsb", R=256):
+    """Fix the step kernel by its options; returns the kernel's name ("auto":
+    the library's default choice, without the autotuner)."""
+    if name == "auto":
+        if variant != "dsb" and R % 128 == 0:
+            return "k_step_rw"
+        return tuned_kernel({"rows_per_warp": 0, "tiled": 0, "tile": 0, "groups": 1}, variant, R)
+    sb.sb_set_option(ctx, sb.SB_OPT_ROWS_PER_WARP, 0)
     if name == "rowgroup2" or name == "rowgroup4":
         sb.sb_set_option(ctx, sb.SB_OPT_ROWS_PER_WARP, int(name[-1]))
         return "k_step_rw"
@@ -291,7 +297,7 @@ def run_ours(args):
         tuned = sb.sb_autotune(ctx, args.variant, R, trial_steps=30)   # untimed set-up
         kname = tuned_kernel(tuned[0], args.variant, R)
     else:
-        kname = set_kernel(sb, ctx, args.kernel)
+        kname = set_kernel(sb, ctx, args.kernel, args.variant, R)
         if args.rows_per_cta:
             sb.sb_set_option(ctx, sb.SB_OPT_STEP_RPC, args.rows_per_cta)
     sched = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
@@ -694,7 +700,7 @@ def run_study(args):
             ref = None
             for name, rpc in kernels:
                 ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, prec)
-                kname = set_kernel(sb, ctx, name)
+                kname = set_kernel(sb, ctx, name, variant, R)
                 sb.sb_set_option(ctx, sb.SB_OPT_STEP_RPC, rpc)
                 sb.sb_run(ctx, variant, 1.0, 0.0, 0.5, 0, R, 7, None, stream)
                 sb.sb_advance(ctx, variant, 1.0, 0.0, 0.5, S, sched, stream)

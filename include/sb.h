@@ -387,7 +387,8 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
  * multiple of 128: one warp owns a group of that many rows (grouped on the
  * host, on first use, so that they share neighbours) and walks the sorted
  * union of their columns, loading each neighbour row of x once for all of
- * them. 0 (default) turns it off. Same
+ * them. 0 turns it off. -1 (default) chooses: groups of 2 for aSB and bSB
+ * unless SB_OPT_TILED or SB_OPT_STEP_RT is set, off for dSB. Same
  * FMA order as the untiled kernel, so the states are identical. With it,
  * SB_OPT_STEP_RPC sets rows per CTA (divided by the group size) and
  * SB_OPT_STEP_RT = 128 makes a warp cover 128 replicas instead of 256. */

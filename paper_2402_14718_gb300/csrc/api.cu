@@ -128,7 +128,7 @@ struct sb_ctx {
   uint32_t* d_s_umask = nullptr;
   int* d_err = nullptr;  // set by a kernel whose bounded wait gave up
   // row-group step kernel (k_step_rw): groups of RW rows and their union entries
-  int rw_rows = 0;       // 0: off; 2 or 4 rows per warp
+  int rw_rows = -1;      // -1: automatic (2 for aSB / bSB, off for dSB); 0: off; 2 or 4
   int rw_built = 0;      // RW the tables below were built for (0: none)
   int32_t rw_ngroups = 0;
   int64_t rw_E = 0;
@@ -850,11 +850,15 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   // row-group kernel: chosen, R a multiple of 128, tables valid
   int rw = 0, rw_nch = 0;
   sbd::RwArgs ra{};
-  if (!streamed && c->rw_rows && c->groups == 1 && c->R % 128 == 0) {
-    sb_status st0 = ensure_rw(c, c->rw_rows);
+  // automatic choice: row groups of 2 for aSB / bSB, which gather FP32 x;
+  // dSB keeps its sign-byte kernel (fewer instructions per neighbour)
+  const int rw_want = c->rw_rows < 0 ? (variant == SB_DSB ? 0 : 2) : c->rw_rows;
+  const bool rw_auto_ok = c->rw_rows >= 0 || (!c->use_tiled && c->step_rt == 0);
+  if (!streamed && rw_want && rw_auto_ok && c->groups == 1 && c->R % 128 == 0) {
+    sb_status st0 = ensure_rw(c, rw_want);
     if (st0) return st0;
-    if (c->rw_built == c->rw_rows) {
-      rw = c->rw_rows;
+    if (c->rw_built == rw_want) {
+      rw = rw_want;
       rw_nch = (c->R % 256 == 0 && c->step_rt != 128) ? 2 : 1;
       ra.gptr = c->d_rw_gptr;
       ra.grows = c->d_rw_rows;
@@ -1806,8 +1810,8 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value) {
       return SB_OK;
     }
     case 9:  // SB_OPT_ROWS_PER_WARP
-      if (value != 0 && value != 2 && value != 4) {
-        set_error("sb_set_option: SB_OPT_ROWS_PER_WARP must be 0, 2 or 4");
+      if (value != -1 && value != 0 && value != 2 && value != 4) {
+        set_error("sb_set_option: SB_OPT_ROWS_PER_WARP must be -1, 0, 2 or 4");
         return SB_ERR_ARG;
       }
       ctx->rw_rows = (int)value;
