@@ -94,7 +94,7 @@ def job_value(units_per_rank, world_size, ms):
 # replica tile) and the step-kernel sources (sha256 prefix of kernels.cu,
 # kernels.cuh, rw.cu, stream.cu); any other combination reports null.
 MEASURED_TRAFFIC = {
-    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "8359cb6d4e693882"): 89570560 + 33273600,
+    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "a9cf31ce74d7c077"): 89570048 + 33239040,
 }
 
 
