@@ -218,18 +218,31 @@ def workload(name, sb_steps):
 
 
 # ---------------------------------------------------------------- oracle (CPU) leg
+_ORACLE_PROBLEMS = {}
+
+
+def oracle_problem(w):
+    """The workload's event, QUBO and Ising form built by the oracle (cached)."""
+    key = (w["seed"], w["n_tracks"], w["noise_frac"], tuple(sorted(w["cuts"].items())))
+    if key not in _ORACLE_PROBLEMS:
+        from oracle import events as oev, ising, qubo as oq
+        kw = dict(w["cuts"])
+        kw["five_hit_rule"] = bool(kw["five_hit_rule"])
+        ev = oev.generate(w["seed"], oev.EventParams(n_tracks=w["n_tracks"],
+                                                     noise_frac=w["noise_frac"]))
+        q = oq.build_qubo(ev, oq.BuildParams(**kw))
+        J, h, _ = ising.to_ising(q)
+        _ORACLE_PROBLEMS[key] = (q.n, J, h, ising.c0_auto(J, q.n))
+    return _ORACLE_PROBLEMS[key]
+
+
 def oracle_sample(w, variant, target_s=15.0, seed=1):
     """Time the FP64 oracle on a bounded sample of the workload: the full QUBO
     and replica count, as many SB steps as fit in about ``target_s`` seconds."""
-    from oracle import events as oev, ising, qubo as oq, sb as osb
-    kw = dict(w["cuts"])
-    kw["five_hit_rule"] = bool(kw["five_hit_rule"])
-    ev = oev.generate(w["seed"], oev.EventParams(n_tracks=w["n_tracks"], noise_frac=w["noise_frac"]))
-    q = oq.build_qubo(ev, oq.BuildParams(**kw))
-    J, h, _ = ising.to_ising(q)
-    c0 = ising.c0_auto(J, q.n)
+    from oracle import sb as osb
+    n, J, h, c0 = oracle_problem(w)
     R, S = w["replicas"], w["steps"]
-    x, y = osb.init_state(seed, q.n, R)
+    x, y = osb.init_state(seed, n, R)
     sched = osb.linear_schedule(w["a0"], S)
     v = {"asb": osb.ASB, "bsb": osb.BSB, "dsb": osb.DSB}[variant]
     t0 = time.perf_counter()
@@ -238,9 +251,67 @@ def oracle_sample(w, variant, target_s=15.0, seed=1):
         x, y = osb.step(J, h, x, y, float(sched[k]), w["a0"], c0, w["dt"], v)
         k += 1
     dt = time.perf_counter() - t0
-    return {"value": q.n * R * k / dt, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{k} of {S} SB steps, N={q.n}, R={R}, FP64 NumPy/SciPy, one thread",
+    return {"value": n * R * k / dt, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} of {S} SB steps, N={n}, R={R}, FP64 NumPy/SciPy, one thread",
             "seconds": dt}
+
+
+def _oracle_steps(job):
+    """Worker of the all-cores oracle timing: k oracle steps on a slice of the replicas."""
+    J, h, x, y, sched, a0, c0, dt, v, k = job
+    from oracle import sb as osb
+    for i in range(k):
+        x, y = osb.step(J, h, x, y, float(sched[i]), a0, c0, dt, v)
+    return x.shape[1]
+
+
+def cpu_model():
+    """Host CPU as /proc/cpuinfo names it (model name, or the part number on Arm)."""
+    import platform
+    name = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read().splitlines()
+        for key in ("model name", "CPU part"):
+            vals = [l.split(":", 1)[1].strip() for l in info if l.startswith(key)]
+            if vals:
+                name = vals[0] if key == "model name" else key + " " + vals[0]
+                break
+    except OSError:
+        pass
+    return f"{platform.machine()} {name}".strip()
+
+
+def oracle_all_cores(w, variant, k, seed=1):
+    """The same oracle, as it stands, on every host core: the replicas split into
+    one slice per process (spawned, so safe after CUDA use), k steps each."""
+    import multiprocessing as mp
+    from oracle import sb as osb
+    n, J, h, c0 = oracle_problem(w)
+    R = w["replicas"]
+    x, y = osb.init_state(seed, n, R)
+    sched = osb.linear_schedule(w["a0"], w["steps"])[:k]
+    v = {"asb": osb.ASB, "bsb": osb.BSB, "dsb": osb.DSB}[variant]
+    P = max(1, min(os.cpu_count() or 1, R))
+    cuts = np.linspace(0, R, P + 1).astype(int)
+    jobs = [(J, h, x[:, a:b].copy(), y[:, a:b].copy(), sched, w["a0"], c0, w["dt"], v, k)
+            for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+    saved = os.environ.get("OMP_NUM_THREADS")
+    os.environ["OMP_NUM_THREADS"] = "1"
+    try:
+        with mp.get_context("spawn").Pool(len(jobs)) as pool:
+            pool.map(_oracle_steps, [j[:-1] + (1,) for j in jobs])   # start-up and imports
+            t0 = time.perf_counter()
+            pool.map(_oracle_steps, jobs)
+            dt = time.perf_counter() - t0
+    finally:
+        if saved is None:
+            os.environ.pop("OMP_NUM_THREADS", None)
+        else:
+            os.environ["OMP_NUM_THREADS"] = saved
+    return {"value": n * R * k / dt, "cores": len(jobs),
+            "sample": f"{k} SB steps, N={n}, R={R} split over {len(jobs)} processes, "
+                      f"FP64 NumPy/SciPy, one thread each"}
 
 
 def run_reference(args):
@@ -407,7 +478,11 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and N <= 100000:
         cpu = oracle_sample(w, args.variant)
+        k = int(cpu["sample"].split()[0])
         cpu.pop("seconds", None)
+        cpu["cpu"] = cpu_model()
+        cpu["nproc"] = os.cpu_count()
+        cpu["all_cores"] = oracle_all_cores(w, args.variant, k)
 
     launches_per_step = 3 + S + 4   # set_c0 + init + set_c0, S x step, energy partial/reduce/argmin/best_T
     line = {"metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws,
