@@ -5,9 +5,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/sb.h"
@@ -24,18 +26,57 @@ namespace {
 
 const int kEnergyRowsMin = 64;
 
+// A run of steps is captured into a CUDA graph the second time the same run
+// shape is asked for in a row, and replayed from then on; the first time it is
+// launched directly, so a one-off run starts on the GPU without waiting for a
+// capture and instantiation.
 struct GraphCache {
   cudaGraphExec_t exec = nullptr;
-  int variant = -1, steps = -1, R = -1, cur = -1, G = -1, tiled = -1, rpc = -1, tiles = -1;
-  int unroll = -1, sgn = -1, groups = -1, stream = -1, rw = -1, nch = -1;
-  float a0 = 0.f, dt = 0.f;
-  const float* sched = nullptr;
+  std::vector<int64_t> key;   // run shape of exec
+  std::vector<int64_t> seen;  // run shape last launched directly
   void reset() {
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
-    steps = -1;
+    key.clear();
+    seen.clear();
   }
 };
+
+// f(part, begin, end) over [0, count) cut into `parts` contiguous ranges, on up
+// to `parts` host threads (fewer when the machine has fewer; sequential for
+// small counts or when a thread cannot be started).
+template <typename F>
+void parallel_parts(int64_t count, int parts, F f) {
+  auto range = [&](int p, int64_t& b, int64_t& e) {
+    b = count * p / parts;
+    e = count * (p + 1) / parts;
+  };
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int T = std::min(parts, (int)std::max(1u, std::min(hw, 16u)));
+  if (T <= 1 || count < 8192) {
+    for (int p = 0; p < parts; ++p) {
+      int64_t b, e;
+      range(p, b, e);
+      f(p, b, e);
+    }
+    return;
+  }
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    for (int p; (p = next.fetch_add(1)) < parts;) {
+      int64_t b, e;
+      range(p, b, e);
+      f(p, b, e);
+    }
+  };
+  std::vector<std::thread> th;
+  try {
+    for (int t = 1; t < T; ++t) th.emplace_back(work);
+  } catch (...) {
+  }
+  work();
+  for (auto& x : th) x.join();
+}
 
 }  // namespace
 
@@ -179,49 +220,81 @@ sb_status validate_csr(int32_t n, int64_t nnz, const int32_t* rowptr, const int3
     set_error("CSR: rowptr[0] must be 0 and rowptr[n] must equal nnz");
     return SB_ERR_CSR;
   }
-  for (int32_t i = 0; i < n; ++i) {
+  for (int32_t i = 0; i < n; ++i)  // every row range inside [0, nnz] before any col access
     if (rowptr[i + 1] < rowptr[i]) {
       set_error("CSR: rowptr decreases at row " + std::to_string(i));
       return SB_ERR_CSR;
     }
-    if (!std::isfinite(lin[i])) {
-      set_error("linear term is not finite at row " + std::to_string(i));
-      return SB_ERR_ARG;
+  // the first failing row (in row order) is reported; rows are checked in parallel parts
+  struct Fail {
+    int32_t row = INT32_MAX;
+    sb_status st = SB_OK;
+    std::string msg;
+  };
+  const int parts = 64;
+  std::vector<Fail> fail(parts);
+  auto first_failure = [&]() -> sb_status {
+    const Fail* f = nullptr;
+    for (const Fail& x : fail)
+      if (x.st != SB_OK && (!f || x.row < f->row)) f = &x;
+    if (!f) return SB_OK;
+    set_error(f->msg);
+    return f->st;
+  };
+  parallel_parts(n, parts, [&](int part, int64_t b, int64_t e) {
+    Fail& F = fail[part];
+    auto bad = [&](int32_t i, sb_status st, const std::string& m) {
+      F.row = i;
+      F.st = st;
+      F.msg = m;
+    };
+    for (int32_t i = (int32_t)b; i < (int32_t)e && F.st == SB_OK; ++i) {
+      if (!std::isfinite(lin[i])) {
+        bad(i, SB_ERR_ARG, "linear term is not finite at row " + std::to_string(i));
+        break;
+      }
+      for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        const int32_t j = col[p];
+        if (j < 0 || j >= n) {
+          bad(i, SB_ERR_CSR, "CSR: column out of range in row " + std::to_string(i));
+          break;
+        }
+        if (j == i) {
+          bad(i, SB_ERR_CSR, "CSR: diagonal entry in row " + std::to_string(i));
+          break;
+        }
+        if (p > rowptr[i] && col[p - 1] >= j) {
+          bad(i, SB_ERR_CSR, "CSR: columns not strictly ascending in row " + std::to_string(i));
+          break;
+        }
+        if (!std::isfinite(val[p])) {
+          bad(i, SB_ERR_ARG, "CSR: value not finite in row " + std::to_string(i));
+          break;
+        }
+      }
     }
-    for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-      const int32_t j = col[p];
-      if (j < 0 || j >= n) {
-        set_error("CSR: column out of range in row " + std::to_string(i));
-        return SB_ERR_CSR;
-      }
-      if (j == i) {
-        set_error("CSR: diagonal entry in row " + std::to_string(i));
-        return SB_ERR_CSR;
-      }
-      if (p > rowptr[i] && col[p - 1] >= j) {
-        set_error("CSR: columns not strictly ascending in row " + std::to_string(i));
-        return SB_ERR_CSR;
-      }
-      if (!std::isfinite(val[p])) {
-        set_error("CSR: value not finite in row " + std::to_string(i));
-        return SB_ERR_ARG;
-      }
-    }
-  }
+  });
+  sb_status st = first_failure();
+  if (st) return st;
   // symmetry: (i, j, v) needs (j, i, v)
-  for (int32_t i = 0; i < n; ++i)
-    for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-      const int32_t j = col[p];
-      const int32_t* b = col + rowptr[j];
-      const int32_t* e = col + rowptr[j + 1];
-      const int32_t* f = std::lower_bound(b, e, i);
-      if (f == e || *f != i || val[rowptr[j] + (f - b)] != val[p]) {
-        set_error("CSR: matrix is not symmetric at (" + std::to_string(i) + ", " +
-                  std::to_string(j) + ")");
-        return SB_ERR_CSR;
+  parallel_parts(n, parts, [&](int part, int64_t b, int64_t e) {
+    Fail& F = fail[part];
+    for (int32_t i = (int32_t)b; i < (int32_t)e && F.st == SB_OK; ++i)
+      for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        const int32_t j = col[p];
+        const int32_t* lo = col + rowptr[j];
+        const int32_t* hi = col + rowptr[j + 1];
+        const int32_t* f = std::lower_bound(lo, hi, i);
+        if (f == hi || *f != i || val[rowptr[j] + (f - lo)] != val[p]) {
+          F.row = i;
+          F.st = SB_ERR_CSR;
+          F.msg = "CSR: matrix is not symmetric at (" + std::to_string(i) + ", " +
+                  std::to_string(j) + ")";
+          break;
+        }
       }
-    }
-  return SB_OK;
+  });
+  return first_failure();
 }
 
 void free_readout(sb_ctx* c) {
@@ -568,12 +641,16 @@ sb_status ensure_stream(sb_ctx* c) {
   return SB_OK;
 }
 
-// Tables of the row-group kernel. Groups of RW rows are formed greedily in row
+// Tables of the row-group kernel. Rows are cut into 64 contiguous parts (built
+// on parallel host threads; the cut, and so the tables, do not depend on the
+// thread count). Within a part, groups of RW rows are formed greedily in row
 // order: the first row not yet placed anchors a group, which then takes, one
-// at a time, the unplaced candidate (a neighbour of the anchor or one of the
-// next 7 rows) adding the fewest new columns to the group's union. A group's
-// entries are the sorted union of its rows' columns (a k-way merge of the CSR
-// rows), each with an RW-bit mask and the CSR position of every slot.
+// at a time, the unplaced candidate of the same part (a neighbour of the
+// anchor or one of the next 7 rows) adding the fewest new columns to the
+// group's union. A group's entries are the sorted union of its rows' columns
+// (a k-way merge of the CSR rows), each with an RW-bit mask and the CSR
+// position of every slot. The grouping only decides which rows share loads;
+// every row still accumulates its own nonzeros in CSR order.
 struct RwHost {
   bool ok = false;
   std::vector<int32_t> gptr, rows, ent, pos;
@@ -582,66 +659,88 @@ struct RwHost {
 RwHost build_rw(int32_t n, const int32_t* rp, const int32_t* col, int RW) {
   RwHost t;
   if (n >= (1 << 27) || RW < 2 || RW > sbd::kRwMaxRows) return t;
-  // greedy grouping
-  std::vector<char> placed(n, 0);
-  std::vector<int32_t> stamp(n, -1);
-  int32_t ng = 0;
-  for (int32_t i = 0; i < n; ++i) {
-    if (placed[i]) continue;
-    placed[i] = 1;
-    const size_t g0 = t.rows.size();
-    t.rows.push_back(i);
-    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) stamp[col[p]] = ng;
-    for (int k = 1; k < RW; ++k) {
-      int32_t best = -1, best_add = INT32_MAX;
-      auto consider = [&](int32_t j) {
-        if (placed[j]) return;
-        int32_t add = 0;
-        for (int32_t p = rp[j]; p < rp[j + 1] && add < best_add; ++p) add += stamp[col[p]] != ng;
-        if (add < best_add) {
-          best_add = add;
-          best = j;
-        }
-      };
-      for (int32_t p = rp[i]; p < rp[i + 1] && best_add > 0; ++p) consider(col[p]);
-      for (int32_t j = i + 1; j < std::min(n, i + 8) && best_add > 0; ++j) consider(j);
-      if (best < 0) break;
-      placed[best] = 1;
-      t.rows.push_back(best);
-      for (int32_t p = rp[best]; p < rp[best + 1]; ++p) stamp[col[p]] = ng;
-    }
-    t.rows.resize(g0 + RW, -1);
-    ++ng;
-  }
-  t.gptr.reserve((size_t)ng + 1);
-  t.ent.reserve((size_t)rp[n]);
-  t.pos.reserve((size_t)rp[n] * RW);
-  t.gptr.push_back(0);
-  for (int32_t g = 0; g < ng; ++g) {
-    int32_t p[sbd::kRwMaxRows], pe[sbd::kRwMaxRows];
-    for (int q = 0; q < RW; ++q) {
-      const int32_t row = t.rows[(size_t)g * RW + q];
-      p[q] = row >= 0 ? rp[row] : 0;
-      pe[q] = row >= 0 ? rp[row + 1] : 0;
-    }
-    for (;;) {
-      int32_t cmin = INT32_MAX;
-      for (int q = 0; q < RW; ++q)
-        if (p[q] < pe[q]) cmin = std::min(cmin, col[p[q]]);
-      if (cmin == INT32_MAX) break;
-      int32_t mask = 0;
-      for (int q = 0; q < RW; ++q) {
-        if (p[q] < pe[q] && col[p[q]] == cmin) {
-          mask |= 1 << q;
-          t.pos.push_back(p[q]++);
-        } else {
-          t.pos.push_back(-1);
-        }
+  const int parts = 64;
+  struct Part {
+    std::vector<int32_t> rows, cnt, ent, pos;
+  };
+  std::vector<Part> P(parts);
+  parallel_parts(n, parts, [&](int part, int64_t b64, int64_t e64) {
+    const int32_t b = (int32_t)b64, e = (int32_t)e64;
+    Part& q = P[part];
+    if (e <= b) return;
+    std::vector<char> placed((size_t)(e - b), 0);
+    std::vector<int32_t> stamp((size_t)n, -1);
+    int32_t ng = 0;
+    for (int32_t i = b; i < e; ++i) {
+      if (placed[i - b]) continue;
+      placed[i - b] = 1;
+      const size_t g0 = q.rows.size();
+      q.rows.push_back(i);
+      for (int32_t p = rp[i]; p < rp[i + 1]; ++p) stamp[col[p]] = ng;
+      for (int k = 1; k < RW; ++k) {
+        int32_t best = -1, best_add = INT32_MAX;
+        auto consider = [&](int32_t j) {
+          if (j < b || j >= e || placed[j - b]) return;
+          int32_t add = 0;
+          for (int32_t p = rp[j]; p < rp[j + 1] && add < best_add; ++p) add += stamp[col[p]] != ng;
+          if (add < best_add) {
+            best_add = add;
+            best = j;
+          }
+        };
+        for (int32_t p = rp[i]; p < rp[i + 1] && best_add > 0; ++p) consider(col[p]);
+        for (int32_t j = i + 1; j < std::min(e, i + 8) && best_add > 0; ++j) consider(j);
+        if (best < 0) break;
+        placed[best - b] = 1;
+        q.rows.push_back(best);
+        for (int32_t p = rp[best]; p < rp[best + 1]; ++p) stamp[col[p]] = ng;
       }
-      t.ent.push_back((cmin << 4) | mask);
+      q.rows.resize(g0 + RW, -1);
+      ++ng;
     }
-    if (t.ent.size() > (size_t)INT32_MAX / 8) return t;
-    t.gptr.push_back((int32_t)t.ent.size());
+    for (int32_t g = 0; g < ng; ++g) {
+      int32_t p[sbd::kRwMaxRows], pe[sbd::kRwMaxRows];
+      for (int k = 0; k < RW; ++k) {
+        const int32_t row = q.rows[(size_t)g * RW + k];
+        p[k] = row >= 0 ? rp[row] : 0;
+        pe[k] = row >= 0 ? rp[row + 1] : 0;
+      }
+      const size_t before = q.ent.size();
+      for (;;) {
+        int32_t cmin = INT32_MAX;
+        for (int k = 0; k < RW; ++k)
+          if (p[k] < pe[k]) cmin = std::min(cmin, col[p[k]]);
+        if (cmin == INT32_MAX) break;
+        int32_t mask = 0;
+        for (int k = 0; k < RW; ++k) {
+          if (p[k] < pe[k] && col[p[k]] == cmin) {
+            mask |= 1 << k;
+            q.pos.push_back(p[k]++);
+          } else {
+            q.pos.push_back(-1);
+          }
+        }
+        q.ent.push_back((cmin << 4) | mask);
+      }
+      q.cnt.push_back((int32_t)(q.ent.size() - before));
+    }
+  });
+  size_t E = 0, G = 0;
+  for (const Part& q : P) {
+    E += q.ent.size();
+    G += q.cnt.size();
+  }
+  if (E > (size_t)INT32_MAX / 8) return t;
+  t.gptr.reserve(G + 1);
+  t.rows.reserve(G * RW);
+  t.ent.reserve(E);
+  t.pos.reserve(E * RW);
+  t.gptr.push_back(0);
+  for (const Part& q : P) {
+    for (int32_t c : q.cnt) t.gptr.push_back(t.gptr.back() + c);
+    t.rows.insert(t.rows.end(), q.rows.begin(), q.rows.end());
+    t.ent.insert(t.ent.end(), q.ent.begin(), q.ent.end());
+    t.pos.insert(t.pos.end(), q.pos.begin(), q.pos.end());
   }
   t.ok = true;
   return t;
@@ -1038,8 +1137,19 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     a.tile0 = 0;
     return err;
   };
-  const bool graph = c->use_graph && steps >= 8;
-  if (!graph) {
+  std::vector<int64_t> key;
+  if (c->use_graph && steps >= 8) {
+    int32_t a0b = 0, dtb = 0;
+    memcpy(&a0b, &a.a0, 4);
+    memcpy(&dtb, &a.dt, 4);
+    key = {variant, steps, c->R, c->cur, a0b, dtb, (int64_t)(intptr_t)sched, t.G, tiled, a.rpc,
+           t.tiles, a.unroll, sgn, ngroups, streamed, rw, rw_nch};
+  }
+  GraphCache& gc = c->graph;
+  const bool replay = !key.empty() && gc.exec && gc.key == key;
+  const bool capture = !key.empty() && !replay && gc.seen == key;
+  if (!replay && !capture) {
+    if (!key.empty()) gc.seen = key;
     SB_CUDA(launch_all(c->cur, stream));
     if (steps & 1) c->cur ^= 1;
     if (c->l2_persist && win_max) {  // leave the caller's stream without our window
@@ -1049,12 +1159,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     }
     return SB_OK;
   }
-  GraphCache& gc = c->graph;
-  if (!(gc.exec && gc.variant == variant && gc.steps == steps && gc.R == c->R &&
-        gc.cur == c->cur && gc.a0 == a.a0 && gc.dt == a.dt && gc.sched == sched && gc.G == t.G &&
-        gc.tiled == tiled && gc.rpc == a.rpc && gc.tiles == t.tiles && gc.unroll == a.unroll &&
-        gc.sgn == sgn && gc.groups == ngroups && gc.stream == streamed && gc.rw == rw &&
-        gc.nch == rw_nch)) {
+  if (capture) {
     gc.reset();
     cudaGraph_t g = nullptr;
     SB_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -1065,23 +1170,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     cudaError_t e3 = cudaGraphInstantiate(&gc.exec, g, 0);
     cudaGraphDestroy(g);
     SB_CUDA(e3);
-    gc.variant = variant;
-    gc.steps = steps;
-    gc.R = c->R;
-    gc.cur = c->cur;
-    gc.a0 = a.a0;
-    gc.dt = a.dt;
-    gc.sched = sched;
-    gc.G = t.G;
-    gc.tiled = tiled;
-    gc.rpc = a.rpc;
-    gc.tiles = t.tiles;
-    gc.unroll = a.unroll;
-    gc.sgn = sgn;
-    gc.groups = ngroups;
-    gc.stream = streamed;
-    gc.rw = rw;
-    gc.nch = rw_nch;
+    gc.key = key;
   }
   SB_CUDA(cudaGraphLaunch(gc.exec, stream));
   if (steps & 1) c->cur ^= 1;

@@ -76,3 +76,46 @@ def test_malformed_csr_is_rejected_before_any_device_work(case):
     with pytest.raises(sb.SbError) as ei:
         sb.sb_create(3, rowptr, col, val, np.zeros(3))
     assert ei.value.code == _lib.SB_ERR_CSR
+
+
+@pytest.mark.parametrize("case", ["diag", "range", "asym", "nan"])
+def test_large_malformed_csr_reports_the_first_bad_row(case):
+    """Rows are checked on several host threads when the CSR is large; the
+    error still names the first bad row in row order (two faults planted in
+    different parts of a 100,000-row chain)."""
+    import paper_2402_14718_gb300 as sb
+    from paper_2402_14718_gb300 import _lib
+    n = 100000
+    rows, cols = [], []
+    for i in range(n):
+        for j in (i - 1, i + 1):
+            if 0 <= j < n:
+                rows.append(i)
+                cols.append(j)
+    rowptr = np.zeros(n + 1, np.int32)
+    np.add.at(rowptr, np.array(rows) + 1, 1)
+    rowptr = np.cumsum(rowptr).astype(np.int32)
+    col = np.array(cols, np.int32)
+    val = np.full(len(col), -1.0)
+    lin = np.zeros(n)
+    first, second = 70001, 90001
+    if case == "diag":
+        col[rowptr[first]] = first
+        col[rowptr[second]] = second
+        want, code = f"diagonal entry in row {first}", _lib.SB_ERR_CSR
+    elif case == "range":
+        col[rowptr[first + 1] - 1] = n + 5
+        col[rowptr[second + 1] - 1] = n + 5
+        want, code = f"column out of range in row {first}", _lib.SB_ERR_CSR
+    elif case == "asym":
+        val[rowptr[second]] = 0.5
+        val[rowptr[first]] = 0.5
+        want, code = f"not symmetric at ({first - 1}, {first})", _lib.SB_ERR_CSR
+    else:
+        lin[second] = np.nan
+        val[rowptr[first]] = np.inf
+        want, code = f"value not finite in row {first}", _lib.SB_ERR_ARG
+    with pytest.raises(sb.SbError) as ei:
+        sb.sb_create(n, rowptr, col, val, lin)
+    assert ei.value.code == code
+    assert want in sb.lib.sb_last_error().decode()
