@@ -285,17 +285,21 @@ sb_status sb_set_weights(sb_ctx* ctx, const int8_t* cls, const double* quality, 
  * (section "Simulated Bifurcation", Eq. 5-8, with the field term of sb_run):
  *   L = (1/R) sum_r [ -(1/2) x_S,r^T J x_S,r - h^T x_S,r ],
  * x_S the positions after `steps` bSB steps from the Philox start of `seed`.
- * The run is repeated on the device with (x, y) kept every `ckpt_every` steps;
- * each segment is then recomputed (recording the pre-wall momentum and the
- * wall mask) and reversed. The wall is treated as the piecewise map it is:
+ * The run is repeated on the device with (x, y) kept at the start of every
+ * `ckpt_every`-step segment; the last segment records, as it runs, the
+ * pre-wall momentum, the wall mask and J x, each earlier one is recomputed
+ * with that recording, and every segment is then reversed. With
+ * ckpt_every >= steps the whole run is recorded once and nothing is
+ * recomputed (fastest; memory grows with steps). The wall is treated as the piecewise map it is:
  * where it fires the new position is a constant and no adjoint flows through.
  * c0 (> 0) is an input of the gradient path (no automatic c0 here).
  * Outputs (host, may be NULL): out_loss; out_grads[4] = dL/d dt, dL/d c0,
  * dL/d w_q, dL/d w_c (the last two are NaN unless sb_set_weights was called);
  * d_grad_sched: device FP64 [steps] = dL/d a_k (may be NULL).
  * a_sched: device FP32 [steps] or NULL for the linear ramp. Single-event
- * contexts only. Work memory: 2 (steps/ckpt_every + 1) + 2 ckpt_every + 4
- * state-sized FP32 arrays plus ckpt_every byte masks. Synchronous; discards
+ * contexts only. Work memory: 2 (ceil(steps / ckpt_every) - 1) + 3 K + 4
+ * state-sized FP32 arrays plus K byte masks, K = min(ckpt_every, steps).
+ * Synchronous; discards
  * the current state.
  */
 sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t steps,

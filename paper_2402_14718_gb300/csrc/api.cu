@@ -1617,7 +1617,8 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
     dfree(acc);
     dfree(ga);
   };
-  if ((st = dalloc(&ck_x, NR * n_ck)) || (st = dalloc(&ck_y, NR * n_ck)) ||
+  // checkpoints for all segments but the last, which is recorded on the way forward
+  if ((st = dalloc(&ck_x, NR * (n_ck - 1))) || (st = dalloc(&ck_y, NR * (n_ck - 1))) ||
       (st = dalloc(&seg_x, NR * (K + 1))) || (st = dalloc(&seg_yt, NR * K)) ||
       (st = dalloc(&seg_f, NR * K)) ||
       (st = dalloc(&seg_m, NR * K)) || (st = dalloc(&lx, NR)) || (st = dalloc(&ly, NR)) ||
@@ -1657,12 +1658,11 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
   ok(sbd::launch_set_c0(ctx->d_c0ev, ctx->d_c0auto, c0, 1, s));
   ok(sbd::launch_init(ctx->d_x[0], ctx->d_y, nullptr, ctx->d_ev_row0, n, R, seed, s));
   int cur = 0;
-  // forward, keeping (x, y) at the start of every segment
-  for (int32_t c = 0; c < n_ck && e == cudaSuccess; ++c) {
+  // forward, keeping (x, y) at the start of every segment but the last
+  for (int32_t c = 0; c + 1 < n_ck && e == cudaSuccess; ++c) {
     ok(cudaMemcpyAsync(ck_x + NR * c, ctx->d_x[cur], NR * 4, cudaMemcpyDeviceToDevice, s));
     ok(cudaMemcpyAsync(ck_y + NR * c, ctx->d_y, NR * 4, cudaMemcpyDeviceToDevice, s));
-    const int32_t L = std::min(K, S - c * K);
-    for (int32_t j = 0; j < L && e == cudaSuccess; ++j) {
+    for (int32_t j = 0; j < K && e == cudaSuccess; ++j) {
       a.k = c * K + j;
       a.xin = ctx->d_x[cur];
       a.xout = ctx->d_x[cur ^ 1];
@@ -1671,6 +1671,26 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
       cur ^= 1;
     }
   }
+  // the last segment, recorded as it runs: x_k, pre-wall momentum, wall mask, J x_k
+  const int32_t c_last = n_ck - 1;
+  const int32_t L_last = S - c_last * K;
+  auto record_segment = [&](int32_t c, int32_t L) {
+    for (int32_t j = 0; j < L && e == cudaSuccess; ++j) {
+      a.k = c * K + j;
+      a.xin = seg_x + NR * j;
+      a.xout = seg_x + NR * (j + 1);
+      a.y = ctx->d_y;
+      a.ytil = seg_yt + NR * j;
+      a.mask = seg_m + NR * j;
+      a.frec = seg_f + NR * j;
+      ok(sbd::launch_step(SB_BSB, ctx->jbf16, t, a, s));
+    }
+    a.ytil = nullptr;
+    a.mask = nullptr;
+    a.frec = nullptr;
+  };
+  ok(cudaMemcpyAsync(seg_x, ctx->d_x[cur], NR * 4, cudaMemcpyDeviceToDevice, s));
+  record_segment(c_last, L_last);
   ok(cudaMemsetAsync(gh, 0, (size_t)n * 8, s));
   ok(cudaMemsetAsync(acc, 0, 6 * 8, s));
   ok(cudaMemsetAsync(ga, 0, (size_t)S * 8, s));
@@ -1690,7 +1710,7 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
   g.dt = (float)dt;
   g.sched = sched;
   g.k = 0;
-  g.x = ctx->d_x[cur];
+  g.x = seg_x + NR * L_last;  // x_S
   g.ytil = nullptr;
   g.mask = nullptr;
   g.frec = nullptr;
@@ -1701,24 +1721,15 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
   g.acc = acc;
   g.ga = nullptr;
   ok(sbd::launch_adj_init(ctx->jbf16, t, g, s));
-  // reverse sweep, one segment at a time: recompute it with recording, then reverse it
+  // reverse sweep, one segment at a time: recompute it with recording (the
+  // last one is recorded already), then reverse it
   for (int32_t c = n_ck - 1; c >= 0 && e == cudaSuccess; --c) {
     const int32_t L = std::min(K, S - c * K);
-    ok(cudaMemcpyAsync(seg_x, ck_x + NR * c, NR * 4, cudaMemcpyDeviceToDevice, s));
-    ok(cudaMemcpyAsync(ctx->d_y, ck_y + NR * c, NR * 4, cudaMemcpyDeviceToDevice, s));
-    for (int32_t j = 0; j < L && e == cudaSuccess; ++j) {
-      a.k = c * K + j;
-      a.xin = seg_x + NR * j;
-      a.xout = seg_x + NR * (j + 1);
-      a.y = ctx->d_y;
-      a.ytil = seg_yt + NR * j;
-      a.mask = seg_m + NR * j;
-      a.frec = seg_f + NR * j;
-      ok(sbd::launch_step(SB_BSB, ctx->jbf16, t, a, s));
+    if (c < c_last) {
+      ok(cudaMemcpyAsync(seg_x, ck_x + NR * c, NR * 4, cudaMemcpyDeviceToDevice, s));
+      ok(cudaMemcpyAsync(ctx->d_y, ck_y + NR * c, NR * 4, cudaMemcpyDeviceToDevice, s));
+      record_segment(c, L);
     }
-    a.ytil = nullptr;
-    a.mask = nullptr;
-    a.frec = nullptr;
     for (int32_t j = L - 1; j >= 0 && e == cudaSuccess; --j) {
       g.k = c * K + j;
       g.x = seg_x + NR * j;

@@ -767,19 +767,23 @@ __global__ void k_adj_phase1(const AdjArgs a) {
 }
 
 // Momentum update reversed: lx_k = lx~ - dt (a0 - a_k) ly~ + dt c0 J ly~, ly_k = ly~,
-// and the gradient contributions of this step (FP64). One gather of ly~ gives
-// both J ly~ and C ly~ (conflict entries only); J x_k comes recorded from the
+// and the gradient contributions of this step. One gather of ly~ gives both
+// J ly~ and C ly~ (conflict entries only); J x_k comes recorded from the
 // forward recomputation, and sum ly~ (C x_k) = sum x_k (C ly~) since C is
-// symmetric.
+// symmetric. Each element's gradient terms are products of FP32 values formed
+// in FP32 and summed in FP64 (FP64 arithmetic is scarce on this part). A
+// block walks several row groups (grid-stride), so only a few blocks per SM
+// add their sums into the shared FP64 totals.
 template <int V, int NCH, typename JT>
 __global__ void __launch_bounds__(kBlock) k_adj_phase2(const AdjArgs a) {
   const int G = a.G;
   const int gid = threadIdx.x / G, g = threadIdx.x - gid * G;
-  const int row = blockIdx.x * (blockDim.x / G) + gid;
   const int C = a.R / V;
   const int ch0 = blockIdx.y * (G * NCH) + g;
-  double gdt = 0.0, gc0 = 0.0, ga = 0.0, gwc = 0.0, ghr = 0.0;
-  if (row < a.n) {
+  double gdt = 0.0, gc0 = 0.0, ga = 0.0, gwc = 0.0;
+  const int rstep = gridDim.x * (blockDim.x / G);
+  for (int row = blockIdx.x * (blockDim.x / G) + gid; row < a.n; row += rstep) {
+    double ghr = 0.0;
     const unsigned mask = group_mask(G);
     const JT* J = static_cast<const JT*>(a.J);
     float sJ[NCH][V], sC[NCH][V];
@@ -797,7 +801,36 @@ __global__ void __launch_bounds__(kBlock) k_adj_phase2(const AdjArgs a) {
         mv = jval(J, pb + g);
         mk = a.cls[pb + g];
       }
-      for (int q = 0; q < cnt; ++q) {
+      int q = 0;
+      for (; q + 4 <= cnt; q += 4) {  // four neighbours' loads in flight, then their FMAs in order
+        int c[4], kc[4];
+        float w[4];
+        Vec<V> uv[4][NCH];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          c[u] = __shfl_sync(mask, mc, q + u, G);
+          w[u] = __shfl_sync(mask, mv, q + u, G);
+          kc[u] = __shfl_sync(mask, mk, q + u, G);
+#pragma unroll
+          for (int j = 0; j < NCH; ++j) {
+            const int ch = ch0 + j * G;
+            if (ch < C) uv[u][j].ldg(a.lyt + (size_t)c[u] * a.R + (size_t)ch * V);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int j = 0; j < NCH; ++j) {
+            const int ch = ch0 + j * G;
+            if (ch >= C) continue;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              sJ[j][v] = fmaf(w[u], uv[u][j].v[v], sJ[j][v]);
+              if (kc[u]) sC[j][v] += uv[u][j].v[v];
+            }
+          }
+      }
+      for (; q < cnt; ++q) {
         const int c = __shfl_sync(mask, mc, q, G);
         const float w = __shfl_sync(mask, mv, q, G);
         const int kc = __shfl_sync(mask, mk, q, G);
@@ -817,6 +850,8 @@ __global__ void __launch_bounds__(kBlock) k_adj_phase2(const AdjArgs a) {
     }
     const float hi = a.h[row];
     const float pa = a.a0 - __ldg(a.sched + a.k);
+    const float dtc0 = a.dt * a.c0;
+    float tdt = 0.f, tc0 = 0.f, ta = 0.f, twc = 0.f, thr = 0.f;
 #pragma unroll
     for (int j = 0; j < NCH; ++j) {
       const int ch = ch0 + j * G;
@@ -827,17 +862,22 @@ __global__ void __launch_bounds__(kBlock) k_adj_phase2(const AdjArgs a) {
         const float x = a.x[idx + v];
         const float lyt = a.lyt[idx + v];
         const float lxt = a.lx[idx + v];
-        const double f = a.frec[idx + v];
-        const double F = -(double)pa * x + (double)a.c0 * (f + hi);
-        gdt += (double)lyt * F + (double)lxt * a.a0 * (double)a.ytil[idx + v];
-        gc0 += (double)lyt * a.dt * (f + hi);
-        ga += (double)lyt * a.dt * x;
-        gwc += (double)a.dt * a.c0 * (double)x * (-0.25 * (double)sC[j][v]);
-        ghr += (double)a.dt * a.c0 * lyt;
+        const float fh = a.frec[idx + v] + hi;
+        const float F = -pa * x + a.c0 * fh;
+        tdt += lyt * F + lxt * a.a0 * a.ytil[idx + v];
+        tc0 += lyt * a.dt * fh;
+        ta += lyt * a.dt * x;
+        twc += dtc0 * x * (-0.25f * sC[j][v]);
+        thr += dtc0 * lyt;
         a.lx[idx + v] = lxt - a.dt * pa * lyt + a.dt * a.c0 * sJ[j][v];
         a.ly[idx + v] = lyt;
       }
     }
+    gdt += tdt;
+    gc0 += tc0;
+    ga += ta;
+    gwc += twc;
+    ghr = thr;
     for (int off = G / 2; off > 0; off >>= 1) ghr += __shfl_down_sync(mask, ghr, off, G);
     if (g == 0) atomicAdd(a.gh + row, ghr);
   }
@@ -864,6 +904,11 @@ cudaError_t launch_adj_vn(int which, int jbf16, const Tiling& t, const AdjArgs& 
     else
       k_adj_init<V, NCH, float><<<grid, kBlock, 0, s>>>(a);
   } else {
+    // a few blocks per SM walk the rows, so few blocks add into the FP64 totals
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+      grid.x = std::min<unsigned>(grid.x, (unsigned)std::max(1, 4 * sms / (int)grid.y));
     if (jbf16)
       k_adj_phase2<V, NCH, __nv_bfloat16><<<grid, kBlock, 0, s>>>(a);
     else

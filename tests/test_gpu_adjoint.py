@@ -43,7 +43,7 @@ def _close(gg, go, rel=1e-3):
     assert np.max(np.abs(gg["sched"] - go["sched"])) <= rel * scale
 
 
-@pytest.mark.parametrize("S,K", [(30, 8), (30, 30), (45, 1)])
+@pytest.mark.parametrize("S,K", [(30, 8), (30, 30), (45, 1), (30, 64)])
 def test_adjoint_matches_oracle_event100(S, K):
     _, qc, _, qo = workload_qubos("event100")
     lg, gg = _gpu(qc, 8, S, 3, 0.3, 0.5, K)
@@ -99,7 +99,8 @@ def test_autograd_function_full_workload():
     loss = sb.SBRelaxedEnergy.apply(dt, c0, a, wq, wc, ctx, qc.cls, qc.quality, 32, 5, 32)
     loss.backward()
     l2, g2 = sb.sb_backward(ctx, 1.0, 0.3, 0.5, S, 32, 5, a.detach().cuda(), 32)
-    assert float(loss.detach()) == l2
+    # the loss is an FP64 sum combined with atomics between blocks: last-bit order effects
+    assert float(loss.detach()) == pytest.approx(l2, rel=1e-13)
     assert float(dt.grad) == pytest.approx(g2["dt"], rel=1e-9)
     assert float(wc.grad) == pytest.approx(g2["w_c"], rel=1e-9)
     assert a.grad.shape == (S,) and torch.isfinite(a.grad).all()
