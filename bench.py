@@ -91,10 +91,10 @@ def job_value(units_per_rank, world_size, ms):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step-kernel
 # launch, from an ncu capture of that launch (third step, direct launch), keyed
 # by workload, variant, kernel, its configuration (rows per warp, rows per CTA,
-# replica tile) and the step-kernel sources (sha256 prefix of kernels.cu,
-# kernels.cuh, rw.cu, stream.cu); any other combination reports null.
+# replica tile) and that kernel's sources (sha256 prefix, kernel_source_hash);
+# any other combination reports null.
 MEASURED_TRAFFIC = {
-    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "a9cf31ce74d7c077"): 89570048 + 33239040,
+    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "fd6de93553f1e0d1"): 89570048 + 33239040,
 }
 
 
@@ -140,11 +140,16 @@ def R_cfg(tuned):
     return (tuned[0]["rows_per_warp"], tuned[0]["rows_per_cta"], tuned[0]["tile"])
 
 
-def kernel_source_hash():
+# source files that define each step kernel (and the headers they include)
+KERNEL_SOURCES = {"k_step_rw": ("rw.cu", "kernels.cuh", "signs.cuh"),
+                  "k_step_stream": ("stream.cu", "kernels.cuh", "signs.cuh")}
+
+
+def kernel_source_hash(kname="k_step"):
     import hashlib
     d = os.path.join(ROOT, "paper_2402_14718_gb300", "csrc", "device")
     h = hashlib.sha256()
-    for f in ("kernels.cu", "kernels.cuh", "rw.cu", "stream.cu"):
+    for f in KERNEL_SOURCES.get(kname, ("kernels.cu", "kernels.cuh", "signs.cuh")):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -432,7 +437,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm,
                 "traffic": MEASURED_TRAFFIC.get((args.workload, args.variant, kname, R_cfg(tuned),
-                                                  kernel_source_hash())),
+                                                  kernel_source_hash(kname))),
                 "kernel": kname,
                 "peak_source": src, "alg_bytes_per_launch": alg_bytes,
                 "kstep_us": kstep_s * 1e6}
