@@ -37,7 +37,7 @@ typedef enum {
   SB_ERR_ARG = 1,      /* invalid argument (null pointer, size out of range) */
   SB_ERR_CSR = 2,      /* malformed CSR: unsorted, out of range, diagonal, asymmetric */
   SB_ERR_CUDA = 3,     /* a CUDA runtime call failed; see sb_last_error() */
-  SB_ERR_OOM = 4,      /* device allocation failed */
+  SB_ERR_OOM = 4,      /* device or host allocation failed (no C++ exception crosses this API) */
   SB_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up */
   SB_ERR_STATE = 6     /* call out of order (e.g. readout before any run) */
 } sb_status;

@@ -14,6 +14,7 @@
 
 #include "../../include/sb.h"
 #include "device/kernels.cuh"
+#include "guard.h"
 
 namespace sbh {
 static thread_local std::string g_err;
@@ -44,30 +45,28 @@ struct GraphCache {
 
 // f(part, begin, end) over [0, count) cut into `parts` contiguous ranges, on up
 // to `parts` host threads (fewer when the machine has fewer; sequential for
-// small counts or when a thread cannot be started).
+// small counts or when a thread cannot be started). Returns false if f threw
+// (e.g. a failed allocation) in any part; the remaining parts still run.
 template <typename F>
-void parallel_parts(int64_t count, int parts, F f) {
-  auto range = [&](int p, int64_t& b, int64_t& e) {
-    b = count * p / parts;
-    e = count * (p + 1) / parts;
+bool parallel_parts(int64_t count, int parts, F f) {
+  std::atomic<bool> ok{true};
+  auto run = [&](int p) {
+    const int64_t b = count * p / parts, e = count * (p + 1) / parts;
+    try {
+      f(p, b, e);
+    } catch (...) {
+      ok = false;
+    }
   };
   const unsigned hw = std::thread::hardware_concurrency();
   const int T = std::min(parts, (int)std::max(1u, std::min(hw, 16u)));
   if (T <= 1 || count < 8192) {
-    for (int p = 0; p < parts; ++p) {
-      int64_t b, e;
-      range(p, b, e);
-      f(p, b, e);
-    }
-    return;
+    for (int p = 0; p < parts; ++p) run(p);
+    return ok;
   }
   std::atomic<int> next{0};
   auto work = [&]() {
-    for (int p; (p = next.fetch_add(1)) < parts;) {
-      int64_t b, e;
-      range(p, b, e);
-      f(p, b, e);
-    }
+    for (int p; (p = next.fetch_add(1)) < parts;) run(p);
   };
   std::vector<std::thread> th;
   try {
@@ -76,6 +75,7 @@ void parallel_parts(int64_t count, int parts, F f) {
   }
   work();
   for (auto& x : th) x.join();
+  return ok;
 }
 
 }  // namespace
@@ -241,7 +241,7 @@ sb_status validate_csr(int32_t n, int64_t nnz, const int32_t* rowptr, const int3
     set_error(f->msg);
     return f->st;
   };
-  parallel_parts(n, parts, [&](int part, int64_t b, int64_t e) {
+  bool done = parallel_parts(n, parts, [&](int part, int64_t b, int64_t e) {
     Fail& F = fail[part];
     auto bad = [&](int32_t i, sb_status st, const std::string& m) {
       F.row = i;
@@ -276,8 +276,12 @@ sb_status validate_csr(int32_t n, int64_t nnz, const int32_t* rowptr, const int3
   });
   sb_status st = first_failure();
   if (st) return st;
+  if (!done) {
+    set_error("CSR check: host allocation failed");
+    return SB_ERR_OOM;
+  }
   // symmetry: (i, j, v) needs (j, i, v)
-  parallel_parts(n, parts, [&](int part, int64_t b, int64_t e) {
+  done = parallel_parts(n, parts, [&](int part, int64_t b, int64_t e) {
     Fail& F = fail[part];
     for (int32_t i = (int32_t)b; i < (int32_t)e && F.st == SB_OK; ++i)
       for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
@@ -294,7 +298,12 @@ sb_status validate_csr(int32_t n, int64_t nnz, const int32_t* rowptr, const int3
         }
       }
   });
-  return first_failure();
+  st = first_failure();
+  if (!st && !done) {
+    set_error("CSR check: host allocation failed");
+    return SB_ERR_OOM;
+  }
+  return st;
 }
 
 void free_readout(sb_ctx* c) {
@@ -664,7 +673,7 @@ RwHost build_rw(int32_t n, const int32_t* rp, const int32_t* col, int RW) {
     std::vector<int32_t> rows, cnt, ent, pos;
   };
   std::vector<Part> P(parts);
-  parallel_parts(n, parts, [&](int part, int64_t b64, int64_t e64) {
+  const bool built = parallel_parts(n, parts, [&](int part, int64_t b64, int64_t e64) {
     const int32_t b = (int32_t)b64, e = (int32_t)e64;
     Part& q = P[part];
     if (e <= b) return;
@@ -725,6 +734,7 @@ RwHost build_rw(int32_t n, const int32_t* rp, const int32_t* col, int RW) {
       q.cnt.push_back((int32_t)(q.ent.size() - before));
     }
   });
+  if (!built) return t;  // a part ran out of host memory: no tables, the untiled kernel runs
   size_t E = 0, G = 0;
   for (const Part& q : P) {
     E += q.ent.size();
@@ -1224,76 +1234,78 @@ sb_status sb_create_batch(int32_t n_events, const int32_t* n_per_event,
                           const int64_t* nnz_per_event, const int32_t* rowptr,
                           const int32_t* col, const double* qval, const double* qlin,
                           sb_jprec prec, sb_ctx** out) {
-  if (!out) {
-    set_error("sb_create_batch: null output pointer");
-    return SB_ERR_ARG;
-  }
-  *out = nullptr;
-  if (n_events < 1 || !n_per_event || !nnz_per_event || !rowptr || !qlin ||
-      (prec != SB_J_FP32 && prec != SB_J_BF16)) {
-    set_error("sb_create: invalid argument (event count, null pointer or precision)");
-    return SB_ERR_ARG;
-  }
-  int64_t ntot = 0, ztot = 0;
-  for (int32_t e = 0; e < n_events; ++e) {
-    if (n_per_event[e] < 1 || nnz_per_event[e] < 0) {
-      set_error("sb_create: every event needs n >= 1 and nnz >= 0");
+  return sbh::guarded("sb_create_batch", [&]() -> sb_status {
+    if (!out) {
+      set_error("sb_create_batch: null output pointer");
       return SB_ERR_ARG;
     }
-    ntot += n_per_event[e];
-    ztot += nnz_per_event[e];
-  }
-  if (ntot >= 0x7FFFFFFFll || ztot >= 0x7FFFFFFFll) {
-    set_error("sb_create: total rows and nonzeros must stay below 2^31 - 1");
-    return SB_ERR_ARG;
-  }
-  if (ztot > 0 && (!col || !qval)) {
-    set_error("sb_create: null CSR arrays");
-    return SB_ERR_ARG;
-  }
-  // validate each event and build the global CSR (global column indices)
-  std::vector<int32_t> grp((size_t)ntot + 1), gcol((size_t)ztot);
-  std::vector<int32_t> ev_row0(n_events + 1);
-  int64_t rp_off = 0, z_off = 0, r_off = 0;
-  for (int32_t e = 0; e < n_events; ++e) {
-    const int32_t ne = n_per_event[e];
-    const int64_t ze = nnz_per_event[e];
-    const int32_t* rp = rowptr + rp_off;
-    sb_status st = validate_csr(ne, ze, rp, col + z_off, qval + z_off, qlin + r_off);
+    *out = nullptr;
+    if (n_events < 1 || !n_per_event || !nnz_per_event || !rowptr || !qlin ||
+        (prec != SB_J_FP32 && prec != SB_J_BF16)) {
+      set_error("sb_create: invalid argument (event count, null pointer or precision)");
+      return SB_ERR_ARG;
+    }
+    int64_t ntot = 0, ztot = 0;
+    for (int32_t e = 0; e < n_events; ++e) {
+      if (n_per_event[e] < 1 || nnz_per_event[e] < 0) {
+        set_error("sb_create: every event needs n >= 1 and nnz >= 0");
+        return SB_ERR_ARG;
+      }
+      ntot += n_per_event[e];
+      ztot += nnz_per_event[e];
+    }
+    if (ntot >= 0x7FFFFFFFll || ztot >= 0x7FFFFFFFll) {
+      set_error("sb_create: total rows and nonzeros must stay below 2^31 - 1");
+      return SB_ERR_ARG;
+    }
+    if (ztot > 0 && (!col || !qval)) {
+      set_error("sb_create: null CSR arrays");
+      return SB_ERR_ARG;
+    }
+    // validate each event and build the global CSR (global column indices)
+    std::vector<int32_t> grp((size_t)ntot + 1), gcol((size_t)ztot);
+    std::vector<int32_t> ev_row0(n_events + 1);
+    int64_t rp_off = 0, z_off = 0, r_off = 0;
+    for (int32_t e = 0; e < n_events; ++e) {
+      const int32_t ne = n_per_event[e];
+      const int64_t ze = nnz_per_event[e];
+      const int32_t* rp = rowptr + rp_off;
+      sb_status st = validate_csr(ne, ze, rp, col + z_off, qval + z_off, qlin + r_off);
+      if (st) {
+        if (n_events > 1) set_error("event " + std::to_string(e) + ": " + sbh::g_err);
+        return st;
+      }
+      ev_row0[e] = (int32_t)r_off;
+      for (int32_t i = 0; i < ne; ++i) grp[r_off + i] = (int32_t)(z_off + rp[i]);
+      for (int64_t p = 0; p < ze; ++p) gcol[z_off + p] = (int32_t)(col[z_off + p] + r_off);
+      rp_off += ne + 1;
+      z_off += ze;
+      r_off += ne;
+    }
+    grp[ntot] = (int32_t)ztot;
+    ev_row0[n_events] = (int32_t)ntot;
+    sb_ctx* c = new (std::nothrow) sb_ctx;
+    if (!c) {
+      set_error("sb_create: host allocation failed");
+      return SB_ERR_OOM;
+    }
+    c->E = n_events;
+    c->n = (int32_t)ntot;
+    c->nnz = ztot;
+    c->jbf16 = prec == SB_J_BF16;
+    c->ev_row0 = ev_row0;
+    c->ev_nnz.assign(nnz_per_event, nnz_per_event + n_events);
+    sb_status st = create_common(c, grp.data(), gcol.data(), qval, qlin);
+    c->h_rowptr.swap(grp);
+    c->h_col.swap(gcol);
     if (st) {
-      if (n_events > 1) set_error("event " + std::to_string(e) + ": " + sbh::g_err);
+      free_all(c);
+      delete c;
       return st;
     }
-    ev_row0[e] = (int32_t)r_off;
-    for (int32_t i = 0; i < ne; ++i) grp[r_off + i] = (int32_t)(z_off + rp[i]);
-    for (int64_t p = 0; p < ze; ++p) gcol[z_off + p] = (int32_t)(col[z_off + p] + r_off);
-    rp_off += ne + 1;
-    z_off += ze;
-    r_off += ne;
-  }
-  grp[ntot] = (int32_t)ztot;
-  ev_row0[n_events] = (int32_t)ntot;
-  sb_ctx* c = new (std::nothrow) sb_ctx;
-  if (!c) {
-    set_error("sb_create: host allocation failed");
-    return SB_ERR_OOM;
-  }
-  c->E = n_events;
-  c->n = (int32_t)ntot;
-  c->nnz = ztot;
-  c->jbf16 = prec == SB_J_BF16;
-  c->ev_row0 = ev_row0;
-  c->ev_nnz.assign(nnz_per_event, nnz_per_event + n_events);
-  sb_status st = create_common(c, grp.data(), gcol.data(), qval, qlin);
-  c->h_rowptr.swap(grp);
-  c->h_col.swap(gcol);
-  if (st) {
-    free_all(c);
-    delete c;
-    return st;
-  }
-  *out = c;
-  return SB_OK;
+    *out = c;
+    return SB_OK;
+  });
 }
 
 void sb_destroy(sb_ctx* ctx) {
@@ -1328,70 +1340,76 @@ sb_status sb_info(const sb_ctx* ctx, int32_t e, int32_t* n, int64_t* nnz, double
 sb_status sb_run(sb_ctx* ctx, sb_variant variant, double a0, double c0, double dt,
                  int32_t steps, int32_t replicas, uint64_t seed, const float* a_sched,
                  void* stream) {
-  sb_status st = check_run_args(ctx, variant, a0, c0, dt, steps);
-  if (st) return st;
-  if (replicas < 1 || replicas > 65535) {
-    set_error("sb_run: replicas must be in [1, 65535]");
-    return SB_ERR_ARG;
-  }
-  if ((size_t)ctx->n * (size_t)replicas >= ((size_t)1 << 40)) {
-    set_error("sb_run: state too large");
-    return SB_ERR_ARG;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  if ((st = ensure_state(ctx, replicas))) return st;
-  const float* sched = a_sched;
-  if (!sched && steps > 0) {
-    if (ctx->sched_len != steps || ctx->sched_a0 != a0) {
-      dfree(ctx->d_sched);
-      if ((st = dalloc(&ctx->d_sched, steps))) return st;
-      SB_CUDA(sbd::launch_linear_schedule(ctx->d_sched, steps, a0, s));
-      ctx->sched_len = steps;
-      ctx->sched_a0 = a0;
+  return sbh::guarded("sb_run", [&]() -> sb_status {
+    sb_status st = check_run_args(ctx, variant, a0, c0, dt, steps);
+    if (st) return st;
+    if (replicas < 1 || replicas > 65535) {
+      set_error("sb_run: replicas must be in [1, 65535]");
+      return SB_ERR_ARG;
     }
-    sched = ctx->d_sched;
-  }
-  SB_CUDA(sbd::launch_set_c0(ctx->d_c0ev, ctx->d_c0auto, c0, ctx->E, s));
-  ctx->cur = 0;
-  SB_CUDA(sbd::launch_init(ctx->d_x[0], ctx->d_y, ctx->d_row_event, ctx->d_ev_row0, ctx->n,
-                           ctx->R, seed, s));
-  ctx->have_state = true;
-  return enqueue_steps(ctx, variant, a0, dt, steps, sched, s);
+    if ((size_t)ctx->n * (size_t)replicas >= ((size_t)1 << 40)) {
+      set_error("sb_run: state too large");
+      return SB_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ensure_state(ctx, replicas))) return st;
+    const float* sched = a_sched;
+    if (!sched && steps > 0) {
+      if (ctx->sched_len != steps || ctx->sched_a0 != a0) {
+        dfree(ctx->d_sched);
+        if ((st = dalloc(&ctx->d_sched, steps))) return st;
+        SB_CUDA(sbd::launch_linear_schedule(ctx->d_sched, steps, a0, s));
+        ctx->sched_len = steps;
+        ctx->sched_a0 = a0;
+      }
+      sched = ctx->d_sched;
+    }
+    SB_CUDA(sbd::launch_set_c0(ctx->d_c0ev, ctx->d_c0auto, c0, ctx->E, s));
+    ctx->cur = 0;
+    SB_CUDA(sbd::launch_init(ctx->d_x[0], ctx->d_y, ctx->d_row_event, ctx->d_ev_row0, ctx->n,
+                             ctx->R, seed, s));
+    ctx->have_state = true;
+    return enqueue_steps(ctx, variant, a0, dt, steps, sched, s);
+  });
 }
 
 sb_status sb_advance(sb_ctx* ctx, sb_variant variant, double a0, double c0, double dt,
                      int32_t steps, const float* a_sched, void* stream) {
-  sb_status st = check_run_args(ctx, variant, a0, c0, dt, steps);
-  if (st) return st;
-  if (!ctx->have_state) {
-    set_error("sb_advance: no state (call sb_run or sb_set_state first)");
-    return SB_ERR_STATE;
-  }
-  if (steps > 0 && !a_sched) {
-    set_error("sb_advance: a_sched is required");
-    return SB_ERR_ARG;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  SB_CUDA(sbd::launch_set_c0(ctx->d_c0ev, ctx->d_c0auto, c0, ctx->E, s));
-  return enqueue_steps(ctx, variant, a0, dt, steps, a_sched, s);
+  return sbh::guarded("sb_advance", [&]() -> sb_status {
+    sb_status st = check_run_args(ctx, variant, a0, c0, dt, steps);
+    if (st) return st;
+    if (!ctx->have_state) {
+      set_error("sb_advance: no state (call sb_run or sb_set_state first)");
+      return SB_ERR_STATE;
+    }
+    if (steps > 0 && !a_sched) {
+      set_error("sb_advance: a_sched is required");
+      return SB_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    SB_CUDA(sbd::launch_set_c0(ctx->d_c0ev, ctx->d_c0auto, c0, ctx->E, s));
+    return enqueue_steps(ctx, variant, a0, dt, steps, a_sched, s);
+  });
 }
 
 sb_status sb_set_state(sb_ctx* ctx, const float* x, const float* y, int32_t replicas,
                        int32_t on_device) {
-  if (!ctx || !x || !y || replicas < 1 || replicas > 65535) {
-    set_error("sb_set_state: invalid argument");
-    return SB_ERR_ARG;
-  }
-  sb_status st = ensure_state(ctx, replicas);
-  if (st) return st;
-  const size_t bytes = (size_t)ctx->n * replicas * 4;
-  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  SB_CUDA(cudaDeviceSynchronize());
-  ctx->cur = 0;
-  SB_CUDA(cudaMemcpy(ctx->d_x[0], x, bytes, k));
-  SB_CUDA(cudaMemcpy(ctx->d_y, y, bytes, k));
-  ctx->have_state = true;
-  return SB_OK;
+  return sbh::guarded("sb_set_state", [&]() -> sb_status {
+    if (!ctx || !x || !y || replicas < 1 || replicas > 65535) {
+      set_error("sb_set_state: invalid argument");
+      return SB_ERR_ARG;
+    }
+    sb_status st = ensure_state(ctx, replicas);
+    if (st) return st;
+    const size_t bytes = (size_t)ctx->n * replicas * 4;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    SB_CUDA(cudaDeviceSynchronize());
+    ctx->cur = 0;
+    SB_CUDA(cudaMemcpy(ctx->d_x[0], x, bytes, k));
+    SB_CUDA(cudaMemcpy(ctx->d_y, y, bytes, k));
+    ctx->have_state = true;
+    return SB_OK;
+  });
 }
 
 sb_status sb_get_state(const sb_ctx* ctx, float* x, float* y, int32_t on_device) {
@@ -1414,525 +1432,539 @@ sb_status sb_get_state(const sb_ctx* ctx, float* x, float* y, int32_t on_device)
 }
 
 sb_status sb_energy(sb_ctx* ctx, const int8_t* spins, int32_t replicas, double* out_E) {
-  if (!ctx || !out_E || replicas < 1 || replicas > 65535) {
-    set_error("sb_energy: invalid argument");
-    return SB_ERR_ARG;
-  }
-  sb_status st;
-  if (spins) {
-    if (ctx->spins_cap_R < replicas) {
-      dfree(ctx->d_spins);
-      if ((st = dalloc(&ctx->d_spins, (size_t)ctx->n * replicas))) return st;
-      ctx->spins_cap_R = replicas;
+  return sbh::guarded("sb_energy", [&]() -> sb_status {
+    if (!ctx || !out_E || replicas < 1 || replicas > 65535) {
+      set_error("sb_energy: invalid argument");
+      return SB_ERR_ARG;
     }
-    SB_CUDA(cudaMemcpy(ctx->d_spins, spins, (size_t)ctx->n * replicas, cudaMemcpyHostToDevice));
-  } else {
-    if (!ctx->have_state || ctx->R != replicas) {
-      set_error("sb_energy: no current state with that replica count");
-      return SB_ERR_STATE;
+    sb_status st;
+    if (spins) {
+      if (ctx->spins_cap_R < replicas) {
+        dfree(ctx->d_spins);
+        if ((st = dalloc(&ctx->d_spins, (size_t)ctx->n * replicas))) return st;
+        ctx->spins_cap_R = replicas;
+      }
+      SB_CUDA(cudaMemcpy(ctx->d_spins, spins, (size_t)ctx->n * replicas, cudaMemcpyHostToDevice));
+    } else {
+      if (!ctx->have_state || ctx->R != replicas) {
+        set_error("sb_energy: no current state with that replica count");
+        return SB_ERR_STATE;
+      }
     }
-  }
-  if ((st = readout(ctx, spins ? ctx->d_spins : nullptr, replicas, 0))) return st;
-  SB_CUDA(cudaDeviceSynchronize());
-  if (!spins && (st = check_wait_flag(ctx))) return st;
-  SB_CUDA(cudaMemcpy(out_E, ctx->d_Eall, (size_t)ctx->E * replicas * 8, cudaMemcpyDeviceToHost));
-  return SB_OK;
+    if ((st = readout(ctx, spins ? ctx->d_spins : nullptr, replicas, 0))) return st;
+    SB_CUDA(cudaDeviceSynchronize());
+    if (!spins && (st = check_wait_flag(ctx))) return st;
+    SB_CUDA(cudaMemcpy(out_E, ctx->d_Eall, (size_t)ctx->E * replicas * 8, cudaMemcpyDeviceToHost));
+    return SB_OK;
+  });
 }
 
 sb_status sb_readout_device(sb_ctx* ctx, double* d_E_all, double* d_best_E, int32_t* d_best_r,
                             uint8_t* d_T, void* stream) {
-  if (!ctx) {
-    set_error("sb_readout_device: null context");
-    return SB_ERR_ARG;
-  }
-  if (!ctx->have_state) {
-    set_error("sb_readout_device: no state");
-    return SB_ERR_STATE;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  sb_status st = readout(ctx, nullptr, ctx->R, s);
-  if (st) return st;
-  if (d_T)
-    SB_CUDA(sbd::launch_best_T(ctx->d_x[ctx->cur], ctx->d_row_event, ctx->d_bestr, ctx->n,
-                               ctx->R, d_T, s));
-  if (d_E_all)
-    SB_CUDA(cudaMemcpyAsync(d_E_all, ctx->d_Eall, (size_t)ctx->E * ctx->R * 8,
-                            cudaMemcpyDeviceToDevice, s));
-  if (d_best_E)
-    SB_CUDA(cudaMemcpyAsync(d_best_E, ctx->d_bestE, ctx->E * 8, cudaMemcpyDeviceToDevice, s));
-  if (d_best_r)
-    SB_CUDA(cudaMemcpyAsync(d_best_r, ctx->d_bestr, ctx->E * 4, cudaMemcpyDeviceToDevice, s));
-  return SB_OK;
+  return sbh::guarded("sb_readout_device", [&]() -> sb_status {
+    if (!ctx) {
+      set_error("sb_readout_device: null context");
+      return SB_ERR_ARG;
+    }
+    if (!ctx->have_state) {
+      set_error("sb_readout_device: no state");
+      return SB_ERR_STATE;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    sb_status st = readout(ctx, nullptr, ctx->R, s);
+    if (st) return st;
+    if (d_T)
+      SB_CUDA(sbd::launch_best_T(ctx->d_x[ctx->cur], ctx->d_row_event, ctx->d_bestr, ctx->n,
+                                 ctx->R, d_T, s));
+    if (d_E_all)
+      SB_CUDA(cudaMemcpyAsync(d_E_all, ctx->d_Eall, (size_t)ctx->E * ctx->R * 8,
+                              cudaMemcpyDeviceToDevice, s));
+    if (d_best_E)
+      SB_CUDA(cudaMemcpyAsync(d_best_E, ctx->d_bestE, ctx->E * 8, cudaMemcpyDeviceToDevice, s));
+    if (d_best_r)
+      SB_CUDA(cudaMemcpyAsync(d_best_r, ctx->d_bestr, ctx->E * 4, cudaMemcpyDeviceToDevice, s));
+    return SB_OK;
+  });
 }
 
 sb_status sb_best(sb_ctx* ctx, uint8_t* out_T, double* out_E, int32_t* out_replica) {
-  if (!ctx) {
-    set_error("sb_best: null context");
-    return SB_ERR_ARG;
-  }
-  sb_status st = sb_readout_device(ctx, nullptr, nullptr, nullptr, out_T ? ctx->d_T : nullptr, 0);
-  if (st) return st;
-  SB_CUDA(cudaDeviceSynchronize());
-  if ((st = check_wait_flag(ctx))) return st;
-  if (out_T) SB_CUDA(cudaMemcpy(out_T, ctx->d_T, ctx->n, cudaMemcpyDeviceToHost));
-  if (out_E) SB_CUDA(cudaMemcpy(out_E, ctx->d_bestE, ctx->E * 8, cudaMemcpyDeviceToHost));
-  if (out_replica)
-    SB_CUDA(cudaMemcpy(out_replica, ctx->d_bestr, ctx->E * 4, cudaMemcpyDeviceToHost));
-  return SB_OK;
+  return sbh::guarded("sb_best", [&]() -> sb_status {
+    if (!ctx) {
+      set_error("sb_best: null context");
+      return SB_ERR_ARG;
+    }
+    sb_status st = sb_readout_device(ctx, nullptr, nullptr, nullptr, out_T ? ctx->d_T : nullptr, 0);
+    if (st) return st;
+    SB_CUDA(cudaDeviceSynchronize());
+    if ((st = check_wait_flag(ctx))) return st;
+    if (out_T) SB_CUDA(cudaMemcpy(out_T, ctx->d_T, ctx->n, cudaMemcpyDeviceToHost));
+    if (out_E) SB_CUDA(cudaMemcpy(out_E, ctx->d_bestE, ctx->E * 8, cudaMemcpyDeviceToHost));
+    if (out_replica)
+      SB_CUDA(cudaMemcpy(out_replica, ctx->d_bestr, ctx->E * 4, cudaMemcpyDeviceToHost));
+    return SB_OK;
+  });
 }
 
 sb_status sb_set_weights(sb_ctx* ctx, const int8_t* cls, const double* quality, double w_q,
                          double w_c) {
-  if (!ctx || !quality || (!cls && ctx->nnz > 0) || !std::isfinite(w_q) || !std::isfinite(w_c)) {
-    set_error("sb_set_weights: invalid argument");
-    return SB_ERR_ARG;
-  }
-  if (ctx->E != 1) {
-    set_error("sb_set_weights: single-event contexts only");
-    return SB_ERR_ARG;
-  }
-  const int32_t n = ctx->n;
-  const int32_t* rp = ctx->h_rowptr.data();
-  const int32_t* col = ctx->h_col.data();
-  std::vector<double> qv((size_t)ctx->nnz), ql(n), nconf(n, 0.0);
-  for (int32_t i = 0; i < n; ++i) {
-    if (!std::isfinite(quality[i])) {
-      set_error("sb_set_weights: quality not finite");
+  return sbh::guarded("sb_set_weights", [&]() -> sb_status {
+    if (!ctx || !quality || (!cls && ctx->nnz > 0) || !std::isfinite(w_q) || !std::isfinite(w_c)) {
+      set_error("sb_set_weights: invalid argument");
       return SB_ERR_ARG;
     }
-    ql[i] = w_q * quality[i];
-    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
-      if (cls[p] != 0 && cls[p] != 1) {
-        set_error("sb_set_weights: class tags must be 0 (consistent) or 1 (conflict)");
+    if (ctx->E != 1) {
+      set_error("sb_set_weights: single-event contexts only");
+      return SB_ERR_ARG;
+    }
+    const int32_t n = ctx->n;
+    const int32_t* rp = ctx->h_rowptr.data();
+    const int32_t* col = ctx->h_col.data();
+    std::vector<double> qv((size_t)ctx->nnz), ql(n), nconf(n, 0.0);
+    for (int32_t i = 0; i < n; ++i) {
+      if (!std::isfinite(quality[i])) {
+        set_error("sb_set_weights: quality not finite");
         return SB_ERR_ARG;
       }
-      const int32_t j = col[p];
-      const int32_t* f = std::lower_bound(col + rp[j], col + rp[j + 1], i);
-      if (cls[rp[j] + (f - (col + rp[j]))] != cls[p]) {
-        set_error("sb_set_weights: class tags are not symmetric");
-        return SB_ERR_CSR;
+      ql[i] = w_q * quality[i];
+      for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+        if (cls[p] != 0 && cls[p] != 1) {
+          set_error("sb_set_weights: class tags must be 0 (consistent) or 1 (conflict)");
+          return SB_ERR_ARG;
+        }
+        const int32_t j = col[p];
+        const int32_t* f = std::lower_bound(col + rp[j], col + rp[j + 1], i);
+        if (cls[rp[j] + (f - (col + rp[j]))] != cls[p]) {
+          set_error("sb_set_weights: class tags are not symmetric");
+          return SB_ERR_CSR;
+        }
+        qv[p] = cls[p] ? w_c : -1.0;
+        nconf[i] += cls[p] ? 1.0 : 0.0;
       }
-      qv[p] = cls[p] ? w_c : -1.0;
-      nconf[i] += cls[p] ? 1.0 : 0.0;
     }
-  }
-  sb_status st;
-  if (!ctx->d_cls) {
-    if ((st = dalloc(&ctx->d_cls, (size_t)ctx->nnz)) || (st = dalloc(&ctx->d_quality, (size_t)n)) ||
-        (st = dalloc(&ctx->d_nconf, (size_t)n)))
+    sb_status st;
+    if (!ctx->d_cls) {
+      if ((st = dalloc(&ctx->d_cls, (size_t)ctx->nnz)) || (st = dalloc(&ctx->d_quality, (size_t)n)) ||
+          (st = dalloc(&ctx->d_nconf, (size_t)n)))
+        return st;
+    }
+    SB_CUDA(cudaDeviceSynchronize());
+    if (ctx->nnz) {
+      SB_CUDA(cudaMemcpy(ctx->d_cls, cls, (size_t)ctx->nnz, cudaMemcpyHostToDevice));
+      SB_CUDA(cudaMemcpy(ctx->d_qval, qv.data(), (size_t)ctx->nnz * 8, cudaMemcpyHostToDevice));
+    }
+    SB_CUDA(cudaMemcpy(ctx->d_quality, quality, (size_t)n * 8, cudaMemcpyHostToDevice));
+    SB_CUDA(cudaMemcpy(ctx->d_nconf, nconf.data(), (size_t)n * 8, cudaMemcpyHostToDevice));
+    SB_CUDA(cudaMemcpy(ctx->d_qlin, ql.data(), (size_t)n * 8, cudaMemcpyHostToDevice));
+    double *row_off = nullptr, *row_sq = nullptr;
+    if ((st = dalloc(&row_off, (size_t)n)) || (st = dalloc(&row_sq, (size_t)n))) {
+      dfree(row_off);
+      dfree(row_sq);
       return st;
-  }
-  SB_CUDA(cudaDeviceSynchronize());
-  if (ctx->nnz) {
-    SB_CUDA(cudaMemcpy(ctx->d_cls, cls, (size_t)ctx->nnz, cudaMemcpyHostToDevice));
-    SB_CUDA(cudaMemcpy(ctx->d_qval, qv.data(), (size_t)ctx->nnz * 8, cudaMemcpyHostToDevice));
-  }
-  SB_CUDA(cudaMemcpy(ctx->d_quality, quality, (size_t)n * 8, cudaMemcpyHostToDevice));
-  SB_CUDA(cudaMemcpy(ctx->d_nconf, nconf.data(), (size_t)n * 8, cudaMemcpyHostToDevice));
-  SB_CUDA(cudaMemcpy(ctx->d_qlin, ql.data(), (size_t)n * 8, cudaMemcpyHostToDevice));
-  double *row_off = nullptr, *row_sq = nullptr;
-  if ((st = dalloc(&row_off, (size_t)n)) || (st = dalloc(&row_sq, (size_t)n))) {
+    }
+    cudaError_t e1 = sbd::launch_convert(ctx->d_rowptr, ctx->d_col, ctx->d_qval, ctx->d_qlin, n,
+                                         ctx->d_J, ctx->jbf16, ctx->d_h64, ctx->d_h32, row_off,
+                                         row_sq, 0);
+    cudaError_t e2 = sbd::launch_event_stats(row_off, row_sq, ctx->d_ev_row0, 1, ctx->d_offset,
+                                             ctx->d_sigma, ctx->d_c0auto, 0);
+    cudaError_t e3 = cudaDeviceSynchronize();
     dfree(row_off);
     dfree(row_sq);
-    return st;
-  }
-  cudaError_t e1 = sbd::launch_convert(ctx->d_rowptr, ctx->d_col, ctx->d_qval, ctx->d_qlin, n,
-                                       ctx->d_J, ctx->jbf16, ctx->d_h64, ctx->d_h32, row_off,
-                                       row_sq, 0);
-  cudaError_t e2 = sbd::launch_event_stats(row_off, row_sq, ctx->d_ev_row0, 1, ctx->d_offset,
-                                           ctx->d_sigma, ctx->d_c0auto, 0);
-  cudaError_t e3 = cudaDeviceSynchronize();
-  dfree(row_off);
-  dfree(row_sq);
-  SB_CUDA(e1);
-  SB_CUDA(e2);
-  SB_CUDA(e3);
-  SB_CUDA(cudaMemcpy(ctx->offset.data(), ctx->d_offset, 8, cudaMemcpyDeviceToHost));
-  SB_CUDA(cudaMemcpy(ctx->sigma.data(), ctx->d_sigma, 8, cudaMemcpyDeviceToHost));
-  SB_CUDA(cudaMemcpy(ctx->c0_auto.data(), ctx->d_c0auto, 8, cudaMemcpyDeviceToHost));
-  // the tiled kernel's packed words carry J: rebuild them
-  dfree(ctx->d_blk_row0);
-  dfree(ctx->d_blk_u0);
-  dfree(ctx->d_ucol);
-  dfree(ctx->d_own);
-  if (ctx->d_tz) cudaFree(ctx->d_tz);
-  ctx->d_tz = nullptr;
-  ctx->graph.reset();
-  if (ctx->tiles_built && (st = setup_tiles(ctx, rp, col))) return st;
-  // the row-group kernel's entries carry J too
-  if ((st = refill_rw(ctx))) return st;
-  ctx->have_classes = true;
-  return SB_OK;
+    SB_CUDA(e1);
+    SB_CUDA(e2);
+    SB_CUDA(e3);
+    SB_CUDA(cudaMemcpy(ctx->offset.data(), ctx->d_offset, 8, cudaMemcpyDeviceToHost));
+    SB_CUDA(cudaMemcpy(ctx->sigma.data(), ctx->d_sigma, 8, cudaMemcpyDeviceToHost));
+    SB_CUDA(cudaMemcpy(ctx->c0_auto.data(), ctx->d_c0auto, 8, cudaMemcpyDeviceToHost));
+    // the tiled kernel's packed words carry J: rebuild them
+    dfree(ctx->d_blk_row0);
+    dfree(ctx->d_blk_u0);
+    dfree(ctx->d_ucol);
+    dfree(ctx->d_own);
+    if (ctx->d_tz) cudaFree(ctx->d_tz);
+    ctx->d_tz = nullptr;
+    ctx->graph.reset();
+    if (ctx->tiles_built && (st = setup_tiles(ctx, rp, col))) return st;
+    // the row-group kernel's entries carry J too
+    if ((st = refill_rw(ctx))) return st;
+    ctx->have_classes = true;
+    return SB_OK;
+  });
 }
 
 sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t steps,
                       int32_t replicas, uint64_t seed, const float* a_sched, int32_t ckpt_every,
                       double* out_loss, double* out_grads, double* d_grad_sched, void* stream) {
-  sb_status st = check_run_args(ctx, SB_BSB, a0, c0, dt, steps);
-  if (st) return st;
-  if (ctx->E != 1 || !(c0 > 0.0) || steps < 1 || ckpt_every < 1 || replicas < 1 ||
-      replicas > 65535) {
-    set_error("sb_backward: single event, c0 > 0, steps >= 1, ckpt_every >= 1, 1 <= R <= 65535");
-    return SB_ERR_ARG;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  if ((st = ensure_state(ctx, replicas))) return st;
-  const int32_t n = ctx->n, R = replicas, S = steps, K = std::min(ckpt_every, steps);
-  const size_t NR = (size_t)n * R;
-  const int32_t n_ck = (S + K - 1) / K;
-  if (!ctx->d_cls) {  // no class tags: weight-scale gradients are reported as NaN
-    if ((st = dalloc(&ctx->d_cls, (size_t)ctx->nnz)) || (st = dalloc(&ctx->d_quality, (size_t)n)) ||
-        (st = dalloc(&ctx->d_nconf, (size_t)n)))
+  return sbh::guarded("sb_backward", [&]() -> sb_status {
+    sb_status st = check_run_args(ctx, SB_BSB, a0, c0, dt, steps);
+    if (st) return st;
+    if (ctx->E != 1 || !(c0 > 0.0) || steps < 1 || ckpt_every < 1 || replicas < 1 ||
+        replicas > 65535) {
+      set_error("sb_backward: single event, c0 > 0, steps >= 1, ckpt_every >= 1, 1 <= R <= 65535");
+      return SB_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ensure_state(ctx, replicas))) return st;
+    const int32_t n = ctx->n, R = replicas, S = steps, K = std::min(ckpt_every, steps);
+    const size_t NR = (size_t)n * R;
+    const int32_t n_ck = (S + K - 1) / K;
+    if (!ctx->d_cls) {  // no class tags: weight-scale gradients are reported as NaN
+      if ((st = dalloc(&ctx->d_cls, (size_t)ctx->nnz)) || (st = dalloc(&ctx->d_quality, (size_t)n)) ||
+          (st = dalloc(&ctx->d_nconf, (size_t)n)))
+        return st;
+      SB_CUDA(cudaMemset(ctx->d_cls, 0, std::max<size_t>((size_t)ctx->nnz, 1)));
+      SB_CUDA(cudaMemset(ctx->d_quality, 0, (size_t)n * 8));
+      SB_CUDA(cudaMemset(ctx->d_nconf, 0, (size_t)n * 8));
+    }
+    const float* sched = a_sched;
+    if (!sched) {
+      if (ctx->sched_len != S || ctx->sched_a0 != a0) {
+        dfree(ctx->d_sched);
+        if ((st = dalloc(&ctx->d_sched, S))) return st;
+        SB_CUDA(sbd::launch_linear_schedule(ctx->d_sched, S, a0, s));
+        ctx->sched_len = S;
+        ctx->sched_a0 = a0;
+      }
+      sched = ctx->d_sched;
+    }
+    float *ck_x = nullptr, *ck_y = nullptr, *seg_x = nullptr, *seg_yt = nullptr, *seg_f = nullptr;
+    float *lx = nullptr, *ly = nullptr, *lyt = nullptr;
+    uint8_t* seg_m = nullptr;
+    double *gh = nullptr, *acc = nullptr, *ga = nullptr;
+    auto cleanup = [&]() {
+      dfree(ck_x);
+      dfree(ck_y);
+      dfree(seg_x);
+      dfree(seg_yt);
+      dfree(seg_f);
+      dfree(seg_m);
+      dfree(lx);
+      dfree(ly);
+      dfree(lyt);
+      dfree(gh);
+      dfree(acc);
+      dfree(ga);
+    };
+    // checkpoints for all segments but the last, which is recorded on the way forward
+    if ((st = dalloc(&ck_x, NR * (n_ck - 1))) || (st = dalloc(&ck_y, NR * (n_ck - 1))) ||
+        (st = dalloc(&seg_x, NR * (K + 1))) || (st = dalloc(&seg_yt, NR * K)) ||
+        (st = dalloc(&seg_f, NR * K)) ||
+        (st = dalloc(&seg_m, NR * K)) || (st = dalloc(&lx, NR)) || (st = dalloc(&ly, NR)) ||
+        (st = dalloc(&lyt, NR)) || (st = dalloc(&gh, (size_t)n)) || (st = dalloc(&acc, 6)) ||
+        (st = dalloc(&ga, (size_t)S))) {
+      cleanup();
       return st;
-    SB_CUDA(cudaMemset(ctx->d_cls, 0, std::max<size_t>((size_t)ctx->nnz, 1)));
-    SB_CUDA(cudaMemset(ctx->d_quality, 0, (size_t)n * 8));
-    SB_CUDA(cudaMemset(ctx->d_nconf, 0, (size_t)n * 8));
-  }
-  const float* sched = a_sched;
-  if (!sched) {
-    if (ctx->sched_len != S || ctx->sched_a0 != a0) {
-      dfree(ctx->d_sched);
-      if ((st = dalloc(&ctx->d_sched, S))) return st;
-      SB_CUDA(sbd::launch_linear_schedule(ctx->d_sched, S, a0, s));
-      ctx->sched_len = S;
-      ctx->sched_a0 = a0;
     }
-    sched = ctx->d_sched;
-  }
-  float *ck_x = nullptr, *ck_y = nullptr, *seg_x = nullptr, *seg_yt = nullptr, *seg_f = nullptr;
-  float *lx = nullptr, *ly = nullptr, *lyt = nullptr;
-  uint8_t* seg_m = nullptr;
-  double *gh = nullptr, *acc = nullptr, *ga = nullptr;
-  auto cleanup = [&]() {
-    dfree(ck_x);
-    dfree(ck_y);
-    dfree(seg_x);
-    dfree(seg_yt);
-    dfree(seg_f);
-    dfree(seg_m);
-    dfree(lx);
-    dfree(ly);
-    dfree(lyt);
-    dfree(gh);
-    dfree(acc);
-    dfree(ga);
-  };
-  // checkpoints for all segments but the last, which is recorded on the way forward
-  if ((st = dalloc(&ck_x, NR * (n_ck - 1))) || (st = dalloc(&ck_y, NR * (n_ck - 1))) ||
-      (st = dalloc(&seg_x, NR * (K + 1))) || (st = dalloc(&seg_yt, NR * K)) ||
-      (st = dalloc(&seg_f, NR * K)) ||
-      (st = dalloc(&seg_m, NR * K)) || (st = dalloc(&lx, NR)) || (st = dalloc(&ly, NR)) ||
-      (st = dalloc(&lyt, NR)) || (st = dalloc(&gh, (size_t)n)) || (st = dalloc(&acc, 6)) ||
-      (st = dalloc(&ga, (size_t)S))) {
-    cleanup();
-    return st;
-  }
-  cudaError_t e = cudaSuccess;
-  auto ok = [&](cudaError_t x) {
-    if (e == cudaSuccess) e = x;
-    return e == cudaSuccess;
-  };
-  const sbd::Tiling t = sbd::make_tiling(R);
-  sbd::StepArgs a;
-  a.rowptr = ctx->d_rowptr;
-  a.col = ctx->d_col;
-  a.J = ctx->d_J;
-  a.h = ctx->d_h32;
-  a.row_event = nullptr;
-  a.c0_ev = ctx->d_c0ev;
-  a.sched = sched;
-  a.a0 = (float)a0;
-  a.dt = (float)dt;
-  a.dta0 = (float)(dt * a0);
-  a.n = n;
-  a.R = R;
-  a.G = t.G;
-  a.rpc = 256 / t.G;
-  a.unroll = 4;
-  a.tile0 = 0;
-  a.ytil = nullptr;
-  a.mask = nullptr;
-  a.frec = nullptr;
-  a.sgn_in = nullptr;
-  a.sgn_out = nullptr;
-  ok(sbd::launch_set_c0(ctx->d_c0ev, ctx->d_c0auto, c0, 1, s));
-  ok(sbd::launch_init(ctx->d_x[0], ctx->d_y, nullptr, ctx->d_ev_row0, n, R, seed, s));
-  int cur = 0;
-  // forward, keeping (x, y) at the start of every segment but the last
-  for (int32_t c = 0; c + 1 < n_ck && e == cudaSuccess; ++c) {
-    ok(cudaMemcpyAsync(ck_x + NR * c, ctx->d_x[cur], NR * 4, cudaMemcpyDeviceToDevice, s));
-    ok(cudaMemcpyAsync(ck_y + NR * c, ctx->d_y, NR * 4, cudaMemcpyDeviceToDevice, s));
-    for (int32_t j = 0; j < K && e == cudaSuccess; ++j) {
-      a.k = c * K + j;
-      a.xin = ctx->d_x[cur];
-      a.xout = ctx->d_x[cur ^ 1];
-      a.y = ctx->d_y;
-      ok(sbd::launch_step(SB_BSB, ctx->jbf16, t, a, s));
-      cur ^= 1;
-    }
-  }
-  // the last segment, recorded as it runs: x_k, pre-wall momentum, wall mask, J x_k
-  const int32_t c_last = n_ck - 1;
-  const int32_t L_last = S - c_last * K;
-  auto record_segment = [&](int32_t c, int32_t L) {
-    for (int32_t j = 0; j < L && e == cudaSuccess; ++j) {
-      a.k = c * K + j;
-      a.xin = seg_x + NR * j;
-      a.xout = seg_x + NR * (j + 1);
-      a.y = ctx->d_y;
-      a.ytil = seg_yt + NR * j;
-      a.mask = seg_m + NR * j;
-      a.frec = seg_f + NR * j;
-      ok(sbd::launch_step(SB_BSB, ctx->jbf16, t, a, s));
-    }
+    cudaError_t e = cudaSuccess;
+    auto ok = [&](cudaError_t x) {
+      if (e == cudaSuccess) e = x;
+      return e == cudaSuccess;
+    };
+    const sbd::Tiling t = sbd::make_tiling(R);
+    sbd::StepArgs a;
+    a.rowptr = ctx->d_rowptr;
+    a.col = ctx->d_col;
+    a.J = ctx->d_J;
+    a.h = ctx->d_h32;
+    a.row_event = nullptr;
+    a.c0_ev = ctx->d_c0ev;
+    a.sched = sched;
+    a.a0 = (float)a0;
+    a.dt = (float)dt;
+    a.dta0 = (float)(dt * a0);
+    a.n = n;
+    a.R = R;
+    a.G = t.G;
+    a.rpc = 256 / t.G;
+    a.unroll = 4;
+    a.tile0 = 0;
     a.ytil = nullptr;
     a.mask = nullptr;
     a.frec = nullptr;
-  };
-  ok(cudaMemcpyAsync(seg_x, ctx->d_x[cur], NR * 4, cudaMemcpyDeviceToDevice, s));
-  record_segment(c_last, L_last);
-  ok(cudaMemsetAsync(gh, 0, (size_t)n * 8, s));
-  ok(cudaMemsetAsync(acc, 0, 6 * 8, s));
-  ok(cudaMemsetAsync(ga, 0, (size_t)S * 8, s));
-  sbd::AdjArgs g;
-  g.rowptr = ctx->d_rowptr;
-  g.col = ctx->d_col;
-  g.J = ctx->d_J;
-  g.cls = ctx->d_cls;
-  g.h = ctx->d_h32;
-  g.quality = ctx->d_quality;
-  g.nconf = ctx->d_nconf;
-  g.n = n;
-  g.R = R;
-  g.G = t.G;
-  g.a0 = (float)a0;
-  g.c0 = (float)c0;
-  g.dt = (float)dt;
-  g.sched = sched;
-  g.k = 0;
-  g.x = seg_x + NR * L_last;  // x_S
-  g.ytil = nullptr;
-  g.mask = nullptr;
-  g.frec = nullptr;
-  g.lx = lx;
-  g.ly = ly;
-  g.lyt = lyt;
-  g.gh = gh;
-  g.acc = acc;
-  g.ga = nullptr;
-  ok(sbd::launch_adj_init(ctx->jbf16, t, g, s));
-  // reverse sweep, one segment at a time: recompute it with recording (the
-  // last one is recorded already), then reverse it
-  for (int32_t c = n_ck - 1; c >= 0 && e == cudaSuccess; --c) {
-    const int32_t L = std::min(K, S - c * K);
-    if (c < c_last) {
-      ok(cudaMemcpyAsync(seg_x, ck_x + NR * c, NR * 4, cudaMemcpyDeviceToDevice, s));
-      ok(cudaMemcpyAsync(ctx->d_y, ck_y + NR * c, NR * 4, cudaMemcpyDeviceToDevice, s));
-      record_segment(c, L);
+    a.sgn_in = nullptr;
+    a.sgn_out = nullptr;
+    ok(sbd::launch_set_c0(ctx->d_c0ev, ctx->d_c0auto, c0, 1, s));
+    ok(sbd::launch_init(ctx->d_x[0], ctx->d_y, nullptr, ctx->d_ev_row0, n, R, seed, s));
+    int cur = 0;
+    // forward, keeping (x, y) at the start of every segment but the last
+    for (int32_t c = 0; c + 1 < n_ck && e == cudaSuccess; ++c) {
+      ok(cudaMemcpyAsync(ck_x + NR * c, ctx->d_x[cur], NR * 4, cudaMemcpyDeviceToDevice, s));
+      ok(cudaMemcpyAsync(ck_y + NR * c, ctx->d_y, NR * 4, cudaMemcpyDeviceToDevice, s));
+      for (int32_t j = 0; j < K && e == cudaSuccess; ++j) {
+        a.k = c * K + j;
+        a.xin = ctx->d_x[cur];
+        a.xout = ctx->d_x[cur ^ 1];
+        a.y = ctx->d_y;
+        ok(sbd::launch_step(SB_BSB, ctx->jbf16, t, a, s));
+        cur ^= 1;
+      }
     }
-    for (int32_t j = L - 1; j >= 0 && e == cudaSuccess; --j) {
-      g.k = c * K + j;
-      g.x = seg_x + NR * j;
-      g.ytil = seg_yt + NR * j;
-      g.mask = seg_m + NR * j;
-      g.frec = seg_f + NR * j;
-      g.ga = ga + g.k;
-      ok(sbd::launch_adj_phase1(g, s));
-      ok(sbd::launch_adj_phase2(ctx->jbf16, t, g, s));
+    // the last segment, recorded as it runs: x_k, pre-wall momentum, wall mask, J x_k
+    const int32_t c_last = n_ck - 1;
+    const int32_t L_last = S - c_last * K;
+    auto record_segment = [&](int32_t c, int32_t L) {
+      for (int32_t j = 0; j < L && e == cudaSuccess; ++j) {
+        a.k = c * K + j;
+        a.xin = seg_x + NR * j;
+        a.xout = seg_x + NR * (j + 1);
+        a.y = ctx->d_y;
+        a.ytil = seg_yt + NR * j;
+        a.mask = seg_m + NR * j;
+        a.frec = seg_f + NR * j;
+        ok(sbd::launch_step(SB_BSB, ctx->jbf16, t, a, s));
+      }
+      a.ytil = nullptr;
+      a.mask = nullptr;
+      a.frec = nullptr;
+    };
+    ok(cudaMemcpyAsync(seg_x, ctx->d_x[cur], NR * 4, cudaMemcpyDeviceToDevice, s));
+    record_segment(c_last, L_last);
+    ok(cudaMemsetAsync(gh, 0, (size_t)n * 8, s));
+    ok(cudaMemsetAsync(acc, 0, 6 * 8, s));
+    ok(cudaMemsetAsync(ga, 0, (size_t)S * 8, s));
+    sbd::AdjArgs g;
+    g.rowptr = ctx->d_rowptr;
+    g.col = ctx->d_col;
+    g.J = ctx->d_J;
+    g.cls = ctx->d_cls;
+    g.h = ctx->d_h32;
+    g.quality = ctx->d_quality;
+    g.nconf = ctx->d_nconf;
+    g.n = n;
+    g.R = R;
+    g.G = t.G;
+    g.a0 = (float)a0;
+    g.c0 = (float)c0;
+    g.dt = (float)dt;
+    g.sched = sched;
+    g.k = 0;
+    g.x = seg_x + NR * L_last;  // x_S
+    g.ytil = nullptr;
+    g.mask = nullptr;
+    g.frec = nullptr;
+    g.lx = lx;
+    g.ly = ly;
+    g.lyt = lyt;
+    g.gh = gh;
+    g.acc = acc;
+    g.ga = nullptr;
+    ok(sbd::launch_adj_init(ctx->jbf16, t, g, s));
+    // reverse sweep, one segment at a time: recompute it with recording (the
+    // last one is recorded already), then reverse it
+    for (int32_t c = n_ck - 1; c >= 0 && e == cudaSuccess; --c) {
+      const int32_t L = std::min(K, S - c * K);
+      if (c < c_last) {
+        ok(cudaMemcpyAsync(seg_x, ck_x + NR * c, NR * 4, cudaMemcpyDeviceToDevice, s));
+        ok(cudaMemcpyAsync(ctx->d_y, ck_y + NR * c, NR * 4, cudaMemcpyDeviceToDevice, s));
+        record_segment(c, L);
+      }
+      for (int32_t j = L - 1; j >= 0 && e == cudaSuccess; --j) {
+        g.k = c * K + j;
+        g.x = seg_x + NR * j;
+        g.ytil = seg_yt + NR * j;
+        g.mask = seg_m + NR * j;
+        g.frec = seg_f + NR * j;
+        g.ga = ga + g.k;
+        ok(sbd::launch_adj_phase1(g, s));
+        ok(sbd::launch_adj_phase2(ctx->jbf16, t, g, s));
+      }
     }
-  }
-  ok(sbd::launch_adj_final(g, acc + 4, s));
-  if (d_grad_sched) ok(cudaMemcpyAsync(d_grad_sched, ga, (size_t)S * 8, cudaMemcpyDeviceToDevice, s));
-  ok(cudaStreamSynchronize(s));
-  double h_acc[6] = {0, 0, 0, 0, 0, 0};
-  ok(cudaMemcpy(h_acc, acc, sizeof(h_acc), cudaMemcpyDeviceToHost));
-  cleanup();
-  ctx->have_state = false;  // x holds x_S but y was reused by the recomputation
-  SB_CUDA(e);
-  if (out_loss) *out_loss = h_acc[0];
-  if (out_grads) {
-    const double nan = std::nan("");
-    out_grads[0] = h_acc[1];
-    out_grads[1] = h_acc[2];
-    out_grads[2] = ctx->have_classes ? h_acc[4] : nan;
-    out_grads[3] = ctx->have_classes ? h_acc[3] + h_acc[5] : nan;
-  }
-  return SB_OK;
+    ok(sbd::launch_adj_final(g, acc + 4, s));
+    if (d_grad_sched) ok(cudaMemcpyAsync(d_grad_sched, ga, (size_t)S * 8, cudaMemcpyDeviceToDevice, s));
+    ok(cudaStreamSynchronize(s));
+    double h_acc[6] = {0, 0, 0, 0, 0, 0};
+    ok(cudaMemcpy(h_acc, acc, sizeof(h_acc), cudaMemcpyDeviceToHost));
+    cleanup();
+    ctx->have_state = false;  // x holds x_S but y was reused by the recomputation
+    SB_CUDA(e);
+    if (out_loss) *out_loss = h_acc[0];
+    if (out_grads) {
+      const double nan = std::nan("");
+      out_grads[0] = h_acc[1];
+      out_grads[1] = h_acc[2];
+      out_grads[2] = ctx->have_classes ? h_acc[4] : nan;
+      out_grads[3] = ctx->have_classes ? h_acc[3] + h_acc[5] : nan;
+    }
+    return SB_OK;
+  });
 }
 
 sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
 
 sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t trial_steps,
                       int32_t* out_cfg, float* out_us_per_step, void* stream) {
-  if (!ctx || replicas < 1 || replicas > 65535 || trial_steps < 1 || trial_steps > 100000) {
-    set_error("sb_autotune: invalid argument");
-    return SB_ERR_ARG;
-  }
-  sb_status st = check_run_args(ctx, variant, 1.0, 0.0, 0.5, trial_steps);
-  if (st) return st;
-  cudaStream_t s = (cudaStream_t)stream;
-  // candidates: (tiled, replica-tile width, rows per CTA); invalid ones are skipped
-  struct Cand {
-    int tiled, rt, rpc, unroll, groups, l2, rw;
-  };
-  std::vector<Cand> cands = {
-      {0, 0, 0, 4, 1, 0, 0},  {0, 0, 32, 4, 1, 0, 0},  {0, 0, 0, 4, 1, 1, 0},
-      {0, 0, 32, 4, 1, 1, 0}, {0, 128, 0, 4, 1, 0, 0}, {0, 128, 32, 4, 1, 0, 0},
-      {0, 64, 0, 4, 1, 0, 0}, {0, 32, 0, 4, 1, 0, 0},  {0, 0, 0, 4, 2, 0, 0},
-      {0, 0, 32, 4, 2, 0, 0}, {0, 0, 0, 4, 4, 0, 0},   {1, 0, 0, 4, 1, 0, 0},
-      {0, 0, 0, 4, 1, 0, 2},  {0, 0, 32, 4, 1, 0, 2},  {0, 0, 64, 4, 1, 0, 2},
-      {0, 128, 0, 4, 1, 0, 2}, {0, 0, 0, 4, 1, 0, 4},  {0, 0, 64, 4, 1, 0, 4}};
-  const int keep_graph = ctx->use_graph;
-  ctx->use_graph = 0;
-  if ((st = ensure_state(ctx, replicas))) return st;
-  float* sched = nullptr;
-  if ((st = dalloc(&sched, (size_t)trial_steps))) return st;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  float best_us = 3.0e38f;
-  int best = 0;
-  cudaError_t err = cudaEventCreate(&e0);
-  if (err == cudaSuccess) err = cudaEventCreate(&e1);
-  if (err == cudaSuccess) err = sbd::launch_linear_schedule(sched, trial_steps, 1.0, s);
-  for (size_t k = 0; k < cands.size() && err == cudaSuccess; ++k) {
-    const Cand& c = cands[k];
-    if (c.tiled) {
-      if (replicas % sbd::kTileRT != 0) continue;
-      if ((st = ensure_tiles(ctx))) break;
-      if (!ctx->tiled_ok) continue;
+  return sbh::guarded("sb_autotune", [&]() -> sb_status {
+    if (!ctx || replicas < 1 || replicas > 65535 || trial_steps < 1 || trial_steps > 100000) {
+      set_error("sb_autotune: invalid argument");
+      return SB_ERR_ARG;
     }
-    if (c.rt && (replicas % c.rt != 0)) continue;
-    if (c.rw && replicas % 128 != 0) continue;
-    if (c.groups > 1) {
-      const int rt = replicas / c.groups;
-      if (replicas % (4 * c.groups) != 0 || rt > 128 || ((rt / 4) & (rt / 4 - 1)) != 0) continue;
+    sb_status st = check_run_args(ctx, variant, 1.0, 0.0, 0.5, trial_steps);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // candidates: (tiled, replica-tile width, rows per CTA); invalid ones are skipped
+    struct Cand {
+      int tiled, rt, rpc, unroll, groups, l2, rw;
+    };
+    std::vector<Cand> cands = {
+        {0, 0, 0, 4, 1, 0, 0},  {0, 0, 32, 4, 1, 0, 0},  {0, 0, 0, 4, 1, 1, 0},
+        {0, 0, 32, 4, 1, 1, 0}, {0, 128, 0, 4, 1, 0, 0}, {0, 128, 32, 4, 1, 0, 0},
+        {0, 64, 0, 4, 1, 0, 0}, {0, 32, 0, 4, 1, 0, 0},  {0, 0, 0, 4, 2, 0, 0},
+        {0, 0, 32, 4, 2, 0, 0}, {0, 0, 0, 4, 4, 0, 0},   {1, 0, 0, 4, 1, 0, 0},
+        {0, 0, 0, 4, 1, 0, 2},  {0, 0, 32, 4, 1, 0, 2},  {0, 0, 64, 4, 1, 0, 2},
+        {0, 128, 0, 4, 1, 0, 2}, {0, 0, 0, 4, 1, 0, 4},  {0, 0, 64, 4, 1, 0, 4}};
+    const int keep_graph = ctx->use_graph;
+    ctx->use_graph = 0;
+    if ((st = ensure_state(ctx, replicas))) return st;
+    float* sched = nullptr;
+    if ((st = dalloc(&sched, (size_t)trial_steps))) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float best_us = 3.0e38f;
+    int best = 0;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    if (err == cudaSuccess) err = sbd::launch_linear_schedule(sched, trial_steps, 1.0, s);
+    for (size_t k = 0; k < cands.size() && err == cudaSuccess; ++k) {
+      const Cand& c = cands[k];
+      if (c.tiled) {
+        if (replicas % sbd::kTileRT != 0) continue;
+        if ((st = ensure_tiles(ctx))) break;
+        if (!ctx->tiled_ok) continue;
+      }
+      if (c.rt && (replicas % c.rt != 0)) continue;
+      if (c.rw && replicas % 128 != 0) continue;
+      if (c.groups > 1) {
+        const int rt = replicas / c.groups;
+        if (replicas % (4 * c.groups) != 0 || rt > 128 || ((rt / 4) & (rt / 4 - 1)) != 0) continue;
+      }
+      ctx->use_tiled = c.tiled;
+      ctx->step_rt = c.rt;
+      ctx->step_rpc = c.rpc;
+      ctx->step_unroll = c.unroll;
+      ctx->groups = c.groups;
+      ctx->rw_rows = c.rw;
+      if ((st = c.l2 ? l2_persist_on(ctx) : l2_persist_off(ctx))) break;
+      ctx->l2_persist = c.l2;
+      ctx->graph.reset();
+      if ((st = sb_run(ctx, variant, 1.0, 0.0, 0.5, 0, replicas, 12345, nullptr, stream))) break;
+      if ((st = enqueue_steps(ctx, variant, 1.0, 0.5, std::min(trial_steps, 4), sched, s))) break;
+      err = cudaEventRecord(e0, s);
+      if (err != cudaSuccess) break;
+      if ((st = enqueue_steps(ctx, variant, 1.0, 0.5, trial_steps, sched, s))) break;
+      err = cudaEventRecord(e1, s);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      const float us = ms * 1000.f / trial_steps;
+      if (err == cudaSuccess && us < best_us) {
+        best_us = us;
+        best = (int)k;
+      }
     }
-    ctx->use_tiled = c.tiled;
-    ctx->step_rt = c.rt;
-    ctx->step_rpc = c.rpc;
-    ctx->step_unroll = c.unroll;
-    ctx->groups = c.groups;
-    ctx->rw_rows = c.rw;
-    if ((st = c.l2 ? l2_persist_on(ctx) : l2_persist_off(ctx))) break;
-    ctx->l2_persist = c.l2;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dfree(sched);
+    ctx->use_graph = keep_graph;
+    ctx->have_state = false;
+    if (st) return st;
+    SB_CUDA(err);
+    ctx->use_tiled = cands[best].tiled;
+    ctx->step_rt = cands[best].rt;
+    ctx->step_rpc = cands[best].rpc;
+    ctx->step_unroll = cands[best].unroll;
+    ctx->groups = cands[best].groups;
+    ctx->l2_persist = cands[best].l2;
+    if ((st = ctx->l2_persist ? l2_persist_on(ctx) : l2_persist_off(ctx))) return st;
+    ctx->rw_rows = cands[best].rw;
     ctx->graph.reset();
-    if ((st = sb_run(ctx, variant, 1.0, 0.0, 0.5, 0, replicas, 12345, nullptr, stream))) break;
-    if ((st = enqueue_steps(ctx, variant, 1.0, 0.5, std::min(trial_steps, 4), sched, s))) break;
-    err = cudaEventRecord(e0, s);
-    if (err != cudaSuccess) break;
-    if ((st = enqueue_steps(ctx, variant, 1.0, 0.5, trial_steps, sched, s))) break;
-    err = cudaEventRecord(e1, s);
-    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-    const float us = ms * 1000.f / trial_steps;
-    if (err == cudaSuccess && us < best_us) {
-      best_us = us;
-      best = (int)k;
+    if (out_cfg) {
+      out_cfg[0] = cands[best].tiled;
+      out_cfg[1] = cands[best].rt;
+      out_cfg[2] = cands[best].rpc;
+      out_cfg[3] = cands[best].unroll;
+      out_cfg[4] = cands[best].groups;
+      out_cfg[5] = cands[best].l2;
+      out_cfg[6] = cands[best].rw;
     }
-  }
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
-  dfree(sched);
-  ctx->use_graph = keep_graph;
-  ctx->have_state = false;
-  if (st) return st;
-  SB_CUDA(err);
-  ctx->use_tiled = cands[best].tiled;
-  ctx->step_rt = cands[best].rt;
-  ctx->step_rpc = cands[best].rpc;
-  ctx->step_unroll = cands[best].unroll;
-  ctx->groups = cands[best].groups;
-  ctx->l2_persist = cands[best].l2;
-  if ((st = ctx->l2_persist ? l2_persist_on(ctx) : l2_persist_off(ctx))) return st;
-  ctx->rw_rows = cands[best].rw;
-  ctx->graph.reset();
-  if (out_cfg) {
-    out_cfg[0] = cands[best].tiled;
-    out_cfg[1] = cands[best].rt;
-    out_cfg[2] = cands[best].rpc;
-    out_cfg[3] = cands[best].unroll;
-    out_cfg[4] = cands[best].groups;
-    out_cfg[5] = cands[best].l2;
-    out_cfg[6] = cands[best].rw;
-  }
-  if (out_us_per_step) *out_us_per_step = best_us;
-  return SB_OK;
+    if (out_us_per_step) *out_us_per_step = best_us;
+    return SB_OK;
+  });
 }
 
 sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value) {
-  if (!ctx) {
-    set_error("sb_set_option: null context");
-    return SB_ERR_ARG;
-  }
-  switch (key) {
-    case 0:  // SB_OPT_GRAPH
-      ctx->use_graph = value != 0;
-      if (!ctx->use_graph) ctx->graph.reset();
-      return SB_OK;
-    case 1:  // SB_OPT_TILED
-      ctx->use_tiled = value != 0;
-      ctx->graph.reset();
-      return SB_OK;
-    case 2:  // SB_OPT_STEP_RT
-      if (value != 0 && (value % 4 != 0 || value > 128 || value < 4 ||
-                         ((value / 4) & (value / 4 - 1)) != 0)) {
-        set_error("sb_set_option: SB_OPT_STEP_RT must be 0 or 4 * (a power of two <= 32)");
-        return SB_ERR_ARG;
-      }
-      ctx->step_rt = (int)value;
-      ctx->graph.reset();
-      return SB_OK;
-    case 3:  // SB_OPT_STEP_RPC
-      if (value < -1 || value > (1 << 20)) {
-        set_error("sb_set_option: SB_OPT_STEP_RPC out of range");
-        return SB_ERR_ARG;
-      }
-      ctx->step_rpc = (int)value;
-      ctx->graph.reset();
-      return SB_OK;
-    case 4:  // SB_OPT_STEP_UNROLL
-      if (value != 4) {
-        set_error("sb_set_option: SB_OPT_STEP_UNROLL must be 4 (8 measured slower and was removed)");
-        return SB_ERR_ARG;
-      }
-      ctx->step_unroll = (int)value;
-      ctx->graph.reset();
-      return SB_OK;
-    case 5:  // SB_OPT_DSB_SIGNS
-      ctx->dsb_signs = value != 0;
-      ctx->graph.reset();
-      return SB_OK;
-    case 7: {  // SB_OPT_L2_PERSIST
-      const sb_status st = value ? l2_persist_on(ctx) : l2_persist_off(ctx);
-      if (st) return st;
-      ctx->l2_persist = value != 0;
-      ctx->graph.reset();
-      return SB_OK;
-    }
-    case 9:  // SB_OPT_ROWS_PER_WARP
-      if (value != -1 && value != 0 && value != 2 && value != 4) {
-        set_error("sb_set_option: SB_OPT_ROWS_PER_WARP must be -1, 0, 2 or 4");
-        return SB_ERR_ARG;
-      }
-      ctx->rw_rows = (int)value;
-      ctx->graph.reset();
-      return SB_OK;
-    case 8:  // SB_OPT_STREAM
-      ctx->use_stream = value != 0;
-      ctx->graph.reset();
-      return SB_OK;
-    case 6:  // SB_OPT_REPLICA_GROUPS
-      if (value < 1 || value > 64) {
-        set_error("sb_set_option: SB_OPT_REPLICA_GROUPS must be in [1, 64]");
-        return SB_ERR_ARG;
-      }
-      ctx->groups = (int)value;
-      ctx->graph.reset();
-      return SB_OK;
-    default:
-      set_error("sb_set_option: unknown key");
+  return sbh::guarded("sb_set_option", [&]() -> sb_status {
+    if (!ctx) {
+      set_error("sb_set_option: null context");
       return SB_ERR_ARG;
-  }
+    }
+    switch (key) {
+      case 0:  // SB_OPT_GRAPH
+        ctx->use_graph = value != 0;
+        if (!ctx->use_graph) ctx->graph.reset();
+        return SB_OK;
+      case 1:  // SB_OPT_TILED
+        ctx->use_tiled = value != 0;
+        ctx->graph.reset();
+        return SB_OK;
+      case 2:  // SB_OPT_STEP_RT
+        if (value != 0 && (value % 4 != 0 || value > 128 || value < 4 ||
+                           ((value / 4) & (value / 4 - 1)) != 0)) {
+          set_error("sb_set_option: SB_OPT_STEP_RT must be 0 or 4 * (a power of two <= 32)");
+          return SB_ERR_ARG;
+        }
+        ctx->step_rt = (int)value;
+        ctx->graph.reset();
+        return SB_OK;
+      case 3:  // SB_OPT_STEP_RPC
+        if (value < -1 || value > (1 << 20)) {
+          set_error("sb_set_option: SB_OPT_STEP_RPC out of range");
+          return SB_ERR_ARG;
+        }
+        ctx->step_rpc = (int)value;
+        ctx->graph.reset();
+        return SB_OK;
+      case 4:  // SB_OPT_STEP_UNROLL
+        if (value != 4) {
+          set_error("sb_set_option: SB_OPT_STEP_UNROLL must be 4 (8 measured slower and was removed)");
+          return SB_ERR_ARG;
+        }
+        ctx->step_unroll = (int)value;
+        ctx->graph.reset();
+        return SB_OK;
+      case 5:  // SB_OPT_DSB_SIGNS
+        ctx->dsb_signs = value != 0;
+        ctx->graph.reset();
+        return SB_OK;
+      case 7: {  // SB_OPT_L2_PERSIST
+        const sb_status st = value ? l2_persist_on(ctx) : l2_persist_off(ctx);
+        if (st) return st;
+        ctx->l2_persist = value != 0;
+        ctx->graph.reset();
+        return SB_OK;
+      }
+      case 9:  // SB_OPT_ROWS_PER_WARP
+        if (value != -1 && value != 0 && value != 2 && value != 4) {
+          set_error("sb_set_option: SB_OPT_ROWS_PER_WARP must be -1, 0, 2 or 4");
+          return SB_ERR_ARG;
+        }
+        ctx->rw_rows = (int)value;
+        ctx->graph.reset();
+        return SB_OK;
+      case 8:  // SB_OPT_STREAM
+        ctx->use_stream = value != 0;
+        ctx->graph.reset();
+        return SB_OK;
+      case 6:  // SB_OPT_REPLICA_GROUPS
+        if (value < 1 || value > 64) {
+          set_error("sb_set_option: SB_OPT_REPLICA_GROUPS must be in [1, 64]");
+          return SB_ERR_ARG;
+        }
+        ctx->groups = (int)value;
+        ctx->graph.reset();
+        return SB_OK;
+      default:
+        set_error("sb_set_option: unknown key");
+        return SB_ERR_ARG;
+    }
+  });
 }
 
 }  // extern "C"

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../host/host_internal.h"
+#include "../guard.h"
 
 namespace {
 
@@ -513,239 +514,241 @@ struct Pool {
 
 extern "C" sb_status sb_qubo_build_device(const sb_event* ev, const sb_build_params* bp,
                                           sb_qubo** out, double* out_device_ms, void* stream) {
-  if (!ev || !bp || !out) {
-    sbh::set_error("sb_qubo_build_device: null argument");
-    return SB_ERR_ARG;
-  }
-  *out = nullptr;
-  if ((bp->coupling_mode != 0 && bp->coupling_mode != 1) ||
-      (bp->bias_mode != 0 && bp->bias_mode != 1) ||
-      (bp->bias_mode == 1 && !(bp->gamma > 0.0 && bp->lambda > 0.0))) {
-    sbh::set_error("sb_qubo_build_device: coupling_mode / bias_mode must be 0 or 1");
-    return SB_ERR_ARG;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  const int32_t nh = (int32_t)ev->layer.size();
-  int nl = 0;
-  for (int32_t h = 0; h < nh; ++h) nl = std::max(nl, ev->layer[h] + 1);
-  std::vector<int32_t> lstart(nl + 2, 0);
-  for (int32_t h = 0; h < nh; ++h) lstart[ev->layer[h] + 1]++;
-  for (int l = 0; l < nl; ++l) lstart[l + 1] += lstart[l];
-  lstart[nl + 1] = lstart[nl];
-  Pool P;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  auto fail = [&](cudaError_t e) {
-    cudaGetLastError();  // clear a non-sticky error (allocation) before returning
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    sbh::set_error(std::string("sb_qubo_build_device: ") + cudaGetErrorString(e));
-    return e == cudaErrorMemoryAllocation ? SB_ERR_OOM : SB_ERR_CUDA;
-  };
+  return sbh::guarded("sb_qubo_build_device", [&]() -> sb_status {
+    if (!ev || !bp || !out) {
+      sbh::set_error("sb_qubo_build_device: null argument");
+      return SB_ERR_ARG;
+    }
+    *out = nullptr;
+    if ((bp->coupling_mode != 0 && bp->coupling_mode != 1) ||
+        (bp->bias_mode != 0 && bp->bias_mode != 1) ||
+        (bp->bias_mode == 1 && !(bp->gamma > 0.0 && bp->lambda > 0.0))) {
+      sbh::set_error("sb_qubo_build_device: coupling_mode / bias_mode must be 0 or 1");
+      return SB_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int32_t nh = (int32_t)ev->layer.size();
+    int nl = 0;
+    for (int32_t h = 0; h < nh; ++h) nl = std::max(nl, ev->layer[h] + 1);
+    std::vector<int32_t> lstart(nl + 2, 0);
+    for (int32_t h = 0; h < nh; ++h) lstart[ev->layer[h] + 1]++;
+    for (int l = 0; l < nl; ++l) lstart[l + 1] += lstart[l];
+    lstart[nl + 1] = lstart[nl];
+    Pool P;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto fail = [&](cudaError_t e) {
+      cudaGetLastError();  // clear a non-sticky error (allocation) before returning
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      sbh::set_error(std::string("sb_qubo_build_device: ") + cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? SB_ERR_OOM : SB_ERR_CUDA;
+    };
 #define SB_B(call)                           \
-  do {                                       \
-    cudaError_t e_ = (call);                 \
-    if (e_ != cudaSuccess) return fail(e_);  \
-  } while (0)
-  Hits H;
-  int32_t* d_layer = P.get<int32_t>(nh);
-  double* d_r = P.get<double>(nh);
-  double* d_phi = P.get<double>(nh);
-  double* d_z = P.get<double>(nh);
-  double* d_x = P.get<double>(nh);
-  double* d_y = P.get<double>(nh);
-  int32_t* d_ls = P.get<int32_t>(nl + 2);
-  SB_B(P.err);
-  if (nh) {
-    SB_B(cudaMemcpyAsync(d_layer, ev->layer.data(), nh * 4, cudaMemcpyHostToDevice, s));
-    SB_B(cudaMemcpyAsync(d_r, ev->r.data(), nh * 8, cudaMemcpyHostToDevice, s));
-    SB_B(cudaMemcpyAsync(d_phi, ev->phi.data(), nh * 8, cudaMemcpyHostToDevice, s));
-    SB_B(cudaMemcpyAsync(d_z, ev->z.data(), nh * 8, cudaMemcpyHostToDevice, s));
-    SB_B(cudaMemcpyAsync(d_x, ev->x.data(), nh * 8, cudaMemcpyHostToDevice, s));
-    SB_B(cudaMemcpyAsync(d_y, ev->y.data(), nh * 8, cudaMemcpyHostToDevice, s));
-  }
-  SB_B(cudaMemcpyAsync(d_ls, lstart.data(), (nl + 2) * 4, cudaMemcpyHostToDevice, s));
-  H.layer = d_layer;
-  H.r = d_r;
-  H.phi = d_phi;
-  H.z = d_z;
-  H.x = d_x;
-  H.y = d_y;
-  H.lstart = d_ls;
-  H.nh = nh;
-  H.nl = nl;
-  Cuts p;
-  p.dphi_slope = bp->dphi_slope;
-  p.dphi_margin = bp->dphi_margin;
-  p.z0_max = bp->z0_max;
-  p.kappa_max = bp->kappa_max;
-  p.dtheta_max = bp->dtheta_max;
-  p.dkappa_max = bp->dkappa_max;
-  p.w_q = bp->w_q;
-  p.w_c = bp->w_c;
-  p.five_hit_rule = bp->five_hit_rule;
-  p.coupling_mode = bp->coupling_mode;
-  p.bias_mode = bp->bias_mode;
-  p.s_min = bp->s_min;
-  p.alpha = bp->alpha;
-  p.beta = bp->beta;
-  p.gamma = bp->gamma;
-  p.lambda = bp->lambda;
-  SB_B(cudaEventRecord(e0, s));
-  // 1. doublets
-  long long* dcnt = P.get<long long>(nh + 1);
-  long long* doff = P.get<long long>(nh + 1);
-  SB_B(P.err);
-  SB_B(cudaMemsetAsync(dcnt, 0, (nh + 1) * 8, s));
-  k_doublet_count<<<grid_of(nh), kB, 0, s>>>(H, p, dcnt);
-  SB_B(cudaGetLastError());
-  long long nd = 0;
-  SB_B(exclusive_scan(dcnt, doff, nh + 1, &nd, s));
-  int32_t* d_out = P.get<int32_t>(nd);
-  double* d_theta = P.get<double>(nd);
-  SB_B(P.err);
-  k_doublet_write<<<grid_of(nh), kB, 0, s>>>(H, p, doff, d_out, d_theta);
-  SB_B(cudaGetLastError());
-  // 2. triplets, lexicographic by construction (a, then b, then c ascending)
-  long long* tcnt = P.get<long long>(nh + 1);
-  long long* toff = P.get<long long>(nh + 1);
-  SB_B(P.err);
-  SB_B(cudaMemsetAsync(tcnt, 0, (nh + 1) * 8, s));
-  k_triplets<false><<<grid_of(nh), kB, 0, s>>>(H, p, doff, d_out, d_theta, nullptr, tcnt, nullptr,
-                                               nullptr, nullptr, nullptr, nullptr);
-  SB_B(cudaGetLastError());
-  long long nt = 0;
-  SB_B(exclusive_scan(tcnt, toff, nh + 1, &nt, s));
-  if (nt >= 0x7FFFFFFFLL) return fail(cudaErrorInvalidValue);
-  int32_t* ta = P.get<int32_t>(nt);
-  int32_t* tb = P.get<int32_t>(nt);
-  int32_t* tc = P.get<int32_t>(nt);
-  double* tk = P.get<double>(nt);
-  double* tdth = P.get<double>(nt);
-  SB_B(P.err);
-  k_triplets<true><<<grid_of(nh), kB, 0, s>>>(H, p, doff, d_out, d_theta, toff, nullptr, ta, tb,
-                                              tc, tk, tdth);
-  SB_B(cudaGetLastError());
-  // 3. hit -> triplet incidence (ascending triplet order per hit)
-  unsigned long long* hcnt = P.get<unsigned long long>(nh + 1);
-  unsigned long long* hfill = P.get<unsigned long long>(nh + 1);
-  long long* hoff = P.get<long long>(nh + 1);
-  int32_t* list = P.get<int32_t>(3 * nt);
-  SB_B(P.err);
-  SB_B(cudaMemsetAsync(hcnt, 0, (nh + 1) * 8, s));
-  SB_B(cudaMemsetAsync(hfill, 0, (nh + 1) * 8, s));
-  k_incidence_count<<<grid_of(nt), kB, 0, s>>>(ta, tb, tc, nt, hcnt);
-  SB_B(cudaGetLastError());
-  long long ninc = 0;
-  SB_B(exclusive_scan(reinterpret_cast<long long*>(hcnt), hoff, nh + 1, &ninc, s));
-  k_incidence_fill<<<grid_of(nt), kB, 0, s>>>(ta, tb, tc, nt, hoff, hfill, list);
-  SB_B(cudaGetLastError());
-  k_incidence_sort<<<grid_of(nh), kB, 0, s>>>(hoff, nh, list);
-  SB_B(cudaGetLastError());
-  // 4. pairs
-  Trip T;
-  T.a = ta;
-  T.b = tb;
-  T.c = tc;
-  T.k = tk;
-  T.dth = tdth;
-  T.n = nt;
-  long long* pcnt = P.get<long long>(nt + 1);
-  long long* poff = P.get<long long>(nt + 1);
-  SB_B(P.err);
-  SB_B(cudaMemsetAsync(pcnt, 0, (nt + 1) * 8, s));
-  k_pairs<<<grid_of(nt), kB, 0, s>>>(H, p, T, hoff, list, nullptr, pcnt, nullptr, nullptr);
-  SB_B(cudaGetLastError());
-  long long np = 0;
-  SB_B(exclusive_scan(pcnt, poff, nt + 1, &np, s));
-  int32_t* pj = P.get<int32_t>(np);
-  int8_t* pcls = P.get<int8_t>(np);
-  SB_B(P.err);
-  k_pairs<<<grid_of(nt), kB, 0, s>>>(H, p, T, hoff, list, poff, nullptr, pj, pcls);
-  SB_B(cudaGetLastError());
-  // 5. pruning
-  uint8_t* has_succ = P.get<uint8_t>(nt);
-  uint8_t* has_pred = P.get<uint8_t>(nt);
-  uint8_t* keep = P.get<uint8_t>(nt);
-  long long* keep_ll = P.get<long long>(nt + 1);
-  long long* newidx = P.get<long long>(nt + 1);
-  SB_B(P.err);
-  SB_B(cudaMemsetAsync(has_succ, 0, std::max<long long>(nt, 1), s));
-  SB_B(cudaMemsetAsync(has_pred, 0, std::max<long long>(nt, 1), s));
-  SB_B(cudaMemsetAsync(keep, 0, std::max<long long>(nt, 1), s));
-  SB_B(cudaMemsetAsync(keep_ll, 0, (nt + 1) * 8, s));
-  k_links<<<grid_of(nt), kB, 0, s>>>(H, T, poff, pj, pcls, has_succ, has_pred);
-  SB_B(cudaGetLastError());
-  k_keep<<<grid_of(nt), kB, 0, s>>>(H, p, T, poff, pj, pcls, has_succ, has_pred, keep);
-  SB_B(cudaGetLastError());
-  k_u8_to_ll<<<grid_of(nt), kB, 0, s>>>(keep, keep_ll, nt);
-  SB_B(cudaGetLastError());
-  long long n = 0;
-  SB_B(exclusive_scan(keep_ll, newidx, nt + 1, &n, s));
-  // 6. CSR over the survivors
-  long long* rcnt = P.get<long long>(n + 1);
-  long long* roff = P.get<long long>(n + 1);
-  SB_B(P.err);
-  SB_B(cudaMemsetAsync(rcnt, 0, (n + 1) * 8, s));
-  k_rows<<<grid_of(nt), kB, 0, s>>>(T, poff, pj, keep, newidx, rcnt);
-  SB_B(cudaGetLastError());
-  long long nnz = 0;
-  SB_B(exclusive_scan(rcnt, roff, n + 1, &nnz, s));
-  if (nnz >= 0x7FFFFFFFLL) return fail(cudaErrorInvalidValue);
-  int32_t* col = P.get<int32_t>(nnz);
-  double* val = P.get<double>(nnz);
-  int8_t* cls = P.get<int8_t>(nnz);
-  double* quality = P.get<double>(n);
-  double* lin = P.get<double>(n);
-  int32_t* trip = P.get<int32_t>(3 * n);
-  double* kappa = P.get<double>(n);
-  double* dtheta = P.get<double>(n);
-  SB_B(P.err);
-  k_rows_write<<<grid_of(nt), kB, 0, s>>>(H, p, T, poff, pj, pcls, keep, newidx, roff, col, val,
-                                          cls, quality, lin, trip, kappa, dtheta);
-  SB_B(cudaGetLastError());
-  SB_B(cudaEventRecord(e1, s));
-  // copy out
-  sb_qubo* q = new (std::nothrow) sb_qubo;
-  if (!q) return fail(cudaErrorMemoryAllocation);
-  q->n = (int32_t)n;
-  q->rowptr.resize(n + 1);
-  q->col.resize(nnz);
-  q->val.resize(nnz);
-  q->cls.resize(nnz);
-  q->quality.resize(n);
-  q->lin.resize(n);
-  q->trip.resize(3 * n);
-  q->kappa.resize(n);
-  q->dtheta.resize(n);
-  std::vector<long long> ro(n + 1);
-  cudaError_t e = cudaMemcpyAsync(ro.data(), roff, (n + 1) * 8, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && nnz) {
-    e = cudaMemcpyAsync(q->col.data(), col, nnz * 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(q->val.data(), val, nnz * 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(q->cls.data(), cls, nnz, cudaMemcpyDeviceToHost, s);
-  }
-  if (e == cudaSuccess && n) {
-    e = cudaMemcpyAsync(q->quality.data(), quality, n * 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(q->lin.data(), lin, n * 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(q->trip.data(), trip, 3 * n * 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(q->kappa.data(), kappa, n * 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(q->dtheta.data(), dtheta, n * 8, cudaMemcpyDeviceToHost, s);
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) {
-    delete q;
-    return fail(e);
-  }
-  ro[n] = nnz;
-  for (long long i = 0; i <= n; ++i) q->rowptr[i] = (int32_t)ro[i];
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  if (out_device_ms) *out_device_ms = ms;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  *out = q;
-  return SB_OK;
+    do {                                       \
+      cudaError_t e_ = (call);                 \
+      if (e_ != cudaSuccess) return fail(e_);  \
+    } while (0)
+    Hits H;
+    int32_t* d_layer = P.get<int32_t>(nh);
+    double* d_r = P.get<double>(nh);
+    double* d_phi = P.get<double>(nh);
+    double* d_z = P.get<double>(nh);
+    double* d_x = P.get<double>(nh);
+    double* d_y = P.get<double>(nh);
+    int32_t* d_ls = P.get<int32_t>(nl + 2);
+    SB_B(P.err);
+    if (nh) {
+      SB_B(cudaMemcpyAsync(d_layer, ev->layer.data(), nh * 4, cudaMemcpyHostToDevice, s));
+      SB_B(cudaMemcpyAsync(d_r, ev->r.data(), nh * 8, cudaMemcpyHostToDevice, s));
+      SB_B(cudaMemcpyAsync(d_phi, ev->phi.data(), nh * 8, cudaMemcpyHostToDevice, s));
+      SB_B(cudaMemcpyAsync(d_z, ev->z.data(), nh * 8, cudaMemcpyHostToDevice, s));
+      SB_B(cudaMemcpyAsync(d_x, ev->x.data(), nh * 8, cudaMemcpyHostToDevice, s));
+      SB_B(cudaMemcpyAsync(d_y, ev->y.data(), nh * 8, cudaMemcpyHostToDevice, s));
+    }
+    SB_B(cudaMemcpyAsync(d_ls, lstart.data(), (nl + 2) * 4, cudaMemcpyHostToDevice, s));
+    H.layer = d_layer;
+    H.r = d_r;
+    H.phi = d_phi;
+    H.z = d_z;
+    H.x = d_x;
+    H.y = d_y;
+    H.lstart = d_ls;
+    H.nh = nh;
+    H.nl = nl;
+    Cuts p;
+    p.dphi_slope = bp->dphi_slope;
+    p.dphi_margin = bp->dphi_margin;
+    p.z0_max = bp->z0_max;
+    p.kappa_max = bp->kappa_max;
+    p.dtheta_max = bp->dtheta_max;
+    p.dkappa_max = bp->dkappa_max;
+    p.w_q = bp->w_q;
+    p.w_c = bp->w_c;
+    p.five_hit_rule = bp->five_hit_rule;
+    p.coupling_mode = bp->coupling_mode;
+    p.bias_mode = bp->bias_mode;
+    p.s_min = bp->s_min;
+    p.alpha = bp->alpha;
+    p.beta = bp->beta;
+    p.gamma = bp->gamma;
+    p.lambda = bp->lambda;
+    SB_B(cudaEventRecord(e0, s));
+    // 1. doublets
+    long long* dcnt = P.get<long long>(nh + 1);
+    long long* doff = P.get<long long>(nh + 1);
+    SB_B(P.err);
+    SB_B(cudaMemsetAsync(dcnt, 0, (nh + 1) * 8, s));
+    k_doublet_count<<<grid_of(nh), kB, 0, s>>>(H, p, dcnt);
+    SB_B(cudaGetLastError());
+    long long nd = 0;
+    SB_B(exclusive_scan(dcnt, doff, nh + 1, &nd, s));
+    int32_t* d_out = P.get<int32_t>(nd);
+    double* d_theta = P.get<double>(nd);
+    SB_B(P.err);
+    k_doublet_write<<<grid_of(nh), kB, 0, s>>>(H, p, doff, d_out, d_theta);
+    SB_B(cudaGetLastError());
+    // 2. triplets, lexicographic by construction (a, then b, then c ascending)
+    long long* tcnt = P.get<long long>(nh + 1);
+    long long* toff = P.get<long long>(nh + 1);
+    SB_B(P.err);
+    SB_B(cudaMemsetAsync(tcnt, 0, (nh + 1) * 8, s));
+    k_triplets<false><<<grid_of(nh), kB, 0, s>>>(H, p, doff, d_out, d_theta, nullptr, tcnt, nullptr,
+                                                 nullptr, nullptr, nullptr, nullptr);
+    SB_B(cudaGetLastError());
+    long long nt = 0;
+    SB_B(exclusive_scan(tcnt, toff, nh + 1, &nt, s));
+    if (nt >= 0x7FFFFFFFLL) return fail(cudaErrorInvalidValue);
+    int32_t* ta = P.get<int32_t>(nt);
+    int32_t* tb = P.get<int32_t>(nt);
+    int32_t* tc = P.get<int32_t>(nt);
+    double* tk = P.get<double>(nt);
+    double* tdth = P.get<double>(nt);
+    SB_B(P.err);
+    k_triplets<true><<<grid_of(nh), kB, 0, s>>>(H, p, doff, d_out, d_theta, toff, nullptr, ta, tb,
+                                                tc, tk, tdth);
+    SB_B(cudaGetLastError());
+    // 3. hit -> triplet incidence (ascending triplet order per hit)
+    unsigned long long* hcnt = P.get<unsigned long long>(nh + 1);
+    unsigned long long* hfill = P.get<unsigned long long>(nh + 1);
+    long long* hoff = P.get<long long>(nh + 1);
+    int32_t* list = P.get<int32_t>(3 * nt);
+    SB_B(P.err);
+    SB_B(cudaMemsetAsync(hcnt, 0, (nh + 1) * 8, s));
+    SB_B(cudaMemsetAsync(hfill, 0, (nh + 1) * 8, s));
+    k_incidence_count<<<grid_of(nt), kB, 0, s>>>(ta, tb, tc, nt, hcnt);
+    SB_B(cudaGetLastError());
+    long long ninc = 0;
+    SB_B(exclusive_scan(reinterpret_cast<long long*>(hcnt), hoff, nh + 1, &ninc, s));
+    k_incidence_fill<<<grid_of(nt), kB, 0, s>>>(ta, tb, tc, nt, hoff, hfill, list);
+    SB_B(cudaGetLastError());
+    k_incidence_sort<<<grid_of(nh), kB, 0, s>>>(hoff, nh, list);
+    SB_B(cudaGetLastError());
+    // 4. pairs
+    Trip T;
+    T.a = ta;
+    T.b = tb;
+    T.c = tc;
+    T.k = tk;
+    T.dth = tdth;
+    T.n = nt;
+    long long* pcnt = P.get<long long>(nt + 1);
+    long long* poff = P.get<long long>(nt + 1);
+    SB_B(P.err);
+    SB_B(cudaMemsetAsync(pcnt, 0, (nt + 1) * 8, s));
+    k_pairs<<<grid_of(nt), kB, 0, s>>>(H, p, T, hoff, list, nullptr, pcnt, nullptr, nullptr);
+    SB_B(cudaGetLastError());
+    long long np = 0;
+    SB_B(exclusive_scan(pcnt, poff, nt + 1, &np, s));
+    int32_t* pj = P.get<int32_t>(np);
+    int8_t* pcls = P.get<int8_t>(np);
+    SB_B(P.err);
+    k_pairs<<<grid_of(nt), kB, 0, s>>>(H, p, T, hoff, list, poff, nullptr, pj, pcls);
+    SB_B(cudaGetLastError());
+    // 5. pruning
+    uint8_t* has_succ = P.get<uint8_t>(nt);
+    uint8_t* has_pred = P.get<uint8_t>(nt);
+    uint8_t* keep = P.get<uint8_t>(nt);
+    long long* keep_ll = P.get<long long>(nt + 1);
+    long long* newidx = P.get<long long>(nt + 1);
+    SB_B(P.err);
+    SB_B(cudaMemsetAsync(has_succ, 0, std::max<long long>(nt, 1), s));
+    SB_B(cudaMemsetAsync(has_pred, 0, std::max<long long>(nt, 1), s));
+    SB_B(cudaMemsetAsync(keep, 0, std::max<long long>(nt, 1), s));
+    SB_B(cudaMemsetAsync(keep_ll, 0, (nt + 1) * 8, s));
+    k_links<<<grid_of(nt), kB, 0, s>>>(H, T, poff, pj, pcls, has_succ, has_pred);
+    SB_B(cudaGetLastError());
+    k_keep<<<grid_of(nt), kB, 0, s>>>(H, p, T, poff, pj, pcls, has_succ, has_pred, keep);
+    SB_B(cudaGetLastError());
+    k_u8_to_ll<<<grid_of(nt), kB, 0, s>>>(keep, keep_ll, nt);
+    SB_B(cudaGetLastError());
+    long long n = 0;
+    SB_B(exclusive_scan(keep_ll, newidx, nt + 1, &n, s));
+    // 6. CSR over the survivors
+    long long* rcnt = P.get<long long>(n + 1);
+    long long* roff = P.get<long long>(n + 1);
+    SB_B(P.err);
+    SB_B(cudaMemsetAsync(rcnt, 0, (n + 1) * 8, s));
+    k_rows<<<grid_of(nt), kB, 0, s>>>(T, poff, pj, keep, newidx, rcnt);
+    SB_B(cudaGetLastError());
+    long long nnz = 0;
+    SB_B(exclusive_scan(rcnt, roff, n + 1, &nnz, s));
+    if (nnz >= 0x7FFFFFFFLL) return fail(cudaErrorInvalidValue);
+    int32_t* col = P.get<int32_t>(nnz);
+    double* val = P.get<double>(nnz);
+    int8_t* cls = P.get<int8_t>(nnz);
+    double* quality = P.get<double>(n);
+    double* lin = P.get<double>(n);
+    int32_t* trip = P.get<int32_t>(3 * n);
+    double* kappa = P.get<double>(n);
+    double* dtheta = P.get<double>(n);
+    SB_B(P.err);
+    k_rows_write<<<grid_of(nt), kB, 0, s>>>(H, p, T, poff, pj, pcls, keep, newidx, roff, col, val,
+                                            cls, quality, lin, trip, kappa, dtheta);
+    SB_B(cudaGetLastError());
+    SB_B(cudaEventRecord(e1, s));
+    // copy out
+    sb_qubo* q = new (std::nothrow) sb_qubo;
+    if (!q) return fail(cudaErrorMemoryAllocation);
+    q->n = (int32_t)n;
+    q->rowptr.resize(n + 1);
+    q->col.resize(nnz);
+    q->val.resize(nnz);
+    q->cls.resize(nnz);
+    q->quality.resize(n);
+    q->lin.resize(n);
+    q->trip.resize(3 * n);
+    q->kappa.resize(n);
+    q->dtheta.resize(n);
+    std::vector<long long> ro(n + 1);
+    cudaError_t e = cudaMemcpyAsync(ro.data(), roff, (n + 1) * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && nnz) {
+      e = cudaMemcpyAsync(q->col.data(), col, nnz * 4, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(q->val.data(), val, nnz * 8, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(q->cls.data(), cls, nnz, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess && n) {
+      e = cudaMemcpyAsync(q->quality.data(), quality, n * 8, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(q->lin.data(), lin, n * 8, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(q->trip.data(), trip, 3 * n * 4, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(q->kappa.data(), kappa, n * 8, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(q->dtheta.data(), dtheta, n * 8, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      delete q;
+      return fail(e);
+    }
+    ro[n] = nnz;
+    for (long long i = 0; i <= n; ++i) q->rowptr[i] = (int32_t)ro[i];
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (out_device_ms) *out_device_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *out = q;
+    return SB_OK;
 #undef SB_B
+  });
 }

@@ -12,6 +12,7 @@
 #include <utility>
 
 #include "host_internal.h"
+#include "../guard.h"
 
 namespace {
 
@@ -94,65 +95,66 @@ extern "C" void sb_build_params_default(sb_build_params* p) {
 }
 
 extern "C" sb_status sb_qubo_build(const sb_event* ev, const sb_build_params* p, sb_qubo** out) {
-  if (!ev || !p || !out) {
-    sbh::set_error("sb_qubo_build: null argument");
-    return SB_ERR_ARG;
-  }
-  if ((p->coupling_mode != 0 && p->coupling_mode != 1) || (p->bias_mode != 0 && p->bias_mode != 1) ||
-      (p->bias_mode == 1 && !(p->gamma > 0.0 && p->lambda > 0.0))) {
-    sbh::set_error("sb_qubo_build: coupling_mode / bias_mode must be 0 or 1, gamma and lambda > 0");
-    return SB_ERR_ARG;
-  }
-  *out = nullptr;
-  const int32_t nh = (int32_t)ev->layer.size();
-  int nl = 0;
-  for (int32_t h = 0; h < nh; ++h) nl = std::max(nl, ev->layer[h] + 1);
+  return sbh::guarded("sb_qubo_build", [&]() -> sb_status {
+    if (!ev || !p || !out) {
+      sbh::set_error("sb_qubo_build: null argument");
+      return SB_ERR_ARG;
+    }
+    if ((p->coupling_mode != 0 && p->coupling_mode != 1) || (p->bias_mode != 0 && p->bias_mode != 1) ||
+        (p->bias_mode == 1 && !(p->gamma > 0.0 && p->lambda > 0.0))) {
+      sbh::set_error("sb_qubo_build: coupling_mode / bias_mode must be 0 or 1, gamma and lambda > 0");
+      return SB_ERR_ARG;
+    }
+    *out = nullptr;
+    const int32_t nh = (int32_t)ev->layer.size();
+    int nl = 0;
+    for (int32_t h = 0; h < nh; ++h) nl = std::max(nl, ev->layer[h] + 1);
 
-  // hit ids per layer (hits are sorted by layer, so each layer is a contiguous range)
-  std::vector<int32_t> lstart(nl + 1, 0);
-  for (int32_t h = 0; h < nh; ++h) lstart[ev->layer[h] + 1]++;
-  for (int l = 0; l < nl; ++l) lstart[l + 1] += lstart[l];
+    // hit ids per layer (hits are sorted by layer, so each layer is a contiguous range)
+    std::vector<int32_t> lstart(nl + 1, 0);
+    for (int32_t h = 0; h < nh; ++h) lstart[ev->layer[h] + 1]++;
+    for (int l = 0; l < nl; ++l) lstart[l + 1] += lstart[l];
 
-  // 1. doublets, lexicographic in (in, out)
-  std::vector<Doublet> dbl;
-  for (int l = 0; l + 1 < nl; ++l) {
-    for (int32_t h = lstart[l]; h < lstart[l + 1]; ++h) {
-      const double ph = ev->phi[h], rh = ev->r[h], zh = ev->z[h];
-      for (int32_t o = lstart[l + 1]; o < lstart[l + 2]; ++o) {
-        double dphi = ev->phi[o] - ph;
-        dphi = dphi - kTwoPi * floor((dphi + M_PI) / kTwoPi);
-        double dr = ev->r[o] - rh;
-        double win = p->dphi_slope * dr + p->dphi_margin / rh;
-        double z0 = zh - rh * (ev->z[o] - zh) / dr;
-        if (fabs(dphi) <= win && fabs(z0) <= p->z0_max)
-          dbl.push_back(Doublet{h, o, atan2(ev->r[o] - rh, ev->z[o] - zh)});
+    // 1. doublets, lexicographic in (in, out)
+    std::vector<Doublet> dbl;
+    for (int l = 0; l + 1 < nl; ++l) {
+      for (int32_t h = lstart[l]; h < lstart[l + 1]; ++h) {
+        const double ph = ev->phi[h], rh = ev->r[h], zh = ev->z[h];
+        for (int32_t o = lstart[l + 1]; o < lstart[l + 2]; ++o) {
+          double dphi = ev->phi[o] - ph;
+          dphi = dphi - kTwoPi * floor((dphi + M_PI) / kTwoPi);
+          double dr = ev->r[o] - rh;
+          double win = p->dphi_slope * dr + p->dphi_margin / rh;
+          double z0 = zh - rh * (ev->z[o] - zh) / dr;
+          if (fabs(dphi) <= win && fabs(z0) <= p->z0_max)
+            dbl.push_back(Doublet{h, o, atan2(ev->r[o] - rh, ev->z[o] - zh)});
+        }
       }
     }
-  }
 
-  // 2. triplets (Eq. 16)
-  std::vector<std::vector<int32_t>> incoming(nh), outgoing(nh);  // doublet indices
-  for (int32_t d = 0; d < (int32_t)dbl.size(); ++d) {
-    outgoing[dbl[d].in].push_back(d);
-    incoming[dbl[d].out].push_back(d);
-  }
-  std::vector<Triplet> trip;
-  for (int32_t b = 0; b < nh; ++b) {
-    for (int32_t di : incoming[b]) {
-      const int32_t a = dbl[di].in;
-      for (int32_t dj : outgoing[b]) {
-        const int32_t c = dbl[dj].out;
-        double kap = curvature(ev->x[a], ev->y[a], ev->x[b], ev->y[b], ev->x[c], ev->y[c]);
-        double dth = fabs(dbl[dj].theta - dbl[di].theta);
-        if (fabs(kap) <= p->kappa_max && dth <= p->dtheta_max)
-          trip.push_back(Triplet{a, b, c, kap, dth});
+    // 2. triplets (Eq. 16)
+    std::vector<std::vector<int32_t>> incoming(nh), outgoing(nh);  // doublet indices
+    for (int32_t d = 0; d < (int32_t)dbl.size(); ++d) {
+      outgoing[dbl[d].in].push_back(d);
+      incoming[dbl[d].out].push_back(d);
+    }
+    std::vector<Triplet> trip;
+    for (int32_t b = 0; b < nh; ++b) {
+      for (int32_t di : incoming[b]) {
+        const int32_t a = dbl[di].in;
+        for (int32_t dj : outgoing[b]) {
+          const int32_t c = dbl[dj].out;
+          double kap = curvature(ev->x[a], ev->y[a], ev->x[b], ev->y[b], ev->x[c], ev->y[c]);
+          double dth = fabs(dbl[dj].theta - dbl[di].theta);
+          if (fabs(kap) <= p->kappa_max && dth <= p->dtheta_max)
+            trip.push_back(Triplet{a, b, c, kap, dth});
+        }
       }
     }
-  }
-  std::sort(trip.begin(), trip.end(), [](const Triplet& s, const Triplet& t) {
-    if (s.a != t.a) return s.a < t.a;
-    if (s.b != t.b) return s.b < t.b;
-    return s.c < t.c;
+    std::sort(trip.begin(), trip.end(), [](const Triplet& s, const Triplet& t) {
+      if (s.a != t.a) return s.a < t.a;
+      if (s.b != t.b) return s.b < t.b;
+      return s.c < t.c;
   });
   const int32_t nt = (int32_t)trip.size();
 
@@ -257,6 +259,7 @@ extern "C" sb_status sb_qubo_build(const sb_event* ev, const sb_build_params* p,
   }
   *out = q;
   return SB_OK;
+  });
 }
 
 extern "C" sb_status sb_qubo_sizes(const sb_qubo* q, int32_t* n, int64_t* nnz) {
