@@ -839,7 +839,7 @@ def run_study(args):
         q = sb.sb_qubo_build(ev, sb.build_params(**w["cuts"]))
         ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_FP32)
         sb.sb_set_weights(ctx, q.cls, q.quality, 1.0, 1.0)
-        S, R, c0 = w["steps"], w["replicas"], sb.sb_info(ctx)["c0_auto"]
+        S, R, c0 = (args.sb_steps or w["steps"]), w["replicas"], sb.sb_info(ctx)["c0_auto"]
         sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)   # both directions launch one kernel per step
         sb.sb_run(ctx, "bsb", 1.0, c0, 0.5, S, R, 1, None, stream)
         sb.sb_backward(ctx, 1.0, c0, 0.5, S, R, 1, None, 32)
