@@ -94,7 +94,7 @@ def job_value(units_per_rank, world_size, ms):
 # replica tile) and that kernel's sources (sha256 prefix, kernel_source_hash);
 # any other combination reports null.
 MEASURED_TRAFFIC = {
-    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "fd6de93553f1e0d1"): 89570048 + 33239040,
+    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "eedc785f5fd10c30"): 89663488 + 32859136,
 }
 
 

@@ -984,7 +984,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
       ra.n = c->n;
       ra.R = c->R;
       ra.ngroups = c->rw_ngroups;
-      ra.gpc = std::max(8, c->step_rpc > 0 ? c->step_rpc / rw : 0);
+      ra.gpc = std::max(sbd::kRwBlock / 32, c->step_rpc > 0 ? c->step_rpc / rw : 0);
     }
   }
   if (streamed) {

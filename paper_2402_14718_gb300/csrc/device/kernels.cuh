@@ -239,6 +239,10 @@ struct RwArgs {
   uint8_t* sgn_out;          // dSB: sgn(x_{k+1}) + 128, written with x_{k+1}
 };
 constexpr int kRwMaxRows = 4;  // RW is 2 or 4 (the mask has 4 bits)
+#ifndef SB_RW_BLOCK
+#define SB_RW_BLOCK 128
+#endif
+constexpr int kRwBlock = SB_RW_BLOCK;  // threads per CTA of k_step_rw (one row group per warp)
 // nch = 2: a warp covers 256 replicas of a row (two float4 per lane), grid.y = R / 256;
 // nch = 1: 128 replicas, grid.y = R / 128. R must be a multiple of 128 * nch.
 cudaError_t launch_step_rw(int variant, int jbf16, int rw, int nch, const RwArgs& a,

@@ -21,7 +21,6 @@
 namespace sbd {
 namespace {
 
-constexpr int kRwBlock = 256;
 // union entries in flight per warp (x rows loaded before their FMAs) and the
 // launch-bounds residency hint; defaults measured best on the 1000-track event
 #ifndef SB_RW_UB_NCH2
