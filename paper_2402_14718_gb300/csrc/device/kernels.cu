@@ -374,8 +374,16 @@ __global__ void __launch_bounds__(kBlock) k_step_r1(const StepArgs a) {
 // neighbour's signs for 16 replicas. G = R / 16 lanes own a row (R / 16 a power
 // of two, <= 32). Same CSR-order FMA sequence per replica as k_step.
 
+#ifndef SB_DSB_BLOCK
+#define SB_DSB_BLOCK 128
+#endif
+#ifndef SB_DSB_MINB
+#define SB_DSB_MINB 1
+#endif
+constexpr int kDsbBlock = SB_DSB_BLOCK;  // threads per CTA of k_step_dsb16
+
 template <typename JT>
-__global__ void __launch_bounds__(kBlock) k_step_dsb16(const StepArgs a) {
+__global__ void __launch_bounds__(kDsbBlock, SB_DSB_MINB) k_step_dsb16(const StepArgs a) {
   const int G = a.G;
   const int gid = threadIdx.x / G;
   const int g = threadIdx.x - gid * G;
@@ -1213,11 +1221,15 @@ cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs&
     return cudaGetLastError();
   }
   if (variant == 2 && a.sgn_in && a.G * 16 == a.R && t.tiles == 1 && t.V == 16) {
-    dim3 grid((a.n + a.rpc - 1) / a.rpc, 1);
+    // a CTA walks rpc rows (one row per G-lane group at 256 threads)
+    const int rpc = a.rpc * kDsbBlock / kBlock > 0 ? a.rpc * kDsbBlock / kBlock : 1;
+    StepArgs b = a;
+    b.rpc = rpc;
+    dim3 grid((a.n + rpc - 1) / rpc, 1);
     if (jbf16)
-      k_step_dsb16<__nv_bfloat16><<<grid, kBlock, 0, s>>>(a);
+      k_step_dsb16<__nv_bfloat16><<<grid, kDsbBlock, 0, s>>>(b);
     else
-      k_step_dsb16<float><<<grid, kBlock, 0, s>>>(a);
+      k_step_dsb16<float><<<grid, kDsbBlock, 0, s>>>(b);
     return cudaGetLastError();
   }
   if (t.V == 4) {
