@@ -129,11 +129,15 @@ __device__ __forceinline__ unsigned group_mask(int G) {
 // neighbours in flight at once.
 // MODE: 0 aSB, 1 bSB, 2 dSB gathering x (sgn at use), 3 dSB gathering int8
 // signs, 4 bSB also recording the pre-wall momentum and the wall mask.
-#ifndef SB_STEP_MIN_BLOCKS
-#define SB_STEP_MIN_BLOCKS 1
-#endif
+// CTAs per SM the compiler is asked to fit: with two or four chunks per thread
+// the free choice takes 101 / 168 registers (two / one CTA per SM); bounding it
+// gives 80 / 128 registers and three / two CTAs without spills
+template <int NCH>
+struct StepMinBlocks {
+  static constexpr int value = NCH == 2 ? 3 : (NCH == 4 ? 2 : 1);
+};
 template <int V, int NCH, int MODE, typename JT>
-__global__ void __launch_bounds__(kBlock, SB_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
+__global__ void __launch_bounds__(kBlock, StepMinBlocks<NCH>::value) k_step(const StepArgs a) {
   constexpr int VARIANT = MODE == 3 ? 2 : (MODE == 4 ? 1 : MODE);
   constexpr bool use_sgn = MODE == 3;
   constexpr bool record = MODE == 4;
