@@ -52,6 +52,9 @@ def parse():
                     help="step kernel: auto (sb_autotune picks), or a fixed one: untiled (one "
                          "row per warp), rowgroup2/4 (rows per warp), stream (bulk-copy ring), "
                          "tiled (shared-memory row blocks)")
+    ap.add_argument("--dsb-signs", type=int, default=-1, choices=[-1, 0, 1],
+                    help="dSB gather form (SB_OPT_DSB_SIGNS): 0 FP32 positions, 1 sign bytes; "
+                         "-1 keeps the library default")
     ap.add_argument("--rows-per-cta", type=int, default=0,
                     help="with a fixed --kernel: rows per CTA (SB_OPT_STEP_RPC)")
     ap.add_argument("--profile-steps", type=int, default=0,
@@ -98,13 +101,16 @@ MEASURED_TRAFFIC = {
 }
 
 
-def set_kernel(sb, ctx, name, variant="bsb", R=256):
+def set_kernel(sb, ctx, name, variant="bsb", R=256, dsb_signs=-1):
     """Fix the step kernel by its options; returns the kernel's name ("auto":
     the library's default choice, without the autotuner)."""
+    if dsb_signs >= 0:
+        sb.sb_set_option(ctx, sb.SB_OPT_DSB_SIGNS, dsb_signs)
     if name == "auto":
         if variant != "dsb" and R % 128 == 0:
             return "k_step_rw"
-        return tuned_kernel({"rows_per_warp": 0, "tiled": 0, "tile": 0, "groups": 1}, variant, R)
+        return tuned_kernel({"rows_per_warp": 0, "tiled": 0, "tile": 0, "groups": 1}, variant, R,
+                            dsb_signs)
     sb.sb_set_option(ctx, sb.SB_OPT_ROWS_PER_WARP, 0)
     if name == "rowgroup2" or name == "rowgroup4":
         sb.sb_set_option(ctx, sb.SB_OPT_ROWS_PER_WARP, int(name[-1]))
@@ -115,17 +121,23 @@ def set_kernel(sb, ctx, name, variant="bsb", R=256):
     if name == "tiled":
         sb.sb_set_option(ctx, sb.SB_OPT_TILED, 1)
         return "k_step_tiled"
-    return "k_step"
+    return tuned_kernel({"rows_per_warp": 0, "tiled": 0, "tile": 0, "groups": 1}, variant, R,
+                        dsb_signs)
 
 
-def tuned_kernel(cfg, variant, R):
+# the library's default dSB gather form (SB_OPT_DSB_SIGNS)
+DSB_SIGNS_DEFAULT = 1
+
+
+def tuned_kernel(cfg, variant, R, dsb_signs=-1):
     """Name of the step kernel the context runs with autotuned configuration cfg
     (the selection order of the library: row-group, tiled, dSB signs, one replica)."""
+    signs = DSB_SIGNS_DEFAULT if dsb_signs < 0 else dsb_signs
     if cfg["rows_per_warp"] and R % 128 == 0:
         return "k_step_rw"
     if cfg["tiled"] and R % 32 == 0:
         return "k_step_tiled"
-    if (variant == "dsb" and cfg["tile"] == 0 and cfg["groups"] == 1 and R % 16 == 0
+    if (variant == "dsb" and signs and cfg["tile"] == 0 and cfg["groups"] == 1 and R % 16 == 0
             and R // 16 <= 32 and (R // 16) & (R // 16 - 1) == 0):
         return "k_step_dsb16"
     if R == 1:
@@ -370,10 +382,12 @@ def run_ours(args):
     ctx = sb.sb_create(N, q.rowptr, q.col, q.val, q.lin, prec)
     tuned = None
     if args.kernel == "auto" and not args.profile_steps:
+        if args.dsb_signs >= 0:
+            sb.sb_set_option(ctx, sb.SB_OPT_DSB_SIGNS, args.dsb_signs)
         tuned = sb.sb_autotune(ctx, args.variant, R, trial_steps=30)   # untimed set-up
-        kname = tuned_kernel(tuned[0], args.variant, R)
+        kname = tuned_kernel(tuned[0], args.variant, R, args.dsb_signs)
     else:
-        kname = set_kernel(sb, ctx, args.kernel, args.variant, R)
+        kname = set_kernel(sb, ctx, args.kernel, args.variant, R, args.dsb_signs)
         if args.rows_per_cta:
             sb.sb_set_option(ctx, sb.SB_OPT_STEP_RPC, args.rows_per_cta)
     sched = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
@@ -660,6 +674,8 @@ def run_batch(args):
     NS = sum(q.n for q in qs)
     NZ = sum(q.nnz for q in qs)
     ctx = sb.sb_create_batch([(q.rowptr, q.col, q.val, q.lin) for q in qs], sb.SB_J_BF16)
+    if args.dsb_signs >= 0:
+        sb.sb_set_option(ctx, sb.SB_OPT_DSB_SIGNS, args.dsb_signs)
     cfg, us = sb.sb_autotune(ctx, variant, R, trial_steps=20)
     sched = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
     E = len(qs)
@@ -723,7 +739,8 @@ def run_batch(args):
                        "autotune": cfg, "autotune_us_per_step": us, "host_build_s": t_build},
             "roofline": {"bound": "hbm", "achieved": alg_bytes / sweep / 1e9, "peak": hbm,
                          "unit": "GB/s", "frac": alg_bytes / sweep / 1e9 / hbm, "traffic": None,
-                         "kernel": tuned_kernel(cfg, variant, R), "peak_source": src,
+                         "kernel": tuned_kernel(cfg, variant, R, args.dsb_signs),
+                         "peak_source": src,
                          "alg_bytes_per_launch": alg_bytes,
                          "kstep_us": sweep * 1e6},
             "plain_fp32_spin_updates_per_s": plain,
@@ -778,9 +795,10 @@ def run_study(args):
                    ("rowgroup4", 0), ("stream", 0), ("tiled", 0)]
         for variant in ("bsb", "dsb"):
             ref = None
-            for name, rpc in kernels:
+            for name, rpc, signs in [(k, r, -1) for k, r in kernels] + (
+                    [("untiled", 0, 0)] if variant == "dsb" else []):
                 ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, prec)
-                kname = set_kernel(sb, ctx, name, variant, R)
+                kname = set_kernel(sb, ctx, name, variant, R, signs)
                 sb.sb_set_option(ctx, sb.SB_OPT_STEP_RPC, rpc)
                 sb.sb_run(ctx, variant, 1.0, 0.0, 0.5, 0, R, 7, None, stream)
                 sb.sb_advance(ctx, variant, 1.0, 0.0, 0.5, S, sched, stream)
@@ -800,7 +818,8 @@ def run_study(args):
                     best = min(best, e0.elapsed_time(e1) * 1e3 / S)
                 print(json.dumps({"study": "kernels", "workload": args.workload, "N": q.n,
                                   "nnz": q.nnz, "R": R, "variant": variant, "kernel": kname,
-                                  "option": name, "rows_per_cta": rpc, "us_per_step": best,
+                                  "option": name, "rows_per_cta": rpc, "dsb_signs": signs,
+                                  "us_per_step": best,
                                   "same_state_as_first": same}), flush=True)
                 sb.sb_destroy(ctx)
         return 0

@@ -149,11 +149,13 @@ struct sb_ctx {
   int step_rpc = 0;   // rows per CTA of the untiled kernel (0: one row per group, -1: one wave)
   int step_unroll = 4;
   int dsb_signs = 1;  // dSB gathers int8 signs instead of FP32 positions
+  // every |J_ij| < 2^125, so the sign-byte gathers may double J exactly
+  bool j_small = true;
   int groups = 1;     // replica groups run one after another (each for all steps)
   int l2_persist = 0; // mark each step's source x as L2-persisting (access-policy window)
   bool l2_raised = false;  // this context raised the persisting-L2 set-aside
   size_t l2_saved = 0;     // the set-aside before it did
-  uint8_t* d_sgn[2] = {nullptr, nullptr};  // dSB signs, biased by 128
+  uint8_t* d_sgn[2] = {nullptr, nullptr};  // dSB sign bytes (top byte of sgn / 2)
   int sms = 0;
   // streamed step kernel (k_step_stream): per-CTA row chunks cut into blocks
   // with their neighbour-column unions; built on first use
@@ -841,6 +843,18 @@ sb_status check_wait_flag(const sb_ctx* c) {
   return SB_OK;
 }
 
+// |J_ij| <= sqrt(sum of J^2 over the event) = sigma_J sqrt(n (n - 1)) (the
+// definition of sigma_J over the n (n - 1) off-diagonal places), so this bound
+// keeps 2 J finite and exact in FP32 / BF16 for the sign-byte gathers
+void note_j_range(sb_ctx* c) {
+  double m = 0.0;
+  for (int32_t e = 0; e < c->E; ++e) {
+    const double n = (double)(c->ev_row0[e + 1] - c->ev_row0[e]);
+    if (n >= 2.0) m = std::max(m, c->sigma[e] * std::sqrt(n * (n - 1.0)));
+  }
+  c->j_small = m < 0x1p125;
+}
+
 sb_status create_common(sb_ctx* c, const int32_t* rowptr, const int32_t* col, const double* qval,
                         const double* qlin) {
   SB_CUDA(cudaGetDevice(&c->device));
@@ -905,6 +919,7 @@ sb_status create_common(sb_ctx* c, const int32_t* rowptr, const int32_t* col, co
   SB_CUDA(cudaMemcpy(c->offset.data(), c->d_offset, c->E * 8, cudaMemcpyDeviceToHost));
   SB_CUDA(cudaMemcpy(c->sigma.data(), c->d_sigma, c->E * 8, cudaMemcpyDeviceToHost));
   SB_CUDA(cudaMemcpy(c->c0_auto.data(), c->d_c0auto, c->E * 8, cudaMemcpyDeviceToHost));
+  note_j_range(c);
   SB_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   return SB_OK;
 }
@@ -1010,7 +1025,10 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     sa.jbuf_bytes = c->stream_jbuf;
     sa.err = c->d_err;
   }
-  const bool dsb16 = !streamed && !rw && variant == SB_DSB && c->dsb_signs && c->step_rt == 0 &&
+  // the 16-replica dSB kernel exists only with sign bytes: its tiling and the
+  // byte condition below must agree
+  const bool dsb16 = !streamed && !rw && variant == SB_DSB && c->dsb_signs && c->j_small &&
+                     c->step_rt == 0 &&
                      c->groups == 1 && sbd::dsb16_ok(c->R) &&
                      !(c->tiled_ok && c->use_tiled && c->R % sbd::kTileRT == 0);
   const sbd::Tiling t = dsb16 ? sbd::make_tiling_dsb16(c->R) : step_tiling(c);
@@ -1064,13 +1082,16 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   ta.n = c->n;
   ta.R = c->R;
   ta.nb = c->nb;
-  const int sgn =
-      (variant == SB_DSB && c->dsb_signs && !tiled && !streamed && c->R % 4 == 0) ? 1 : 0;
-  if (sgn && !c->d_sgn[0]) {
+  const int sgn = (variant == SB_DSB && c->dsb_signs && c->j_small && !tiled && !streamed &&
+                   c->R % 4 == 0) ? 1 : 0;
+  if (sgn && !(c->d_sgn[0] && c->d_sgn[1])) {
+    dfree(c->d_sgn[0]);  // a failed earlier attempt may have left one of the pair
+    dfree(c->d_sgn[1]);
     sb_status st2;
     const size_t cnt = (size_t)c->n * c->R;
     if ((st2 = dalloc(&c->d_sgn[0], cnt)) || (st2 = dalloc(&c->d_sgn[1], cnt))) return st2;
   }
+
   size_t win_max = 0;
   if (c->l2_persist) {
     int v = 0;
@@ -1575,6 +1596,7 @@ sb_status sb_set_weights(sb_ctx* ctx, const int8_t* cls, const double* quality, 
     SB_CUDA(cudaMemcpy(ctx->offset.data(), ctx->d_offset, 8, cudaMemcpyDeviceToHost));
     SB_CUDA(cudaMemcpy(ctx->sigma.data(), ctx->d_sigma, 8, cudaMemcpyDeviceToHost));
     SB_CUDA(cudaMemcpy(ctx->c0_auto.data(), ctx->d_c0auto, 8, cudaMemcpyDeviceToHost));
+    note_j_range(ctx);
     // the tiled kernel's packed words carry J: rebuild them
     dfree(ctx->d_blk_row0);
     dfree(ctx->d_blk_u0);

@@ -97,16 +97,16 @@ struct Vec<1> {
   __device__ __forceinline__ void st(float* p) const { *p = v[0]; }
 };
 
-// V signs (biased bytes) of one chunk as floats
+// V sign bytes of one chunk as the floats sgn / 2
 template <int V>
 __device__ __forceinline__ void ld_signs(const uint8_t* p, float (&out)[V]) {
   if (V == 4) {
     const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(p));
 #pragma unroll
-    for (int v = 0; v < V; ++v) out[v] = sign_of_byte(w, v);
+    for (int v = 0; v < V; ++v) out[v] = half_sign_of_byte(w, v);
   } else {
 #pragma unroll
-    for (int v = 0; v < V; ++v) out[v] = sign_of_byte(__ldg(p + v), 0);
+    for (int v = 0; v < V; ++v) out[v] = half_sign_of_byte(__ldg(p + v), 0);
   }
 }
 
@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(kBlock, StepMinBlocks<NCH>::value) k_step(cons
     if (g < cnt) {
       mc = __ldg(a.col + pb + g);
       mv = jval(J, pb + g);
+      if (use_sgn) mv += mv;  // 2 J: sign bytes read as sgn / 2
     }
     int q = 0;
     for (; q + U <= cnt; q += U) {
@@ -408,6 +409,7 @@ __global__ void __launch_bounds__(kDsbBlock, SB_DSB_MINB) k_step_dsb16(const Ste
       if (g < cnt) {
         mc = __ldg(a.col + pb + g);
         mv = jval(J, pb + g);
+        mv += mv;  // 2 J: sign bytes read as sgn / 2
       }
       int q = 0;
       for (; q + 4 <= cnt; q += 4) {
@@ -426,7 +428,8 @@ __global__ void __launch_bounds__(kDsbBlock, SB_DSB_MINB) k_step_dsb16(const Ste
         for (int u = 0; u < 4; ++u) {
           const unsigned ww[4] = {sv[u].x, sv[u].y, sv[u].z, sv[u].w};
 #pragma unroll
-          for (int v = 0; v < 16; ++v) acc[v] = fmaf(w[u], sign_of_byte(ww[v >> 2], v & 3), acc[v]);
+          for (int v = 0; v < 16; ++v)
+            acc[v] = fmaf(w[u], half_sign_of_byte(ww[v >> 2], v & 3), acc[v]);
         }
       }
       for (; q < cnt; ++q) {
@@ -435,7 +438,7 @@ __global__ void __launch_bounds__(kDsbBlock, SB_DSB_MINB) k_step_dsb16(const Ste
         const uint4 s4 = __ldg(reinterpret_cast<const uint4*>(a.sgn_in + (size_t)c * R + 16 * g));
         const unsigned ww[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-        for (int v = 0; v < 16; ++v) acc[v] = fmaf(w, sign_of_byte(ww[v >> 2], v & 3), acc[v]);
+        for (int v = 0; v < 16; ++v) acc[v] = fmaf(w, half_sign_of_byte(ww[v >> 2], v & 3), acc[v]);
       }
     }
     const float pa = a.a0 - __ldg(a.sched + a.k);
@@ -1236,6 +1239,7 @@ cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs&
       k_step_dsb16<float><<<grid, kDsbBlock, 0, s>>>(b);
     return cudaGetLastError();
   }
+  if (t.V == 16) return cudaErrorInvalidValue;  // that tiling needs the dSB sign bytes
   if (t.V == 4) {
     if (t.NCH == 1) return launch_step_v<4, 1>(variant, jbf16, t, a, s);
     if (t.NCH == 2) return launch_step_v<4, 2>(variant, jbf16, t, a, s);

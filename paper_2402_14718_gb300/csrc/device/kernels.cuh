@@ -42,8 +42,8 @@ struct StepArgs {
   float* ytil;            // optional: momentum after the update, before the wall [n x R]
   uint8_t* mask;          // optional: 1 where the wall fired [n x R]
   float* frec;            // optional (with ytil): the coupling sum J g(x) [n x R]
-  const uint8_t* sgn_in;  // dSB: sgn(x_k) + 128 [n x R] gathered instead of x (NULL: use x)
-  uint8_t* sgn_out;       // dSB: sgn(x_{k+1}) + 128 written with x_{k+1} (may be NULL)
+  const uint8_t* sgn_in;  // dSB: sign bytes of x_k [n x R] gathered instead of x (NULL: use x)
+  uint8_t* sgn_out;       // dSB: sign bytes of x_{k+1}, written with x_{k+1} (may be NULL)
   int32_t unroll;         // neighbours in flight per thread (4)
   int32_t tile0;          // first replica tile of this launch (sequential replica groups)
 };
@@ -85,7 +85,7 @@ cudaError_t launch_pack_tz(const void* J, int jbf16, const uint16_t* lidx, int64
 
 cudaError_t launch_init(float* x, float* y, const int32_t* row_event, const int32_t* ev_row0,
                         int32_t n, int32_t R, uint64_t seed, cudaStream_t s);
-// s[i] = sgn(x[i]) + 128 (bytes 127, 128, 129)
+// s[i] = sign byte of x[i]: 0x3F, 0xBF, 0x00 for x > 0, x < 0, x = 0 (signs.cuh)
 cudaError_t launch_signs(const float* x, uint8_t* s, size_t count, cudaStream_t st);
 // blocks of the untiled step kernel resident per SM for this tiling and unroll
 int step_blocks_per_sm(int variant, int jbf16, const Tiling& t, int unroll);
@@ -235,8 +235,8 @@ struct RwArgs {
   int32_t n, R;
   int32_t ngroups;
   int32_t gpc;               // row groups per CTA (a CTA walks a contiguous chunk)
-  const uint8_t* sgn_in;     // dSB: sgn(x_k) + 128 [n x R] gathered instead of x (NULL: use x)
-  uint8_t* sgn_out;          // dSB: sgn(x_{k+1}) + 128, written with x_{k+1}
+  const uint8_t* sgn_in;     // dSB: sign bytes of x_k [n x R] gathered instead of x (NULL: use x)
+  uint8_t* sgn_out;          // dSB: sign bytes of x_{k+1}, written with x_{k+1}
 };
 constexpr int kRwMaxRows = 4;  // RW is 2 or 4 (the mask has 4 bits)
 #ifndef SB_RW_BLOCK

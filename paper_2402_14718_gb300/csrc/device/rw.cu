@@ -108,7 +108,7 @@ struct JPack<2, float> {
 
 
 // MODE: 0 aSB, 1 bSB, 2 dSB gathering x (sgn at use), 3 dSB gathering the
-// biased sign bytes written by the previous step (4 bytes per lane chunk)
+// sign bytes written by the previous step (4 bytes per lane chunk)
 template <int RW, int NCH, int MODE, typename JT>
 __global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a) {
   constexpr int VARIANT = MODE == 3 ? 2 : MODE;
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a
             for (int j = 0; j < NCH; ++j) {
               const uint32_t t = __ldg(ps + 32 * j);
 #pragma unroll
-              for (int k = 0; k < 4; ++k) xv[u][j][k] = sign_of_byte(t, k);
+              for (int k = 0; k < 4; ++k) xv[u][j][k] = half_sign_of_byte(t, k);
             }
           } else {
             const float4* px = reinterpret_cast<const float4*>(xl + (size_t)(v >> 4) * rb);
@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a
 #pragma unroll
           for (int q = 0; q < RW; ++q)
             if (m[u] & (1u << q)) {
-              const float wq = w[u].get(q);
+              float wq = w[u].get(q);
+              if (use_sgn) wq += wq;  // 2 J: sign bytes read as sgn / 2
 #pragma unroll
               for (int j = 0; j < NCH; ++j)
 #pragma unroll

@@ -8,17 +8,19 @@ namespace sbd {
 // sgn(x) with sgn(0) = 0, as a float, in compares and selects only.
 __device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
 
-// A sign stored as one byte, biased by 128: 127, 128 or 129 for -1, 0, +1.
+// A sign stored as one byte: the top byte of the float +0.5 (0x3F), -0.5
+// (0xBF) or +0 (0x00), for x > 0, x < 0 and x = 0.
 __device__ __forceinline__ uint32_t sign_byte(float x) {
-  return 128u + (x > 0.f ? 1u : 0u) - (x < 0.f ? 1u : 0u);
+  return x > 0.f ? 0x3Fu : (x < 0.f ? 0xBFu : 0u);
 }
 
-// Byte k of w (a biased sign) as the float -1, 0 or +1, exactly: the byte is
-// placed in the low mantissa byte of 2^23 (bits 0x4B000000), which then reads
-// 2^23 + byte, and 2^23 + 128 is subtracted. One byte permute and one add,
-// both at full rate.
-__device__ __forceinline__ float sign_of_byte(uint32_t w, int k) {
-  return __int_as_float((int)__byte_perm(w, 0x4B000000u, 0x7650u | (uint32_t)k)) - 8388736.0f;
+// Byte k of w as the float sgn / 2 (+0.5, -0.5 or +0) in one byte permute: the
+// byte goes to the top of a word whose other bytes are zero. A coupling
+// product takes it with the doubled weight: fma(2 J, sgn / 2, acc) equals
+// fma(J, sgn, acc) bit for bit, since 2 J is exact (|J| < 2^127) and the
+// product 2 J * sgn / 2 = J sgn is exact, leaving the one rounding of the sum.
+__device__ __forceinline__ float half_sign_of_byte(uint32_t w, int k) {
+  return __int_as_float((int)__byte_perm(w, 0u, 0x0444u | ((uint32_t)k << 12)));
 }
 
 }  // namespace sbd

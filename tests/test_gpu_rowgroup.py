@@ -177,3 +177,49 @@ def test_dsb_exact_zero_and_wall_positions_against_oracle(rw, signs):
     xo, yo = osb.step(J, h, x64, y64, a32, 1.0, c0, 0.5, osb.DSB)
     xpre = osb.prewall_x(J, h, x64, y64, a32, 1.0, c0, 0.5, osb.DSB)
     compare_step(outs[0][0], outs[0][1], xo, yo, xpre)
+
+
+def _with_huge_pairs(q, b_pair):
+    """q plus a coupling b_pair between rows 2k and 2k + 1 (k = 0, 1, ...), with
+    a_i - b_pair / 2 as the linear terms so that the field h stays small."""
+    D = np.zeros((q.n, q.n))
+    for i in range(q.n):
+        D[i, q.col[q.rowptr[i]:q.rowptr[i + 1]]] = q.val[q.rowptr[i]:q.rowptr[i + 1]]
+    for k in range(q.n // 2):
+        D[2 * k, 2 * k + 1] = D[2 * k + 1, 2 * k] = b_pair
+    rp = np.zeros(q.n + 1, np.int32)
+    cols, vals = [], []
+    for i in range(q.n):
+        nz = np.nonzero(D[i])[0]
+        cols.append(nz)
+        vals.append(D[i, nz])
+        rp[i + 1] = rp[i] + len(nz)
+    lin = q.lin - b_pair / 2 * (np.arange(q.n) < 2 * (q.n // 2))
+    return inputs.QuboArrays(q.n, rp, np.concatenate(cols).astype(np.int32),
+                             np.concatenate(vals), lin)
+
+
+@pytest.mark.parametrize("prec", [sb.SB_J_FP32, sb.SB_J_BF16])
+def test_dsb_sign_bytes_keep_exact_with_huge_couplings(prec):
+    """Sign bytes read as sgn / 2 and take the doubled weight 2 J, which would
+    overflow for |J| >= 2^127. With J = 2e38 on every row every dSB form must
+    still equal the FP32-position gather bit for bit (the library then gathers
+    positions); with J = 1e36 (sqrt(sum J^2) < 2^125) the sign-byte forms run
+    and agree too. c0 scales the coupling sum back to O(1)."""
+    base = inputs.random_qubo(300, 6, seed=12)
+    for b_pair, c0 in ((-8e38, 1e-38), (-4e36, 1e-36)):
+        q = _with_huge_pairs(base, b_pair)
+        x0, y0 = inputs.random_state(q.n, 128, 81, 0.9)
+        for R, rw in ((128, 0), (128, 2), (48, 0)):
+            outs = []
+            for signs in (1, 0):
+                ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, prec)
+                sb.sb_set_option(ctx, sb.SB_OPT_ROWS_PER_WARP, rw)
+                sb.sb_set_option(ctx, sb.SB_OPT_DSB_SIGNS, signs)
+                sb.sb_set_state(ctx, x0[:, :R].copy(), y0[:, :R].copy())
+                sb.sb_advance(ctx, "dsb", 1.0, c0, 0.5, 12,
+                              _sched(np.float32(np.linspace(0, 1, 12))))
+                outs.append(sb.sb_get_state(ctx))
+                sb.sb_destroy(ctx)
+            assert np.all(np.isfinite(outs[0][0])) and np.all(np.isfinite(outs[0][1]))
+            assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
