@@ -97,7 +97,8 @@ def job_value(units_per_rank, world_size, ms):
 # replica tile) and that kernel's sources (sha256 prefix, kernel_source_hash);
 # any other combination reports null.
 MEASURED_TRAFFIC = {
-    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "eedc785f5fd10c30"): 89663488 + 32859136,
+    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "1a17b421e478ee10"): 89664768 + 33082624,
+    ("event1000", "dsb", "k_step_dsb16", (0, 0, 0), "59c4db3545697cf6"): 100393728 + 39327232,
 }
 
 
@@ -791,15 +792,20 @@ def run_study(args):
         prec = sb.SB_J_BF16 if w["jprec"] == "bf16" else sb.SB_J_FP32
         S = 200
         sched = torch.tensor(np.linspace(0, 1, S).astype(np.float32), device=dev)
-        kernels = [("untiled", 0), ("untiled", 32), ("rowgroup2", 0), ("rowgroup2", 32),
-                   ("rowgroup4", 0), ("stream", 0), ("tiled", 0)]
+        # (option, rows per CTA, replica tile (0: automatic), dSB gather form)
+        kernels = [("untiled", 0, 0, -1), ("untiled", 32, 0, -1), ("rowgroup2", 0, 0, -1),
+                   ("rowgroup2", 32, 0, -1), ("rowgroup2", 0, 128, -1), ("rowgroup4", 0, 0, -1),
+                   ("rowgroup4", 0, 128, -1), ("stream", 0, 0, -1), ("tiled", 0, 0, -1)]
         for variant in ("bsb", "dsb"):
             ref = None
-            for name, rpc, signs in [(k, r, -1) for k, r in kernels] + (
-                    [("untiled", 0, 0)] if variant == "dsb" else []):
+            for name, rpc, rt, signs in kernels + (
+                    [("untiled", 0, 0, 0)] if variant == "dsb" else []):
+                if rt and R % rt:
+                    continue
                 ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, prec)
                 kname = set_kernel(sb, ctx, name, variant, R, signs)
                 sb.sb_set_option(ctx, sb.SB_OPT_STEP_RPC, rpc)
+                sb.sb_set_option(ctx, sb.SB_OPT_STEP_RT, rt)
                 sb.sb_run(ctx, variant, 1.0, 0.0, 0.5, 0, R, 7, None, stream)
                 sb.sb_advance(ctx, variant, 1.0, 0.0, 0.5, S, sched, stream)
                 x, y = sb.sb_get_state(ctx)
@@ -818,7 +824,8 @@ def run_study(args):
                     best = min(best, e0.elapsed_time(e1) * 1e3 / S)
                 print(json.dumps({"study": "kernels", "workload": args.workload, "N": q.n,
                                   "nnz": q.nnz, "R": R, "variant": variant, "kernel": kname,
-                                  "option": name, "rows_per_cta": rpc, "dsb_signs": signs,
+                                  "option": name, "rows_per_cta": rpc, "replica_tile": rt,
+                                  "dsb_signs": signs,
                                   "us_per_step": best,
                                   "same_state_as_first": same}), flush=True)
                 sb.sb_destroy(ctx)

@@ -356,8 +356,9 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
  *   thread group, -1 = one wave of CTAs over the SMs); a CTA walks a contiguous
  *   row chunk so rows in flight share neighbour rows in L1.
  *   SB_OPT_STEP_UNROLL (4): neighbour rows gathered at once per thread (4).
- *   SB_OPT_DSB_SIGNS (5): 1 (default) lets dSB gather int8 copies of sgn(x)
- *   (written by the step that writes x) instead of FP32 positions.
+ *   SB_OPT_DSB_SIGNS (5): 1 (default) lets dSB gather one byte per sign of x
+ *   (written by the step that writes x) instead of FP32 positions; taken only
+ *   while every |J_ij| < 2^125 (bounded through sigma_J), else positions.
  *   SB_OPT_REPLICA_GROUPS (6): run the replicas as this many groups one after
  *   another, each for all steps (R / groups replicas per group, a multiple of 4
  *   with R / (4 groups) a power of two <= 32), so a group's state stays in L2.

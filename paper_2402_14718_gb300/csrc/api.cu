@@ -1832,7 +1832,8 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
         {0, 64, 0, 4, 1, 0, 0}, {0, 32, 0, 4, 1, 0, 0},  {0, 0, 0, 4, 2, 0, 0},
         {0, 0, 32, 4, 2, 0, 0}, {0, 0, 0, 4, 4, 0, 0},   {1, 0, 0, 4, 1, 0, 0},
         {0, 0, 0, 4, 1, 0, 2},  {0, 0, 32, 4, 1, 0, 2},  {0, 0, 64, 4, 1, 0, 2},
-        {0, 128, 0, 4, 1, 0, 2}, {0, 0, 0, 4, 1, 0, 4},  {0, 0, 64, 4, 1, 0, 4}};
+        {0, 128, 0, 4, 1, 0, 2}, {0, 0, 0, 4, 1, 0, 4},  {0, 0, 64, 4, 1, 0, 4},
+        {0, 128, 0, 4, 1, 0, 4}};
     const int keep_graph = ctx->use_graph;
     ctx->use_graph = 0;
     if ((st = ensure_state(ctx, replicas))) return st;
