@@ -98,7 +98,7 @@ def job_value(units_per_rank, world_size, ms):
 # any other combination reports null.
 MEASURED_TRAFFIC = {
     ("event1000", "bsb", "k_step_rw", (2, 0, 0), "1a17b421e478ee10"): 89664768 + 33082624,
-    ("event1000", "dsb", "k_step_dsb16", (0, 0, 0), "59c4db3545697cf6"): 100393728 + 39327232,
+    ("event1000", "dsb", "k_step_dsb16", (0, 0, 0), "59aa88cffd9b6550"): 100401664 + 39776000,
 }
 
 
