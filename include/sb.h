@@ -297,10 +297,11 @@ sb_status sb_set_weights(sb_ctx* ctx, const int8_t* cls, const double* quality, 
  * dL/d w_q, dL/d w_c (the last two are NaN unless sb_set_weights was called);
  * d_grad_sched: device FP64 [steps] = dL/d a_k (may be NULL).
  * a_sched: device FP32 [steps] or NULL for the linear ramp. Single-event
- * contexts only. Work memory: 2 (ceil(steps / ckpt_every) - 1) + 3 K + 4
- * state-sized FP32 arrays plus K byte masks, K = min(ckpt_every, steps).
- * Synchronous; discards
- * the current state.
+ * contexts only. Work memory: 2 (ceil(steps / ckpt_every) - 1) + 3 K + 5
+ * state-sized FP32 arrays plus K byte masks, K = min(ckpt_every, steps); it
+ * stays with the context for the next call of the same (steps, replicas, K)
+ * and is freed by a call of another shape or by sb_destroy.
+ * Synchronous; discards the current state.
  */
 sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t steps,
                       int32_t replicas, uint64_t seed, const float* a_sched, int32_t ckpt_every,

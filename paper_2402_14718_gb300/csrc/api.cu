@@ -180,6 +180,14 @@ struct sb_ctx {
   int32_t* d_rw_ent = nullptr;
   int32_t* d_rw_pos = nullptr;  // CSR position of each entry's RW slots (-1: absent)
   void* d_rw_ejv = nullptr;     // J of each entry's RW slots
+  // sb_backward's work memory, kept for the next call of the same shape
+  struct AdjWork {
+    int32_t n = 0, R = 0, S = 0, K = 0;
+    float *ck_x = nullptr, *ck_y = nullptr, *seg_x = nullptr, *seg_yt = nullptr, *seg_f = nullptr;
+    float *lx = nullptr, *ly = nullptr, *lyt[2] = {nullptr, nullptr};
+    uint8_t* seg_m = nullptr;
+    double *gh = nullptr, *acc = nullptr, *ga = nullptr;
+  } adj;
 };
 
 namespace {
@@ -325,7 +333,26 @@ void free_state(sb_ctx* c) {
   c->graph.reset();
 }
 
+void free_adj(sb_ctx* c) {
+  sb_ctx::AdjWork& w = c->adj;
+  dfree(w.ck_x);
+  dfree(w.ck_y);
+  dfree(w.seg_x);
+  dfree(w.seg_yt);
+  dfree(w.seg_f);
+  dfree(w.seg_m);
+  dfree(w.lx);
+  dfree(w.ly);
+  dfree(w.lyt[0]);
+  dfree(w.lyt[1]);
+  dfree(w.gh);
+  dfree(w.acc);
+  dfree(w.ga);
+  w.n = w.R = w.S = w.K = 0;
+}
+
 void free_all(sb_ctx* c) {
+  free_adj(c);
   free_state(c);
   free_readout(c);
   dfree(c->d_rowptr);
@@ -1648,34 +1675,30 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
       }
       sched = ctx->d_sched;
     }
-    float *ck_x = nullptr, *ck_y = nullptr, *seg_x = nullptr, *seg_yt = nullptr, *seg_f = nullptr;
-    float *lx = nullptr, *ly = nullptr, *lyt = nullptr;
-    uint8_t* seg_m = nullptr;
-    double *gh = nullptr, *acc = nullptr, *ga = nullptr;
-    auto cleanup = [&]() {
-      dfree(ck_x);
-      dfree(ck_y);
-      dfree(seg_x);
-      dfree(seg_yt);
-      dfree(seg_f);
-      dfree(seg_m);
-      dfree(lx);
-      dfree(ly);
-      dfree(lyt);
-      dfree(gh);
-      dfree(acc);
-      dfree(ga);
-    };
-    // checkpoints for all segments but the last, which is recorded on the way forward
-    if ((st = dalloc(&ck_x, NR * (n_ck - 1))) || (st = dalloc(&ck_y, NR * (n_ck - 1))) ||
-        (st = dalloc(&seg_x, NR * (K + 1))) || (st = dalloc(&seg_yt, NR * K)) ||
-        (st = dalloc(&seg_f, NR * K)) ||
-        (st = dalloc(&seg_m, NR * K)) || (st = dalloc(&lx, NR)) || (st = dalloc(&ly, NR)) ||
-        (st = dalloc(&lyt, NR)) || (st = dalloc(&gh, (size_t)n)) || (st = dalloc(&acc, 6)) ||
-        (st = dalloc(&ga, (size_t)S))) {
-      cleanup();
-      return st;
+    // work memory: checkpoints for all segments but the last (recorded on the
+    // way forward), one segment's recording, the adjoint state (two buffers
+    // for the adjoint of y~: a reverse step reads one, writes the other)
+    sb_ctx::AdjWork& w = ctx->adj;
+    if (w.n != n || w.R != R || w.S != S || w.K != K) {
+      free_adj(ctx);
+      if ((st = dalloc(&w.ck_x, NR * (n_ck - 1))) || (st = dalloc(&w.ck_y, NR * (n_ck - 1))) ||
+          (st = dalloc(&w.seg_x, NR * (K + 1))) || (st = dalloc(&w.seg_yt, NR * K)) ||
+          (st = dalloc(&w.seg_f, NR * K)) || (st = dalloc(&w.seg_m, NR * K)) ||
+          (st = dalloc(&w.lx, NR)) || (st = dalloc(&w.ly, NR)) || (st = dalloc(&w.lyt[0], NR)) ||
+          (st = dalloc(&w.lyt[1], NR)) || (st = dalloc(&w.gh, (size_t)n)) ||
+          (st = dalloc(&w.acc, 6)) || (st = dalloc(&w.ga, (size_t)S))) {
+        free_adj(ctx);
+        return st;
+      }
+      w.n = n;
+      w.R = R;
+      w.S = S;
+      w.K = K;
     }
+    float *ck_x = w.ck_x, *ck_y = w.ck_y, *seg_x = w.seg_x, *seg_yt = w.seg_yt, *seg_f = w.seg_f;
+    float *lx = w.lx, *ly = w.ly;
+    uint8_t* seg_m = w.seg_m;
+    double *gh = w.gh, *acc = w.acc, *ga = w.ga;
     cudaError_t e = cudaSuccess;
     auto ok = [&](cudaError_t x) {
       if (e == cudaSuccess) e = x;
@@ -1765,7 +1788,7 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
     g.frec = nullptr;
     g.lx = lx;
     g.ly = ly;
-    g.lyt = lyt;
+    g.lyt = w.lyt[0];
     g.gh = gh;
     g.acc = acc;
     g.ga = nullptr;
@@ -1779,6 +1802,9 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
         ok(cudaMemcpyAsync(ctx->d_y, ck_y + NR * c, NR * 4, cudaMemcpyDeviceToDevice, s));
         record_segment(c, L);
       }
+      // phase 1 (through the wall) of a segment's last step runs alone; every
+      // other step's phase 1 is fused into the reverse step after it
+      int lb = 0;  // lyt buffer holding the adjoint of y~ of the step being reversed
       for (int32_t j = L - 1; j >= 0 && e == cudaSuccess; --j) {
         g.k = c * K + j;
         g.x = seg_x + NR * j;
@@ -1786,8 +1812,14 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
         g.mask = seg_m + NR * j;
         g.frec = seg_f + NR * j;
         g.ga = ga + g.k;
-        ok(sbd::launch_adj_phase1(g, s));
+        g.lyt = w.lyt[lb];
+        if (j == L - 1) ok(sbd::launch_adj_phase1(g, s));
+        g.mask_prev = j > 0 ? seg_m + NR * (j - 1) : nullptr;
+        g.lyt_out = j > 0 ? w.lyt[lb ^ 1] : nullptr;
         ok(sbd::launch_adj_phase2(ctx->jbf16, t, g, s));
+        g.mask_prev = nullptr;
+        g.lyt_out = nullptr;
+        lb ^= 1;
       }
     }
     ok(sbd::launch_adj_final(g, acc + 4, s));
@@ -1795,7 +1827,6 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
     ok(cudaStreamSynchronize(s));
     double h_acc[6] = {0, 0, 0, 0, 0, 0};
     ok(cudaMemcpy(h_acc, acc, sizeof(h_acc), cudaMemcpyDeviceToHost));
-    cleanup();
     ctx->have_state = false;  // x holds x_S but y was reused by the recomputation
     SB_CUDA(e);
     if (out_loss) *out_loss = h_acc[0];

@@ -868,6 +868,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_phase2(const AdjArgs a) {
     const float hi = a.h[row];
     const float pa = a.a0 - __ldg(a.sched + a.k);
     const float dtc0 = a.dt * a.c0;
+    const float dta0 = a.dt * a.a0;
     float tdt = 0.f, tc0 = 0.f, ta = 0.f, twc = 0.f, thr = 0.f;
 #pragma unroll
     for (int j = 0; j < NCH; ++j) {
@@ -886,8 +887,16 @@ __global__ void __launch_bounds__(kBlock) k_adj_phase2(const AdjArgs a) {
         ta += lyt * a.dt * x;
         twc += dtc0 * x * (-0.25f * sC[j][v]);
         thr += dtc0 * lyt;
-        a.lx[idx + v] = lxt - a.dt * pa * lyt + a.dt * a.c0 * sJ[j][v];
-        a.ly[idx + v] = lyt;
+        const float lxk = lxt - a.dt * pa * lyt + a.dt * a.c0 * sJ[j][v];
+        if (a.mask_prev) {  // phase 1 of step k - 1 on this element (as k_adj_phase1)
+          const bool keep = a.mask_prev[idx + v] == 0;
+          const float lxp = keep ? lxk : 0.f;
+          a.lx[idx + v] = lxp;
+          a.lyt_out[idx + v] = (keep ? lyt : 0.f) + dta0 * lxp;
+        } else {
+          a.lx[idx + v] = lxk;
+          a.ly[idx + v] = lyt;
+        }
       }
     }
     gdt += tdt;

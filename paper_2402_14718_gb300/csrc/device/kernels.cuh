@@ -145,6 +145,11 @@ struct AdjArgs {
   float* lx;                 // adjoint of x
   float* ly;                 // adjoint of y
   float* lyt;                // adjoint of y~ (gathered by neighbours in phase 2)
+  // phase 2 with the next step's phase 1 fused in: m_{k-1} and where the
+  // adjoint of y~_{k-1} goes (not lyt, which neighbours still read); lx then
+  // receives lx~_{k-1} and ly is not written. NULL mask_prev: plain phase 2.
+  const uint8_t* mask_prev = nullptr;
+  float* lyt_out = nullptr;
   double* gh;                // [n] dL/dh_i
   double* acc;               // [4]: loss, dL/ddt, dL/dc0, dL/dw_c (trajectory + explicit)
   double* ga;                // dL/da_k of this step (one double)

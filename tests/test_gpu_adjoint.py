@@ -105,3 +105,29 @@ def test_autograd_function_full_workload():
     assert float(wc.grad) == pytest.approx(g2["w_c"], rel=1e-9)
     assert a.grad.shape == (S,) and torch.isfinite(a.grad).all()
     assert all(torch.isfinite(t.grad) for t in (dt, c0, wq, wc))
+
+
+def test_work_memory_kept_between_calls_of_one_shape():
+    """sb_backward keeps its work memory for the next call of the same shape
+    and reallocates on another shape; results repeat (to the FP64 atomics'
+    ordering) whichever call comes first."""
+    _, qc, _, qo = workload_qubos("event100")
+    ctx = sb.sb_create(qc.n, qc.rowptr, qc.col, qc.val, qc.lin, sb.SB_J_FP32)
+    sb.sb_set_weights(ctx, qc.cls, qc.quality, 1.0, 1.0)
+
+    def run(S, R, K):
+        d_sched = torch.tensor(np.float32(osb.linear_schedule(1.0, S)), device="cuda")
+        g_a = torch.zeros(S, dtype=torch.float64, device="cuda")
+        loss, g = sb.sb_backward(ctx, 1.0, 0.3, 0.5, S, R, 3, d_sched, K, g_a)
+        g["sched"] = g_a.cpu().numpy()
+        return loss, g
+
+    first = run(30, 8, 8)
+    for shape in ((30, 8, 8), (30, 8, 5), (31, 8, 8), (30, 16, 8), (30, 8, 8)):
+        again = run(*shape)
+        if shape == (30, 8, 8):
+            assert again[0] == pytest.approx(first[0], rel=1e-13)
+            _close(again[1], first[1], rel=1e-10)
+    lo, go = _oracle(qo, 8, 30, 3, 0.3, 0.5)
+    assert first[0] == pytest.approx(lo, rel=1e-4)
+    _close(first[1], go)
