@@ -399,6 +399,14 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
  * SB_OPT_STEP_RPC sets rows per CTA (divided by the group size) and
  * SB_OPT_STEP_RT = 128 makes a warp cover 128 replicas instead of 256. */
 #define SB_OPT_ROWS_PER_WARP 9
+/* SB_OPT_HEAVY_FIRST (10): 1 dispatches the row-group kernel's CTAs (chunks
+ * of consecutive row groups) in order of decreasing cost, so that the CTAs
+ * that start last in a step are the light ones; 0 dispatches them in row
+ * order, which keeps the neighbour rows of the CTAs in flight together in L2;
+ * -1 (default) takes 1 when the gathered array (x, or the dSB sign bytes)
+ * fits in half of the L2, else 0. Each group is computed the same way either
+ * way: same states. */
+#define SB_OPT_HEAVY_FIRST 10
 sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
 
 /*

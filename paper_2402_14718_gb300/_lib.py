@@ -25,6 +25,7 @@ SB_OPT_REPLICA_GROUPS = 6
 SB_OPT_L2_PERSIST = 7
 SB_OPT_STREAM = 8
 SB_OPT_ROWS_PER_WARP = 9
+SB_OPT_HEAVY_FIRST = 10
 
 
 class SbEventParams(ctypes.Structure):

@@ -172,6 +172,11 @@ struct sb_ctx {
   int* d_err = nullptr;  // set by a kernel whose bounded wait gave up
   // row-group step kernel (k_step_rw): groups of RW rows and their union entries
   int rw_rows = -1;      // -1: automatic (2 for aSB / bSB, off for dSB); 0: off; 2 or 4
+  // dispatch the row-group CTAs heaviest chunk first: 1 on, 0 off, -1 when
+  // the gathered array fits in half of the L2 (otherwise row order keeps the
+  // neighbour rows of CTAs in flight together in L2)
+  int rw_heavy_first = -1;
+  int l2_bytes = 0;
   int rw_built = 0;      // RW the tables below were built for (0: none)
   int32_t rw_ngroups = 0;
   int64_t rw_E = 0;
@@ -180,6 +185,9 @@ struct sb_ctx {
   int32_t* d_rw_ent = nullptr;
   int32_t* d_rw_pos = nullptr;  // CSR position of each entry's RW slots (-1: absent)
   void* d_rw_ejv = nullptr;     // J of each entry's RW slots
+  std::vector<int32_t> h_rw_gptr;  // host copy of the group pointers
+  int32_t* d_rw_order = nullptr;   // chunk of each CTA, heaviest chunk first
+  int32_t rw_order_gpc = 0;        // groups per chunk the order was made for
   // sb_backward's work memory, kept for the next call of the same shape
   struct AdjWork {
     int32_t n = 0, R = 0, S = 0, K = 0;
@@ -395,6 +403,8 @@ void free_all(sb_ctx* c) {
   dfree(c->d_rw_rows);
   dfree(c->d_rw_ent);
   dfree(c->d_rw_pos);
+  dfree(c->d_rw_order);
+  c->rw_order_gpc = 0;
   if (c->d_rw_ejv) cudaFree(c->d_rw_ejv);
   c->d_rw_ejv = nullptr;
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -802,6 +812,8 @@ sb_status ensure_rw(sb_ctx* c, int RW) {
   dfree(c->d_rw_rows);
   dfree(c->d_rw_ent);
   dfree(c->d_rw_pos);
+  dfree(c->d_rw_order);
+  c->rw_order_gpc = 0;
   if (c->d_rw_ejv) cudaFree(c->d_rw_ejv);
   c->d_rw_ejv = nullptr;
   c->rw_built = 0;
@@ -828,7 +840,35 @@ sb_status ensure_rw(sb_ctx* c, int RW) {
   c->rw_ngroups = (int32_t)t.gptr.size() - 1;
   c->rw_E = (int64_t)t.ent.size();
   c->rw_built = RW;
+  c->h_rw_gptr = std::move(t.gptr);
   return refill_rw(c);
+}
+
+// Dispatch order of the row-group CTAs: chunks of gpc consecutive groups
+// sorted by decreasing cost (a CTA holds its slot until its slowest warp, so
+// a chunk costs about its largest group: union entries plus a fixed share for
+// the update), so that the CTAs that start last in a step are the light ones.
+sb_status ensure_rw_order(sb_ctx* c, int gpc) {
+  if (c->d_rw_order && c->rw_order_gpc == gpc) return SB_OK;
+  dfree(c->d_rw_order);
+  c->rw_order_gpc = 0;
+  const std::vector<int32_t>& gp = c->h_rw_gptr;
+  const int32_t G = (int32_t)gp.size() - 1;
+  const int32_t nch = (G + gpc - 1) / gpc;
+  std::vector<int32_t> cost(nch, 0), order(nch);
+  for (int32_t g = 0; g < G; ++g) {
+    const int32_t w = gp[g + 1] - gp[g] + 8;
+    int32_t& m = cost[g / gpc];
+    if (w > m) m = w;
+  }
+  for (int32_t i = 0; i < nch; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+  sb_status st = dalloc(&c->d_rw_order, order.size());
+  if (st) return st;
+  SB_CUDA(cudaMemcpy(c->d_rw_order, order.data(), order.size() * 4, cudaMemcpyHostToDevice));
+  c->rw_order_gpc = gpc;
+  return SB_OK;
 }
 
 // The persisting-L2 set-aside belongs to the process's CUDA context. It is
@@ -1027,6 +1067,19 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
       ra.R = c->R;
       ra.ngroups = c->rw_ngroups;
       ra.gpc = std::max(sbd::kRwBlock / 32, c->step_rpc > 0 ? c->step_rpc / rw : 0);
+      ra.cta_order = nullptr;
+      bool heavy = c->rw_heavy_first > 0;
+      if (c->rw_heavy_first < 0) {
+        if (!c->l2_bytes)
+          SB_CUDA(cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, c->device));
+        const bool sgn_rw = variant == SB_DSB && c->dsb_signs && c->j_small;
+        heavy = (size_t)c->n * c->R * (sgn_rw ? 1 : 4) * 2 <= (size_t)c->l2_bytes;
+      }
+      if (heavy) {
+        st0 = ensure_rw_order(c, ra.gpc);
+        if (st0) return st0;
+        ra.cta_order = c->d_rw_order;
+      }
     }
   }
   if (streamed) {
@@ -1201,7 +1254,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     memcpy(&a0b, &a.a0, 4);
     memcpy(&dtb, &a.dt, 4);
     key = {variant, steps, c->R, c->cur, a0b, dtb, (int64_t)(intptr_t)sched, t.G, tiled, a.rpc,
-           t.tiles, a.unroll, sgn, ngroups, streamed, rw, rw_nch};
+           t.tiles, a.unroll, sgn, ngroups, streamed, rw, rw_nch, ra.cta_order != nullptr};
   }
   GraphCache& gc = c->graph;
   const bool replay = !key.empty() && gc.exec && gc.key == key;
@@ -2000,6 +2053,14 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value) {
           return SB_ERR_ARG;
         }
         ctx->rw_rows = (int)value;
+        ctx->graph.reset();
+        return SB_OK;
+      case 10:  // SB_OPT_HEAVY_FIRST
+        if (value < -1 || value > 1) {
+          set_error("sb_set_option: SB_OPT_HEAVY_FIRST must be -1, 0 or 1");
+          return SB_ERR_ARG;
+        }
+        ctx->rw_heavy_first = (int)value;
         ctx->graph.reset();
         return SB_OK;
       case 8:  // SB_OPT_STREAM

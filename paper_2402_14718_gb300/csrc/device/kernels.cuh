@@ -242,6 +242,9 @@ struct RwArgs {
   int32_t gpc;               // row groups per CTA (a CTA walks a contiguous chunk)
   const uint8_t* sgn_in;     // dSB: sign bytes of x_k [n x R] gathered instead of x (NULL: use x)
   uint8_t* sgn_out;          // dSB: sign bytes of x_{k+1}, written with x_{k+1}
+  // CTA b works on chunk cta_order[b] (chunks of gpc groups, heaviest first,
+  // so that the last CTAs of a step are light); NULL: chunk b
+  const int32_t* cta_order = nullptr;
 };
 constexpr int kRwMaxRows = 4;  // RW is 2 or 4 (the mask has 4 bits)
 #ifndef SB_RW_BLOCK

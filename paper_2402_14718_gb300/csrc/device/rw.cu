@@ -123,9 +123,10 @@ __global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a
   const char* xl = use_sgn ? reinterpret_cast<const char*>(a.sgn_in + rep0)
                            : reinterpret_cast<const char*>(a.xin + rep0);
   const unsigned rb = (use_sgn ? 1u : 4u) * (unsigned)R;
-  const int g_end = min(a.ngroups, (blockIdx.x + 1) * a.gpc);
+  const int chunk = a.cta_order ? __ldg(a.cta_order + blockIdx.x) : (int)blockIdx.x;
+  const int g_end = min(a.ngroups, (chunk + 1) * a.gpc);
   const float pa = a.a0 - __ldg(a.sched + a.k);
-  for (int grp = blockIdx.x * a.gpc + wid; grp < g_end; grp += kRwBlock / 32) {
+  for (int grp = chunk * a.gpc + wid; grp < g_end; grp += kRwBlock / 32) {
     float acc[RW][NCH][4];
 #pragma unroll
     for (int q = 0; q < RW; ++q)

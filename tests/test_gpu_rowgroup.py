@@ -19,9 +19,10 @@ pytestmark = pytest.mark.gpu
 VARIANTS = ["asb", "bsb", "dsb"]
 
 
-def _run(q, prec, variant, R, steps, rw, seed=3, graph=1, rt=0, rpc=0, state=None):
+def _run(q, prec, variant, R, steps, rw, seed=3, graph=1, rt=0, rpc=0, state=None, heavy=1):
     ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, prec)
     sb.sb_set_option(ctx, sb.SB_OPT_ROWS_PER_WARP, rw)
+    sb.sb_set_option(ctx, sb.SB_OPT_HEAVY_FIRST, heavy)
     sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, graph)
     sb.sb_set_option(ctx, sb.SB_OPT_STEP_RT, rt)
     sb.sb_set_option(ctx, sb.SB_OPT_STEP_RPC, rpc)
@@ -39,6 +40,7 @@ def _same(q, prec, variant, R, steps, rw, **kw):
     _, xg, yg = _run(q, prec, variant, R, steps, rw, **kw)
     kw.pop("rt", None)
     kw.pop("rpc", None)
+    kw.pop("heavy", None)
     _, xu, yu = _run(q, prec, variant, R, steps, 0, **kw)
     assert np.array_equal(xg, xu) and np.array_equal(yg, yu)
 
@@ -52,6 +54,27 @@ def test_rowgroup_and_untiled_bit_identical(rw, variant, prec, R):
     R = 64 is not a multiple of 128 and falls back to the untiled kernel."""
     _, qc, _, _ = workload_qubos("event500")
     _same(qc, prec, variant, R, 25, rw)
+
+
+@pytest.mark.parametrize("rpc", [0, 32, 64])
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_rowgroup_row_order_dispatch(rpc, variant):
+    """SB_OPT_HEAVY_FIRST = 0 (CTAs in row order) against the untiled kernel;
+    the default heavy-first order is covered by every other row-group test."""
+    _, qc, _, _ = workload_qubos("event500")
+    _same(qc, sb.SB_J_BF16, variant, 256, 15, 2, rpc=rpc, heavy=0)
+    _same(qc, sb.SB_J_FP32, variant, 128, 15, 4, rpc=rpc, heavy=0)
+
+
+def test_heavy_first_option_range_and_auto():
+    """-1 (default) picks the order from the L2 fit; the states are the same
+    under every order."""
+    _, qc, _, _ = workload_qubos("event500")
+    ctx = sb.sb_create(qc.n, qc.rowptr, qc.col, qc.val, qc.lin)
+    with pytest.raises(sb.SbError):
+        sb.sb_set_option(ctx, sb.SB_OPT_HEAVY_FIRST, 2)
+    sb.sb_destroy(ctx)
+    _same(qc, sb.SB_J_BF16, "bsb", 256, 15, 2, heavy=-1)
 
 
 @pytest.mark.parametrize("rt,rpc", [(128, 0), (0, 32), (128, 64), (0, -1)])
