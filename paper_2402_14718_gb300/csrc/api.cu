@@ -177,6 +177,8 @@ struct sb_ctx {
   // neighbour rows of CTAs in flight together in L2)
   int rw_heavy_first = -1;
   int l2_bytes = 0;
+  int32_t* d_row_order = nullptr;  // chunk of each k_step_dsb16 CTA, heaviest first
+  int32_t row_order_rpc = 0;
   int rw_built = 0;      // RW the tables below were built for (0: none)
   int32_t rw_ngroups = 0;
   int64_t rw_E = 0;
@@ -361,6 +363,8 @@ void free_adj(sb_ctx* c) {
 
 void free_all(sb_ctx* c) {
   free_adj(c);
+  dfree(c->d_row_order);
+  c->row_order_rpc = 0;
   free_state(c);
   free_readout(c);
   dfree(c->d_rowptr);
@@ -848,6 +852,42 @@ sb_status ensure_rw(sb_ctx* c, int RW) {
 // sorted by decreasing cost (a CTA holds its slot until its slowest warp, so
 // a chunk costs about its largest group: union entries plus a fixed share for
 // the update), so that the CTAs that start last in a step are the light ones.
+// Heavy-first dispatch pays where the end of a step is a large part of it (few
+// waves of CTAs) and scattering the rows in flight costs nothing (the gathered
+// array stays in L2); SB_OPT_HEAVY_FIRST forces it on or off.
+bool heavy_first(sb_ctx* c, size_t gather_bytes, int64_t ctas) {
+  if (c->rw_heavy_first >= 0) return c->rw_heavy_first > 0;
+  if (!c->l2_bytes && cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, c->device))
+    cudaGetLastError();
+  if (!c->sms && cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device))
+    cudaGetLastError();
+  return gather_bytes * 2 <= (size_t)c->l2_bytes && ctas <= (int64_t)c->sms * 9 * 8;
+}
+
+// Dispatch order of the dSB sign-byte kernel's CTAs: chunks of rpc rows by
+// decreasing cost (the largest row degree of the chunk plus a fixed share).
+sb_status ensure_row_order(sb_ctx* c, int rpc) {
+  if (c->d_row_order && c->row_order_rpc == rpc) return SB_OK;
+  dfree(c->d_row_order);
+  c->row_order_rpc = 0;
+  const std::vector<int32_t>& rp = c->h_rowptr;
+  const int32_t nch = (c->n + rpc - 1) / rpc;
+  std::vector<int32_t> cost(nch, 0), order(nch);
+  for (int32_t i = 0; i < c->n; ++i) {
+    const int32_t w = rp[i + 1] - rp[i] + 8;
+    int32_t& m = cost[i / rpc];
+    if (w > m) m = w;
+  }
+  for (int32_t i = 0; i < nch; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+  sb_status st = dalloc(&c->d_row_order, order.size());
+  if (st) return st;
+  SB_CUDA(cudaMemcpy(c->d_row_order, order.data(), order.size() * 4, cudaMemcpyHostToDevice));
+  c->row_order_rpc = rpc;
+  return SB_OK;
+}
+
 sb_status ensure_rw_order(sb_ctx* c, int gpc) {
   if (c->d_rw_order && c->rw_order_gpc == gpc) return SB_OK;
   dfree(c->d_rw_order);
@@ -1068,14 +1108,9 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
       ra.ngroups = c->rw_ngroups;
       ra.gpc = std::max(sbd::kRwBlock / 32, c->step_rpc > 0 ? c->step_rpc / rw : 0);
       ra.cta_order = nullptr;
-      bool heavy = c->rw_heavy_first > 0;
-      if (c->rw_heavy_first < 0) {
-        if (!c->l2_bytes)
-          SB_CUDA(cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, c->device));
-        const bool sgn_rw = variant == SB_DSB && c->dsb_signs && c->j_small;
-        heavy = (size_t)c->n * c->R * (sgn_rw ? 1 : 4) * 2 <= (size_t)c->l2_bytes;
-      }
-      if (heavy) {
+      const bool sgn_rw = variant == SB_DSB && c->dsb_signs && c->j_small;
+      const int64_t ctas = ((int64_t)c->rw_ngroups + ra.gpc - 1) / ra.gpc;
+      if (heavy_first(c, (size_t)c->n * c->R * (sgn_rw ? 1 : 4), ctas)) {
         st0 = ensure_rw_order(c, ra.gpc);
         if (st0) return st0;
         ra.cta_order = c->d_rw_order;
@@ -1142,6 +1177,15 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   a.mask = nullptr;
   a.sgn_in = nullptr;
   a.sgn_out = nullptr;
+  a.cta_order = nullptr;
+  if (dsb16) {
+    const int rpc16 = sbd::dsb16_rows_per_cta(a.rpc);
+    if (heavy_first(c, (size_t)c->n * c->R, ((int64_t)c->n + rpc16 - 1) / rpc16)) {
+      sb_status st2 = ensure_row_order(c, rpc16);
+      if (st2) return st2;
+      a.cta_order = c->d_row_order;
+    }
+  }
   const int tiled =
       (!streamed && !rw && c->tiled_ok && c->use_tiled && c->R % sbd::kTileRT == 0) ? 1 : 0;
   sbd::TiledArgs ta;
@@ -1254,7 +1298,8 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     memcpy(&a0b, &a.a0, 4);
     memcpy(&dtb, &a.dt, 4);
     key = {variant, steps, c->R, c->cur, a0b, dtb, (int64_t)(intptr_t)sched, t.G, tiled, a.rpc,
-           t.tiles, a.unroll, sgn, ngroups, streamed, rw, rw_nch, ra.cta_order != nullptr};
+           t.tiles, a.unroll, sgn, ngroups, streamed, rw, rw_nch, ra.cta_order != nullptr,
+           a.cta_order != nullptr};
   }
   GraphCache& gc = c->graph;
   const bool replay = !key.empty() && gc.exec && gc.key == key;

@@ -398,8 +398,9 @@ __global__ void __launch_bounds__(kDsbBlock, SB_DSB_MINB) k_step_dsb16(const Ste
   const unsigned mask = group_mask(G);
   const int R = a.R;
   const JT* J = static_cast<const JT*>(a.J);
-  const int row_end = min(a.n, (blockIdx.x + 1) * a.rpc);
-  for (int row = blockIdx.x * a.rpc + gid; row < row_end; row += groups) {
+  const int chunk = a.cta_order ? __ldg(a.cta_order + blockIdx.x) : (int)blockIdx.x;
+  const int row_end = min(a.n, (chunk + 1) * a.rpc);
+  for (int row = chunk * a.rpc + gid; row < row_end; row += groups) {
     float acc[16];
 #pragma unroll
     for (int v = 0; v < 16; ++v) acc[v] = 0.f;
@@ -1220,6 +1221,11 @@ int grid_for(size_t work, int block) {
 
 }  // namespace
 
+int dsb16_rows_per_cta(int rpc) {
+  return rpc * kDsbBlock / kBlock > 0 ? rpc * kDsbBlock / kBlock : 1;
+}
+
+
 cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs& a,
                         cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
@@ -1240,7 +1246,7 @@ cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs&
   }
   if (variant == 2 && a.sgn_in && a.G * 16 == a.R && t.tiles == 1 && t.V == 16) {
     // a CTA walks rpc rows (one row per G-lane group at 256 threads)
-    const int rpc = a.rpc * kDsbBlock / kBlock > 0 ? a.rpc * kDsbBlock / kBlock : 1;
+    const int rpc = dsb16_rows_per_cta(a.rpc);
     StepArgs b = a;
     b.rpc = rpc;
     dim3 grid((a.n + rpc - 1) / rpc, 1);

@@ -21,6 +21,8 @@ Tiling make_tiling(int R);
 Tiling make_tiling_rt(int R, int RT);
 // dSB with int8 signs, 16 replicas per lane: valid when R / 16 is a power of two <= 32.
 bool dsb16_ok(int R);
+// rows per CTA of k_step_dsb16 for a step's rows-per-CTA setting rpc
+int dsb16_rows_per_cta(int rpc);
 Tiling make_tiling_dsb16(int R);
 
 struct StepArgs {
@@ -44,6 +46,9 @@ struct StepArgs {
   float* frec;            // optional (with ytil): the coupling sum J g(x) [n x R]
   const uint8_t* sgn_in;  // dSB: sign bytes of x_k [n x R] gathered instead of x (NULL: use x)
   uint8_t* sgn_out;       // dSB: sign bytes of x_{k+1}, written with x_{k+1} (may be NULL)
+  // k_step_dsb16: CTA b takes row chunk cta_order[b] (chunks of
+  // dsb16_rows_per_cta(rpc) rows, heaviest first); NULL: chunk b
+  const int32_t* cta_order = nullptr;
   int32_t unroll;         // neighbours in flight per thread (4)
   int32_t tile0;          // first replica tile of this launch (sequential replica groups)
 };

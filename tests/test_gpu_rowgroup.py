@@ -60,10 +60,13 @@ def test_rowgroup_and_untiled_bit_identical(rw, variant, prec, R):
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_rowgroup_row_order_dispatch(rpc, variant):
     """SB_OPT_HEAVY_FIRST = 0 (CTAs in row order) against the untiled kernel;
-    the default heavy-first order is covered by every other row-group test."""
+    the heavy-first order is covered by every other row-group test (and, for
+    the dSB sign-byte kernel, by the automatic choice on these sizes)."""
     _, qc, _, _ = workload_qubos("event500")
     _same(qc, sb.SB_J_BF16, variant, 256, 15, 2, rpc=rpc, heavy=0)
     _same(qc, sb.SB_J_FP32, variant, 128, 15, 4, rpc=rpc, heavy=0)
+    if variant == "dsb":   # the sign-byte kernel: row order against the default order
+        _same(qc, sb.SB_J_BF16, variant, 256, 15, 0, rpc=rpc, heavy=0)
 
 
 def test_heavy_first_option_range_and_auto():
