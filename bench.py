@@ -97,8 +97,8 @@ def job_value(units_per_rank, world_size, ms):
 # replica tile) and that kernel's sources (sha256 prefix, kernel_source_hash);
 # any other combination reports null.
 MEASURED_TRAFFIC = {
-    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "1a17b421e478ee10"): 89664768 + 33082624,
-    ("event1000", "dsb", "k_step_dsb16", (0, 0, 0), "59aa88cffd9b6550"): 100401664 + 39776000,
+    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "7ee48fbf18d329f6"): 91347200 + 37270784,
+    ("event1000", "dsb", "k_step_dsb16", (0, 0, 0), "f42d2b28fa6acf68"): 100595712 + 39079168,
 }
 
 
