@@ -407,6 +407,12 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
  * fits in half of the L2, else 0. Each group is computed the same way either
  * way: same states. */
 #define SB_OPT_HEAVY_FIRST 10
+/* SB_OPT_R1_LANES (11): with one replica (R = 1), 8, 16 or 32 lanes share a
+ * row: they load its couplings and gather its neighbours' positions in
+ * parallel, then form the coupling sum in CSR order as the one-thread kernel
+ * does (same states). 0: one thread per row. -1 (default): the widest group
+ * for which rows x lanes fit in the SMs' resident threads, else 0. */
+#define SB_OPT_R1_LANES 11
 sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
 
 /*

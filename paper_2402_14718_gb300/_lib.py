@@ -26,6 +26,7 @@ SB_OPT_L2_PERSIST = 7
 SB_OPT_STREAM = 8
 SB_OPT_ROWS_PER_WARP = 9
 SB_OPT_HEAVY_FIRST = 10
+SB_OPT_R1_LANES = 11
 
 
 class SbEventParams(ctypes.Structure):

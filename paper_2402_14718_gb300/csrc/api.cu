@@ -176,6 +176,7 @@ struct sb_ctx {
   // the gathered array fits in half of the L2 (otherwise row order keeps the
   // neighbour rows of CTAs in flight together in L2)
   int rw_heavy_first = -1;
+  int r1_lanes = -1;  // one replica: lanes per row (0: one thread per row; -1: automatic)
   int l2_bytes = 0;
   int32_t* d_row_order = nullptr;  // chunk of each k_step_dsb16 CTA, heaviest first
   int32_t row_order_rpc = 0;
@@ -888,6 +889,20 @@ sb_status ensure_row_order(sb_ctx* c, int rpc) {
   return SB_OK;
 }
 
+// One replica: lanes per row. Groups of lanes pay where rows alone leave the
+// GPU's thread slots idle (they multiply the instructions of the coupling sum
+// by the group width), so the automatic choice is the widest group with
+// rows x lanes within the SMs' resident threads, else one thread per row.
+int r1_lanes_for(sb_ctx* c) {
+  if (c->r1_lanes >= 0) return c->r1_lanes;
+  if (!c->sms && cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device))
+    cudaGetLastError();
+  const int64_t cap = (int64_t)std::max(c->sms, 1) * 2048;
+  for (int G : {32, 16, 8})
+    if ((int64_t)c->n * G <= cap) return G;
+  return 0;
+}
+
 sb_status ensure_rw_order(sb_ctx* c, int gpc) {
   if (c->d_rw_order && c->rw_order_gpc == gpc) return SB_OK;
   dfree(c->d_rw_order);
@@ -1178,6 +1193,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   a.sgn_in = nullptr;
   a.sgn_out = nullptr;
   a.cta_order = nullptr;
+  a.r1_lanes = r1_lanes_for(c);
   if (dsb16) {
     const int rpc16 = sbd::dsb16_rows_per_cta(a.rpc);
     if (heavy_first(c, (size_t)c->n * c->R, ((int64_t)c->n + rpc16 - 1) / rpc16)) {
@@ -1299,7 +1315,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     memcpy(&dtb, &a.dt, 4);
     key = {variant, steps, c->R, c->cur, a0b, dtb, (int64_t)(intptr_t)sched, t.G, tiled, a.rpc,
            t.tiles, a.unroll, sgn, ngroups, streamed, rw, rw_nch, ra.cta_order != nullptr,
-           a.cta_order != nullptr};
+           a.cta_order != nullptr, a.r1_lanes};
   }
   GraphCache& gc = c->graph;
   const bool replay = !key.empty() && gc.exec && gc.key == key;
@@ -1825,6 +1841,7 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
     a.frec = nullptr;
     a.sgn_in = nullptr;
     a.sgn_out = nullptr;
+    a.r1_lanes = r1_lanes_for(ctx);
     ok(sbd::launch_set_c0(ctx->d_c0ev, ctx->d_c0auto, c0, 1, s));
     ok(sbd::launch_init(ctx->d_x[0], ctx->d_y, nullptr, ctx->d_ev_row0, n, R, seed, s));
     int cur = 0;
@@ -2098,6 +2115,14 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value) {
           return SB_ERR_ARG;
         }
         ctx->rw_rows = (int)value;
+        ctx->graph.reset();
+        return SB_OK;
+      case 11:  // SB_OPT_R1_LANES
+        if (value != -1 && value != 0 && value != 8 && value != 16 && value != 32) {
+          set_error("sb_set_option: SB_OPT_R1_LANES must be -1, 0, 8, 16 or 32");
+          return SB_ERR_ARG;
+        }
+        ctx->r1_lanes = (int)value;
         ctx->graph.reset();
         return SB_OK;
       case 10:  // SB_OPT_HEAVY_FIRST

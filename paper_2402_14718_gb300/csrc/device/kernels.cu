@@ -374,6 +374,68 @@ __global__ void __launch_bounds__(kBlock) k_step_r1(const StepArgs a) {
   a.y[row] = y;
 }
 
+// One replica, G lanes per row: the lanes load the row's (col, J) and gather
+// the neighbours' positions G x 4 at a time (all in flight together), then every
+// lane runs the same FMA chain in CSR order over the shuffled values, so the
+// sum is the one k_step_r1 forms, bit for bit, with one round trip per 4G
+// neighbours instead of one per eight. Lane 0 of the group writes the row.
+template <int G, int MODE, typename JT>
+__global__ void __launch_bounds__(kBlock) k_step_r1g(const StepArgs a) {
+  constexpr int VARIANT = MODE == 4 ? 1 : MODE;
+  constexpr bool record = MODE == 4;
+  constexpr int U = 4;
+  const int gid = threadIdx.x / G, g = threadIdx.x - gid * G;
+  const int row = blockIdx.x * (kBlock / G) + gid;
+  if (row >= a.n) return;  // the whole group leaves together
+  const unsigned mask = group_mask(G);
+  const JT* J = static_cast<const JT*>(a.J);
+  const int p0 = __ldg(a.rowptr + row), p1 = __ldg(a.rowptr + row + 1);
+  float acc = 0.f;
+  for (int pb = p0; pb < p1; pb += G * U) {
+    float w[U], xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = pb + u * G + g;
+      int c = row;
+      w[u] = 0.f;
+      if (p < p1) {
+        c = __ldg(a.col + p);
+        w[u] = jval(J, p);
+      }
+      xv[u] = __ldg(a.xin + c);
+    }
+    const int cnt = min(G * U, p1 - pb);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float s = VARIANT == 2 ? sgnf(xv[u]) : xv[u];
+      const int lim = min(G, cnt - u * G);
+      for (int j = 0; j < lim; ++j)
+        acc = fmaf(__shfl_sync(mask, w[u], j, G), __shfl_sync(mask, s, j, G), acc);
+    }
+  }
+  if (g != 0) return;
+  const float pa = a.a0 - __ldg(a.sched + a.k);
+  const int e = a.row_event ? __ldg(a.row_event + row) : 0;
+  const float c0 = __ldg(a.c0_ev + e);
+  float x = __ldg(a.xin + row), y = a.y[row];
+  float force = -pa * x + c0 * (acc + __ldg(a.h + row));
+  if (VARIANT == 0) force -= x * x * x;
+  y = y + a.dt * force;
+  x = x + a.dta0 * y;
+  if (record) {
+    a.ytil[row] = y;
+    a.frec[row] = acc;
+  }
+  const bool wall = VARIANT != 0 && fabsf(x) > 1.f;
+  if (record) a.mask[row] = wall ? 1 : 0;
+  if (wall) {
+    x = copysignf(1.f, x);
+    y = 0.f;
+  }
+  a.xout[row] = x;
+  a.y[row] = y;
+}
+
 // ---------------------------------------------------------------- dSB, 16 signs per lane
 // dSB gathering int8 signs with 16 replicas per lane: one 16-byte load brings a
 // neighbour's signs for 16 replicas. G = R / 16 lanes own a row (R / 16 a power
@@ -1230,8 +1292,31 @@ cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs&
                         cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   if (a.R == 1 && !a.sgn_in && a.rpc == 256 / t.G) {
-    const int grid = (a.n + kBlock - 1) / kBlock;
     const int mode = (variant == 1 && a.ytil) ? 4 : variant;
+    if (a.r1_lanes == 8 || a.r1_lanes == 16 || a.r1_lanes == 32) {
+      const int grid = (int)(((int64_t)a.n * a.r1_lanes + kBlock - 1) / kBlock);
+#define SB_R1G(GG, M)                                                                 \
+  (jbf16 ? (k_step_r1g<GG, M, __nv_bfloat16><<<grid, kBlock, 0, s>>>(a), 0) \
+         : (k_step_r1g<GG, M, float><<<grid, kBlock, 0, s>>>(a), 0))
+#define SB_R1G_M(GG)                \
+  switch (mode) {                   \
+    case 0: SB_R1G(GG, 0); break;   \
+    case 1: SB_R1G(GG, 1); break;   \
+    case 2: SB_R1G(GG, 2); break;   \
+    default: SB_R1G(GG, 4); break;  \
+  }
+      if (a.r1_lanes == 8) {
+        SB_R1G_M(8)
+      } else if (a.r1_lanes == 16) {
+        SB_R1G_M(16)
+      } else {
+        SB_R1G_M(32)
+      }
+#undef SB_R1G_M
+#undef SB_R1G
+      return cudaGetLastError();
+    }
+    const int grid = (a.n + kBlock - 1) / kBlock;
 #define SB_R1(M)                                                        \
   (jbf16 ? (k_step_r1<M, __nv_bfloat16><<<grid, kBlock, 0, s>>>(a), 0) \
          : (k_step_r1<M, float><<<grid, kBlock, 0, s>>>(a), 0))

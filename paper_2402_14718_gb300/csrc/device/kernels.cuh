@@ -44,6 +44,7 @@ struct StepArgs {
   float* ytil;            // optional: momentum after the update, before the wall [n x R]
   uint8_t* mask;          // optional: 1 where the wall fired [n x R]
   float* frec;            // optional (with ytil): the coupling sum J g(x) [n x R]
+  int32_t r1_lanes = 0;   // R = 1: lanes per row (8, 16, 32: k_step_r1g; else one thread per row)
   const uint8_t* sgn_in;  // dSB: sign bytes of x_k [n x R] gathered instead of x (NULL: use x)
   uint8_t* sgn_out;       // dSB: sign bytes of x_{k+1}, written with x_{k+1} (may be NULL)
   // k_step_dsb16: CTA b takes row chunk cta_order[b] (chunks of

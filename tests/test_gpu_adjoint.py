@@ -131,3 +131,25 @@ def test_work_memory_kept_between_calls_of_one_shape():
     lo, go = _oracle(qo, 8, 30, 3, 0.3, 0.5)
     assert first[0] == pytest.approx(lo, rel=1e-4)
     _close(first[1], go)
+
+
+def test_one_replica_lane_groups_in_the_adjoint():
+    """The recording step of sb_backward at R = 1 with lane groups gives the
+    gradients of the one-thread form (to the FP64 atomics' ordering)."""
+    _, qc, _, qo = workload_qubos("event100")
+    out = []
+    for lanes in (16, 0):
+        ctx = sb.sb_create(qc.n, qc.rowptr, qc.col, qc.val, qc.lin, sb.SB_J_FP32)
+        sb.sb_set_weights(ctx, qc.cls, qc.quality, 1.0, 1.0)
+        sb.sb_set_option(ctx, sb.SB_OPT_R1_LANES, lanes)
+        d_sched = torch.tensor(np.float32(osb.linear_schedule(1.0, 30)), device="cuda")
+        g_a = torch.zeros(30, dtype=torch.float64, device="cuda")
+        loss, g = sb.sb_backward(ctx, 1.0, 0.3, 0.5, 30, 1, 3, d_sched, 8, g_a)
+        g["sched"] = g_a.cpu().numpy()
+        out.append((loss, g))
+        sb.sb_destroy(ctx)
+    assert out[0][0] == pytest.approx(out[1][0], rel=1e-13)
+    _close(out[0][1], out[1][1], rel=1e-10)
+    lo, go = _oracle(qo, 1, 30, 3, 0.3, 0.5)
+    assert out[0][0] == pytest.approx(lo, rel=1e-4)
+    _close(out[0][1], go)

@@ -475,3 +475,34 @@ def test_l2_persist_option_bit_identical():
             out.append(sb.sb_get_state(ctx))
     for o in out[1:]:
         assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])
+
+
+@pytest.mark.parametrize("lanes", [8, 16, 32])
+@pytest.mark.parametrize("variant", ["asb", "bsb", "dsb"])
+def test_one_replica_lane_groups_bit_identical(lanes, variant):
+    """SB_OPT_R1_LANES: G lanes per row gather in parallel and form the same
+    CSR-order FMA chain as the one-thread-per-row kernel (R = 1): equal states
+    for FP32 and BF16 J, graph replay and direct launches, a batched context."""
+    _, qc, _, _ = workload_qubos("event1000")
+    qs = [workload_qubos("event100")[1], qc]
+    dt = 0.1 if variant == "asb" else 0.5
+    for prec in (sb.SB_J_FP32, sb.SB_J_BF16):
+        for graph in (1, 0):
+            outs = []
+            for r1 in (lanes, 0):
+                ctx = sb.sb_create(qc.n, qc.rowptr, qc.col, qc.val, qc.lin, prec)
+                sb.sb_set_option(ctx, sb.SB_OPT_R1_LANES, r1)
+                sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, graph)
+                sb.sb_run(ctx, variant, 1.0, 0.0, dt, 60, 1, seed=2)
+                sb.sb_run(ctx, variant, 1.0, 0.0, dt, 60, 1, seed=2)
+                outs.append(sb.sb_get_state(ctx))
+                sb.sb_destroy(ctx)
+            assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    outs = []
+    for r1 in (lanes, 0):
+        ctxb = sb.sb_create_batch([(q.rowptr, q.col, q.val, q.lin) for q in qs])
+        sb.sb_set_option(ctxb, sb.SB_OPT_R1_LANES, r1)
+        sb.sb_run(ctxb, variant, 1.0, 0.0, dt, 40, 1, seed=3)
+        outs.append(sb.sb_get_state(ctxb))
+        sb.sb_destroy(ctxb)
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
