@@ -97,8 +97,8 @@ def job_value(units_per_rank, world_size, ms):
 # replica tile) and that kernel's sources (sha256 prefix, kernel_source_hash);
 # any other combination reports null.
 MEASURED_TRAFFIC = {
-    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "7ee48fbf18d329f6"): 91347200 + 37270784,
-    ("event1000", "dsb", "k_step_dsb16", (0, 0, 0), "f42d2b28fa6acf68"): 100595712 + 39079168,
+    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "a409442e9862ff70"): 91319296 + 37600256,
+    ("event1000", "dsb", "k_step_dsb16", (0, 0, 0), "4236c91a6c79f841"): 100602368 + 39244032,
 }
 
 
