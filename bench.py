@@ -168,6 +168,30 @@ def kernel_source_hash(kname="k_step"):
     return h.hexdigest()[:16]
 
 
+def gather_rate(sb, ctx, kname, variant, N, nnz, R, kstep_s, stream):
+    """On-chip side of the step: the neighbour-row bytes one launch reads
+    (through L1 / L2; x stays in L2 on the bench workloads) and their rate,
+    beside the rate of random whole-row reads of an array of x's size measured
+    now by sb_gather_probe (no L1 reuse there, so a kernel whose rows repeat in
+    L1 can exceed it)."""
+    rw, entries = sb.sb_step_info(ctx)
+    signs = variant == "dsb" and kname in ("k_step_dsb16",)
+    elem = 1 if signs else 4
+    if kname == "k_step_rw" and rw:
+        gbytes = entries * R * elem
+    else:
+        gbytes = nnz * R * elem
+    out = {"bytes_per_launch": gbytes, "tb_per_s": gbytes / kstep_s / 1e12,
+           "rows": "union entries of the row groups" if kname == "k_step_rw" and rw
+           else "one neighbour row per nonzero"}
+    row_bytes = R * elem
+    if row_bytes % 512 == 0:
+        probe = sb.sb_gather_probe(N * R * elem, row_bytes, 5, 1, stream)
+        out.update({"probe_tb_per_s": probe / 1e12, "frac_of_probe": gbytes / kstep_s / probe,
+                    "probe_row_bytes": row_bytes})
+    return out
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -456,6 +480,7 @@ def run_ours(args):
                 "kernel": kname,
                 "peak_source": src, "alg_bytes_per_launch": alg_bytes,
                 "kstep_us": kstep_s * 1e6}
+    roofline["gather"] = gather_rate(sb, ctx, kname, args.variant, N, nnz, R, kstep_s, stream)
 
     # end to end through the public API with host buffers (pinned), every step:
     # H2D of the QUBO, conversion, init, S steps, readout, D2H of the result

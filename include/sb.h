@@ -211,6 +211,27 @@ sb_status sb_info(const sb_ctx* ctx, int32_t e, int32_t* n, int64_t* nnz, double
 int32_t sb_num_events(const sb_ctx* ctx);
 int32_t sb_total_rows(const sb_ctx* ctx);
 
+/* Row-group tables of the step kernel (SB_OPT_ROWS_PER_WARP), built on the
+ * first run that uses them: rows per warp (0: not built) and the number of
+ * union entries, each of which reads one neighbour row per step (the step's
+ * on-chip gather is union_entries x R x 4 bytes). Either pointer may be NULL. */
+sb_status sb_step_info(const sb_ctx* ctx, int32_t* rows_per_warp, int64_t* union_entries);
+
+/*
+ * sb_gather_probe -- a diagnostic of the on-chip bound of the coupling product
+ * (no SB arithmetic): the rate at which the GPU reads whole rows of an array
+ * at random row indices, as the step reads neighbour rows. array_bytes: size
+ * of the array (e.g. the state x, N x R x 4); row_bytes: one row (R x 4 for
+ * FP32 positions), a positive multiple of 512; about 64 reads per row (at most
+ * 2^23), indices from splitmix64(seed). Each warp reads two rows at a time with
+ * 16-byte loads per lane, all SMs fully occupied; the best of `repeats` timed
+ * launches (CUDA events on `stream`, after one untimed one) is returned in
+ * *out_bytes_per_s (host). Allocates and frees its own device memory;
+ * synchronises the stream. SB_ERR_ARG for bad sizes, SB_ERR_OOM / SB_ERR_CUDA.
+ */
+sb_status sb_gather_probe(int64_t array_bytes, int32_t row_bytes, int32_t repeats, uint64_t seed,
+                          double* out_bytes_per_s, void* stream);
+
 /*
  * sb_run -- SB time evolution, section "Simulated Bifurcation":
  *   aSB (Eq. 1-2), bSB (Eq. 5-8, wall at |x| > 1), dSB (Eq. 9-12, sgn(x_j) in

@@ -23,7 +23,8 @@ __all__ = [
     "SB_OPT_STEP_UNROLL", "SB_OPT_DSB_SIGNS", "SB_OPT_REPLICA_GROUPS", "SB_OPT_L2_PERSIST", "SbError",
     "event_params", "build_params", "sb_event_generate", "sb_qubo_build", "sb_tracks",
     "sb_qubo_build_device",
-    "sb_create", "sb_create_batch", "sb_destroy", "sb_info", "sb_run", "sb_advance",
+    "sb_create", "sb_create_batch", "sb_destroy", "sb_info", "sb_step_info", "sb_gather_probe",
+    "sb_run", "sb_advance",
     "sb_set_state", "sb_get_state", "sb_energy", "sb_best", "sb_readout_device", "sb_set_option",
     "sb_energy_noalloc", "sb_autotune", "sb_set_weights", "sb_backward", "SBRelaxedEnergy",
     "sb_version", "LIB_PATH",
@@ -248,6 +249,23 @@ def sb_info(ctx, e=0):
                       ctypes.byref(sig), ctypes.byref(c0)))
     return {"n": n.value, "nnz": nnz.value, "offset": off.value, "sigma_j": sig.value,
             "c0_auto": c0.value}
+
+
+def sb_step_info(ctx):
+    """(rows per warp of the row-group tables, 0 if not built; union entries)."""
+    rw = ctypes.c_int32()
+    ent = ctypes.c_int64()
+    check(lib.sb_step_info(ctx.handle, ctypes.byref(rw), ctypes.byref(ent)))
+    return rw.value, ent.value
+
+
+def sb_gather_probe(array_bytes, row_bytes, repeats=5, seed=1, stream=None):
+    """Bytes per second of random whole-row reads (see include/sb.h)."""
+    out = ctypes.c_double()
+    check(lib.sb_gather_probe(int(array_bytes), int(row_bytes), int(repeats),
+                              ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), ctypes.byref(out),
+                              _stream(stream)))
+    return out.value
 
 
 def sb_run(ctx, variant, a0, c0, dt, steps, replicas, seed, a_sched=None, stream=None):

@@ -75,6 +75,8 @@ _SIGS = {
     "sb_create_batch": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_int32, P(c_void_p)]),
     "sb_destroy": (None, [c_void_p]),
+    "sb_step_info": (c_int32, [c_void_p, P(c_int32), P(c_int64)]),
+    "sb_gather_probe": (c_int32, [c_int64, c_int32, c_int32, c_uint64, P(c_double), c_void_p]),
     "sb_info": (c_int32, [c_void_p, c_int32, P(c_int32), P(c_int64), P(c_double), P(c_double),
                           P(c_double)]),
     "sb_num_events": (c_int32, [c_void_p]),

@@ -14,6 +14,7 @@
 
 #include "../../include/sb.h"
 #include "device/kernels.cuh"
+#include "device/probe.cuh"
 #include "guard.h"
 
 namespace sbh {
@@ -1497,6 +1498,88 @@ sb_status sb_info(const sb_ctx* ctx, int32_t e, int32_t* n, int64_t* nnz, double
   if (sigma_j) *sigma_j = ctx->sigma[e];
   if (c0_auto) *c0_auto = ctx->c0_auto[e];
   return SB_OK;
+}
+
+sb_status sb_step_info(const sb_ctx* ctx, int32_t* rows_per_warp, int64_t* union_entries) {
+  if (!ctx) {
+    set_error("sb_step_info: null context");
+    return SB_ERR_ARG;
+  }
+  if (rows_per_warp) *rows_per_warp = ctx->rw_built;
+  if (union_entries) *union_entries = ctx->rw_built ? ctx->rw_E : 0;
+  return SB_OK;
+}
+
+sb_status sb_gather_probe(int64_t array_bytes, int32_t row_bytes, int32_t repeats, uint64_t seed,
+                          double* out_bytes_per_s, void* stream) {
+  return sbh::guarded("sb_gather_probe", [&]() -> sb_status {
+    if (row_bytes <= 0 || row_bytes % 512 != 0 || array_bytes < 2LL * row_bytes || repeats < 1 ||
+        !out_bytes_per_s) {
+      set_error("sb_gather_probe: row_bytes a positive multiple of 512, at least two rows, "
+                "repeats >= 1, out_bytes_per_s not NULL");
+      return SB_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t rows = array_bytes / row_bytes;
+    // about 64 reads per row, at most 2^23 reads, an even count
+    const int64_t count = std::min<int64_t>(int64_t(1) << 23, std::max<int64_t>(rows * 64, 2)) & ~int64_t(1);
+    std::vector<int32_t> idx((size_t)count);
+    uint64_t z = seed;
+    for (int64_t i = 0; i < count; ++i) {  // splitmix64
+      z += 0x9E3779B97F4A7C15ull;
+      uint64_t v = z;
+      v = (v ^ (v >> 30)) * 0xBF58476D1CE4E5B9ull;
+      v = (v ^ (v >> 27)) * 0x94D049BB133111EBull;
+      v ^= v >> 31;
+      idx[(size_t)i] = (int32_t)(v % (uint64_t)rows);
+    }
+    int dev = 0, sms = 0;
+    SB_CUDA(cudaGetDevice(&dev));
+    SB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int per = sbd::gather_probe_blocks_per_sm();
+    if (per <= 0) {
+      set_error("sb_gather_probe: occupancy query failed");
+      return SB_ERR_CUDA;
+    }
+    const int grid = sms * per;
+    const size_t nwarps = (size_t)grid * sbd::gather_probe_block() / 32;
+    float4* a = nullptr;
+    int32_t* d_idx = nullptr;
+    float* out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+      dfree(a);
+      dfree(d_idx);
+      dfree(out);
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+    };
+    sb_status st;
+    if ((st = dalloc(&a, (size_t)rows * row_bytes / 16)) || (st = dalloc(&d_idx, (size_t)count)) ||
+        (st = dalloc(&out, nwarps))) {
+      cleanup();
+      return st;
+    }
+    cudaError_t e = cudaMemsetAsync(a, 0, (size_t)rows * row_bytes, s);
+    if (e == cudaSuccess) e = cudaMemcpy(d_idx, idx.data(), (size_t)count * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best_ms = 3.0e38f;
+    for (int t = 0; t <= repeats && e == cudaSuccess; ++t) {  // the first launch warms up
+      e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess)
+        e = sbd::launch_gather_probe(a, rows, row_bytes / 16, d_idx, count, out, grid, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && t > 0) best_ms = std::min(best_ms, ms);
+    }
+    cleanup();
+    SB_CUDA(e);
+    *out_bytes_per_s = (double)count * row_bytes / (best_ms * 1e-3);
+    return SB_OK;
+  });
 }
 
 sb_status sb_run(sb_ctx* ctx, sb_variant variant, double a0, double c0, double dt,
