@@ -56,6 +56,23 @@ def test_host_argument_errors():
                             ctypes.byref(h)) == _lib.SB_ERR_ARG
 
 
+def test_diagnostic_argument_errors():
+    """sb_step_info and sb_gather_probe check their arguments before any device
+    work."""
+    import paper_2402_14718_gb300 as sb
+    from paper_2402_14718_gb300 import _lib
+    assert sb.lib.sb_step_info(None, None, None) == _lib.SB_ERR_ARG
+    out = ctypes.c_double()
+    for array_bytes, row_bytes, repeats, ptr in ((1 << 20, 100, 1, ctypes.byref(out)),
+                                                 (1 << 20, 0, 1, ctypes.byref(out)),
+                                                 (512, 512, 1, ctypes.byref(out)),
+                                                 (1 << 20, 1024, 0, ctypes.byref(out)),
+                                                 (1 << 20, 1024, 1, None)):
+        assert sb.lib.sb_gather_probe(array_bytes, row_bytes, repeats, 1, ptr,
+                                      None) == _lib.SB_ERR_ARG
+    assert "sb_gather_probe" in sb.lib.sb_last_error().decode()
+
+
 @pytest.mark.parametrize("case", ["unsorted", "diag", "asym", "range", "rowptr"])
 def test_malformed_csr_is_rejected_before_any_device_work(case):
     import paper_2402_14718_gb300 as sb

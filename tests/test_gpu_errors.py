@@ -11,6 +11,7 @@ torch = pytest.importorskip("torch")
 import paper_2402_14718_gb300 as sb
 from paper_2402_14718_gb300 import _lib
 from tests import inputs
+from tests.gpu_common import workload_qubos
 
 pytestmark = pytest.mark.gpu
 
@@ -100,3 +101,19 @@ def test_degenerate_sizes():
     sb.sb_run(ctx2, "bsb", 1.0, 0.0, 0.5, 20, 65535, 1)
     T, E, r = sb.sb_best(ctx2)
     assert 0 <= r[0] < 65535 and np.isfinite(E[0])
+
+
+def test_gather_probe_and_step_info():
+    """The gather probe returns a finite positive rate (random whole-row reads
+    of an L2-sized and of an HBM-sized array); sb_step_info reports the
+    row-group tables once a run has built them."""
+    r_small = sb.sb_gather_probe(40 << 20, 1024, 2, 3)
+    r_large = sb.sb_gather_probe(512 << 20, 512, 2, 3)
+    assert 1e11 < r_small < 1e15 and 1e11 < r_large < 1e15
+    _, qc, _, _ = workload_qubos("event500")
+    ctx = sb.sb_create(qc.n, qc.rowptr, qc.col, qc.val, qc.lin, sb.SB_J_BF16)
+    assert sb.sb_step_info(ctx) == (0, 0)
+    sb.sb_run(ctx, "bsb", 1.0, 0.0, 0.5, 3, 256, seed=1)
+    rw, entries = sb.sb_step_info(ctx)
+    assert rw == 2 and qc.nnz / 2 <= entries <= qc.nnz
+    sb.sb_destroy(ctx)
