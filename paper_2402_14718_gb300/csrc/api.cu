@@ -725,7 +725,46 @@ RwHost build_rw(int32_t n, const int32_t* rp, const int32_t* col, int RW) {
     std::vector<char> placed((size_t)(e - b), 0);
     std::vector<int32_t> stamp((size_t)n, -1);
     int32_t ng = 0;
-    for (int32_t i = b; i < e; ++i) {
+    if (RW == 2) {
+      // The union entries of a pair are deg i + deg j - |N(i) & N(j)|, so the
+      // pairing that reads the fewest rows is a maximum-weight matching with
+      // the common-neighbour counts as weights. Greedy by decreasing weight over
+      // the candidate pairs (neighbours within the part and the next seven
+      // rows), ties by row order; zero-weight pairs last, so that rows still
+      // share a warp. Groups follow in order of their first row.
+      struct Cand {
+        int32_t w, i, j;
+      };
+      std::vector<Cand> cands;
+      for (int32_t i = b; i < e; ++i) {
+        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) stamp[col[p]] = i;
+        auto add = [&](int32_t j) {
+          int32_t w = 0;
+          for (int32_t p = rp[j]; p < rp[j + 1]; ++p) w += stamp[col[p]] == i;
+          cands.push_back({w, i, j});
+        };
+        for (int32_t p = rp[i]; p < rp[i + 1]; ++p)
+          if (col[p] > i && col[p] < e) add(col[p]);
+        for (int32_t j = i + 1; j < std::min(e, i + 8); ++j)
+          if (stamp[j] != i) add(j);  // not a neighbour: not added above
+      }
+      std::stable_sort(cands.begin(), cands.end(),
+                       [](const Cand& x, const Cand& y) { return x.w > y.w; });
+      std::vector<int32_t> mate((size_t)(e - b), -1);
+      for (const Cand& c : cands)
+        if (mate[c.i - b] < 0 && mate[c.j - b] < 0) {
+          mate[c.i - b] = c.j;
+          mate[c.j - b] = c.i;
+        }
+      for (int32_t i = b; i < e; ++i) {
+        const int32_t m = mate[i - b];
+        if (m >= 0 && m < i) continue;  // placed with its partner
+        q.rows.push_back(i);
+        q.rows.push_back(m);
+        ++ng;
+      }
+    }
+    for (int32_t i = b; i < e && RW != 2; ++i) {
       if (placed[i - b]) continue;
       placed[i - b] = 1;
       const size_t g0 = q.rows.size();
