@@ -136,3 +136,24 @@ def test_large_malformed_csr_reports_the_first_bad_row(case):
         sb.sb_create(n, rowptr, col, val, lin)
     assert ei.value.code == code
     assert want in sb.lib.sb_last_error().decode()
+
+
+def test_binding_constants_match_the_header():
+    """Every SB_OPT_* value and the status / variant / precision enums of
+    include/sb.h equal the binding's constants."""
+    from paper_2402_14718_gb300 import _lib
+    text = open(os.path.join(ROOT, "include", "sb.h")).read()
+    opts = dict(re.findall(r"^#define (SB_OPT_[A-Z0-9_]+) (\d+)", text, flags=re.M))
+    assert opts, "no SB_OPT_* in the header"
+    for name, value in opts.items():
+        assert getattr(_lib, name) == int(value), name
+    body = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    for enum in re.findall(r"typedef enum\s*\{(.*?)\}", body, flags=re.S):
+        value = -1
+        for item in enum.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            name, _, expr = item.partition("=")
+            value = int(expr) if expr.strip() else value + 1
+            assert getattr(_lib, name.strip()) == value, name
