@@ -743,8 +743,15 @@ RwHost build_rw(int32_t n, const int32_t* rp, const int32_t* col, int RW) {
           for (int32_t p = rp[j]; p < rp[j + 1]; ++p) w += stamp[col[p]] == i;
           cands.push_back({w, i, j});
         };
-        for (int32_t p = rp[i]; p < rp[i + 1]; ++p)
-          if (col[p] > i && col[p] < e) add(col[p]);
+        // at most 192 neighbour candidates per row (the weights cost the sum of
+        // the candidates' degrees; track QUBO rows have up to ~300 neighbours,
+        // a dense QUBO could have thousands)
+        int32_t taken = 0;
+        for (int32_t p = rp[i]; p < rp[i + 1] && taken < 192; ++p)
+          if (col[p] > i && col[p] < e) {
+            add(col[p]);
+            ++taken;
+          }
         for (int32_t j = i + 1; j < std::min(e, i + 8); ++j)
           if (stamp[j] != i) add(j);  // not a neighbour: not added above
       }
