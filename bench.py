@@ -97,7 +97,7 @@ def job_value(units_per_rank, world_size, ms):
 # replica tile) and that kernel's sources (sha256 prefix, kernel_source_hash);
 # any other combination reports null.
 MEASURED_TRAFFIC = {
-    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "a2e01c40c1d8718c"): 90944256 + 37262592,
+    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "4594a2ea3d3969fb"): 90862592 + 37640704,
     ("event1000", "dsb", "k_step_dsb16", (0, 0, 0), "4236c91a6c79f841"): 100602368 + 39244032,
 }
 
