@@ -99,6 +99,8 @@ def job_value(units_per_rank, world_size, ms):
 MEASURED_TRAFFIC = {
     ("event1000", "bsb", "k_step_rw", (2, 0, 0), "4594a2ea3d3969fb"): 90862592 + 37640704,
     ("event1000", "dsb", "k_step_dsb16", (0, 0, 0), "4236c91a6c79f841"): 100602368 + 39244032,
+    # to the 10 MB that ncu prints at this size
+    ("batch512", "dsb", "k_step_dsb16", (0, 0, 0), "4236c91a6c79f841"): 4280000000 + 3220000000,
 }
 
 
@@ -702,6 +704,16 @@ def run_batch(args):
     ctx = sb.sb_create_batch([(q.rowptr, q.col, q.val, q.lin) for q in qs], sb.SB_J_BF16)
     if args.dsb_signs >= 0:
         sb.sb_set_option(ctx, sb.SB_OPT_DSB_SIGNS, args.dsb_signs)
+    if args.profile_steps:
+        # profiling driver: the library's default step (the autotuner's pick on
+        # this batch), one direct launch per step, no timing
+        sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
+        sb.sb_run(ctx, variant, a0, 0.0, dt, 0, R, 1, None, stream)
+        sch = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
+        sb.sb_advance(ctx, variant, a0, 0.0, dt, min(args.profile_steps, S), sch, stream)
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"profile_steps": args.profile_steps, "sum_N": NS, "sum_nnz": NZ, "R": R}))
+        return 0
     cfg, us = sb.sb_autotune(ctx, variant, R, trial_steps=20)
     sched = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
     E = len(qs)
@@ -764,7 +776,11 @@ def run_batch(args):
                        "replicas": R, "sb_steps": S, "variant": variant, "J": "bf16",
                        "autotune": cfg, "autotune_us_per_step": us, "host_build_s": t_build},
             "roofline": {"bound": "hbm", "achieved": alg_bytes / sweep / 1e9, "peak": hbm,
-                         "unit": "GB/s", "frac": alg_bytes / sweep / 1e9 / hbm, "traffic": None,
+                         "unit": "GB/s", "frac": alg_bytes / sweep / 1e9 / hbm,
+                         "traffic": MEASURED_TRAFFIC.get(
+                             ("batch512", variant, tuned_kernel(cfg, variant, R, args.dsb_signs),
+                              (cfg["rows_per_warp"], cfg["rows_per_cta"], cfg["tile"]),
+                              kernel_source_hash(tuned_kernel(cfg, variant, R, args.dsb_signs)))),
                          "kernel": tuned_kernel(cfg, variant, R, args.dsb_signs),
                          "peak_source": src,
                          "alg_bytes_per_launch": alg_bytes,
