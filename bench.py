@@ -101,6 +101,7 @@ MEASURED_TRAFFIC = {
     ("event1000", "dsb", "k_step_dsb16", (0, 0, 0), "4236c91a6c79f841"): 100602368 + 39244032,
     # to the 10 MB that ncu prints at this size
     ("batch512", "dsb", "k_step_dsb16", (0, 0, 0), "4236c91a6c79f841"): 4280000000 + 3220000000,
+    ("batch512", "dsb", "k_step_dsb16", (0, 32, 0), "4236c91a6c79f841"): 4280000000 + 3220000000,
 }
 
 
@@ -708,6 +709,8 @@ def run_batch(args):
         # profiling driver: the library's default step (the autotuner's pick on
         # this batch), one direct launch per step, no timing
         sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
+        if args.rows_per_cta:
+            sb.sb_set_option(ctx, sb.SB_OPT_STEP_RPC, args.rows_per_cta)
         sb.sb_run(ctx, variant, a0, 0.0, dt, 0, R, 1, None, stream)
         sch = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
         sb.sb_advance(ctx, variant, a0, 0.0, dt, min(args.profile_steps, S), sch, stream)
