@@ -339,25 +339,31 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
  * cudaFree is not acceptable). It calls no cudaMalloc, cudaFree or allocating
  * library routine, and needs no sb_ctx.
  *
- * Inputs (device pointers, one QUBO): the CSR of Eq. 13 as for sb_create
- * (rowptr[n+1], col[nnz], qval[nnz] = b_ij; not validated here), qlin[n] = a_i,
- * and exactly one of x (FP32 [n x R], T_i = 1 iff x > 0) or spins (int8
- * [n x R], T_i = 1 iff spin > 0), both replica-minor.
+ * Inputs (device pointers, one QUBO): the same CSR and linear terms as
+ * sb_create takes (rowptr[n+1], col[nnz], qval[nnz], qlin[n]; not validated
+ * here, all four required), and exactly one of x (FP32 [n x R], T_i = 1 iff
+ * x > 0) or spins (int8 [n x R], T_i = 1 iff spin > 0), both replica-minor.
  * Outputs (device): E[R] (QUBO energies, FP64); best_E[1] and best_r[1] (both
- * or neither). Asynchronous on `stream`.
+ * or neither). Asynchronous on `stream`. A NULL required pointer, or sizes
+ * beyond the scratch, return SB_ERR_ARG before anything is launched.
  *
- * Scratch: a static device array of 8 MiB inside the library, held by every
- * GPU that loads the library until the process exits. A call needs
+ * Scratch: a static device array of 8 MiB inside the library. A call needs
  * 8 * ceil(n / B) * R bytes of it plus a small row table (B = 64 rows when
  * R >= 16, 128 or 256 for fewer replicas): e.g. n <= 261,000 rows at R = 256.
  * Larger problems are rejected with SB_ERR_ARG and a message (use sb_energy or
- * sb_readout_device, which allocate). The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture. Every call on a device
- * shares the one array and it keeps the last call's contents (each call
- * writes every scratch entry it reads, so nothing needs clearing); calls that
- * overlap on the GPU (other streams, other threads) race on it and must be
- * serialised by the caller.
+ * sb_readout_device, which allocate).
+ * First call on a device: the array sits in its own code module, which CUDA
+ * loads lazily, so the first call in a context loads that module and commits
+ * the 8 MiB there (a driver allocation, which can synchronise the device or
+ * fail when device memory is exhausted). Make that first call while memory is
+ * still available and no stream is being captured. The array's device address
+ * is then cached per device and context and looked up again when the calling
+ * thread's current context changes (e.g. after cudaDeviceReset); the array
+ * stays committed until that context is destroyed.
+ * Sharing: every call in a context uses the one array and it keeps the last
+ * call's contents (each call writes every scratch entry it reads, so nothing
+ * needs clearing); calls that overlap on the GPU (other streams, other
+ * threads) race on it and must be serialised by the caller.
  */
 sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col,
                             const double* qval, const double* qlin, const float* x,
@@ -405,9 +411,10 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
  * tile of 256, 128 or 64 replicas) into a shared-memory ring with bulk
  * asynchronous copies and eight consumer warps (four rows each) accumulate
  * from it. Same FMA order as the untiled kernel, so the states are identical.
- * Its waits are bounded (2 s): if one gives up, the kernel returns early and
- * the next of sb_best, sb_energy (current state) or sb_get_state returns
- * SB_ERR_TIMEOUT once (the state of that run is not valid).
+ * Its waits are bounded (SB_OPT_WAIT_NS, 2 s by default): if one gives up,
+ * the kernel returns early and the next of sb_best, sb_energy (current state)
+ * or sb_get_state returns SB_ERR_TIMEOUT once (the state of that run is not
+ * valid; the context stays usable).
  * Applies to every variant (dSB gathers FP32 positions on this path). */
 #define SB_OPT_STREAM 8
 /* SB_OPT_ROWS_PER_WARP (9): 2 or 4 uses the row-group step kernel when R is a
@@ -434,6 +441,18 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
  * does (same states). 0: one thread per row. -1 (default): the widest group
  * for which rows x lanes fit in the SMs' resident threads, else 0. */
 #define SB_OPT_R1_LANES 11
+/* SB_OPT_WAIT_NS (12): limit, in nanoseconds of the GPU's global timer, of
+ * every wait of the streamed step kernel (SB_OPT_STREAM) on its shared-memory
+ * pipeline; 2e9 (2 s) by default, accepted in [1e3, 6e10]. */
+#define SB_OPT_WAIT_NS 12
+/* SB_OPT_TEST_SKIP_STAGE (13): test hook of the time-out path of the streamed
+ * step kernel. A stage index s >= 0 makes the producer warp of CTA 0 leave
+ * its s-th ring stage unissued (no barrier arrival, no copy started), so the
+ * consumer warps' wait for that stage runs out after SB_OPT_WAIT_NS, they
+ * record the time-out and return, and the producer drains its copies in
+ * flight with a bound and returns. -1 (default) turns it off. Nothing
+ * faults or hangs either way: every wait is bounded. */
+#define SB_OPT_TEST_SKIP_STAGE 13
 sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
 
 /*

@@ -12,15 +12,16 @@ import numpy as np
 
 from . import _lib
 from ._lib import (SB_ASB, SB_BSB, SB_DSB, SB_J_BF16, SB_J_FP32, SB_OPT_DSB_SIGNS, SB_OPT_GRAPH,
-                   SB_OPT_HEAVY_FIRST, SB_OPT_L2_PERSIST, SB_OPT_R1_LANES, SB_OPT_REPLICA_GROUPS, SB_OPT_ROWS_PER_WARP,
-                   SB_OPT_STEP_RPC,
-                   SB_OPT_STEP_RT, SB_OPT_STEP_UNROLL, SB_OPT_STREAM, SB_OPT_TILED, SbError, check,
-                   lib)
+                   SB_OPT_HEAVY_FIRST, SB_OPT_L2_PERSIST, SB_OPT_R1_LANES, SB_OPT_REPLICA_GROUPS,
+                   SB_OPT_ROWS_PER_WARP, SB_OPT_STEP_RPC, SB_OPT_STEP_RT, SB_OPT_STEP_UNROLL,
+                   SB_OPT_STREAM, SB_OPT_TEST_SKIP_STAGE, SB_OPT_TILED, SB_OPT_WAIT_NS, SbError,
+                   check, lib)
 
 __all__ = [
     "SB_ASB", "SB_BSB", "SB_DSB", "SB_J_FP32", "SB_J_BF16", "SB_OPT_GRAPH", "SB_OPT_TILED",
     "SB_OPT_STREAM", "SB_OPT_ROWS_PER_WARP", "SB_OPT_HEAVY_FIRST", "SB_OPT_R1_LANES", "SB_OPT_STEP_RT", "SB_OPT_STEP_RPC",
-    "SB_OPT_STEP_UNROLL", "SB_OPT_DSB_SIGNS", "SB_OPT_REPLICA_GROUPS", "SB_OPT_L2_PERSIST", "SbError",
+    "SB_OPT_STEP_UNROLL", "SB_OPT_DSB_SIGNS", "SB_OPT_REPLICA_GROUPS", "SB_OPT_L2_PERSIST",
+    "SB_OPT_WAIT_NS", "SB_OPT_TEST_SKIP_STAGE", "SbError",
     "event_params", "build_params", "sb_event_generate", "sb_qubo_build", "sb_tracks",
     "sb_qubo_build_device",
     "sb_create", "sb_create_batch", "sb_destroy", "sb_info", "sb_step_info", "sb_gather_probe",

@@ -1,7 +1,10 @@
 """ctypes declarations of the C ABI in include/sb.h (argument marshalling only).
 
-Loading builds the in-tree library first if it is missing or older than its
-sources; if that fails the import fails: there is no fallback path.
+The library is loaded on the first call through ``lib`` (importing the package
+alone loads nothing, so the numbers-only module ``workloads`` can be imported
+without it). Loading builds the in-tree library first if it is missing or
+older than its sources; if that fails the call raises: there is no fallback
+path.
 """
 import ctypes
 import os
@@ -27,6 +30,8 @@ SB_OPT_STREAM = 8
 SB_OPT_ROWS_PER_WARP = 9
 SB_OPT_HEAVY_FIRST = 10
 SB_OPT_R1_LANES = 11
+SB_OPT_WAIT_NS = 12
+SB_OPT_TEST_SKIP_STAGE = 13
 
 
 class SbEventParams(ctypes.Structure):
@@ -115,7 +120,27 @@ def _load():
     return lib
 
 
-lib = _load()
+class _Lib:
+    """The loaded library, on first attribute access; each resolved entry
+    point is cached on the instance."""
+
+    def __init__(self):
+        self._dll = None
+
+    def __getattr__(self, name):
+        if name.startswith("__"):
+            raise AttributeError(name)
+        if self.__dict__.get("_dll") is None:
+            self.__dict__["_dll"] = _load()
+        fn = getattr(self._dll, name)
+        setattr(self, name, fn)
+        return fn
+
+    def loaded(self):
+        return self.__dict__.get("_dll") is not None
+
+
+lib = _Lib()
 LIB_PATH = _build.LIB
 
 

@@ -171,6 +171,8 @@ struct sb_ctx {
   int32_t* d_s_ucol = nullptr;
   uint32_t* d_s_umask = nullptr;
   int* d_err = nullptr;  // set by a kernel whose bounded wait gave up
+  unsigned long long wait_ns = 2000000000ull;  // limit of the streamed kernel's waits
+  int32_t skip_stage = -1;  // test hook of the streamed kernel (SB_OPT_TEST_SKIP_STAGE)
   // row-group step kernel (k_step_rw): groups of RW rows and their union entries
   int rw_rows = -1;      // -1: automatic (2 for aSB / bSB, off for dSB); 0: off; 2 or 4
   // dispatch the row-group CTAs heaviest chunk first: 1 on, 0 off, -1 when
@@ -1201,6 +1203,8 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     sa.tiles = c->R / sa.W;
     sa.jbuf_bytes = c->stream_jbuf;
     sa.err = c->d_err;
+    sa.wait_ns = c->wait_ns;
+    sa.skip_stage = c->skip_stage;
   }
   // the 16-replica dSB kernel exists only with sign bytes: its tiling and the
   // byte condition below must agree
@@ -2264,6 +2268,22 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value) {
         return SB_OK;
       case 8:  // SB_OPT_STREAM
         ctx->use_stream = value != 0;
+        ctx->graph.reset();
+        return SB_OK;
+      case 12:  // SB_OPT_WAIT_NS
+        if (value < 1000 || value > 60000000000ll) {
+          set_error("sb_set_option: SB_OPT_WAIT_NS must be in [1e3, 6e10] nanoseconds");
+          return SB_ERR_ARG;
+        }
+        ctx->wait_ns = (unsigned long long)value;
+        ctx->graph.reset();
+        return SB_OK;
+      case 13:  // SB_OPT_TEST_SKIP_STAGE
+        if (value < -1 || value > (1 << 30)) {
+          set_error("sb_set_option: SB_OPT_TEST_SKIP_STAGE must be -1 or a stage index");
+          return SB_ERR_ARG;
+        }
+        ctx->skip_stage = (int32_t)value;
         ctx->graph.reset();
         return SB_OK;
       case 6:  // SB_OPT_REPLICA_GROUPS

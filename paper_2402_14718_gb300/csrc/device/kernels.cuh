@@ -209,6 +209,10 @@ struct StreamArgs {
   int32_t nst;               // ring stages
   int32_t jbuf_bytes;        // bytes of each of the two J staging buffers (multiple of 16)
   int* err;                  // set non-zero when a wait gives up (the kernel then returns)
+  unsigned long long wait_ns;  // limit of every wait (globaltimer nanoseconds)
+  // test hook: CTA 0's producer issues nothing for this stage (no arrival, no
+  // copy), so the consumers' wait for it runs out; -1: off
+  int32_t skip_stage;
 };
 
 // Replica-tile width of the streamed kernel for R replicas (0: not supported).

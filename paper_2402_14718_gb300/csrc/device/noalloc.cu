@@ -3,9 +3,14 @@
 //
 // Its scratch -- the block row table and the per-block partial energies that
 // the readout kernels need between their two passes -- lives in the
-// file-scope array g_scratch below (kScratchBytes per GPU, held by every GPU
-// that loads the library until the process exits). Nothing here calls
-// cudaMalloc, cudaFree or any allocating library routine.
+// file-scope array g_scratch below (kScratchBytes per GPU). This file is its
+// own module (the library is linked without relocatable device code), and
+// CUDA loads modules lazily: the first call on a device loads the module and
+// commits the array there (a driver allocation that can synchronise); from
+// then on the array stays committed in that context until the process exits
+// or the context is destroyed. Nothing here calls cudaMalloc, cudaFree or any
+// allocating library routine.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -25,11 +30,59 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Device address of g_scratch, looked up once per device with that device
-// current (in host code the symbol is only a host-side stand-in).
-void* g_scratch_addr[kMaxDevices];
+// Device address of g_scratch, looked up with the device current (in host
+// code the symbol is only a host-side stand-in). The address belongs to the
+// context the module was loaded in: it is cached per device together with
+// that context, and looked up again when the current context differs (after
+// cudaDeviceReset the primary context, and with it the module, is new).
+struct ScratchSlot {
+  CUcontext ctx;
+  void* addr;
+};
+ScratchSlot g_slot[kMaxDevices];
 std::mutex g_scratch_mu;
 
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+
+// cuCtxGetCurrent through the runtime's driver entry point (no link against
+// libcuda, so the library still loads on machines without a driver). Writes
+// NULL when no context is current yet.
+sb_status current_context(CUcontext* out) {
+  static CtxGetCurrentFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) {
+      sbh::set_error(std::string("sb_energy_noalloc: cuCtxGetCurrent entry point: ") +
+                     cudaGetErrorString(e));
+      return SB_ERR_CUDA;
+    }
+    fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  }
+  CUcontext c = nullptr;
+  if (fn(&c) != CUDA_SUCCESS) {
+    sbh::set_error("sb_energy_noalloc: cuCtxGetCurrent failed");
+    return SB_ERR_CUDA;
+  }
+  *out = c;
+  return SB_OK;
+}
+
+sb_status symbol_address(void** p) {
+  cudaError_t e = cudaGetSymbolAddress(p, g_scratch);
+  if (e != cudaSuccess || !*p) {
+    sbh::set_error(std::string("sb_energy_noalloc: cudaGetSymbolAddress: ") +
+                   cudaGetErrorString(e));
+    return SB_ERR_CUDA;
+  }
+  return SB_OK;
+}
+
+// The scratch address in the calling thread's current context (the caller's
+// own context if one is current, else the device's primary context, which
+// the runtime creates on first use).
 sb_status scratch_address(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -42,17 +95,28 @@ sb_status scratch_address(void** out) {
     return SB_ERR_ARG;
   }
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || !p) {
-      sbh::set_error(std::string("sb_energy_noalloc: cudaGetSymbolAddress: ") +
-                     cudaGetErrorString(e));
+  CUcontext ctx = nullptr;
+  sb_status st = current_context(&ctx);
+  if (st) return st;
+  void* p = nullptr;
+  if (!ctx) {  // nothing current yet: the runtime's first call makes the primary context
+    st = symbol_address(&p);
+    if (st) return st;
+    st = current_context(&ctx);
+    if (st) return st;
+    if (!ctx) {
+      sbh::set_error("sb_energy_noalloc: no current CUDA context");
       return SB_ERR_CUDA;
     }
-    g_scratch_addr[dev] = p;
+    g_slot[dev].addr = p;
+    g_slot[dev].ctx = ctx;
+  } else if (!g_slot[dev].addr || g_slot[dev].ctx != ctx) {
+    st = symbol_address(&p);
+    if (st) return st;
+    g_slot[dev].addr = p;
+    g_slot[dev].ctx = ctx;
   }
-  *out = g_scratch_addr[dev];
+  *out = g_slot[dev].addr;
   return SB_OK;
 }
 
@@ -76,10 +140,12 @@ extern "C" sb_status sb_energy_noalloc(int32_t n, const int32_t* d_rowptr, const
                                        const float* d_x, const int8_t* d_spins, int32_t replicas,
                                        double* d_E, double* d_best_E, int32_t* d_best_r,
                                        void* stream) {
-  if (n < 1 || !d_rowptr || !d_qlin || !d_E || replicas < 1 || replicas > 65535 ||
+  if (n < 1 || !d_rowptr || !d_col || !d_qval || !d_qlin || !d_E || replicas < 1 ||
+      replicas > 65535 ||
       ((d_x == nullptr) == (d_spins == nullptr)) || ((d_best_E == nullptr) != (d_best_r == nullptr))) {
     sbh::set_error(
-        "sb_energy_noalloc: need n >= 1, rowptr, qlin, E, 1 <= replicas <= 65535, exactly one of "
+        "sb_energy_noalloc: need n >= 1, rowptr, col, qval, qlin, E, 1 <= replicas <= 65535, "
+        "exactly one of "
         "x / spins, and best_E and best_r both given or both NULL");
     return SB_ERR_ARG;
   }

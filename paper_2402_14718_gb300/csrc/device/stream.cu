@@ -18,9 +18,12 @@
 // column), one FMA per nonzero, as in k_step: both kernels give identical
 // results.
 //
-// Every wait is bounded: after kWaitNs (or once another warp has given up) a
-// warp records a code in *err and returns; the producer first waits, again
-// with a bound, for its copies still in flight.
+// Every wait is bounded: after a.wait_ns (2 s by default; or once another
+// warp has given up) a warp records a code in *err and returns; the producer
+// first waits, again with a bound, for its copies still in flight. A test
+// hook (a.skip_stage) makes CTA 0's producer leave one stage unissued -- no
+// arrival and no copy, so nothing is in flight for it -- which runs the
+// consumers' wait for that stage out.
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
@@ -29,7 +32,6 @@
 namespace sbd {
 namespace {
 
-constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
 constexpr unsigned long long kDrainNs = 200000000ull;   // 0.2 s
 constexpr int kSmemBudgetCap = 232448;                  // 227 KB opt-in per block
 
@@ -78,8 +80,9 @@ __device__ __forceinline__ unsigned long long now_ns() {
 }
 
 // The whole warp waits for the completion of phase parity `par` of `bar`.
-// Returns false (the warp must leave) after kWaitNs, or as soon as *err is set.
-__device__ bool warp_wait(uint32_t bar, uint32_t par, int* err, int code) {
+// Returns false (the warp must leave) after limit_ns, or as soon as *err is set.
+__device__ bool warp_wait(uint32_t bar, uint32_t par, int* err, int code,
+                          unsigned long long limit_ns) {
   if (__all_sync(0xffffffffu, mbar_try(bar, par))) return true;
   const unsigned long long t0 = now_ns();
   for (uint32_t it = 1;; ++it) {
@@ -89,7 +92,7 @@ __device__ bool warp_wait(uint32_t bar, uint32_t par, int* err, int code) {
       if ((threadIdx.x & 31) == 0) {
         if (*(volatile int*)err != 0) {
           quit = 1;
-        } else if (now_ns() - t0 > kWaitNs) {
+        } else if (now_ns() - t0 > limit_ns) {
           atomicCAS(err, 0, code);
           quit = 1;
         }
@@ -100,15 +103,19 @@ __device__ bool warp_wait(uint32_t bar, uint32_t par, int* err, int code) {
 }
 
 // Producer exit: wait (bounded, whatever *err says) until the copies of the
-// last use of every ring stage and both J buffers have landed.
-__device__ void drain(uint32_t full0, int nst, int issued) {
+// last use of every ring stage and both J buffers have landed. A stage that
+// was never issued (the test hook) is skipped: nothing of it is in flight.
+__device__ void drain(uint32_t full0, int nst, int issued, int skipped,
+                      unsigned long long limit_ns) {
+  const unsigned long long lim = limit_ns < kDrainNs ? limit_ns : kDrainNs;
   const int first = issued > nst ? issued - nst : 0;
   for (int g = first; g < issued; ++g) {
+    if (g == skipped) continue;
     const uint32_t bar = full0 + 8u * (uint32_t)(g % nst);
     const uint32_t par = (uint32_t)((g / nst) & 1);
     const unsigned long long t0 = now_ns();
     while (!__all_sync(0xffffffffu, mbar_try(bar, par))) {
-      if (now_ns() - t0 > kDrainNs) break;
+      if (now_ns() - t0 > lim) break;
     }
   }
 }
@@ -211,6 +218,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_step_stream(const StreamA
     }
     int g = 0;  // stages issued
     bool ok = true;
+    const int skip = blockIdx.x == 0 ? a.skip_stage : -1;
     int4 d0 = first, d1 = a.blk[b0 + 1];
     for (int t = 0; t < a.tiles && ok; ++t) {
       const float* xt = a.xin + (size_t)t * W;
@@ -219,7 +227,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_step_stream(const StreamA
         const int jb = lb & 1;
         const int bn = bi + 1 < nb ? b0 + bi + 1 : b0;  // next block (next tile: first block)
         const int4 n0 = a.blk[bn], n1 = a.blk[bn + 1];
-        if (lb >= 2 && !warp_wait(jempty0 + 8u * jb, (uint32_t)(((lb >> 1) - 1) & 1), a.err, 1)) {
+        if (lb >= 2 &&
+            !warp_wait(jempty0 + 8u * jb, (uint32_t)(((lb >> 1) - 1) & 1), a.err, 1, a.wait_ns)) {
           ok = false;
           break;
         }
@@ -227,7 +236,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_step_stream(const StreamA
         for (int s = 0; s < nstg; ++s, ++g) {
           const int slot = g % nst;
           const int use = g / nst;
-          if (use >= 1 && !warp_wait(empty0 + 8u * slot, (uint32_t)((use - 1) & 1), a.err, 2)) {
+          if (use >= 1 &&
+              !warp_wait(empty0 + 8u * slot, (uint32_t)((use - 1) & 1), a.err, 2, a.wait_ns)) {
             ok = false;
             break;
           }
@@ -243,6 +253,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_step_stream(const StreamA
             qc[PF - 1] = __ldg(a.ucol + e);
             qm[PF - 1] = __ldg(a.umask + e);
           }
+          if (g == skip) continue;  // test hook: this stage is never issued
           meta[slot * SPS + lane] = m;
           const unsigned cp = __ballot_sync(0xffffffffu, m != 0);
           const uint32_t jbytes = s == 0 ? (uint32_t)d0.w : 0u;
@@ -263,7 +274,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_step_stream(const StreamA
         d1 = n1;
       }
     }
-    drain(full0, nst, g);
+    drain(full0, nst, g, skip, a.wait_ns);
     return;
   }
 
@@ -320,7 +331,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_step_stream(const StreamA
       for (int e = d0.y; e < d1.y; e += SPS, ++g) {
         const int slot = g % nst;
         const int use = g / nst;
-        if (!warp_wait(full0 + 8u * slot, (uint32_t)(use & 1), a.err, 3)) return;
+        if (!warp_wait(full0 + 8u * slot, (uint32_t)(use & 1), a.err, 3, a.wait_ns)) return;
         const uint32_t mk = (meta[slot * SPS + lane] >> sh) & ((1u << RW) - 1u);
         unsigned act = __ballot_sync(0xffffffffu, mk != 0);
         const float* sb = reinterpret_cast<const float*>(ring + (size_t)slot * SPS * SLOTB);

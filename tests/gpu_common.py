@@ -6,6 +6,7 @@ import numpy as np
 import paper_2402_14718_gb300 as sb
 from paper_2402_14718_gb300.workloads import WORKLOADS
 from oracle import events as oev
+from oracle import ising
 from oracle import qubo as oq
 
 
@@ -26,6 +27,14 @@ def workload_qubos(name):
                                                   noise_frac=w["noise_frac"]))
     qo = oq.build_qubo(ev_o, oracle_params(w["cuts"]))
     return ev_c, qc, ev_o, qo
+
+
+def oracle_c0(qo):
+    """c0 = 0.5 / (sqrt(N) sigma_J) computed by the oracle from its own QUBO;
+    both sides of a parity test take this value (the library's own c0 is
+    compared with it separately)."""
+    J = ising.to_ising(qo)[0]
+    return ising.c0_auto(J, qo.n)
 
 
 def max_rel(a, ref):

@@ -23,7 +23,7 @@ import paper_2402_14718_gb300 as sb
 from paper_2402_14718_gb300.workloads import BATCH512, batch512_tracks
 from oracle import events as oev, ising, qubo as oq, sb as osb
 from tests import inputs
-from tests.gpu_common import compare_step, oracle_params, workload_qubos
+from tests.gpu_common import compare_step, oracle_params, workload_qubos, oracle_c0
 from tests.test_gpu_parity import _oracle_J, _sched
 
 pytestmark = pytest.mark.gpu
@@ -36,7 +36,7 @@ def test_full_size_event10k_builder_and_step_sampled():
     assert np.array_equal(qc.val, qo.val) and np.array_equal(qc.lin, qo.lin)
     R = 128
     ctx = sb.sb_create(qc.n, qc.rowptr, qc.col, qc.val, qc.lin, sb.SB_J_BF16)
-    c0 = sb.sb_info(ctx)["c0_auto"]
+    c0 = oracle_c0(qo)
     x0, y0 = inputs.random_state(qo.n, R, 91, 0.9)
     J, h, _ = _oracle_J(qo, sb.SB_J_BF16)
     rows = np.random.default_rng(1).choice(qo.n, 300, replace=False)

@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 import paper_2402_14718_gb300 as sb
 from oracle import ising, sb as osb, tracks as otr
 from tests import inputs
-from tests.gpu_common import compare_step, max_rel, workload_qubos
+from tests.gpu_common import compare_step, max_rel, workload_qubos, oracle_c0
 
 pytestmark = pytest.mark.gpu
 VARIANTS = [osb.ASB, osb.BSB, osb.DSB]
@@ -97,8 +97,7 @@ def _one_step_case(q, qo, prec, variant, R, seed, a_k, scale, graph=False):
     ctx = _ctx(q, prec)
     if not graph:
         sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
-    info = sb.sb_info(ctx)
-    c0 = info["c0_auto"]
+    c0 = oracle_c0(qo)
     x0, y0 = inputs.random_state(qo.n, R, seed, scale)
     sb.sb_set_state(ctx, x0, y0)
     sb.sb_advance(ctx, variant, 1.0, c0, 0.5, 1, _sched([a_k]))
@@ -145,7 +144,7 @@ def test_short_horizon_from_seeded_start(variant):
     dt = 0.1 if variant == osb.ASB else 0.5
     ctx = _ctx(qc)
     sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
-    c0 = sb.sb_info(ctx)["c0_auto"]
+    c0 = oracle_c0(qo)
     sched = np.float32(np.linspace(0.0, 1.0, 2000))[:S]
     J, h, _ = ising.to_ising(qo)
     # free-running trajectories
@@ -208,7 +207,7 @@ def test_full_size_event1000_step_sampled():
     _, qc, _, qo = workload_qubos("event1000")
     R = 256
     ctx = _ctx(qc, sb.SB_J_BF16)
-    c0 = sb.sb_info(ctx)["c0_auto"]
+    c0 = oracle_c0(qo)
     x0, y0 = inputs.random_state(qo.n, R, 77, 0.9)
     J, h, _ = _oracle_J(qo, sb.SB_J_BF16)
     rows = np.random.default_rng(0).choice(qo.n, 300, replace=False)
@@ -252,7 +251,7 @@ def test_final_energy_statistics_64_replicas(variant):
     ev_c, qc, ev_o, qo = workload_qubos("event100")
     R, S = 64, 2000
     ctx = _ctx(qc)
-    c0 = sb.sb_info(ctx)["c0_auto"]
+    c0 = oracle_c0(qo)
     sb.sb_run(ctx, variant, 1.0, c0, 0.5, S, R, seed=2024)
     E_gpu = sb.sb_energy(ctx, None, R)[0]
     J, h, _ = ising.to_ising(qo)
@@ -290,8 +289,8 @@ def test_batch_matches_oracle_per_event():
         xo, yo = osb.init_state(31, q.n, R, event=e)
         assert np.array_equal(x0[sl].astype(np.float64), xo)
         J, h, _ = ising.to_ising(q)
-        c0 = sb.sb_info(ctx, e)["c0_auto"]
-        assert c0 == pytest.approx(ising.c0_auto(J, q.n), rel=1e-12)
+        c0 = ising.c0_auto(J, q.n)
+        assert sb.sb_info(ctx, e)["c0_auto"] == pytest.approx(c0, rel=1e-12)
         xn, yn = osb.step(J, h, xo, yo, float(np.float32(0.4)), 1.0, c0, 0.5, osb.BSB)
         assert max_rel(x1[sl], xn) < 1e-5 and max_rel(y1[sl], yn) < 1e-5
         np.testing.assert_allclose(E[e], ising.qubo_energy(q, spins[sl]), rtol=1e-12, atol=1e-12)

@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 import paper_2402_14718_gb300 as sb
 from oracle import sb as osb
 from tests import inputs
-from tests.gpu_common import compare_step, workload_qubos
+from tests.gpu_common import compare_step, workload_qubos, oracle_c0
 from tests.test_gpu_parity import _oracle_J, _sched
 
 pytestmark = pytest.mark.gpu
@@ -94,7 +94,7 @@ def test_rowgroup_one_step_against_oracle(variant):
     ctx = sb.sb_create(qc.n, qc.rowptr, qc.col, qc.val, qc.lin, sb.SB_J_FP32)
     sb.sb_set_option(ctx, sb.SB_OPT_ROWS_PER_WARP, 4)
     sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
-    c0 = sb.sb_info(ctx)["c0_auto"]
+    c0 = oracle_c0(qo)
     x0, y0 = inputs.random_state(qo.n, R, 21 + len(variant), 0.8)
     sb.sb_set_state(ctx, x0, y0)
     a_k = 0.61
@@ -192,7 +192,7 @@ def test_dsb_exact_zero_and_wall_positions_against_oracle(rw, signs):
         sb.sb_set_option(ctx, sb.SB_OPT_ROWS_PER_WARP, form[0])
         sb.sb_set_option(ctx, sb.SB_OPT_DSB_SIGNS, form[1])
         sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
-        c0 = sb.sb_info(ctx)["c0_auto"]
+        c0 = oracle_c0(qo)
         sb.sb_set_state(ctx, x0, y0)
         sb.sb_advance(ctx, "dsb", 1.0, c0, 0.5, 1, _sched([0.3]))
         outs.append(sb.sb_get_state(ctx))

@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 import paper_2402_14718_gb300 as sb
 from oracle import sb as osb
 from tests import inputs
-from tests.gpu_common import compare_step, workload_qubos
+from tests.gpu_common import compare_step, workload_qubos, oracle_c0
 from tests.test_gpu_parity import _oracle_J, _sched
 
 pytestmark = pytest.mark.gpu
@@ -58,7 +58,7 @@ def test_stream_one_step_against_oracle(variant):
     ctx = sb.sb_create(qc.n, qc.rowptr, qc.col, qc.val, qc.lin, sb.SB_J_FP32)
     sb.sb_set_option(ctx, sb.SB_OPT_STREAM, 1)
     sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
-    c0 = sb.sb_info(ctx)["c0_auto"]
+    c0 = oracle_c0(qo)
     x0, y0 = inputs.random_state(qo.n, R, 11 + len(variant), 0.8)
     sb.sb_set_state(ctx, x0, y0)
     a_k = 0.37
@@ -134,3 +134,41 @@ def test_stream_full_size_event1000():
     assert np.array_equal(xs, xu) and np.array_equal(ys, yu)
     T, E, r = sb.sb_best(ctx)
     assert 0 <= r < 256 and np.isfinite(E)
+
+
+def test_stream_wait_runs_out_and_the_context_recovers():
+    """The bounded-wait path of the streamed kernel. With the test hook, CTA 0's
+    producer leaves its first ring stage unissued (no arrival, no copy), so the
+    consumers' wait for it runs out after 1 ms; the kernel returns, the next
+    synchronising call reports SB_ERR_TIMEOUT once, and a normal run on the
+    same context then matches the untiled kernel bit for bit and the oracle."""
+    _, qc, _, qo = workload_qubos("event100")
+    R = 64
+    ctx = sb.sb_create(qc.n, qc.rowptr, qc.col, qc.val, qc.lin, sb.SB_J_FP32)
+    sb.sb_set_option(ctx, sb.SB_OPT_STREAM, 1)
+    sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
+    sb.sb_set_option(ctx, sb.SB_OPT_WAIT_NS, 1_000_000)
+    sb.sb_set_option(ctx, sb.SB_OPT_TEST_SKIP_STAGE, 0)
+    sb.sb_run(ctx, "bsb", 1.0, 0.0, 0.5, 2, R, seed=5)
+    with pytest.raises(sb.SbError) as ei:
+        sb.sb_get_state(ctx)
+    assert ei.value.code == 5 and "gave up waiting" in str(ei.value)   # SB_ERR_TIMEOUT
+    # reported once: the flag is cleared
+    sb.sb_set_option(ctx, sb.SB_OPT_TEST_SKIP_STAGE, -1)
+    sb.sb_set_option(ctx, sb.SB_OPT_WAIT_NS, 2_000_000_000)
+    c0 = oracle_c0(qo)
+    x0, y0 = inputs.random_state(qo.n, R, 29, 0.8)
+    sb.sb_set_state(ctx, x0, y0)
+    sb.sb_advance(ctx, "bsb", 1.0, c0, 0.5, 1, _sched([0.45]))
+    xg, yg = sb.sb_get_state(ctx)
+    ref = sb.sb_create(qc.n, qc.rowptr, qc.col, qc.val, qc.lin, sb.SB_J_FP32)
+    sb.sb_set_option(ref, sb.SB_OPT_GRAPH, 0)
+    sb.sb_set_state(ref, x0, y0)
+    sb.sb_advance(ref, "bsb", 1.0, c0, 0.5, 1, _sched([0.45]))
+    xu, yu = sb.sb_get_state(ref)
+    assert np.array_equal(xg, xu) and np.array_equal(yg, yu)
+    J, h, _ = _oracle_J(qo, sb.SB_J_FP32)
+    a32 = float(np.float32(0.45))
+    x64, y64 = x0.astype(np.float64), y0.astype(np.float64)
+    xo, yo = osb.step(J, h, x64, y64, a32, 1.0, c0, 0.5, osb.BSB)
+    compare_step(xg, yg, xo, yo, osb.prewall_x(J, h, x64, y64, a32, 1.0, c0, 0.5, osb.BSB))

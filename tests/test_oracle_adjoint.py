@@ -38,6 +38,7 @@ def test_adjoint_matches_central_differences(S):
     }
     base = {"dt": dt, "c0": c0, "w_q": wq, "w_c": wc}
     mkw = dict(a0=a0, c0=c0, dt=dt, w_q=wq, w_c=wc)
+    checked = []
     for name, f in checks.items():
         lo, hi = dict(mkw), dict(mkw)
         lo[name] = base[name] - h
@@ -47,6 +48,9 @@ def test_adjoint_matches_central_differences(S):
             continue  # a wall event flips inside +-h: the loss has a kink there
         fd = _fd(f, base[name], h)
         assert g[name] == pytest.approx(fd, rel=1e-5, abs=1e-7), name
+        checked.append(name)
+    # a wall kink may excuse one scalar, not all of them
+    assert len(checked) >= 3, checked
     rng = np.random.default_rng(S)
     for k in rng.choice(S, 5, replace=False):
         def fk(v, k=k):

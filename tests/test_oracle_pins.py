@@ -506,3 +506,114 @@ def test_paper_weights_on_clean_tracks():
         z_line = za - ev.r[a] * (zc - za) / (ev.r[c] - ev.r[a])
         expect = 0.2 * (1.0 - math.exp(-abs(z_line) / 0.5))   # d0 = 0 for tracks from the origin
         assert q.quality[i] == pytest.approx(expect, abs=1e-6)
+
+
+# ---------------------------------------------------------------- pins added for c0, bias, pruning, draws
+def test_sigma_j_and_c0_closed_form():
+    """Hand-built 4-variable QUBO with b_01 = b_12 = +1 (both triangles): J = -b/4
+    has k = 4 off-diagonal entries of magnitude 1/4, so the RMS over the n(n-1)
+    = 12 off-diagonal slots is sigma_J = (1/4) sqrt(4/12) and
+    c0 = 0.5 / (sqrt(4) sigma_J) = sqrt(3). A mean-subtracted std, an n^2 or an
+    nnz denominator, or one triangle only would each give another number."""
+    from tests.inputs import QuboArrays
+    q = QuboArrays(4, np.array([0, 1, 3, 4, 4], np.int32), np.array([1, 0, 2, 1], np.int32),
+                   np.array([1.0, 1.0, 1.0, 1.0]), np.zeros(4))
+    J, _, _ = ising.to_ising(q)
+    assert ising.sigma_j(J, 4) == pytest.approx(0.25 * math.sqrt(4.0 / 12.0), rel=1e-15)
+    assert ising.c0_auto(J, 4) == pytest.approx(math.sqrt(3.0), rel=1e-15)
+    # one entry of magnitude v among n = 3 variables: sigma_J = v sqrt(2 / 6)
+    q3 = QuboArrays(3, np.array([0, 1, 2, 2], np.int32), np.array([1, 0], np.int32),
+                    np.array([-2.0, -2.0]), np.zeros(3))
+    J3, _, _ = ising.to_ising(q3)
+    assert ising.sigma_j(J3, 3) == pytest.approx(0.5 * math.sqrt(2.0 / 6.0), rel=1e-15)
+    assert ising.c0_auto(J3, 3) == pytest.approx(0.5 / (math.sqrt(3.0) * 0.5 / math.sqrt(3.0)),
+                                                rel=1e-15)
+
+
+def test_default_bias_from_truth_curvature_and_angle():
+    """Default linear term of Eq. 13 (triplet-quality reading): a_i = w_q (|kappa_i| /
+    kappa_max + dtheta_i / dtheta_max) / 2, here computed from the generator's truth
+    alone -- kappa = 1 / Rc of the helix, dtheta from the truth helix's r-z points --
+    for unsmeared isolated tracks, with w_q = 1.7 and unequal cut scales so that a
+    swapped kappa_max / dtheta_max, a missing 1/2 or a dropped w_q fails."""
+    seed, ev = _separated_seed(4, 0.6)
+    kmax, tmax, wq = 2e-3, 0.2, 1.7
+    p = qubo.BuildParams(dphi_slope=1.5e-3, dphi_margin=1.0, z0_max=100, kappa_max=kmax,
+                         dtheta_max=tmax, dkappa_max=5e-4, w_q=wq)
+    q = qubo.build_qubo(ev, p)
+    assert q.n == 32
+    for i in range(q.n):
+        a, b, c = q.trip[i]
+        qq, pt, eta, phi0, z0, rc = ev.truth[ev.particle[a]]
+
+        def zs(h):
+            return math.sinh(eta) * 2 * rc * math.asin(ev.r[h] / (2 * rc))
+        th1 = math.atan2(ev.r[b] - ev.r[a], zs(b) - zs(a))
+        th2 = math.atan2(ev.r[c] - ev.r[b], zs(c) - zs(b))
+        expect = wq * 0.5 * ((1.0 / rc) / kmax + abs(th2 - th1) / tmax)
+        assert q.lin[i] == pytest.approx(expect, rel=1e-6)
+        assert q.quality[i] == pytest.approx(expect / wq, rel=1e-6)
+
+
+def _hand_event(tracks_spec):
+    """Straight radial tracks (phi, first layer, n layers), z = 0.5 r; hits sorted."""
+    radii = events.LAYER_RADII
+    hits = []
+    for t, (phi, l0, nl) in enumerate(tracks_spec):
+        for l in range(l0, l0 + nl):
+            hits.append((l, phi, 0.5 * radii[l], t))
+    hits.sort(key=lambda h: (h[0], h[1]))
+    ev = events.Event(layer=[], r=[], phi=[], z=[], x=[], y=[], particle=[], n_true=len(hits))
+    for (l, phi, z, part) in hits:
+        r = radii[l]
+        ev.layer.append(l); ev.r.append(r); ev.phi.append(phi); ev.z.append(z)
+        ev.x.append(r * math.cos(phi)); ev.y.append(r * math.sin(phi)); ev.particle.append(part)
+    return ev
+
+
+def test_pruning_keeps_only_five_hit_candidates():
+    """Pruning rule (section "QUBO Generation and Track Finding"): a quadruplet
+    must belong to a candidate of five or more hits. Three isolated straight
+    tracks of 3, 4 and 5 hits: the 3-hit track's triplet is in no quadruplet and
+    is always dropped; the 4-hit track's two triplets form one consistent pair
+    with no consistent neighbour on either side and are dropped under the rule;
+    the 5-hit track keeps its three triplets. Without the rule the 4-hit pair
+    stays."""
+    ev = _hand_event([(-2.0, 0, 3), (0.5, 2, 4), (2.5, 4, 5)])
+    base = dict(dphi_slope=1e-3, dphi_margin=1.0, z0_max=100, kappa_max=2e-3, dtheta_max=0.2,
+                dkappa_max=5e-4)
+    q = qubo.build_qubo(ev, qubo.BuildParams(five_hit_rule=True, **base))
+    parts = sorted(ev.particle[int(t[0])] for t in q.trip)
+    assert parts == [2, 2, 2]
+    assert len(q.col) == 4 and np.all(q.val == -1.0)
+    q2 = qubo.build_qubo(ev, qubo.BuildParams(five_hit_rule=False, **base))
+    parts2 = sorted(ev.particle[int(t[0])] for t in q2.trip)
+    assert parts2 == [1, 1, 2, 2, 2]
+    # the dropped triplets are exactly the ones whose pair has no consistent neighbour
+    trip = qubo.build_triplets(ev, qubo.build_doublets(ev, qubo.BuildParams(**base)),
+                               qubo.BuildParams(**base))
+    assert len(trip) == 1 + 2 + 3
+
+
+def test_track_parameter_draws_follow_the_recipe():
+    """Distribution pins of the generator's draws over 2000 tracks (Kolmogorov-
+    Smirnov against the stated laws, each also rejecting a plausible wrong law):
+    1/pT ~ U[0.1, 1] GeV^-1 (not pT ~ U[1, 10]), eta ~ U(-1, 1), phi0 ~ U[0, 2 pi),
+    z0 ~ N(0, 5 mm), q = +-1 with probability 1/2."""
+    from scipy import stats
+    ev = events.generate(2718, events.EventParams(n_tracks=2000, noise_frac=0.0))
+    q = np.array([t[0] for t in ev.truth])
+    pt = np.array([t[1] for t in ev.truth])
+    eta = np.array([t[2] for t in ev.truth])
+    phi0 = np.array([t[3] for t in ev.truth])
+    z0 = np.array([t[4] for t in ev.truth])
+    assert set(np.unique(q)) == {-1.0, 1.0} and abs(float(np.mean(q))) < 0.1
+    assert stats.kstest(1.0 / pt, lambda v: stats.uniform.cdf(v, 0.1, 0.9)).pvalue > 1e-3
+    assert stats.kstest(pt, lambda v: stats.uniform.cdf(v, 1.0, 9.0)).pvalue < 1e-6
+    assert pt.min() >= 1.0 and pt.max() <= 10.0
+    assert stats.kstest(eta, lambda v: stats.uniform.cdf(v, -1.0, 2.0)).pvalue > 1e-3
+    assert stats.kstest(eta, lambda v: stats.uniform.cdf(v, 0.0, 1.0)).pvalue < 1e-6
+    assert stats.kstest(phi0, lambda v: stats.uniform.cdf(v, 0.0, 2 * math.pi)).pvalue > 1e-3
+    assert stats.kstest(phi0, lambda v: stats.uniform.cdf(v, -math.pi, 2 * math.pi)).pvalue < 1e-6
+    assert stats.kstest(z0, lambda v: stats.norm.cdf(v / 5.0)).pvalue > 1e-3
+    assert stats.kstest(z0, lambda v: stats.norm.cdf(v)).pvalue < 1e-6

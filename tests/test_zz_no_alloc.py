@@ -12,6 +12,7 @@ torch = pytest.importorskip("torch")
 
 import paper_2402_14718_gb300 as sb
 from paper_2402_14718_gb300.workloads import WORKLOADS
+from oracle import events as oev, ising, qubo as oq
 
 pytestmark = pytest.mark.gpu
 
@@ -53,12 +54,38 @@ def test_noalloc_readout_matches_allocating_readout_twice():
         assert int(d_br.item()) == int(br_ref[0])
 
 
+def test_noalloc_readout_matches_the_oracle_energy():
+    """Eq. 13 evaluated by its definition on the oracle's own QUBO of the same
+    event, for seeded spins."""
+    w = WORKLOADS["event100"]
+    q = _qubo("event100")
+    kw = dict(w["cuts"])
+    kw["five_hit_rule"] = bool(kw["five_hit_rule"])
+    qo = oq.build_qubo(oev.generate(w["seed"], oev.EventParams(n_tracks=w["n_tracks"],
+                                                               noise_frac=w["noise_frac"])),
+                       oq.BuildParams(**kw))
+    R = 5
+    T = np.random.default_rng(17).integers(0, 2, size=(qo.n, R)).astype(np.int8)
+    d_E = torch.zeros(R, dtype=torch.float64, device="cuda")
+    sb.sb_energy_noalloc(q.n, _dev(q.rowptr, torch.int32), _dev(q.col, torch.int32),
+                         _dev(q.val, torch.float64), _dev(q.lin, torch.float64), None,
+                         _dev(np.where(T > 0, 1, -1).astype(np.int8), torch.int8), R, d_E)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(d_E.cpu().numpy(), ising.qubo_energy(qo, T), rtol=1e-12, atol=1e-12)
+
+
 def test_noalloc_rejects_sizes_beyond_the_static_scratch():
     n, R = 300000, 256
     d_rowptr = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
     d_qlin = torch.zeros(n, dtype=torch.float64, device="cuda")
+    d_col = torch.zeros(1, dtype=torch.int32, device="cuda")
+    d_qval = torch.zeros(1, dtype=torch.float64, device="cuda")
     d_x = torch.zeros(1, dtype=torch.float32, device="cuda")
     d_E = torch.zeros(R, dtype=torch.float64, device="cuda")
     with pytest.raises(sb.SbError) as ei:
-        sb.sb_energy_noalloc(n, d_rowptr, None, None, d_qlin, d_x, None, R, d_E)
+        sb.sb_energy_noalloc(n, d_rowptr, d_col, d_qval, d_qlin, d_x, None, R, d_E)
     assert ei.value.code == 1 and "static scratch" in str(ei.value)
+    # a NULL column or value array is refused before any launch
+    with pytest.raises(sb.SbError) as ei:
+        sb.sb_energy_noalloc(100, d_rowptr, None, d_qval, d_qlin, d_x, None, 1, d_E)
+    assert ei.value.code == 1
