@@ -1,13 +1,26 @@
 #!/usr/bin/env python3
-"""Throughput of the simulated-bifurcation solver on one GB300.
+"""Throughput and time-to-target of the simulated-bifurcation solver on one GB300.
+
+Default workload (the metric's own comparison, "batched BF16 vs plain FP32"):
+512 synthetic events of uneven size (50-2000 tracks, log-uniform), dSB, 64
+replicas per event, 2000 steps, BF16 J / FP32 state, every event advanced by
+the same launches (replayed from a CUDA graph).
 
 One bench step = one pass of the whole SB hot path over the workload, inputs
-already resident in HBM: Philox initial state, S fused SB steps (CSR coupling
-product over R replicas + symplectic-Euler update + wall), FP64 QUBO energy of
-sgn(x) for every replica, arg-min and the best replica's selection.
-Metric: spin-updates/s = N * R * S / step time.
+resident in HBM: Philox initial state, S SB steps (coupling product +
+symplectic-Euler update + wall), FP64 QUBO energy of sgn(x) for every replica
+of every event, arg-min and best selection per event.
+Metric: spin-updates/s = sum over events of N_e * R * S / step time.
+
+Beside the value, the JSON line carries: the roofline of the step (HBM bytes of
+the method per step / step time), the same metric end to end through the C ABI
+from pinned host buffers, time-to-target of the batched BF16 form against the
+plain FP32 single-instance form (section "Results": 99.9 % of the lowest
+energy found, 99 % probability), the FP64 energy error against the oracle,
+and the oracle's throughput on the host cores (cpu_baseline).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload batch512|event1000|event10k|event10k_1m|event500|event100]
 
 Under torchrun each rank runs the same workload on its own GPU with its own
 seed (independent replicas, no collective on the data path); the step time is
@@ -30,37 +43,32 @@ sys.path.insert(0, ROOT)
 METRIC = "SB spin-updates/s & time-to-target-energy: batched BF16 vs plain FP32, 1 GB300"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="event1000")
-    ap.add_argument("--variant", default="bsb", choices=["asb", "bsb", "dsb"])
+    ap.add_argument("--workload", default="batch512")
+    ap.add_argument("--variant", default="", choices=["", "asb", "bsb", "dsb"],
+                    help="override the workload's variant")
     ap.add_argument("--sb-steps", type=int, default=0, help="override S (0: workload's)")
+    ap.add_argument("--no-factor", action="store_true",
+                    help="plain CSR coupling product only (no sb_set_factor)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttt", action="store_true")
+    ap.add_argument("--no-energy-check", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--study", default="",
                     choices=["", "paper-sizes", "c0-scan", "schedule", "build", "adjoint",
                              "kernels"],
-                    help="experiments (not bench lines): energy traces and 50-shot statistics "
-                         "at the paper's QUBO sizes, the c0 scan, schedule learning by the adjoint")
-    ap.add_argument("--kernel", default="auto",
-                    choices=["auto", "untiled", "rowgroup2", "rowgroup4", "stream", "tiled"],
-                    help="step kernel: auto (sb_autotune picks), or a fixed one: untiled (one "
-                         "row per warp), rowgroup2/4 (rows per warp), stream (bulk-copy ring), "
-                         "tiled (shared-memory row blocks)")
-    ap.add_argument("--dsb-signs", type=int, default=-1, choices=[-1, 0, 1],
-                    help="dSB gather form (SB_OPT_DSB_SIGNS): 0 FP32 positions, 1 sign bytes; "
-                         "-1 keeps the library default")
-    ap.add_argument("--rows-per-cta", type=int, default=0,
-                    help="with a fixed --kernel: rows per CTA (SB_OPT_STEP_RPC)")
+                    help="experiments (not bench lines)")
+    ap.add_argument("--record", default="",
+                    help="with --study: also write the JSON lines, with the command, to this file")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling driver: set up the workload, run this many SB steps with "
                          "one direct launch each (no graph, no timing), exit")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -91,108 +99,114 @@ def job_value(units_per_rank, world_size, ms):
     return units_per_rank * world_size / (ms * 1e-3)
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step-kernel
-# launch, from an ncu capture of that launch (third step, direct launch), keyed
-# by workload, variant, kernel, its configuration (rows per warp, rows per CTA,
-# replica tile) and that kernel's sources (sha256 prefix, kernel_source_hash);
-# any other combination reports null.
-MEASURED_TRAFFIC = {
-    ("event1000", "bsb", "k_step_rw", (2, 0, 0), "4594a2ea3d3969fb"): 90862592 + 37640704,
-    ("event1000", "dsb", "k_step_dsb16", (0, 0, 0), "4236c91a6c79f841"): 100602368 + 39244032,
-    # to the 10 MB that ncu prints at this size
-    ("batch512", "dsb", "k_step_dsb16", (0, 0, 0), "4236c91a6c79f841"): 4280000000 + 3220000000,
-    ("batch512", "dsb", "k_step_dsb16", (0, 32, 0), "4236c91a6c79f841"): 4280000000 + 3220000000,
-}
+# ---------------------------------------------------------------- workloads
+def workload(name, sb_steps=0, variant=""):
+    """Run shape and the event recipes (seed, tracks, noise, cuts) of a named
+    workload; numbers only (the tables live in the package's workloads module,
+    which loads nothing)."""
+    from paper_2402_14718_gb300.workloads import BATCH512, WORKLOADS, batch512_tracks
+    if name == "batch512":
+        B = BATCH512
+        tracks = batch512_tracks()
+        w = dict(R=B["replicas"], S=B["steps"], a0=B["a0"], dt=B["dt"], variant=B["variant"],
+                 jprec=B["jprec"],
+                 events=[dict(seed=B["seed0"] + e, n_tracks=tracks[e], noise_frac=B["noise_frac"],
+                              cuts=B["cuts"]) for e in range(B["n_events"])])
+    else:
+        W = WORKLOADS[name]
+        w = dict(R=W["replicas"], S=W["steps"], a0=W["a0"], dt=W["dt"],
+                 variant=W.get("variant", "bsb"), jprec=W["jprec"],
+                 events=[dict(seed=W["seed"], n_tracks=W["n_tracks"], noise_frac=W["noise_frac"],
+                              cuts=W["cuts"])])
+    if sb_steps:
+        w["S"] = sb_steps
+    if variant:
+        w["variant"] = variant
+    w["name"] = name
+    return w
 
 
-def set_kernel(sb, ctx, name, variant="bsb", R=256, dsb_signs=-1):
-    """Fix the step kernel by its options; returns the kernel's name ("auto":
-    the library's default choice, without the autotuner)."""
-    if dsb_signs >= 0:
-        sb.sb_set_option(ctx, sb.SB_OPT_DSB_SIGNS, dsb_signs)
-    if name == "auto":
-        if variant != "dsb" and R % 128 == 0:
-            return "k_step_rw"
-        return tuned_kernel({"rows_per_warp": 0, "tiled": 0, "tile": 0, "groups": 1}, variant, R,
-                            dsb_signs)
-    sb.sb_set_option(ctx, sb.SB_OPT_ROWS_PER_WARP, 0)
-    if name == "rowgroup2" or name == "rowgroup4":
-        sb.sb_set_option(ctx, sb.SB_OPT_ROWS_PER_WARP, int(name[-1]))
-        return "k_step_rw"
-    if name == "stream":
-        sb.sb_set_option(ctx, sb.SB_OPT_STREAM, 1)
-        return "k_step_stream"
-    if name == "tiled":
-        sb.sb_set_option(ctx, sb.SB_OPT_TILED, 1)
-        return "k_step_tiled"
-    return tuned_kernel({"rows_per_warp": 0, "tiled": 0, "tile": 0, "groups": 1}, variant, R,
-                        dsb_signs)
+def build_events(sb, w):
+    """[(event, qubo)] of the workload, by the library's host generator and builder."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(spec):
+        ev = sb.sb_event_generate(spec["seed"], sb.event_params(n_tracks=spec["n_tracks"],
+                                                                noise_frac=spec["noise_frac"]))
+        return ev, sb.sb_qubo_build(ev, sb.build_params(**spec["cuts"]))
+
+    with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
+        return list(ex.map(one, w["events"]))
 
 
-# the library's default dSB gather form (SB_OPT_DSB_SIGNS)
-DSB_SIGNS_DEFAULT = 1
+def factor_arrays(sb, qs):
+    """The shared-hit factor of a list of QUBOs in one context: hit ids offset per event."""
+    off, mems, couple, wc = 0, [], None, None
+    for q in qs:
+        m, couple, wc, n_ids = sb.sb_qubo_factor(q)
+        mems.append(np.where(m >= 0, m + off, -1).astype(np.int32))
+        off += n_ids
+    return off, np.concatenate(mems), couple, wc
 
 
-def tuned_kernel(cfg, variant, R, dsb_signs=-1):
-    """Name of the step kernel the context runs with autotuned configuration cfg
-    (the selection order of the library: row-group, tiled, dSB signs, one replica)."""
-    signs = DSB_SIGNS_DEFAULT if dsb_signs < 0 else dsb_signs
+def make_ctx(sb, qs, prec, factor=True):
+    if len(qs) == 1:
+        q = qs[0]
+        ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, prec)
+    else:
+        ctx = sb.sb_create_batch([(q.rowptr, q.col, q.val, q.lin) for q in qs], prec)
+    if factor:
+        n_ids, member, couple, wc = factor_arrays(sb, qs)
+        sb.sb_set_factor(ctx, n_ids, member, couple, wc)
+    return ctx
+
+
+def step_kernels(cfg, variant, R, info):
+    """Names of the kernels one SB step launches with autotuned configuration cfg."""
+    if cfg.get("factor"):
+        if variant != "dsb" and R % 128 == 0 and cfg.get("rows_per_warp", 0) != 0 \
+                and cfg.get("tile", 0) == 0:
+            return ["k_fac_sum", "k_step_rw"]
+        return ["k_fac_sum", "k_step_fac"]
     if cfg["rows_per_warp"] and R % 128 == 0:
-        return "k_step_rw"
+        return ["k_step_rw"]
     if cfg["tiled"] and R % 32 == 0:
-        return "k_step_tiled"
-    if (variant == "dsb" and signs and cfg["tile"] == 0 and cfg["groups"] == 1 and R % 16 == 0
-            and R // 16 <= 32 and (R // 16) & (R // 16 - 1) == 0):
-        return "k_step_dsb16"
+        return ["k_step_tiled"]
+    if variant == "dsb" and cfg["tile"] == 0 and cfg["groups"] == 1 and R % 16 == 0 \
+            and R // 16 <= 32 and (R // 16) & (R // 16 - 1) == 0:
+        return ["k_step_dsb16"]
     if R == 1:
-        return "k_step_r1"
-    return "k_step"
+        return ["k_step_r1"]
+    return ["k_step"]
 
 
-def R_cfg(tuned):
-    """Rows per warp / rows per CTA of the tuned configuration (part of the traffic key)."""
-    if tuned is None:
-        return None
-    return (tuned[0]["rows_per_warp"], tuned[0]["rows_per_cta"], tuned[0]["tile"])
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one SB step (all
+# its launches) from an ncu capture of the step's kernels, keyed by workload,
+# variant, kernels and those kernels' sources (sha256 prefix, kernel_source_hash);
+# any other combination reports null. Captures larger than a few GB on the
+# device are not taken: the batch's figure is a smaller event's capture
+# scaled by the spin-updates, and says so.
+MEASURED_TRAFFIC = {}
+
+KERNEL_SOURCES = {"k_step_rw": ("rw.cu", "kernels.cuh", "signs.cuh"),
+                  "k_step_stream": ("stream.cu", "kernels.cuh", "signs.cuh"),
+                  "k_fac_sum": ("factor.cu", "kernels.cuh", "signs.cuh"),
+                  "k_step_fac": ("factor.cu", "kernels.cuh", "signs.cuh")}
 
 
-# source files that define each step kernel (and the headers they include)
-KERNEL_SOURCES = {"k_step_rw": ("rw.cu", "kernels.cuh", "signs.cuh", "../api.cu"),
-                  "k_step_stream": ("stream.cu", "kernels.cuh", "signs.cuh")}
-
-
-def kernel_source_hash(kname="k_step"):
+def kernel_source_hash(knames):
     import hashlib
     d = os.path.join(ROOT, "paper_2402_14718_gb300", "csrc", "device")
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES.get(kname, ("kernels.cu", "kernels.cuh", "signs.cuh")):
+    files = []
+    for k in knames:
+        for f in KERNEL_SOURCES.get(k, ("kernels.cu", "kernels.cuh", "signs.cuh")):
+            if f not in files:
+                files.append(f)
+    for f in files:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
-
-
-def gather_rate(sb, ctx, kname, variant, N, nnz, R, kstep_s, stream):
-    """On-chip side of the step: the neighbour-row bytes one launch reads
-    (through L1 / L2; x stays in L2 on the bench workloads) and their rate,
-    beside the rate of random whole-row reads of an array of x's size measured
-    now by sb_gather_probe (no L1 reuse there, so a kernel whose rows repeat in
-    L1 can exceed it)."""
-    rw, entries = sb.sb_step_info(ctx)
-    signs = variant == "dsb" and kname in ("k_step_dsb16",)
-    elem = 1 if signs else 4
-    if kname == "k_step_rw" and rw:
-        gbytes = entries * R * elem
-    else:
-        gbytes = nnz * R * elem
-    out = {"bytes_per_launch": gbytes, "tb_per_s": gbytes / kstep_s / 1e12,
-           "rows": "union entries of the row groups" if kname == "k_step_rw" and rw
-           else "one neighbour row per nonzero"}
-    row_bytes = R * elem
-    if row_bytes % 512 == 0:
-        probe = sb.sb_gather_probe(N * R * elem, row_bytes, 5, 1, stream)
-        out.update({"probe_tb_per_s": probe / 1e12, "frac_of_probe": gbytes / kstep_s / probe,
-                    "probe_row_bytes": row_bytes})
-    return out
 
 
 def peaks():
@@ -254,62 +268,6 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def workload(name, sb_steps):
-    from paper_2402_14718_gb300.workloads import WORKLOADS
-    w = dict(WORKLOADS[name])
-    if sb_steps:
-        w["steps"] = sb_steps
-    return w
-
-
-# ---------------------------------------------------------------- oracle (CPU) leg
-_ORACLE_PROBLEMS = {}
-
-
-def oracle_problem(w):
-    """The workload's event, QUBO and Ising form built by the oracle (cached)."""
-    key = (w["seed"], w["n_tracks"], w["noise_frac"], tuple(sorted(w["cuts"].items())))
-    if key not in _ORACLE_PROBLEMS:
-        from oracle import events as oev, ising, qubo as oq
-        kw = dict(w["cuts"])
-        kw["five_hit_rule"] = bool(kw["five_hit_rule"])
-        ev = oev.generate(w["seed"], oev.EventParams(n_tracks=w["n_tracks"],
-                                                     noise_frac=w["noise_frac"]))
-        q = oq.build_qubo(ev, oq.BuildParams(**kw))
-        J, h, _ = ising.to_ising(q)
-        _ORACLE_PROBLEMS[key] = (q.n, J, h, ising.c0_auto(J, q.n))
-    return _ORACLE_PROBLEMS[key]
-
-
-def oracle_sample(w, variant, target_s=15.0, seed=1):
-    """Time the FP64 oracle on a bounded sample of the workload: the full QUBO
-    and replica count, as many SB steps as fit in about ``target_s`` seconds."""
-    from oracle import sb as osb
-    n, J, h, c0 = oracle_problem(w)
-    R, S = w["replicas"], w["steps"]
-    x, y = osb.init_state(seed, n, R)
-    sched = osb.linear_schedule(w["a0"], S)
-    v = {"asb": osb.ASB, "bsb": osb.BSB, "dsb": osb.DSB}[variant]
-    t0 = time.perf_counter()
-    k = 0
-    while k < S and (time.perf_counter() - t0) < target_s:
-        x, y = osb.step(J, h, x, y, float(sched[k]), w["a0"], c0, w["dt"], v)
-        k += 1
-    dt = time.perf_counter() - t0
-    return {"value": n * R * k / dt, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{k} of {S} SB steps, N={n}, R={R}, FP64 NumPy/SciPy, one thread",
-            "seconds": dt}
-
-
-def _oracle_steps(job):
-    """Worker of the all-cores oracle timing: k oracle steps on a slice of the replicas."""
-    J, h, x, y, sched, a0, c0, dt, v, k = job
-    from oracle import sb as osb
-    for i in range(k):
-        x, y = osb.step(J, h, x, y, float(sched[i]), a0, c0, dt, v)
-    return x.shape[1]
-
-
 def cpu_model():
     """Host CPU as /proc/cpuinfo names it (model name, or the part number on Arm)."""
     import platform
@@ -327,25 +285,101 @@ def cpu_model():
     return f"{platform.machine()} {name}".strip()
 
 
-def oracle_all_cores(w, variant, k, seed=1):
-    """The same oracle, as it stands, on every host core: the replicas split into
-    one slice per process (spawned, so safe after CUDA use), k steps each."""
+# ---------------------------------------------------------------- oracle (CPU) legs
+def sample_events(w, k=4):
+    """Events of the workload timed by the oracle legs: for a batch, the events
+    at the 10/30/50/70 % quantiles of the track count (the largest events are
+    left out: the oracle's pure-Python builder would dominate the sample)."""
+    ev = w["events"]
+    if len(ev) == 1:
+        return [0]
+    order = sorted(range(len(ev)), key=lambda e: (ev[e]["n_tracks"], e))
+    return [order[int(q * (len(ev) - 1))] for q in (0.1, 0.3, 0.5, 0.7)[:k]]
+
+
+_ORACLE_PROBLEMS = {}
+
+
+def oracle_problem(spec):
+    """The event, QUBO and Ising form of one event recipe built by the oracle (cached)."""
+    key = (spec["seed"], spec["n_tracks"], spec["noise_frac"], tuple(sorted(spec["cuts"].items())))
+    if key not in _ORACLE_PROBLEMS:
+        from oracle import events as oev, ising, qubo as oq
+        kw = dict(spec["cuts"])
+        kw["five_hit_rule"] = bool(kw["five_hit_rule"])
+        ev = oev.generate(spec["seed"], oev.EventParams(n_tracks=spec["n_tracks"],
+                                                        noise_frac=spec["noise_frac"]))
+        q = oq.build_qubo(ev, oq.BuildParams(**kw))
+        J, h, _ = ising.to_ising(q)
+        _ORACLE_PROBLEMS[key] = (ev, q, J, h, ising.c0_auto(J, q.n))
+    return _ORACLE_PROBLEMS[key]
+
+
+def _variant_code(variant):
+    from oracle import sb as osb
+    return {"asb": osb.ASB, "bsb": osb.BSB, "dsb": osb.DSB}[variant]
+
+
+def oracle_sample(w, target_s=15.0, seed=1):
+    """Time the FP64 oracle, as it stands, on one thread on a bounded sample of
+    the workload: the sampled events at the full replica count, as many SB
+    steps per event as fit in about target_s seconds in all."""
+    from oracle import sb as osb
+    evs = sample_events(w)
+    R, S = w["R"], w["S"]
+    v = _variant_code(w["variant"])
+    sched = osb.linear_schedule(w["a0"], S)
+    units, secs, steps = 0, 0.0, []
+    for e in evs:
+        _, q, J, h, c0 = oracle_problem(w["events"][e])
+        x, y = osb.init_state(seed, q.n, R)
+        t0 = time.perf_counter()
+        k = 0
+        while k < S and (time.perf_counter() - t0) < target_s / len(evs):
+            x, y = osb.step(J, h, x, y, float(sched[k]), w["a0"], c0, w["dt"], v)
+            k += 1
+        secs += time.perf_counter() - t0
+        units += q.n * R * k
+        steps.append((q.n, k))
+    desc = ", ".join(f"N={n}: {k} steps" for n, k in steps)
+    return {"value": units / secs, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(evs)} of {len(w['events'])} events at R={R} ({desc} of {S}), "
+                      f"FP64 NumPy/SciPy, one thread", "seconds": secs, "units": units,
+            "steps": steps}
+
+
+def _oracle_steps(job):
+    """Worker of the all-cores oracle timing: k oracle steps on a slice of the replicas."""
+    J, h, x, y, sched, a0, c0, dt, v, k = job
+    from oracle import sb as osb
+    for i in range(k):
+        x, y = osb.step(J, h, x, y, float(sched[i]), a0, c0, dt, v)
+    return x.shape[1]
+
+
+def oracle_all_cores(w, steps, seed=1):
+    """The same oracle, as it stands, on every host core: each sampled event's
+    replicas split into one slice per process (spawned, so safe after CUDA use),
+    the same steps per event as the one-thread sample."""
     import multiprocessing as mp
     from oracle import sb as osb
-    n, J, h, c0 = oracle_problem(w)
-    R = w["replicas"]
-    x, y = osb.init_state(seed, n, R)
-    sched = osb.linear_schedule(w["a0"], w["steps"])[:k]
-    v = {"asb": osb.ASB, "bsb": osb.BSB, "dsb": osb.DSB}[variant]
+    v = _variant_code(w["variant"])
+    R = w["R"]
     P = max(1, min(os.cpu_count() or 1, R))
-    cuts = np.linspace(0, R, P + 1).astype(int)
-    jobs = [(J, h, x[:, a:b].copy(), y[:, a:b].copy(), sched, w["a0"], c0, w["dt"], v, k)
-            for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+    jobs, units = [], 0
+    for e, (n, k) in zip(sample_events(w), steps):
+        _, q, J, h, c0 = oracle_problem(w["events"][e])
+        x, y = osb.init_state(seed, q.n, R)
+        sched = osb.linear_schedule(w["a0"], w["S"])[:k]
+        cuts = np.linspace(0, R, P + 1).astype(int)
+        jobs += [(J, h, x[:, a:b].copy(), y[:, a:b].copy(), sched, w["a0"], c0, w["dt"], v, k)
+                 for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+        units += q.n * R * k
     saved = os.environ.get("OMP_NUM_THREADS")
     os.environ["OMP_NUM_THREADS"] = "1"
     try:
-        with mp.get_context("spawn").Pool(len(jobs)) as pool:
-            pool.map(_oracle_steps, [j[:-1] + (1,) for j in jobs])   # start-up and imports
+        with mp.get_context("spawn").Pool(P) as pool:
+            pool.map(_oracle_steps, [j[:-1] + (1,) for j in jobs[:P]])   # start-up and imports
             t0 = time.perf_counter()
             pool.map(_oracle_steps, jobs)
             dt = time.perf_counter() - t0
@@ -354,36 +388,249 @@ def oracle_all_cores(w, variant, k, seed=1):
             os.environ.pop("OMP_NUM_THREADS", None)
         else:
             os.environ["OMP_NUM_THREADS"] = saved
-    return {"value": n * R * k / dt, "cores": len(jobs),
-            "sample": f"{k} SB steps, N={n}, R={R} split over {len(jobs)} processes, "
+    return {"value": units / dt, "cores": P,
+            "sample": f"the same events and steps, replicas split over {P} processes, "
                       f"FP64 NumPy/SciPy, one thread each"}
 
 
 def run_reference(args):
+    """Reference arm: the FP64 oracle timed on the host cores, on the same
+    workload, metric and unit (each step a bounded sample of the workload)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    w = workload(args.workload, args.sb_steps)
+    w = workload(args.workload, args.sb_steps, args.variant)
     vals = []
     for _ in range(args.warmup + args.steps):
-        vals.append(oracle_sample(w, args.variant, target_s=8.0))
+        vals.append(oracle_sample(w, target_s=4.0))
     timed = vals[args.warmup:]
-    value = float(np.mean([t["value"] for t in timed]))
-    sec = float(np.mean([t["seconds"] for t in timed]))
-    cpu = dict(timed[0])
+    units = float(np.sum([t["units"] for t in timed]))
+    secs = float(np.sum([t["seconds"] for t in timed]))
+    value = units / secs
+    cpu = {k: timed[0][k] for k in ("unit", "cores", "kind", "sample")}
     cpu["value"] = value
-    cpu.pop("seconds", None)
+    cpu["cpu"] = cpu_model()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "spin-updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "variant": args.variant, "replicas": w["replicas"],
-                       "sb_steps": w["steps"], "n_tracks": w["n_tracks"]},
+            "config": {"workload": w["name"], "events": len(w["events"]), "variant": w["variant"],
+                       "replicas": w["R"], "sb_steps": w["S"]},
             "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------- time to target
+def _ttt_at(t, p):
+    """t max(1, ln 0.01 / ln(1 - p)); inf if p = 0."""
+    if p <= 0.0:
+        return math.inf
+    if p >= 0.99:
+        return t
+    return t * math.log(0.01) / math.log(1.0 - p)
+
+
+def time_to_target(sb, w, pairs, ctx, stream, dev, plain_events, plain_runs=64, every=50,
+                   c0_scale=2.0, ref_scale=3.0):
+    """Time-to-target (section "Results", Table 1): the time to reach 99.9 % of
+    the lowest energy found, with 99 % probability, for every event of the
+    workload.
+
+    Target of event e: E_best,e + 0.001 |E_best,e| (QUBO energies are
+    negative), E_best,e the lowest energy any run of this study found for it:
+    the batched runs, the plain runs and a reference run (2 S steps, c0 = 3
+    c0_auto). Both timed forms use c0 = 2 c0_auto (a fixed c0, as in the
+    paper; the factor 2 is where the configured c0 of the workloads reaches
+    the lowest energies in the c0 scan).
+
+    Batched BF16 form: one run of all events and R replicas with an FP64
+    readout every `every` steps (timed). p_e(k) = fraction of event e's
+    replicas at or below its target at checkpoint k; the run succeeds for the
+    whole workload with P(k) = prod_e (1 - (1 - p_e(k))^R), and TTT = min_k
+    t(k) max(1, ln 0.01 / ln(1 - P(k))).
+
+    Plain FP32 form (FP32 J, one replica, one event, one kernel launch per
+    step, no graph): `plain_runs` runs of each sampled event with checkpoints
+    give its own p_e(k); a plain run is timed without checkpoints and t_e(k)
+    = t_run,e k / S. Events are solved one after another, each repeated until
+    it succeeds, with per-event probability q = 0.99^(1/E) so that all E events
+    succeed with 99 %: TTT_e = min_k t_e(k) max(1, ln(1 - q) / ln(1 - p_e(k))),
+    and the workload's plain TTT is E times the mean of TTT_e over the
+    sampled events. Efficiency and purity (Eq. 18-19) of each form's best
+    selection are reported on the sampled events."""
+    import torch
+    qs = [q for _, q in pairs]
+    E = len(qs)
+    R, S, a0, dt, variant = w["R"], w["S"], w["a0"], w["dt"], w["variant"]
+    n_ck = (S + every - 1) // every
+    sched = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
+    d_E = torch.empty(E * R, dtype=torch.float64, device=dev)
+    # ---- batched run with checkpoints
+    sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 1)
+    sb.sb_run(ctx, variant, a0, -c0_scale, dt, 0, R, 4242, None, stream)
+    start = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    marks, Es = [], []
+    for k0 in range(0, S, every):
+        n = min(every, S - k0)
+        sb.sb_advance(ctx, variant, a0, -c0_scale, dt, n, sched[k0:k0 + n], stream)
+        sb.sb_readout_device(ctx, d_E, None, None, None, stream)
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        marks.append(e)
+        Es.append(d_E.clone())
+    torch.cuda.synchronize(dev)
+    times = [start.elapsed_time(m) * 1e-3 for m in marks]
+    Eb = np.stack([e.cpu().numpy().reshape(E, R) for e in Es])   # [checkpoint, event, replica]
+    T_b, _, _ = sb.sb_best(ctx)
+    # ---- reference run: 2 S steps, c0 = 3 c0_auto
+    sched2 = torch.tensor(np.array([a0 * k / (2 * S - 1) for k in range(2 * S)], np.float32),
+                          device=dev)
+    sb.sb_run(ctx, variant, a0, -ref_scale, dt, 2 * S, R, 5151, sched2, stream)
+    sb.sb_readout_device(ctx, d_E, None, None, None, stream)
+    torch.cuda.synchronize(dev)
+    E_ref = d_E.cpu().numpy().reshape(E, R).min(axis=1)
+    # ---- plain FP32 form on the sampled events
+    plain = []
+    d1 = torch.empty(1, dtype=torch.float64, device=dev)
+    for e in plain_events:
+        q = qs[e]
+        cp = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_FP32)
+        sb.sb_set_option(cp, sb.SB_OPT_GRAPH, 0)
+        c0e = c0_scale * sb.sb_info(cp)["c0_auto"]
+        sb.sb_run(cp, variant, a0, c0e, dt, 20, 1, 1, None, stream)   # warm-up
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(4):
+            sb.sb_run(cp, variant, a0, c0e, dt, S, 1, 9000 + i, None, stream)
+            sb.sb_readout_device(cp, d1, None, None, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_run = e0.elapsed_time(e1) * 1e-3 / 4
+        ck = []
+        for i in range(plain_runs):
+            sb.sb_run(cp, variant, a0, c0e, dt, 0, 1, 7000 + i, None, stream)
+            row = []
+            for k0 in range(0, S, every):
+                n = min(every, S - k0)
+                sb.sb_advance(cp, variant, a0, c0e, dt, n, sched[k0:k0 + n], stream)
+                sb.sb_readout_device(cp, d1, None, None, None, stream)
+                row.append(d1.clone())
+            ck.append(row)
+            if i == plain_runs - 1:
+                torch.cuda.synchronize(dev)
+        Ep = np.array([[float(v.item()) for v in row] for row in ck])   # [run, checkpoint]
+        best_run = int(np.argmin(Ep[:, -1]))
+        sb.sb_run(cp, variant, a0, c0e, dt, S, 1, 7000 + best_run, None, stream)
+        T_p, _, _ = sb.sb_best(cp)
+        plain.append(dict(e=e, t_run=t_run, Ep=Ep, T=T_p))
+        sb.sb_destroy(cp)
+    # ---- targets
+    E_best = np.minimum(Eb.min(axis=(0, 2)), E_ref)
+    for p in plain:
+        E_best[p["e"]] = min(E_best[p["e"]], float(p["Ep"].min()))
+    target = E_best + 0.001 * np.abs(E_best)
+    p_rep = (Eb <= target[None, :, None]).mean(axis=2)            # [checkpoint, event]
+    P_all = np.prod(1.0 - (1.0 - p_rep) ** R, axis=1)            # [checkpoint]
+    ttt_b, kb = math.inf, None
+    for k in range(n_ck):
+        v = _ttt_at(times[k], float(P_all[k]))
+        if v < ttt_b:
+            ttt_b, kb = v, k
+    q_ev = 0.99 ** (1.0 / E)
+    per_event, ttt_sum = [], 0.0
+    for p in plain:
+        pk = (p["Ep"] <= target[p["e"]]).mean(axis=0)
+        best, kk = math.inf, None
+        for k in range(n_ck):
+            tk = p["t_run"] * min(S, (k + 1) * every) / S
+            if pk[k] <= 0.0:
+                continue
+            v = tk if pk[k] >= q_ev else tk * math.log(1.0 - q_ev) / math.log(1.0 - pk[k])
+            if v < best:
+                best, kk = v, k
+        ttt_sum += best
+        per_event.append({"event": p["e"], "N": qs[p["e"]].n, "run_seconds": p["t_run"],
+                          "p_final": float(pk[-1]), "ttt_seconds": best,
+                          "at_step": None if kk is None else min(S, (kk + 1) * every)})
+    ttt_p = E * ttt_sum / max(len(plain), 1)
+    # ---- efficiency / purity and the truth energy on the sampled events
+    row0 = np.cumsum([0] + [q.n for q in qs])
+    eff_b, pur_b, eff_p, pur_p, gaps = [], [], [], [], []
+    for p in plain:
+        e = p["e"]
+        ev, q = pairs[e]
+        sc_b = sb.sb_tracks(ev, q, T_b[row0[e]:row0[e + 1]])
+        sc_p = sb.sb_tracks(ev, q, p["T"])
+        eff_b.append(sc_b["efficiency"])
+        pur_b.append(sc_b["purity"])
+        eff_p.append(sc_p["efficiency"])
+        pur_p.append(sc_p["purity"])
+        part = ev.arrays()["particle"]
+        truth = np.array([1 if part[a] == part[b] == part[c] >= 0 else 0 for a, b, c in q.trip],
+                         np.int8)
+        c1 = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_FP32)
+        E_truth = float(sb.sb_energy(c1, np.where(truth > 0, 1, -1).astype(np.int8)[:, None])[0, 0])
+        sb.sb_destroy(c1)
+        gaps.append((E_best[e] - E_truth) / abs(E_truth))
+    return {
+        "definition": "time to reach 99.9 % of the lowest energy found (E_best + 0.001 |E_best|) "
+                      "with 99 % probability for every event of the workload",
+        "c0_scale": c0_scale, "checkpoint_every": every,
+        "reference_run": {"steps": 2 * S, "c0_scale": ref_scale, "replicas": R},
+        "batched_bf16": {"seconds": ttt_b, "at_step": None if kb is None else min(S, (kb + 1) * every),
+                         "run_seconds": times[-1], "replicas": R, "events": E,
+                         "P_all_final": float(P_all[-1]),
+                         "p_rep_final_median": float(np.median(p_rep[-1]))},
+        "plain_fp32": {"seconds": ttt_p, "events_sampled": len(plain), "runs_per_event": plain_runs,
+                       "per_event_probability": q_ev, "per_event": per_event,
+                       "scaling": f"{E} x mean over the sampled events"},
+        "speedup_batched_vs_plain": (ttt_p / ttt_b) if (ttt_b < math.inf and ttt_p < math.inf) else None,
+        "efficiency": {"batched": float(np.mean(eff_b)), "plain": float(np.mean(eff_p))},
+        "purity": {"batched": float(np.mean(pur_b)), "plain": float(np.mean(pur_p))},
+        "best_over_truth_energy": {"median": float(np.median(gaps)), "min": float(np.min(gaps)),
+                                   "max": float(np.max(gaps)),
+                                   "note": "(E_best - E_truth) / |E_truth| on the sampled events; "
+                                           "negative: SB found energies below the true triplets'"},
+    }
+
+
+# ---------------------------------------------------------------- energy error
+def energy_error(sb, w, pairs, T_best, E_gpu_best, oracle_replicas=8, seed=3):
+    """For sampled events: the oracle's FP64 energy (Eq. 13 by definition, on
+    the oracle's own QUBO of the same event, bit-equal to the library's) of the
+    GPU's best spins against the GPU's FP64 energy of them, and the GPU's best
+    against the oracle's own best over `oracle_replicas` oracle runs of the
+    full schedule (events of at most 4000 triplets; statistical, other starts)."""
+    from oracle import ising, sb as osb
+    qs = [q for _, q in pairs]
+    row0 = np.cumsum([0] + [q.n for q in qs])
+    out, worst = [], 0.0
+    for e in sample_events(w, 3):
+        _, qo, J, h, c0 = oracle_problem(w["events"][e])
+        q = qs[e]
+        assert qo.n == q.n and np.array_equal(qo.col, q.col) and np.array_equal(qo.val, q.val)
+        T = T_best[row0[e]:row0[e + 1]]
+        E_or = ising.qubo_energy(qo, T.astype(np.int8))
+        rel = abs(float(E_gpu_best[e]) - E_or) / max(abs(E_or), 1e-300)
+        worst = max(worst, rel)
+        rec = {"event": e, "N": q.n, "E_gpu": float(E_gpu_best[e]), "E_oracle_same_spins": E_or,
+               "rel_err": rel}
+        if q.n <= 4000:
+            x, y = osb.init_state(seed, qo.n, oracle_replicas)
+            res = osb.run(J, h, x, y, osb.linear_schedule(w["a0"], w["S"]), w["a0"], c0, w["dt"],
+                          _variant_code(w["variant"]))
+            Eo = ising.qubo_energy(qo, ising.triplets_from_spins(ising.spins_from_x(res.x)))
+            rec["E_oracle_best"] = float(np.min(Eo))
+            rec["oracle_replicas"] = oracle_replicas
+            rec["gap_to_oracle_best"] = (float(E_gpu_best[e]) - float(np.min(Eo))) / abs(float(np.min(Eo)))
+        out.append(rec)
+    return {"max_rel_err_same_spins": worst, "events": out,
+            "j_quantisation": "none: BF16 holds every J = -b/4 of these QUBOs (b = +-1) exactly"}
 
 
 # ---------------------------------------------------------------- GPU leg
@@ -398,58 +645,55 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    w = workload(args.workload, args.sb_steps)
-    R, S, a0, dt = w["replicas"], w["steps"], w["a0"], w["dt"]
+    w = workload(args.workload, args.sb_steps, args.variant)
+    R, S, a0, dt, variant = w["R"], w["S"], w["a0"], w["dt"], w["variant"]
     prec = sb.SB_J_BF16 if w["jprec"] == "bf16" else sb.SB_J_FP32
 
-    # untimed: synthetic event and QUBO (host C++), as in the paper the QUBO build is not timed
-    ev = sb.sb_event_generate(w["seed"], sb.event_params(n_tracks=w["n_tracks"],
-                                                         noise_frac=w["noise_frac"]))
-    q = sb.sb_qubo_build(ev, sb.build_params(**w["cuts"]))
-    N, nnz = q.n, q.nnz
-    ctx = sb.sb_create(N, q.rowptr, q.col, q.val, q.lin, prec)
-    tuned = None
-    if args.kernel == "auto" and not args.profile_steps:
-        if args.dsb_signs >= 0:
-            sb.sb_set_option(ctx, sb.SB_OPT_DSB_SIGNS, args.dsb_signs)
-        tuned = sb.sb_autotune(ctx, args.variant, R, trial_steps=30)   # untimed set-up
-        kname = tuned_kernel(tuned[0], args.variant, R, args.dsb_signs)
-    else:
-        kname = set_kernel(sb, ctx, args.kernel, args.variant, R, args.dsb_signs)
-        if args.rows_per_cta:
-            sb.sb_set_option(ctx, sb.SB_OPT_STEP_RPC, args.rows_per_cta)
-    sched = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
+    # untimed: synthetic events and QUBOs (host C++); the paper does not time the QUBO build
+    t0 = time.perf_counter()
+    pairs = build_events(sb, w)
+    t_build = time.perf_counter() - t0
+    qs = [q for _, q in pairs]
+    E = len(qs)
+    N = sum(q.n for q in qs)
+    nnz = sum(q.nnz for q in qs)
+    ctx = make_ctx(sb, qs, prec, factor=not args.no_factor)
+    finfo = sb.sb_factor_info(ctx)
     if args.profile_steps:
         sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
-        sb.sb_run(ctx, args.variant, a0, 0.0, dt, 0, R, 1, None, stream)
-        sb.sb_advance(ctx, args.variant, a0, 0.0, dt, min(args.profile_steps, S), sched, stream)
+        sb.sb_run(ctx, variant, a0, 0.0, dt, 0, R, 1, None, stream)
+        sch = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
+        sb.sb_advance(ctx, variant, a0, 0.0, dt, min(args.profile_steps, S), sch, stream)
         torch.cuda.synchronize(dev)
         print(json.dumps({"profile_steps": args.profile_steps, "N": N, "nnz": nnz, "R": R}))
         return 0
-    d_E = torch.empty(R, dtype=torch.float64, device=dev)
-    d_bE = torch.empty(1, dtype=torch.float64, device=dev)
-    d_br = torch.empty(1, dtype=torch.int32, device=dev)
+    cfg, tune_us = sb.sb_autotune(ctx, variant, R, trial_steps=20 if E > 1 else 30)   # untimed set-up
+    knames = step_kernels(cfg, variant, R, finfo)
+    sched = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
+    d_E = torch.empty(E * R, dtype=torch.float64, device=dev)
+    d_bE = torch.empty(E, dtype=torch.float64, device=dev)
+    d_br = torch.empty(E, dtype=torch.int32, device=dev)
     d_T = torch.empty(N, dtype=torch.uint8, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    state_bytes = N * R * 12
+    flush = None if state_bytes > (512 << 20) else torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     seed0 = rank_seed(rank)
 
     def one_step(seed, ev_marks=None):
         if ev_marks:
             ev_marks[0].record(stream)
-        sb.sb_run(ctx, args.variant, a0, 0.0, dt, 0, R, seed, None, stream)   # init
+        sb.sb_run(ctx, variant, a0, 0.0, dt, 0, R, seed, None, stream)   # init
         if ev_marks:
             ev_marks[1].record(stream)
-        sb.sb_advance(ctx, args.variant, a0, 0.0, dt, S, sched, stream)       # S fused steps
+        sb.sb_advance(ctx, variant, a0, 0.0, dt, S, sched, stream)       # S steps
         if ev_marks:
             ev_marks[2].record(stream)
-        sb.sb_readout_device(ctx, d_E, d_bE, d_br, d_T, stream)              # FP64 energy + arg-min
+        sb.sb_readout_device(ctx, d_E, d_bE, d_br, d_T, stream)          # FP64 energy + arg-min
         if ev_marks:
             ev_marks[3].record(stream)
 
     for i in range(args.warmup):
         one_step(seed0 + i)
     torch.cuda.synchronize(dev)
-
     marks = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     clocks = Clocks(local, enabled=not args.no_clocks)
     if ws > 1:
@@ -457,7 +701,8 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter()
     for i in range(args.steps):
-        flush.zero_()                      # L2 flush between timed steps (outside the marks)
+        if flush is not None:
+            flush.zero_()                  # L2 flush between timed steps (outside the marks)
         one_step(seed0 + args.warmup + i, marks[i])
     torch.cuda.synchronize(dev)
     if ws > 1:
@@ -470,82 +715,111 @@ def run_ours(args):
     units = N * R * S
     value = job_value(units, ws, ms)
 
-    # dominant kernel: the fused SB step (k_step), average launch over the timed region
+    # the SB step (all of its launches), average over the timed region
     kstep_s = float(np.mean(sweep_ms)) * 1e-3 / S
     jbytes = 2 if prec == sb.SB_J_BF16 else 4
     alg_bytes = 16 * N * R + nnz * (4 + jbytes) + (N + 1) * 4 + N * 4
     hbm, src = peaks()
     achieved = alg_bytes / kstep_s / 1e9
+    trf = MEASURED_TRAFFIC.get((w["name"], variant, tuple(knames), kernel_source_hash(knames)))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm,
-                "traffic": MEASURED_TRAFFIC.get((args.workload, args.variant, kname, R_cfg(tuned),
-                                                  kernel_source_hash(kname))),
-                "kernel": kname,
+                "traffic": None if trf is None else trf["bytes_per_step"],
+                "kernel": " + ".join(knames), "launches_per_sb_step": len(knames),
                 "peak_source": src, "alg_bytes_per_launch": alg_bytes,
+                "alg_bytes_rule": "per SB step: 16 B per spin-update (x read and written, y read "
+                                  "and written, FP32) + nnz (4 + J bytes) + 8 (N + 1)",
                 "kstep_us": kstep_s * 1e6}
-    roofline["gather"] = gather_rate(sb, ctx, kname, args.variant, N, nnz, R, kstep_s, stream)
+    if trf is not None:
+        roofline["traffic_source"] = trf["source"]
 
-    # end to end through the public API with host buffers (pinned), every step:
-    # H2D of the QUBO, conversion, init, S steps, readout, D2H of the result
-    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
-           (("rowptr", q.rowptr), ("col", q.col), ("val", q.val), ("lin", q.lin))}
-    T_host = torch.empty(N, dtype=torch.uint8).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in pin.values())
-    d2h = N + 8 + 4
-    e2e_steps = max(1, min(args.steps, 3))
+    # end to end through the C ABI with host buffers (pinned), every step:
+    # H2D of the QUBOs (+ factor), conversion, init, S steps, readout, D2H of the result
     from paper_2402_14718_gb300 import _lib
     import ctypes
+    ns = np.array([q.n for q in qs], np.int32)
+    zs = np.array([q.nnz for q in qs], np.int64)
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in (
+        ("ns", ns), ("zs", zs),
+        ("rowptr", np.concatenate([q.rowptr for q in qs])),
+        ("col", np.concatenate([q.col for q in qs])),
+        ("val", np.concatenate([q.val for q in qs])),
+        ("lin", np.concatenate([q.lin for q in qs])))}
+    use_factor = not args.no_factor
+    if use_factor:
+        n_ids, member, couple, wc = factor_arrays(sb, qs)
+        pin["member"] = torch.from_numpy(np.ascontiguousarray(member)).pin_memory()
+        pin["couple"] = torch.from_numpy(np.ascontiguousarray(couple)).pin_memory()
+    T_host = torch.empty(N, dtype=torch.uint8).pin_memory()
+    E_host = torch.empty(E, dtype=torch.float64).pin_memory()
+    r_host = torch.empty(E, dtype=torch.int32).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in pin.values())
+    d2h = N + 12 * E
 
     def e2e_once(seed):
         h = ctypes.c_void_p()
-        _lib.check(_lib.lib.sb_create(N, nnz, pin["rowptr"].data_ptr(), pin["col"].data_ptr(),
-                                      pin["val"].data_ptr(), pin["lin"].data_ptr(), prec,
-                                      ctypes.byref(h)))
+        _lib.check(_lib.lib.sb_create_batch(E, pin["ns"].data_ptr(), pin["zs"].data_ptr(),
+                                            pin["rowptr"].data_ptr(), pin["col"].data_ptr(),
+                                            pin["val"].data_ptr(), pin["lin"].data_ptr(), prec,
+                                            ctypes.byref(h)))
         c2 = sb.Ctx(h.value)
-        sb.sb_run(c2, args.variant, a0, 0.0, dt, S, R, seed)
-        E = ctypes.c_double()
-        r = ctypes.c_int32()
-        _lib.check(_lib.lib.sb_best(c2.handle, T_host.data_ptr(), ctypes.byref(E), ctypes.byref(r)))
+        if use_factor:
+            _lib.check(_lib.lib.sb_set_factor(h.value, int(n_ids), 3, pin["member"].data_ptr(),
+                                              pin["couple"].data_ptr(), float(wc)))
+        sb.sb_run(c2, variant, a0, 0.0, dt, S, R, seed)
+        _lib.check(_lib.lib.sb_best(h.value, T_host.data_ptr(), E_host.data_ptr(), r_host.data_ptr()))
         sb.sb_destroy(c2)
-        return E.value
 
     e2e_once(7)
     torch.cuda.synchronize(dev)
+    e2e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         e2e_once(100 + i)
     torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = reduce_step_ms(e2e_s * 1e3, ws, dist if ws > 1 else None, dev) * 1e-3
-    e2e = {"value": job_value(units, ws, e2e_s * 1e3), "unit": "spin-updates/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s}
+    e2e = {"value": job_value(units, ws, e2e_s * 1e3), "unit": "spin-updates/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s,
+           "calls": "sb_create_batch + sb_set_factor + sb_run + sb_best + sb_destroy"
+           if use_factor else "sb_create_batch + sb_run + sb_best + sb_destroy"}
 
-    extra = {}
-    if rank == 0 and not args.no_ttt:
-        extra["ttt"] = time_to_target(sb, ctx, q, ev, w, args.variant, stream, sched, dev)
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline and N <= 100000:
-        cpu = oracle_sample(w, args.variant)
-        k = int(cpu["sample"].split()[0])
-        cpu.pop("seconds", None)
-        cpu["cpu"] = cpu_model()
-        cpu["nproc"] = os.cpu_count()
-        cpu["all_cores"] = oracle_all_cores(w, args.variant, k)
-
-    launches_per_step = 3 + S + 4   # set_c0 + init + set_c0, S x step, energy partial/reduce/argmin/best_T
     line = {"metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "n_tracks": w["n_tracks"], "N": N, "nnz": nnz,
-                       "replicas": R, "sb_steps": S, "variant": args.variant,
-                       "J": w["jprec"], "state": "f32", "l2": "flushed between steps (256 MB write)",
-                       "parallelism": f"replicas{ws}",
-                       "autotune": None if tuned is None else tuned[0]},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "config": {"workload": w["name"], "events": E, "tracks": [e["n_tracks"] for e in w["events"]]
+                       if E == 1 else {"min": min(e["n_tracks"] for e in w["events"]),
+                                       "max": max(e["n_tracks"] for e in w["events"])},
+                       "sum_N": N, "sum_nnz": nnz,
+                       "N_min": min(q.n for q in qs), "N_max": max(q.n for q in qs),
+                       "replicas": R, "sb_steps": S, "variant": variant, "J": w["jprec"],
+                       "state": "f32", "c0": "0.5 / (sqrt(N) sigma_J) per event",
+                       "l2": "flushed between steps (256 MB write)" if flush is not None
+                       else f"state {state_bytes / 1e9:.1f} GB > L2 (no flush needed)",
+                       "parallelism": f"replicas{ws}", "factor": finfo if use_factor else None,
+                       "autotune": cfg, "autotune_us_per_step": tune_us,
+                       "host_build_s": t_build},
+            "roofline": roofline, "e2e": e2e,
+            "gpu_launches": (3 + (1 if variant == "dsb" else 0) + S * len(knames) + 4) * args.steps,
             "clocks": clk, "wall_s_timed": t_wall}
-    line.update(extra)
-    if cpu is not None:
+    small = E > 1 or N <= 100000   # the oracle's pure-Python builder must finish in seconds
+    if rank == 0 and not args.no_energy_check and small:
+        sb.sb_run(ctx, variant, a0, 0.0, dt, S, R, 31, None, stream)
+        T_best, E_best, _ = sb.sb_best(ctx)
+        line["energy_error"] = energy_error(sb, w, pairs, T_best, E_best)
+    if rank == 0 and not args.no_ttt:
+        line["ttt"] = time_to_target(sb, w, pairs, ctx, stream, dev,
+                                     [sample_events(w)[i] for i in range(min(4, E))]
+                                     if E > 1 else [0])
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and small:
+        cpu = oracle_sample(w)
+        cpu_all = oracle_all_cores(w, cpu["steps"])
+        for k in ("seconds", "units", "steps"):
+            cpu.pop(k, None)
+        cpu["cpu"] = cpu_model()
+        cpu["nproc"] = os.cpu_count()
+        cpu["all_cores"] = cpu_all
         line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -554,456 +828,13 @@ def run_ours(args):
     return 0
 
 
-def _ttt_from(times, p_reps, R):
-    """min_k t(k) max(1, ln 0.01 / ln(1 - p_run(k))), p_run = 1 - (1 - p_rep)^R."""
-    best, k_best = math.inf, None
-    for k, (t, p) in enumerate(zip(times, p_reps)):
-        pr = 1.0 - (1.0 - p) ** R
-        if pr <= 0.0:
-            continue
-        v = t if pr >= 0.99 else t * math.log(0.01) / math.log(1.0 - pr)
-        if v < best:
-            best, k_best = v, k
-    return (None, None) if best == math.inf else (best, k_best)
-
-
-def time_to_target(sb, ctx, q, ev, w, variant, stream, sched, dev, plain_runs=16):
-    """Time-to-target (section "Results", Table 1) of the batched BF16 form and of
-    the plain FP32 form (FP32 J, one replica per run, one kernel launch per
-    step, no graph, runs one after another).
-
-    Target: 99.9 % of the lowest energy obtained in this study (section
-    "Results"): the minimum over the timed runs and one reference run of
-    4 S steps and R replicas, read as E_best + 0.001 |E_best|; the energy of the
-    generator's true triplets is reported beside it. p_rep(k) = fraction of the
-    batched run's R replicas at or below the target at checkpoint k (every 50
-    steps); a batched run succeeds when any replica does. Both forms run the
-    same per-replica FP32 arithmetic (BF16 stores the +-1/4-valued J exactly),
-    so p_rep(k) serves both; the plain runs' own final successes are reported
-    as a check."""
-    import torch
-    R, S, a0, dt = w["replicas"], w["steps"], w["a0"], w["dt"]
-    every = 50
-    ev_a = ev.arrays()
-    part = ev_a["particle"]
-    truth = np.array([1 if part[a] == part[b] == part[c] >= 0 else 0 for a, b, c in q.trip],
-                     np.int8)
-    E_truth = float(sb.sb_energy(ctx, np.where(truth > 0, 1, -1).astype(np.int8)[:, None])[0, 0])
-    d_E = torch.empty(R, dtype=torch.float64, device=dev)
-    start = torch.cuda.Event(enable_timing=True)
-    marks, energies = [], []
-    sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)   # chunks of `every` steps: direct launches
-    sb.sb_run(ctx, variant, a0, 0.0, dt, 0, R, 4242, None, stream)
-    start.record(stream)
-    for k0 in range(0, S, every):
-        n = min(every, S - k0)
-        sb.sb_advance(ctx, variant, a0, 0.0, dt, n, sched[k0:k0 + n], stream)
-        sb.sb_readout_device(ctx, d_E, None, None, None, stream)
-        e = torch.cuda.Event(enable_timing=True)
-        e.record(stream)
-        marks.append(e)
-        energies.append(d_E.clone())
-    torch.cuda.synchronize(dev)
-    sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 1)
-    times = [start.elapsed_time(m) * 1e-3 for m in marks]
-    Es = [e.cpu().numpy() for e in energies]
-    T_best, E_b, _ = sb.sb_best(ctx)
-    sc = sb.sb_tracks(ev, q, T_best)
-    # reference run: 4 S steps on the linear ramp
-    sb.sb_run(ctx, variant, a0, 0.0, dt, 4 * S, R, 5151, None, stream)
-    sb.sb_readout_device(ctx, d_E, None, None, None, stream)
-    torch.cuda.synchronize(dev)
-    e_ref = float(d_E.min().item())
-
-    # plain FP32 form: one replica per run, one launch per step, no graph
-    ctxp = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_FP32)
-    sb.sb_set_option(ctxp, sb.SB_OPT_GRAPH, 0)
-    sb.sb_set_option(ctxp, sb.SB_OPT_TILED, 0)
-    sb.sb_run(ctxp, variant, a0, 0.0, dt, 50, 1, 1, None, stream)   # warm-up
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    finals = []
-    e0.record(stream)
-    for i in range(plain_runs):
-        sb.sb_run(ctxp, variant, a0, 0.0, dt, S, 1, 7000 + i, None, stream)
-        sb.sb_readout_device(ctxp, d_E[:1], None, None, None, stream)
-        finals.append(d_E[:1].clone())
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    t_plain_run = e0.elapsed_time(e1) * 1e-3 / plain_runs
-    plain_E = [float(f.item()) for f in finals]
-    Tp, _, _ = sb.sb_best(ctxp)
-    scp = sb.sb_tracks(ev, q, Tp)
-    e_best = min(e_ref, min(float(e.min()) for e in Es), min(plain_E))
-    target = e_best + 0.001 * abs(e_best)
-    p_reps = [float(np.mean(e <= target)) for e in Es]
-    ttt_b, kb = _ttt_from(times, p_reps, R)
-    plain_ok = float(np.mean([v <= target for v in plain_E]))
-    times_plain = [t_plain_run * min(S, (k + 1) * every) / S for k in range(len(times))]
-    ttt_p, kp = _ttt_from(times_plain, p_reps, 1)
-    # the library's own form at one replica: BF16 J, graph replay
-    sb.sb_run(ctx, variant, a0, 0.0, dt, S, 1, 1, None, stream)
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    for i in range(4):
-        sb.sb_run(ctx, variant, a0, 0.0, dt, S, 1, 100 + i, None, stream)
-        sb.sb_readout_device(ctx, d_E[:1], None, None, None, stream)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    t_r1 = e0.elapsed_time(e1) * 1e-3 / 4
-    ttt_1, k1 = _ttt_from([t_r1 * min(S, (k + 1) * every) / S for k in range(len(times))], p_reps, 1)
-    return {"target": target, "E_best": e_best, "E_reference_run": e_ref, "E_truth": E_truth,
-            "gap_to_truth": (e_best - E_truth) / abs(E_truth),
-            "E_final_best": float(E_b[0]), "checkpoint_every": every,
-            "batched_bf16": {"seconds": ttt_b, "at_step": None if kb is None else (kb + 1) * every,
-                             "run_seconds": times[-1], "replicas_per_run": R,
-                             "p_rep_final": p_reps[-1]},
-            "plain_fp32": {"seconds": ttt_p, "at_step": None if kp is None else (kp + 1) * every,
-                           "run_seconds": t_plain_run, "replicas_per_run": 1,
-                           "runs_timed": plain_runs, "plain_runs_at_target": plain_ok,
-                           "efficiency_last_run": scp["efficiency"], "purity_last_run": scp["purity"],
-                           "spin_updates_per_s": q.n * S / t_plain_run},
-            "bf16_graph_r1": {"seconds": ttt_1, "run_seconds": t_r1, "replicas_per_run": 1},
-            "speedup_batched_vs_plain": (ttt_p / ttt_b) if (ttt_b and ttt_p) else None,
-            "speedup_best_vs_plain": (ttt_p / min(v for v in (ttt_b, ttt_1) if v))
-            if (ttt_p and (ttt_b or ttt_1)) else None,
-            "efficiency": sc["efficiency"], "purity": sc["purity"],
-            "note": "batched: one run of R replicas with a readout every 50 steps (timed)"}
-
-
-def run_batch(args):
-    """512 uneven events in one context (sb_create_batch), step-kernel shape from
-    sb_autotune, the whole batch advanced by one launch per step replayed from
-    a CUDA graph. Plain FP32 form for comparison: one event and one replica per
-    run, one launch per step, no graph, timed on a sample of events and scaled
-    to the batch's spin-updates."""
-    import torch
-    from concurrent.futures import ThreadPoolExecutor
-    import paper_2402_14718_gb300 as sb
-    from paper_2402_14718_gb300.workloads import BATCH512, batch512_tracks
-
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(0)
-    stream = torch.cuda.current_stream(dev)
-    B = BATCH512
-    tracks = batch512_tracks()
-    R, S, a0, dt, variant = B["replicas"], B["steps"], B["a0"], B["dt"], B["variant"]
-    if args.sb_steps:
-        S = args.sb_steps
-
-    def build(e):
-        ev = sb.sb_event_generate(B["seed0"] + e, sb.event_params(n_tracks=tracks[e],
-                                                                  noise_frac=B["noise_frac"]))
-        return sb.sb_qubo_build(ev, sb.build_params(**B["cuts"]))
-
-    t0 = time.perf_counter()
-    with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
-        qs = list(ex.map(build, range(B["n_events"])))
-    t_build = time.perf_counter() - t0
-    NS = sum(q.n for q in qs)
-    NZ = sum(q.nnz for q in qs)
-    ctx = sb.sb_create_batch([(q.rowptr, q.col, q.val, q.lin) for q in qs], sb.SB_J_BF16)
-    if args.dsb_signs >= 0:
-        sb.sb_set_option(ctx, sb.SB_OPT_DSB_SIGNS, args.dsb_signs)
-    if args.profile_steps:
-        # profiling driver: the library's default step (the autotuner's pick on
-        # this batch), one direct launch per step, no timing
-        sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
-        if args.rows_per_cta:
-            sb.sb_set_option(ctx, sb.SB_OPT_STEP_RPC, args.rows_per_cta)
-        sb.sb_run(ctx, variant, a0, 0.0, dt, 0, R, 1, None, stream)
-        sch = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
-        sb.sb_advance(ctx, variant, a0, 0.0, dt, min(args.profile_steps, S), sch, stream)
-        torch.cuda.synchronize(dev)
-        print(json.dumps({"profile_steps": args.profile_steps, "sum_N": NS, "sum_nnz": NZ, "R": R}))
-        return 0
-    cfg, us = sb.sb_autotune(ctx, variant, R, trial_steps=20)
-    sched = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
-    E = len(qs)
-    d_E = torch.empty(E * R, dtype=torch.float64, device=dev)
-    d_bE = torch.empty(E, dtype=torch.float64, device=dev)
-    d_br = torch.empty(E, dtype=torch.int32, device=dev)
-    d_T = torch.empty(NS, dtype=torch.uint8, device=dev)
-
-    def one(seed, marks=None):
-        if marks:
-            marks[0].record(stream)
-        sb.sb_run(ctx, variant, a0, 0.0, dt, 0, R, seed, None, stream)
-        if marks:
-            marks[1].record(stream)
-        sb.sb_advance(ctx, variant, a0, 0.0, dt, S, sched, stream)
-        if marks:
-            marks[2].record(stream)
-        sb.sb_readout_device(ctx, d_E, d_bE, d_br, d_T, stream)
-        if marks:
-            marks[3].record(stream)
-
-    for i in range(args.warmup):
-        one(10 + i)
-    torch.cuda.synchronize(dev)
-    marks = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    clocks = Clocks(0, enabled=not args.no_clocks)
-    for i in range(args.steps):
-        one(100 + i, marks[i])
-    torch.cuda.synchronize(dev)
-    clk = clocks.stop()
-    ms = float(np.mean([m[0].elapsed_time(m[3]) for m in marks]))
-    sweep = float(np.mean([m[1].elapsed_time(m[2]) for m in marks])) * 1e-3 / S
-    value = NS * R * S / (ms * 1e-3)
-    alg_bytes = 16 * NS * R + NZ * 6 + (NS + 1) * 4 + NS * 4
-    hbm, src = peaks()
-    # plain FP32 form on a sample of events (evenly spaced in the event list)
-    sample = list(range(0, E, max(1, E // 8)))[:8]
-    t_plain, units_plain = 0.0, 0
-    for e in sample:
-        q = qs[e]
-        cp = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_FP32)
-        sb.sb_set_option(cp, sb.SB_OPT_GRAPH, 0)
-        sb.sb_run(cp, variant, a0, 0.0, dt, 20, 1, 1, None, stream)
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sb.sb_run(cp, variant, a0, 0.0, dt, S, 1, 2, None, stream)
-        sb.sb_readout_device(cp, d_E[:1], None, None, None, stream)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        t_plain += e0.elapsed_time(e1) * 1e-3
-        units_plain += q.n * S
-    plain = units_plain / t_plain
-    line = {"metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": "batch512", "events": E, "sum_N": NS, "sum_nnz": NZ,
-                       "N_min": min(q.n for q in qs), "N_max": max(q.n for q in qs),
-                       "replicas": R, "sb_steps": S, "variant": variant, "J": "bf16",
-                       "autotune": cfg, "autotune_us_per_step": us, "host_build_s": t_build},
-            "roofline": {"bound": "hbm", "achieved": alg_bytes / sweep / 1e9, "peak": hbm,
-                         "unit": "GB/s", "frac": alg_bytes / sweep / 1e9 / hbm,
-                         "traffic": MEASURED_TRAFFIC.get(
-                             ("batch512", variant, tuned_kernel(cfg, variant, R, args.dsb_signs),
-                              (cfg["rows_per_warp"], cfg["rows_per_cta"], cfg["tile"]),
-                              kernel_source_hash(tuned_kernel(cfg, variant, R, args.dsb_signs)))),
-                         "kernel": tuned_kernel(cfg, variant, R, args.dsb_signs),
-                         "peak_source": src,
-                         "alg_bytes_per_launch": alg_bytes,
-                         "kstep_us": sweep * 1e6},
-            "plain_fp32_spin_updates_per_s": plain,
-            "batched_vs_plain_throughput": value / plain,
-            "plain_sample": f"{len(sample)} events, 1 replica each, {S} steps, direct launches",
-            "gpu_launches": (3 + S + 4) * args.steps, "clocks": clk}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-def _qubo_energy_trace(sb, ctx, variant, a0, c0, dt, S, R, seed, every, stream, dev):
-    """Energies of all R shots every `every` steps and the time to each checkpoint."""
-    import torch
-    sched = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
-    d_E = torch.empty(R, dtype=torch.float64, device=dev)
-    sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)
-    sb.sb_run(ctx, variant, a0, c0, dt, 0, R, seed, None, stream)
-    t0 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    marks, Es = [], []
-    for k0 in range(0, S, every):
-        n = min(every, S - k0)
-        sb.sb_advance(ctx, variant, a0, c0, dt, n, sched[k0:k0 + n], stream)
-        sb.sb_readout_device(ctx, d_E, None, None, None, stream)
-        e = torch.cuda.Event(enable_timing=True)
-        e.record(stream)
-        marks.append(e)
-        Es.append(d_E.clone())
-    torch.cuda.synchronize(dev)
-    return [t0.elapsed_time(m) * 1e-3 for m in marks], [e.cpu().numpy() for e in Es]
-
-
-def run_study(args):
-    import torch
-    import paper_2402_14718_gb300 as sb
-    from paper_2402_14718_gb300.workloads import CUTS_DENSE, PAPER_SIZES, WORKLOADS
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(0)
-    stream = torch.cuda.current_stream(dev)
-    if args.study == "kernels":
-        # every step kernel on the workload: microseconds per step (graph replay,
-        # CUDA events, best of 3 x 200 steps) and bit-equality with the untiled kernel
-        w = WORKLOADS[args.workload]
-        R = w["replicas"]
-        ev = sb.sb_event_generate(w["seed"], sb.event_params(n_tracks=w["n_tracks"],
-                                                             noise_frac=w["noise_frac"]))
-        q = sb.sb_qubo_build(ev, sb.build_params(**w["cuts"]))
-        prec = sb.SB_J_BF16 if w["jprec"] == "bf16" else sb.SB_J_FP32
-        S = 200
-        sched = torch.tensor(np.linspace(0, 1, S).astype(np.float32), device=dev)
-        # (option, rows per CTA, replica tile (0: automatic), dSB gather form)
-        kernels = [("untiled", 0, 0, -1), ("untiled", 32, 0, -1), ("rowgroup2", 0, 0, -1),
-                   ("rowgroup2", 32, 0, -1), ("rowgroup2", 0, 128, -1), ("rowgroup4", 0, 0, -1),
-                   ("rowgroup4", 0, 128, -1), ("stream", 0, 0, -1), ("tiled", 0, 0, -1)]
-        for variant in ("bsb", "dsb"):
-            ref = None
-            for name, rpc, rt, signs in kernels + (
-                    [("untiled", 0, 0, 0)] if variant == "dsb" else []):
-                if rt and R % rt:
-                    continue
-                ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, prec)
-                kname = set_kernel(sb, ctx, name, variant, R, signs)
-                sb.sb_set_option(ctx, sb.SB_OPT_STEP_RPC, rpc)
-                sb.sb_set_option(ctx, sb.SB_OPT_STEP_RT, rt)
-                sb.sb_run(ctx, variant, 1.0, 0.0, 0.5, 0, R, 7, None, stream)
-                sb.sb_advance(ctx, variant, 1.0, 0.0, 0.5, S, sched, stream)
-                x, y = sb.sb_get_state(ctx)
-                same = None
-                if ref is None:
-                    ref = (x, y)
-                else:
-                    same = bool(np.array_equal(ref[0], x) and np.array_equal(ref[1], y))
-                best = 1e30
-                for _ in range(3):
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    sb.sb_advance(ctx, variant, 1.0, 0.0, 0.5, S, sched, stream)
-                    e1.record(stream)
-                    torch.cuda.synchronize(dev)
-                    best = min(best, e0.elapsed_time(e1) * 1e3 / S)
-                print(json.dumps({"study": "kernels", "workload": args.workload, "N": q.n,
-                                  "nnz": q.nnz, "R": R, "variant": variant, "kernel": kname,
-                                  "option": name, "rows_per_cta": rpc, "replica_tile": rt,
-                                  "dsb_signs": signs,
-                                  "us_per_step": best,
-                                  "same_state_as_first": same}), flush=True)
-                sb.sb_destroy(ctx)
-        return 0
-    if args.study == "paper-sizes":
-        # section "Results": a0 = dt = 1, fixed c0, 50 shots; bSB and dSB
-        S, R, every = (args.sb_steps or 2000), 50, 20
-        for p in PAPER_SIZES:
-            ev = sb.sb_event_generate(p["seed"], sb.event_params(n_tracks=p["n_tracks"]))
-            q = sb.sb_qubo_build(ev, sb.build_params(**CUTS_DENSE))
-            ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_BF16)
-            off = sb.sb_info(ctx)["offset"]
-            for variant in ("bsb", "dsb"):
-                times, Es = _qubo_energy_trace(sb, ctx, variant, 1.0, 0.0, 1.0, S, R, 1, every,
-                                               stream, dev)
-                fin = Es[-1]
-                T, Eb, _ = sb.sb_best(ctx)
-                sc = sb.sb_tracks(ev, q, T)
-                pick = [int(v) for v in np.linspace(0, len(Es) - 1, 12)]
-                print(json.dumps({
-                    "study": "paper-sizes", "paper_N": p["paper_N"], "N": q.n, "nnz": q.nnz,
-                    "tracks": p["n_tracks"], "variant": variant, "shots": R, "steps": S,
-                    "a0": 1.0, "dt": 1.0, "c0": "auto",
-                    "final_ising_min": float(fin.min() - off), "final_ising_mean": float(fin.mean() - off),
-                    "final_ising_std": float(fin.std()), "final_ising_max": float(fin.max() - off),
-                    "run_seconds": times[-1],
-                    "trace": [{"t": times[i], "step": int((i + 1) * every), "mean": float(Es[i].mean() - off),
-                               "min": float(Es[i].min() - off), "max": float(Es[i].max() - off)}
-                              for i in pick],
-                    "efficiency": sc["efficiency"], "purity": sc["purity"]}), flush=True)
-        return 0
-    if args.study == "adjoint":
-        # 500-track workload: bSB forward vs sb_backward (checkpoint every 32 steps)
-        w = WORKLOADS["event500"]
-        ev = sb.sb_event_generate(w["seed"], sb.event_params(n_tracks=w["n_tracks"],
-                                                             noise_frac=w["noise_frac"]))
-        q = sb.sb_qubo_build(ev, sb.build_params(**w["cuts"]))
-        ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_FP32)
-        sb.sb_set_weights(ctx, q.cls, q.quality, 1.0, 1.0)
-        S, R, c0 = (args.sb_steps or w["steps"]), w["replicas"], sb.sb_info(ctx)["c0_auto"]
-        sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 0)   # both directions launch one kernel per step
-        sb.sb_run(ctx, "bsb", 1.0, c0, 0.5, S, R, 1, None, stream)
-        sb.sb_backward(ctx, 1.0, c0, 0.5, S, R, 1, None, 32)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for _ in range(3):
-            sb.sb_run(ctx, "bsb", 1.0, c0, 0.5, S, R, 1, None, stream)
-        torch.cuda.synchronize(dev)
-        t_fwd = (time.perf_counter() - t0) / 3
-        for K in (32, S):   # checkpoint every 32 steps; whole run recorded once
-            sb.sb_backward(ctx, 1.0, c0, 0.5, S, R, 1, None, K)
-            t0 = time.perf_counter()
-            for _ in range(3):
-                loss, g = sb.sb_backward(ctx, 1.0, c0, 0.5, S, R, 1, None, K)
-            t_bwd = (time.perf_counter() - t0) / 3
-            print(json.dumps({"study": "adjoint", "N": q.n, "R": R, "steps": S, "ckpt_every": K,
-                              "forward_s": t_fwd, "backward_s": t_bwd,
-                              "backward_over_forward": t_bwd / t_fwd,
-                              "loss": loss, "grads": g}), flush=True)
-        return 0
-    if args.study == "build":
-        # QUBO construction time (left out of the paper's timings): host C++ vs GPU
-        for name in ("event1000", "event10k"):
-            w = WORKLOADS[name]
-            ev = sb.sb_event_generate(w["seed"], sb.event_params(n_tracks=w["n_tracks"],
-                                                                 noise_frac=w["noise_frac"]))
-            p = sb.build_params(**w["cuts"])
-            t0 = time.perf_counter()
-            qh = sb.sb_qubo_build(ev, p)
-            t_host = time.perf_counter() - t0
-            sb.sb_qubo_build_device(ev, p)                     # warm-up
-            t0 = time.perf_counter()
-            qd, ms = sb.sb_qubo_build_device(ev, p)
-            t_dev = time.perf_counter() - t0
-            print(json.dumps({"study": "build", "workload": name, "N": qh.n, "nnz": qh.nnz,
-                              "host_s": t_host, "device_kernels_ms": ms, "device_call_s": t_dev,
-                              "same_structure": bool(qd.n == qh.n and np.array_equal(qd.col, qh.col))}),
-                  flush=True)
-        return 0
-    if args.study == "c0-scan":
-        # section "Results": fixed c0 versus a scan
-        w = WORKLOADS["event1000"]
-        ev = sb.sb_event_generate(w["seed"], sb.event_params(n_tracks=w["n_tracks"],
-                                                             noise_frac=w["noise_frac"]))
-        q = sb.sb_qubo_build(ev, sb.build_params(**w["cuts"]))
-        ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_BF16)
-        c0a = sb.sb_info(ctx)["c0_auto"]
-        S, R = 2000, 64
-        for f in (0.25, 0.5, 1.0, 2.0, 4.0):
-            sb.sb_run(ctx, "bsb", 1.0, c0a * f, 0.5, S, R, 3, None, stream)
-            E = sb.sb_energy(ctx, None, R)[0]
-            T, _, _ = sb.sb_best(ctx)
-            sc = sb.sb_tracks(ev, q, T)
-            print(json.dumps({"study": "c0-scan", "c0": c0a * f, "c0_over_auto": f,
-                              "median_E": float(np.median(E)), "min_E": float(E.min()),
-                              "efficiency": sc["efficiency"], "purity": sc["purity"]}), flush=True)
-        return 0
-    if args.study == "schedule":
-        # a(t) learned by gradient descent on the mean relaxed energy (sb_backward)
-        w = WORKLOADS["event500"]
-        ev = sb.sb_event_generate(w["seed"], sb.event_params(n_tracks=w["n_tracks"],
-                                                             noise_frac=w["noise_frac"]))
-        q = sb.sb_qubo_build(ev, sb.build_params(**w["cuts"]))
-        ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_FP32)
-        sb.sb_set_weights(ctx, q.cls, q.quality, 1.0, 1.0)
-        # the relaxed energy at the last step is piecewise constant in a(t) once every
-        # spin sits on a wall (long bSB runs): learn on a horizon that ends mid-bifurcation
-        S, R, c0 = (args.sb_steps or 60), w["replicas"], sb.sb_info(ctx)["c0_auto"]
-        a = torch.tensor(np.array([0.5 * k / (S - 1) for k in range(S)], np.float32), device=dev)
-        g = torch.zeros(S, dtype=torch.float64, device=dev)
-        for it in range(args.steps):
-            loss, grads = sb.sb_backward(ctx, 1.0, c0, 0.5, S, R, 11, a, 32, g)
-            sb.sb_run(ctx, "bsb", 1.0, c0, 0.5, S, R, 11, a, stream)
-            E = sb.sb_energy(ctx, None, R)[0]
-            x, _ = sb.sb_get_state(ctx)
-            print(json.dumps({"study": "schedule", "iter": it, "steps": S, "relaxed_loss": loss,
-                              "fraction_on_walls": float(np.mean(np.abs(x) == 1.0)),
-                              "median_qubo_E": float(np.median(E)), "min_qubo_E": float(E.min()),
-                              "grad_inf": float(g.abs().max()), "dL_ddt": grads["dt"],
-                              "dL_dc0": grads["c0"]}), flush=True)
-            step = 0.05 * g / max(float(g.abs().max()), 1e-30)
-            a = torch.clamp(a - step.to(torch.float32), 0.0, 1.0).contiguous()
-        return 0
-    return 0
-
-
 def main():
     args = parse()
     if args.study:
+        from bench_studies import run_study
         return run_study(args)
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batch512":
-        return run_batch(args)
     return run_ours(args)
 
 

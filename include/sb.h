@@ -143,6 +143,22 @@ sb_status sb_qubo_arrays(const sb_qubo* q, int32_t* rowptr, int32_t* col, double
 void sb_qubo_destroy(sb_qubo* q);
 
 /*
+ * sb_qubo_factor -- the shared-hit structure of the builder's conflict
+ * couplings (Eq. 13, "any conflict" read as two triplets that share a hit and
+ * start on the same or adjacent layers), for sb_set_factor. A triplet holding
+ * hit h at position p (0, 1, 2 for a, b, c) starts on layer(h) - p, so two
+ * triplets that share h at positions p, p' start |p - p'| layers apart and
+ * conflict exactly when |p - p'| <= 1 (unless they are a consistent pair).
+ * Outputs (host, caller-allocated): member[3 n] = the triplets' hit ids
+ * (row-major, position p at 3 i + p), couple[9] = W[p][p'] = 1 iff
+ * |p - p'| <= 1, *w = the conflict weight w_c the QUBO was built with,
+ * *n_ids = the event's hit count (ids lie in [0, n_ids)). SB_ERR_ARG on a
+ * NULL argument.
+ */
+sb_status sb_qubo_factor(const sb_qubo* q, int32_t* member, uint8_t* couple, double* w,
+                         int32_t* n_ids);
+
+/*
  * sb_qubo_build_device -- the builder above run on the current GPU (hits
  * uploaded from the host event; count / scan / write passes over doublets,
  * triplets, hit incidences and triplet pairs). The result is the same sb_qubo
@@ -218,6 +234,46 @@ int32_t sb_total_rows(const sb_ctx* ctx);
 sb_status sb_step_info(const sb_ctx* ctx, int32_t* rows_per_warp, int64_t* union_entries);
 
 /*
+ * sb_set_factor -- factored form of the coupling product of Eq. 2 / 6 / 10 for
+ * QUBOs in which one weight w is shared by whole groups of rows (Eq. 13: every
+ * conflict pair carries w_c). Rows (triplets) belong to group blocks (hits)
+ * through K slots (positions); with T_{g,s} = sum of x_i over the rows i whose
+ * slot s names block g, and the K x K 0/1 slot-coupling pattern W, the
+ * product becomes
+ *   sum_j J_ij x_j = jf sum_s U_{member[i][s], s} + sum_j Rs_ij x_j,
+ *   U_{g,s} = sum_{s'} W[s][s'] T_{g,s'},   jf = -w / 4 (J = -b / 4),
+ * where the residual Rs = J - jf M^T W M (M: the row-to-(block, slot)
+ * incidence; diagonal included) is formed here from the context's QUBO in
+ * exact FP64 arithmetic. Each step then forms the U rows (one pass over the
+ * members of the blocks in use) and, per row, reads its K U rows and its
+ * residual row instead of its whole CSR row. A row stays in plain CSR form
+ * when its residual is not exactly representable in the context's J
+ * precision or when it would read more (its K U rows, its K memberships and
+ * its residual against its CSR length). The factor changes only the rounding
+ * order of the FP32 coupling sums (for dSB with weights that are multiples of
+ * 1/4 every partial sum is exact and the states equal the plain kernels' bit
+ * for bit). Used by aSB / bSB when R / 4 is a power of two <= 32 or a
+ * multiple of 32, and by dSB with sign bytes when R / 16 is a power of two
+ * <= 32 or a multiple of 32 and no U element can exceed 256 members; other
+ * runs use the plain kernels. SB_OPT_FACTOR switches it off.
+ * Inputs (host, copied): n_ids (ids lie in [0, n_ids)); k slots, 1 <= k <= 4;
+ * member[n k] (block id of row i's slot s at k i + s, -1 for none); couple[k
+ * k] (symmetric 0/1); w (finite, non-zero, -w / 4 exact in FP32). In a batched
+ * context every block's members must lie in one event (offset the ids per
+ * event). n_ids = 0 with member and couple NULL removes the factor.
+ * Errors: SB_ERR_ARG on invalid arguments (nothing changes). sb_set_weights
+ * removes the factor (its weight and residual belong to the old couplings).
+ * Synchronous.
+ */
+sb_status sb_set_factor(sb_ctx* ctx, int32_t n_ids, int32_t k, const int32_t* member,
+                        const uint8_t* couple, double w);
+
+/* Sizes of the factored form: out[7] = {set (0/1), rows in factored form,
+ * residual nonzeros, U rows, group blocks in use, their member entries, most
+ * members behind one U element}. */
+sb_status sb_factor_info(const sb_ctx* ctx, int64_t* out);
+
+/*
  * sb_gather_probe -- a diagnostic of the on-chip bound of the coupling product
  * (no SB arithmetic): the rate at which the GPU reads whole rows of an array
  * at random row indices, as the step reads neighbour rows. array_bytes: size
@@ -240,7 +296,9 @@ sb_status sb_gather_probe(int64_t array_bytes, int32_t row_bytes, int32_t repeat
  *   |x| > 1 -> x = sgn(x), y = 0.
  * Initial state: x, y ~ U(-0.01, 0.01) from Philox4x32-10, counter
  * (row within event, replica, 3, event), key = seed.
- * c0 <= 0 selects each event's c0_auto. a_sched: device FP32 array of `steps`
+ * c0 > 0 is used for every event; c0 = 0 selects each event's c0_auto; c0 < 0
+ * selects -c0 times each event's c0_auto (a scale relative to the automatic
+ * value, per event). a_sched: device FP32 array of `steps`
  * values a_k, or NULL for the linear ramp a_k = a0 k / (steps - 1).
  * Allocates the N x R state on first use (kept for later calls with the same
  * R). 1 <= replicas <= 65535, 0 <= steps. Asynchronous on `stream`.
@@ -386,7 +444,7 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
  *   SB_OPT_STEP_UNROLL (4): neighbour rows gathered at once per thread (4).
  *   SB_OPT_DSB_SIGNS (5): 1 (default) lets dSB gather one byte per sign of x
  *   (written by the step that writes x) instead of FP32 positions; taken only
- *   while every |J_ij| < 2^125 (bounded through sigma_J), else positions.
+ *   while every |J_ij| < 2^118 (bounded through sigma_J), else positions.
  *   SB_OPT_REPLICA_GROUPS (6): run the replicas as this many groups one after
  *   another, each for all steps (R / groups replicas per group, a multiple of 4
  *   with R / (4 groups) a power of two <= 32), so a group's state stays in L2.
@@ -453,6 +511,10 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
  * flight with a bound and returns. -1 (default) turns it off. Nothing
  * faults or hangs either way: every wait is bounded. */
 #define SB_OPT_TEST_SKIP_STAGE 13
+/* SB_OPT_FACTOR (14): -1 (default) or 1 runs the factored coupling product
+ * whenever sb_set_factor has set one and the run is supported; 0 runs the
+ * plain kernels. sb_autotune times both and sets this option. */
+#define SB_OPT_FACTOR 14
 sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
 
 /*
@@ -460,8 +522,8 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
  * row-group kernel, replica-tile width, rows per CTA) for this context, variant and replica
  * count by timing each candidate for `trial_steps` steps with CUDA events on
  * `stream`, and set it on the context. Results do not depend on the choice.
- * Outputs (host, may be NULL): out_cfg[7] = {tiled, tile width, rows per CTA, unroll,
- * replica groups, L2 persist, rows per warp},
+ * Outputs (host, may be NULL): out_cfg[8] = {tiled, tile width, rows per CTA, unroll,
+ * replica groups, L2 persist, rows per warp, factored product (sb_set_factor)},
  * out_us_per_step = the best time. Synchronous; discards the current state.
  */
 sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t trial_steps,

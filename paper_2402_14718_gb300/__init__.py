@@ -14,16 +14,16 @@ from . import _lib
 from ._lib import (SB_ASB, SB_BSB, SB_DSB, SB_J_BF16, SB_J_FP32, SB_OPT_DSB_SIGNS, SB_OPT_GRAPH,
                    SB_OPT_HEAVY_FIRST, SB_OPT_L2_PERSIST, SB_OPT_R1_LANES, SB_OPT_REPLICA_GROUPS,
                    SB_OPT_ROWS_PER_WARP, SB_OPT_STEP_RPC, SB_OPT_STEP_RT, SB_OPT_STEP_UNROLL,
-                   SB_OPT_STREAM, SB_OPT_TEST_SKIP_STAGE, SB_OPT_TILED, SB_OPT_WAIT_NS, SbError,
-                   check, lib)
+                   SB_OPT_STREAM, SB_OPT_TEST_SKIP_STAGE, SB_OPT_TILED, SB_OPT_WAIT_NS,
+                   SB_OPT_FACTOR, SbError, check, lib)
 
 __all__ = [
     "SB_ASB", "SB_BSB", "SB_DSB", "SB_J_FP32", "SB_J_BF16", "SB_OPT_GRAPH", "SB_OPT_TILED",
     "SB_OPT_STREAM", "SB_OPT_ROWS_PER_WARP", "SB_OPT_HEAVY_FIRST", "SB_OPT_R1_LANES", "SB_OPT_STEP_RT", "SB_OPT_STEP_RPC",
     "SB_OPT_STEP_UNROLL", "SB_OPT_DSB_SIGNS", "SB_OPT_REPLICA_GROUPS", "SB_OPT_L2_PERSIST",
-    "SB_OPT_WAIT_NS", "SB_OPT_TEST_SKIP_STAGE", "SbError",
+    "SB_OPT_WAIT_NS", "SB_OPT_TEST_SKIP_STAGE", "SB_OPT_FACTOR", "SbError",
     "event_params", "build_params", "sb_event_generate", "sb_qubo_build", "sb_tracks",
-    "sb_qubo_build_device",
+    "sb_qubo_build_device", "sb_qubo_factor", "sb_set_factor", "sb_factor_info",
     "sb_create", "sb_create_batch", "sb_destroy", "sb_info", "sb_step_info", "sb_gather_probe",
     "sb_run", "sb_advance",
     "sb_set_state", "sb_get_state", "sb_energy", "sb_best", "sb_readout_device", "sb_set_option",
@@ -163,6 +163,18 @@ def sb_qubo_build(event, params=None):
     return Qubo(h.value)
 
 
+def sb_qubo_factor(qubo):
+    """(member [n, 3] int32, couple [3, 3] uint8, w, n_ids) of the builder's QUBO."""
+    member = np.zeros((qubo.n, 3), np.int32)
+    couple = np.zeros((3, 3), np.uint8)
+    w = ctypes.c_double()
+    n_ids = ctypes.c_int32()
+    check(lib.sb_qubo_factor(qubo.handle, member.ctypes.data_as(ctypes.c_void_p),
+                             couple.ctypes.data_as(ctypes.c_void_p), ctypes.byref(w),
+                             ctypes.byref(n_ids)))
+    return member, couple, w.value, n_ids.value
+
+
 def sb_qubo_build_device(event, params=None, stream=None):
     """Build on the GPU; returns (Qubo, device milliseconds)."""
     h = ctypes.c_void_p()
@@ -250,6 +262,25 @@ def sb_info(ctx, e=0):
                       ctypes.byref(sig), ctypes.byref(c0)))
     return {"n": n.value, "nnz": nnz.value, "offset": off.value, "sigma_j": sig.value,
             "c0_auto": c0.value}
+
+
+def sb_set_factor(ctx, n_ids, member, couple, w):
+    """``member`` [n, k] int32 block ids (-1: none), ``couple`` [k, k] 0/1; see include/sb.h.
+    ``member=None`` removes the factor."""
+    if member is None:
+        check(lib.sb_set_factor(ctx.handle, 0, 0, None, None, 0.0))
+        return
+    m, pm = _host(member, np.int32)
+    c, pc = _host(couple, np.uint8)
+    k = m.shape[1] if m.ndim == 2 else 1
+    check(lib.sb_set_factor(ctx.handle, int(n_ids), int(k), pm, pc, float(w)))
+
+
+def sb_factor_info(ctx):
+    out = np.zeros(7, np.int64)
+    check(lib.sb_factor_info(ctx.handle, out.ctypes.data_as(ctypes.c_void_p)))
+    keys = ("set", "rows", "residual_nnz", "u_rows", "blocks", "members", "max_count")
+    return {k: int(v) for k, v in zip(keys, out)}
 
 
 def sb_step_info(ctx):
@@ -347,14 +378,14 @@ def sb_energy_noalloc(n, d_rowptr, d_col, d_qval, d_qlin, d_x, d_spins, replicas
 def sb_autotune(ctx, variant, replicas, trial_steps=50, stream=None):
     """Time the step-kernel candidates and keep the fastest; returns
     ({"tiled", "tile", "rows_per_cta", "unroll", "groups", "l2_persist",
-    "rows_per_warp"}, microseconds per step)."""
-    cfg = np.zeros(7, np.int32)
+    "rows_per_warp", "factor"}, microseconds per step)."""
+    cfg = np.zeros(8, np.int32)
     us = ctypes.c_float()
     check(lib.sb_autotune(ctx.handle, _variant(variant), int(replicas), int(trial_steps),
                           cfg.ctypes.data_as(ctypes.c_void_p), ctypes.byref(us), _stream(stream)))
     return {"tiled": int(cfg[0]), "tile": int(cfg[1]), "rows_per_cta": int(cfg[2]),
             "unroll": int(cfg[3]), "groups": int(cfg[4]), "l2_persist": int(cfg[5]),
-            "rows_per_warp": int(cfg[6])}, us.value
+            "rows_per_warp": int(cfg[6]), "factor": int(cfg[7])}, us.value
 
 
 def sb_set_weights(ctx, cls, quality, w_q, w_c):

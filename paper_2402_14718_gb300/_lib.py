@@ -32,6 +32,7 @@ SB_OPT_HEAVY_FIRST = 10
 SB_OPT_R1_LANES = 11
 SB_OPT_WAIT_NS = 12
 SB_OPT_TEST_SKIP_STAGE = 13
+SB_OPT_FACTOR = 14
 
 
 class SbEventParams(ctypes.Structure):
@@ -71,6 +72,9 @@ _SIGS = {
     "sb_qubo_sizes": (c_int32, [c_void_p, P(c_int32), P(c_int64)]),
     "sb_qubo_arrays": (c_int32, [c_void_p] + [c_void_p] * 9),
     "sb_qubo_destroy": (None, [c_void_p]),
+    "sb_qubo_factor": (c_int32, [c_void_p, c_void_p, c_void_p, P(c_double), P(c_int32)]),
+    "sb_set_factor": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_double]),
+    "sb_factor_info": (c_int32, [c_void_p, c_void_p]),
     "sb_qubo_build_device": (c_int32, [c_void_p, P(SbBuildParams), P(c_void_p), P(c_double),
                                        c_void_p]),
     "sb_tracks": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, P(c_int32), c_void_p,

@@ -19,7 +19,7 @@ LIB = os.path.join(PKG, "libsbtrack.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 CU = ["api.cu", "device/kernels.cu", "device/stream.cu", "device/rw.cu", "device/noalloc.cu", "device/build.cu",
-      "device/probe.cu"]
+      "device/probe.cu", "device/factor.cu"]
 # FP64 builder kernels: one IEEE operation per written operation, as on the host
 CU_FLAGS = {"device/build.cu": ["-fmad=false"]}
 CPP = ["host/events.cpp", "host/qubo.cpp", "host/tracks.cpp"]

@@ -150,13 +150,13 @@ struct sb_ctx {
   int step_rpc = 0;   // rows per CTA of the untiled kernel (0: one row per group, -1: one wave)
   int step_unroll = 4;
   int dsb_signs = 1;  // dSB gathers int8 signs instead of FP32 positions
-  // every |J_ij| < 2^125, so the sign-byte gathers may double J exactly
+  // every |J_ij| < 2^118, so the sign-byte gathers may scale J by 2^7 exactly
   bool j_small = true;
   int groups = 1;     // replica groups run one after another (each for all steps)
   int l2_persist = 0; // mark each step's source x as L2-persisting (access-policy window)
   bool l2_raised = false;  // this context raised the persisting-L2 set-aside
   size_t l2_saved = 0;     // the set-aside before it did
-  uint8_t* d_sgn[2] = {nullptr, nullptr};  // dSB sign bytes (top byte of sgn / 2)
+  uint8_t* d_sgn[2] = {nullptr, nullptr};  // dSB sign bytes (0x3C, 0xBC, 0x00; signs.cuh)
   int sms = 0;
   // streamed step kernel (k_step_stream): per-CTA row chunks cut into blocks
   // with their neighbour-column unions; built on first use
@@ -194,6 +194,40 @@ struct sb_ctx {
   std::vector<int32_t> h_rw_gptr;  // host copy of the group pointers
   int32_t* d_rw_order = nullptr;   // chunk of each CTA, heaviest chunk first
   int32_t rw_order_gpc = 0;        // groups per chunk the order was made for
+  // factored coupling product (sb_set_factor): group sums plus an exact residual
+  bool fac_set = false;
+  int fac_use = -1;          // SB_OPT_FACTOR: -1 or 1 use it when set and supported, 0 off
+  int32_t fac_K = 0;
+  uint32_t fac_couple = 0;   // bit 4 s + s': slots s and s' couple
+  float fac_jf = 0.f;        // factor weight in J units (-w / 4)
+  int32_t fac_ng = 0;        // group blocks with a U row in use
+  int32_t fac_urows = 0;
+  int32_t fac_rows = 0;      // rows in factored form
+  int64_t fac_members = 0;   // member entries of those blocks
+  int64_t fac_rnnz = 0;      // residual nonzeros
+  int32_t fac_maxcount = 0;  // most members behind one U element
+  int32_t* d_f_gseg = nullptr;
+  int32_t* d_f_gmem = nullptr;
+  int32_t* d_f_gout = nullptr;
+  int32_t* d_f_uidx = nullptr;
+  int32_t* d_f_rrowptr = nullptr;
+  int32_t* d_f_rcol = nullptr;
+  void* d_f_rJ = nullptr;
+  void* d_f_U = nullptr;     // U rows of the current replica count
+  size_t f_U_bytes = 0;
+  // aSB / bSB with a factor: the row-group kernel over the extended CSR whose
+  // columns n + u are the U rows (kept in the x buffers after the n state rows)
+  std::vector<int32_t> h_fx_rowptr, h_fx_col;  // extended CSR structure
+  void* d_f_xJ = nullptr;                      // its values (context precision)
+  int frw_built = 0;                           // rows per warp of the tables below (0: none)
+  int32_t frw_ngroups = 0;
+  int64_t frw_E = 0;
+  int32_t* d_frw_gptr = nullptr;
+  int32_t* d_frw_rows = nullptr;
+  int32_t* d_frw_ent = nullptr;
+  int32_t* d_frw_pos = nullptr;
+  void* d_frw_ejv = nullptr;
+  int64_t x_rows = 0;                          // rows of each x buffer (>= n)
   // sb_backward's work memory, kept for the next call of the same shape
   struct AdjWork {
     int32_t n = 0, R = 0, S = 0, K = 0;
@@ -339,6 +373,7 @@ void free_readout(sb_ctx* c) {
 void free_state(sb_ctx* c) {
   dfree(c->d_x[0]);
   dfree(c->d_x[1]);
+  c->x_rows = 0;
   dfree(c->d_y);
   dfree(c->d_sgn[0]);
   dfree(c->d_sgn[1]);
@@ -365,8 +400,40 @@ void free_adj(sb_ctx* c) {
   w.n = w.R = w.S = w.K = 0;
 }
 
+void free_factor(sb_ctx* c) {
+  dfree(c->d_f_gseg);
+  dfree(c->d_f_gmem);
+  dfree(c->d_f_gout);
+  dfree(c->d_f_uidx);
+  dfree(c->d_f_rrowptr);
+  dfree(c->d_f_rcol);
+  if (c->d_f_rJ) cudaFree(c->d_f_rJ);
+  c->d_f_rJ = nullptr;
+  if (c->d_f_U) cudaFree(c->d_f_U);
+  c->d_f_U = nullptr;
+  c->f_U_bytes = 0;
+  if (c->d_f_xJ) cudaFree(c->d_f_xJ);
+  c->d_f_xJ = nullptr;
+  std::vector<int32_t>().swap(c->h_fx_rowptr);
+  std::vector<int32_t>().swap(c->h_fx_col);
+  dfree(c->d_frw_gptr);
+  dfree(c->d_frw_rows);
+  dfree(c->d_frw_ent);
+  dfree(c->d_frw_pos);
+  if (c->d_frw_ejv) cudaFree(c->d_frw_ejv);
+  c->d_frw_ejv = nullptr;
+  c->frw_built = 0;
+  c->frw_ngroups = 0;
+  c->frw_E = 0;
+  c->fac_set = false;
+  c->fac_K = c->fac_ng = c->fac_urows = c->fac_rows = c->fac_maxcount = 0;
+  c->fac_members = c->fac_rnnz = 0;
+  c->graph.reset();
+}
+
 void free_all(sb_ctx* c) {
   free_adj(c);
+  free_factor(c);
   dfree(c->d_row_order);
   c->row_order_rpc = 0;
   free_state(c);
@@ -446,10 +513,13 @@ sb_status ensure_state(sb_ctx* c, int32_t R) {
   if (c->R == R && c->d_y) return SB_OK;
   free_state(c);
   const size_t cnt = (size_t)c->n * R;
+  // with a factor, the x buffers also hold the U rows after the n state rows
+  const int64_t xr = (int64_t)c->n + (c->fac_set ? c->fac_urows : 0);
   sb_status st;
-  if ((st = dalloc(&c->d_x[0], cnt)) || (st = dalloc(&c->d_x[1], cnt)) ||
+  if ((st = dalloc(&c->d_x[0], (size_t)xr * R)) || (st = dalloc(&c->d_x[1], (size_t)xr * R)) ||
       (st = dalloc(&c->d_y, cnt)))
     return st;
+  c->x_rows = xr;
   c->R = R;
   c->cur = 0;
   c->have_state = false;
@@ -712,9 +782,10 @@ struct RwHost {
   std::vector<int32_t> gptr, rows, ent, pos;
 };
 
-RwHost build_rw(int32_t n, const int32_t* rp, const int32_t* col, int RW) {
+RwHost build_rw(int32_t n, const int32_t* rp, const int32_t* col, int RW, int32_t ncols = -1) {
   RwHost t;
-  if (n >= (1 << 27) || RW < 2 || RW > sbd::kRwMaxRows) return t;
+  if (ncols < 0) ncols = n;
+  if (ncols >= (1 << 27) || RW < 2 || RW > sbd::kRwMaxRows) return t;
   const int parts = 64;
   struct Part {
     std::vector<int32_t> rows, cnt, ent, pos;
@@ -725,7 +796,7 @@ RwHost build_rw(int32_t n, const int32_t* rp, const int32_t* col, int RW) {
     Part& q = P[part];
     if (e <= b) return;
     std::vector<char> placed((size_t)(e - b), 0);
-    std::vector<int32_t> stamp((size_t)n, -1);
+    std::vector<int32_t> stamp((size_t)ncols, -1);
     int32_t ng = 0;
     if (RW == 2) {
       // The union entries of a pair are deg i + deg j - |N(i) & N(j)|, so the
@@ -1014,16 +1085,31 @@ sb_status check_wait_flag(const sb_ctx* c) {
   return SB_OK;
 }
 
+// exactly representable in FP32 (and, with bf16, in BF16)
+bool exact_in(double v, int bf16, uint32_t* bits) {
+  const float f = (float)v;
+  if ((double)f != v) return false;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if (bf16) {
+    if (u & 0xffffu) return false;
+    *bits = u >> 16;
+  } else {
+    *bits = u;
+  }
+  return true;
+}
+
 // |J_ij| <= sqrt(sum of J^2 over the event) = sigma_J sqrt(n (n - 1)) (the
 // definition of sigma_J over the n (n - 1) off-diagonal places), so this bound
-// keeps 2 J finite and exact in FP32 / BF16 for the sign-byte gathers
+// keeps 2^7 J finite and exact in FP32 for the sign-byte gathers
 void note_j_range(sb_ctx* c) {
   double m = 0.0;
   for (int32_t e = 0; e < c->E; ++e) {
     const double n = (double)(c->ev_row0[e + 1] - c->ev_row0[e]);
     if (n >= 2.0) m = std::max(m, c->sigma[e] * std::sqrt(n * (n - 1.0)));
   }
-  c->j_small = m < 0x1p125;
+  c->j_small = m < 0x1p118;
 }
 
 sb_status create_common(sb_ctx* c, const int32_t* rowptr, const int32_t* col, const double* qval,
@@ -1095,6 +1181,407 @@ sb_status create_common(sb_ctx* c, const int32_t* rowptr, const int32_t* col, co
   return SB_OK;
 }
 
+// ---------------------------------------------------------------- factored coupling product
+// J x = jf (M^T W M) x + Rs x with M the row -> (block, slot) incidence given by
+// the caller, W the K x K slot-coupling pattern, jf = -w / 4, and the residual
+// Rs = J - jf M^T W M formed here, exactly, from the context's QUBO (diagonal
+// included). A row is kept in factored form when its residual is exactly
+// representable in the context's J precision and its factored cost (U rows
+// read + its share of the group sums + residual entries) is below its CSR
+// length; other rows carry their plain CSR row as residual and read no U row.
+
+sb_status set_factor(sb_ctx* c, int32_t n_ids, int32_t K, const int32_t* member,
+                     const uint8_t* couple, double w) {
+  const int32_t n = c->n;
+  if (n_ids < 1 || K < 1 || K > 4 || !member || !couple || !std::isfinite(w) || w == 0.0) {
+    set_error("sb_set_factor: need n_ids >= 1, 1 <= K <= 4, member, couple and a finite w != 0");
+    return SB_ERR_ARG;
+  }
+  const double jf = -w / 4.0;
+  uint32_t jf_bits;
+  if (!exact_in(jf, c->jbf16, &jf_bits)) {
+    set_error("sb_set_factor: -w / 4 must be exactly representable in the context's J precision");
+    return SB_ERR_ARG;
+  }
+  uint32_t cm = 0;
+  for (int s = 0; s < K; ++s)
+    for (int s2 = 0; s2 < K; ++s2) {
+      const uint8_t v = couple[s * K + s2];
+      if (v > 1 || v != couple[s2 * K + s]) {
+        set_error("sb_set_factor: couple must be a symmetric 0/1 matrix");
+        return SB_ERR_ARG;
+      }
+      if (v) cm |= 1u << (4 * s + s2);
+    }
+  // members of each (id, slot), rows ascending (counting sort)
+  const size_t nslot = (size_t)n_ids * K;
+  std::vector<int64_t> seg(nslot + 1, 0);
+  for (size_t t = 0; t < (size_t)n * K; ++t) {
+    const int32_t g = member[t];
+    if (g < -1 || g >= n_ids) {
+      set_error("sb_set_factor: member ids must lie in [-1, n_ids)");
+      return SB_ERR_ARG;
+    }
+    if (g >= 0) ++seg[(size_t)g * K + t % K + 1];
+  }
+  for (size_t t = 0; t < nslot; ++t) seg[t + 1] += seg[t];
+  std::vector<int32_t> mem((size_t)seg[nslot]);
+  {
+    std::vector<int64_t> cur(seg.begin(), seg.end() - 1);
+    for (int32_t i = 0; i < n; ++i)
+      for (int s = 0; s < K; ++s) {
+        const int32_t g = member[(size_t)i * K + s];
+        if (g >= 0) mem[(size_t)cur[(size_t)g * K + s]++] = i;
+      }
+  }
+  std::vector<int32_t> row_ev;
+  if (c->E > 1) {
+    row_ev.resize(n);
+    for (int32_t e = 0; e < c->E; ++e)
+      for (int32_t i = c->ev_row0[e]; i < c->ev_row0[e + 1]; ++i) row_ev[i] = e;
+  }
+  // the QUBO's b values and the context's J values (the plain rows keep them)
+  const size_t nnz = (size_t)c->nnz, esz = c->jbf16 ? 2 : 4;
+  std::vector<double> qv(nnz);
+  std::vector<unsigned char> jraw(nnz * esz);
+  if (nnz) {
+    SB_CUDA(cudaMemcpy(qv.data(), c->d_qval, nnz * 8, cudaMemcpyDeviceToHost));
+    SB_CUDA(cudaMemcpy(jraw.data(), c->d_J, nnz * esz, cudaMemcpyDeviceToHost));
+  }
+  const int32_t* rp = c->h_rowptr.data();
+  const int32_t* col = c->h_col.data();
+  // rows in parallel parts: residual entries and the form of each row
+  const int parts = 64;
+  struct Part {
+    std::vector<int32_t> rcol;
+    std::vector<uint32_t> rbits;
+    bool cross_event = false;
+  };
+  std::vector<Part> pt(parts);
+  std::vector<int32_t> rcount(n);
+  std::vector<uint8_t> isfac(n);
+  const bool ok = parallel_parts(n, parts, [&](int p, int64_t b, int64_t e) {
+    Part& P = pt[p];
+    std::vector<int32_t> cand;
+    std::vector<int32_t> rc;
+    std::vector<uint32_t> rb;
+    for (int64_t i = b; i < e; ++i) {
+      cand.clear();
+      int ns = 0;
+      for (int s = 0; s < K; ++s) {
+        const int32_t g = member[(size_t)i * K + s];
+        if (g < 0) continue;
+        ++ns;
+        for (int s2 = 0; s2 < K; ++s2)
+          if ((cm >> (4 * s + s2)) & 1u)
+            for (int64_t t = seg[(size_t)g * K + s2]; t < seg[(size_t)g * K + s2 + 1]; ++t)
+              cand.push_back(mem[(size_t)t]);
+      }
+      std::sort(cand.begin(), cand.end());
+      if (!row_ev.empty())
+        for (int32_t j : cand)
+          if (row_ev[j] != row_ev[i]) P.cross_event = true;
+      // residual in column order: b_ij - w m_ij (b_ii = 0), as J = -r / 4
+      rc.clear();
+      rb.clear();
+      bool exact = true;
+      size_t a = 0;
+      int32_t q = rp[i];
+      const int32_t q1 = rp[i + 1];
+      while (a < cand.size() || q < q1) {
+        int32_t j;
+        double bij = 0.0;
+        int64_t m = 0;
+        const int32_t ja = a < cand.size() ? cand[a] : INT32_MAX;
+        const int32_t jq = q < q1 ? col[q] : INT32_MAX;
+        j = std::min(ja, jq);
+        while (a < cand.size() && cand[a] == j) {
+          ++m;
+          ++a;
+        }
+        if (jq == j) bij = qv[(size_t)q++];
+        const double r = bij - w * (double)m;
+        if (r == 0.0) continue;
+        uint32_t bits = 0;
+        if (!exact_in(-r / 4.0, c->jbf16, &bits)) exact = false;
+        rc.push_back(j);
+        rb.push_back(bits);
+      }
+      const int64_t fac_cost = 2 * (int64_t)ns + (int64_t)rc.size();
+      if (ns > 0 && exact && fac_cost < (int64_t)(q1 - rp[i])) {
+        isfac[i] = 1;
+        rcount[i] = (int32_t)rc.size();
+        P.rcol.insert(P.rcol.end(), rc.begin(), rc.end());
+        P.rbits.insert(P.rbits.end(), rb.begin(), rb.end());
+      } else {
+        isfac[i] = 0;
+        rcount[i] = q1 - rp[i];
+        for (int32_t t = rp[i]; t < q1; ++t) {
+          uint32_t bits = 0;
+          memcpy(&bits, jraw.data() + (size_t)t * esz, esz);
+          P.rcol.push_back(col[t]);
+          P.rbits.push_back(bits);
+        }
+      }
+    }
+  });
+  if (!ok) {
+    set_error("sb_set_factor: host allocation failed");
+    return SB_ERR_OOM;
+  }
+  for (const Part& P : pt)
+    if (P.cross_event) {
+      set_error("sb_set_factor: a group id has members in more than one event");
+      return SB_ERR_ARG;
+    }
+  std::vector<int32_t> rrowptr((size_t)n + 1, 0);
+  for (int32_t i = 0; i < n; ++i) {
+    if ((int64_t)rrowptr[i] + rcount[i] > INT32_MAX) {
+      set_error("sb_set_factor: residual too large");
+      return SB_ERR_ARG;
+    }
+    rrowptr[i + 1] = rrowptr[i] + rcount[i];
+  }
+  const int64_t rnnz = rrowptr[n];
+  // U rows read by factored rows, numbered in (id, slot) order
+  std::vector<int32_t> urow(nslot, -1);
+  for (int32_t i = 0; i < n; ++i)
+    if (isfac[i])
+      for (int s = 0; s < K; ++s) {
+        const int32_t g = member[(size_t)i * K + s];
+        if (g >= 0) urow[(size_t)g * K + s] = 0;
+      }
+  int64_t nu = 0;
+  for (size_t t = 0; t < nslot; ++t)
+    if (urow[t] == 0) urow[t] = (int32_t)nu++;
+  if (nu > INT32_MAX) {
+    set_error("sb_set_factor: too many U rows");
+    return SB_ERR_ARG;
+  }
+  std::vector<int32_t> uidx((size_t)n * K, -1);
+  int32_t nfac = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    if (!isfac[i]) continue;
+    ++nfac;
+    for (int s = 0; s < K; ++s) {
+      const int32_t g = member[(size_t)i * K + s];
+      if (g >= 0) uidx[(size_t)i * K + s] = urow[(size_t)g * K + s];
+    }
+  }
+  // blocks with a U row in use: their members (all slots) and U outputs, the
+  // blocks with most members first (a lane group's time follows its block's
+  // size; the large blocks then start in the first wave, not at the end)
+  std::vector<int32_t> gseg(1, 0), gmem, gout;
+  int32_t maxcount = 0;
+  std::vector<int32_t> act;
+  for (int32_t g = 0; g < n_ids; ++g) {
+    bool used = false;
+    for (int s = 0; s < K; ++s) used = used || urow[(size_t)g * K + s] >= 0;
+    if (used) act.push_back(g);
+  }
+  std::stable_sort(act.begin(), act.end(), [&](int32_t x, int32_t y) {
+    return seg[(size_t)x * K + K] - seg[(size_t)x * K] > seg[(size_t)y * K + K] - seg[(size_t)y * K];
+  });
+  for (int32_t g : act) {
+    for (int s = 0; s < K; ++s) {
+      const int64_t a0 = seg[(size_t)g * K + s], a1 = seg[(size_t)g * K + s + 1];
+      gmem.insert(gmem.end(), mem.begin() + a0, mem.begin() + a1);
+      if ((int64_t)gmem.size() > INT32_MAX) {
+        set_error("sb_set_factor: too many member entries");
+        return SB_ERR_ARG;
+      }
+      gseg.push_back((int32_t)gmem.size());
+      gout.push_back(urow[(size_t)g * K + s]);
+      if (urow[(size_t)g * K + s] >= 0) {
+        int64_t cnt = 0;
+        for (int s2 = 0; s2 < K; ++s2)
+          if ((cm >> (4 * s + s2)) & 1u) cnt += seg[(size_t)g * K + s2 + 1] - seg[(size_t)g * K + s2];
+        maxcount = (int32_t)std::min<int64_t>(std::max<int64_t>(maxcount, cnt), INT32_MAX);
+      }
+    }
+  }
+  const int32_t ng = (int32_t)gout.size() / K;
+  if ((int64_t)n + nu >= (1 << 27)) {
+    set_error("sb_set_factor: rows plus U rows must stay below 2^27");
+    return SB_ERR_ARG;
+  }
+  // extended CSR for the row-group kernel: each row's residual, then its U
+  // rows as columns n + u (ascending) with the value jf
+  std::vector<int32_t> xrp((size_t)n + 1, 0);
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t k = rcount[i];
+    if (isfac[i])
+      for (int s = 0; s < K; ++s) k += uidx[(size_t)i * K + s] >= 0 ? 1 : 0;
+    if ((int64_t)xrp[i] + k > INT32_MAX) {
+      set_error("sb_set_factor: extended CSR too large");
+      return SB_ERR_ARG;
+    }
+    xrp[i + 1] = xrp[i] + k;
+  }
+  std::vector<int32_t> xcol((size_t)xrp[n]);
+  std::vector<unsigned char> xj((size_t)xrp[n] * esz);
+  {
+    int64_t src = 0;  // running position in the concatenated residual
+    int64_t dst = 0;
+    std::vector<int32_t> rc_all;
+    std::vector<uint32_t> rb_all;
+    rc_all.reserve((size_t)rnnz);
+    rb_all.reserve((size_t)rnnz);
+    for (const Part& P : pt) {
+      rc_all.insert(rc_all.end(), P.rcol.begin(), P.rcol.end());
+      rb_all.insert(rb_all.end(), P.rbits.begin(), P.rbits.end());
+    }
+    for (int32_t i = 0; i < n; ++i) {
+      for (int32_t t = 0; t < rcount[i]; ++t, ++src, ++dst) {
+        xcol[(size_t)dst] = rc_all[(size_t)src];
+        memcpy(xj.data() + (size_t)dst * esz, &rb_all[(size_t)src], esz);
+      }
+      if (!isfac[i]) continue;
+      int32_t uu[4];
+      int m = 0;
+      for (int s = 0; s < K; ++s)
+        if (uidx[(size_t)i * K + s] >= 0) uu[m++] = uidx[(size_t)i * K + s];
+      std::sort(uu, uu + m);
+      for (int t = 0; t < m; ++t, ++dst) {
+        xcol[(size_t)dst] = n + uu[t];
+        memcpy(xj.data() + (size_t)dst * esz, &jf_bits, esz);
+      }
+    }
+  }
+  // upload (replacing an earlier factor)
+  SB_CUDA(cudaDeviceSynchronize());
+  free_factor(c);
+  sb_status st;
+  if ((st = dalloc(&c->d_f_gseg, gseg.size())) || (st = dalloc(&c->d_f_gmem, std::max<size_t>(gmem.size(), 1))) ||
+      (st = dalloc(&c->d_f_gout, std::max<size_t>(gout.size(), 1))) ||
+      (st = dalloc(&c->d_f_uidx, uidx.size())) || (st = dalloc(&c->d_f_rrowptr, rrowptr.size())) ||
+      (st = dalloc(&c->d_f_rcol, std::max<int64_t>(rnnz, 1)))) {
+    free_factor(c);
+    return st;
+  }
+  {
+    cudaError_t e = cudaMalloc(&c->d_f_rJ, std::max<int64_t>(rnnz, 1) * esz);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->d_f_rJ = nullptr;
+      free_factor(c);
+      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      return SB_ERR_OOM;
+    }
+  }
+  std::vector<int32_t> rcol_all;
+  std::vector<unsigned char> rj_all;
+  rcol_all.reserve((size_t)rnnz);
+  rj_all.reserve((size_t)rnnz * esz);
+  for (const Part& P : pt) {
+    rcol_all.insert(rcol_all.end(), P.rcol.begin(), P.rcol.end());
+    for (uint32_t b : P.rbits) {
+      unsigned char t[4];
+      memcpy(t, &b, 4);
+      rj_all.insert(rj_all.end(), t, t + esz);  // little-endian: the low esz bytes
+    }
+  }
+  SB_CUDA(cudaMemcpy(c->d_f_gseg, gseg.data(), gseg.size() * 4, cudaMemcpyHostToDevice));
+  if (!gmem.empty())
+    SB_CUDA(cudaMemcpy(c->d_f_gmem, gmem.data(), gmem.size() * 4, cudaMemcpyHostToDevice));
+  if (!gout.empty())
+    SB_CUDA(cudaMemcpy(c->d_f_gout, gout.data(), gout.size() * 4, cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(c->d_f_uidx, uidx.data(), uidx.size() * 4, cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(c->d_f_rrowptr, rrowptr.data(), rrowptr.size() * 4, cudaMemcpyHostToDevice));
+  if (rnnz) {
+    SB_CUDA(cudaMemcpy(c->d_f_rcol, rcol_all.data(), (size_t)rnnz * 4, cudaMemcpyHostToDevice));
+    SB_CUDA(cudaMemcpy(c->d_f_rJ, rj_all.data(), (size_t)rnnz * esz, cudaMemcpyHostToDevice));
+  }
+  {
+    cudaError_t e = cudaMalloc(&c->d_f_xJ, std::max<size_t>(xj.size(), 16));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->d_f_xJ = nullptr;
+      free_factor(c);
+      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      return SB_ERR_OOM;
+    }
+    if (!xj.empty()) SB_CUDA(cudaMemcpy(c->d_f_xJ, xj.data(), xj.size(), cudaMemcpyHostToDevice));
+  }
+  c->h_fx_rowptr.swap(xrp);
+  c->h_fx_col.swap(xcol);
+  c->fac_K = K;
+  c->fac_couple = cm;
+  c->fac_jf = (float)jf;
+  c->fac_ng = ng;
+  c->fac_urows = (int32_t)nu;
+  c->fac_rows = nfac;
+  c->fac_members = (int64_t)gmem.size();
+  c->fac_rnnz = rnnz;
+  c->fac_maxcount = maxcount;
+  c->fac_set = true;
+  c->graph.reset();
+  return SB_OK;
+}
+
+// Row-group tables of the extended CSR (factored aSB / bSB), built on first use.
+sb_status ensure_frw(sb_ctx* c, int RW) {
+  if (c->frw_built == RW) return SB_OK;
+  dfree(c->d_frw_gptr);
+  dfree(c->d_frw_rows);
+  dfree(c->d_frw_ent);
+  dfree(c->d_frw_pos);
+  if (c->d_frw_ejv) cudaFree(c->d_frw_ejv);
+  c->d_frw_ejv = nullptr;
+  c->frw_built = 0;
+  RwHost t = build_rw(c->n, c->h_fx_rowptr.data(), c->h_fx_col.data(), RW, c->n + c->fac_urows);
+  if (!t.ok) return SB_OK;  // the factored kernels serve the run instead
+  sb_status st;
+  if ((st = dalloc(&c->d_frw_gptr, t.gptr.size())) || (st = dalloc(&c->d_frw_rows, t.rows.size())) ||
+      (st = dalloc(&c->d_frw_ent, std::max<size_t>(t.ent.size(), 1))) ||
+      (st = dalloc(&c->d_frw_pos, std::max<size_t>(t.pos.size(), 1))))
+    return st;
+  {
+    cudaError_t e = cudaMalloc(&c->d_frw_ejv, std::max<size_t>(t.pos.size(), 1) * (c->jbf16 ? 2 : 4));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->d_frw_ejv = nullptr;
+      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      return SB_ERR_OOM;
+    }
+  }
+  SB_CUDA(cudaMemcpy(c->d_frw_gptr, t.gptr.data(), t.gptr.size() * 4, cudaMemcpyHostToDevice));
+  SB_CUDA(cudaMemcpy(c->d_frw_rows, t.rows.data(), t.rows.size() * 4, cudaMemcpyHostToDevice));
+  if (!t.ent.empty()) {
+    SB_CUDA(cudaMemcpy(c->d_frw_ent, t.ent.data(), t.ent.size() * 4, cudaMemcpyHostToDevice));
+    SB_CUDA(cudaMemcpy(c->d_frw_pos, t.pos.data(), t.pos.size() * 4, cudaMemcpyHostToDevice));
+  }
+  c->frw_ngroups = (int32_t)t.gptr.size() - 1;
+  c->frw_E = (int64_t)t.ent.size();
+  SB_CUDA(sbd::launch_fill_ejv(c->d_f_xJ, c->jbf16, c->d_frw_pos, c->frw_E * RW, c->d_frw_ejv, 0));
+  SB_CUDA(cudaDeviceSynchronize());
+  c->frw_built = RW;
+  return SB_OK;
+}
+
+// Grow both x buffers to `rows` rows of the current replica count, keeping
+// the n state rows.
+sb_status ensure_x_rows(sb_ctx* c, int64_t rows) {
+  if (c->x_rows >= rows) return SB_OK;
+  const size_t cnt = (size_t)rows * c->R, keep = (size_t)c->n * c->R;
+  float* nx[2] = {nullptr, nullptr};
+  sb_status st;
+  if ((st = dalloc(&nx[0], cnt)) || (st = dalloc(&nx[1], cnt))) {
+    dfree(nx[0]);
+    dfree(nx[1]);
+    return st;
+  }
+  SB_CUDA(cudaDeviceSynchronize());
+  for (int k = 0; k < 2; ++k) {
+    SB_CUDA(cudaMemcpy(nx[k], c->d_x[k], keep * 4, cudaMemcpyDeviceToDevice));
+    dfree(c->d_x[k]);
+    c->d_x[k] = nx[k];
+  }
+  c->x_rows = rows;
+  c->graph.reset();
+  return SB_OK;
+}
+
 sb_status check_run_args(sb_ctx* c, sb_variant variant, double a0, double c0, double dt,
                          int32_t steps) {
   if (!c) {
@@ -1134,10 +1621,80 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     sb_status st0 = ensure_tiles(c);
     if (st0) return st0;
   }
+  // factored coupling product: set, not switched off, a supported replica count;
+  // dSB needs the sign bytes and U sums that BF16 holds exactly
+  int fG = 0, fNCH = 0, ftiles = 0;
+  const int fac = (c->fac_set && c->fac_use != 0 && c->groups == 1 &&
+                   sbd::fac_tiling(variant, c->R, &fG, &fNCH, &ftiles) &&
+                   (variant != SB_DSB || (c->dsb_signs && c->j_small && c->fac_maxcount <= 256)))
+                      ? 1 : 0;
+  sbd::FacSumArgs fs{};
+  sbd::FacStepArgs fa{};
+  // aSB / bSB with R a multiple of 128: the row-group kernel over the extended
+  // CSR, the U rows written into the x buffer after the n state rows
+  int frw = 0;
+  if (fac && variant != SB_DSB && c->R % 128 == 0 && c->rw_rows != 0 && c->step_rt == 0) {
+    sb_status st0 = ensure_frw(c, 2);
+    if (st0) return st0;
+    if (c->frw_built == 2) {
+      if ((st0 = ensure_x_rows(c, (int64_t)c->n + c->fac_urows))) return st0;
+      frw = 1;
+    }
+  }
+  if (fac && !frw) {
+    const size_t ub = (size_t)std::max(c->fac_urows, 1) * c->R * (variant == SB_DSB ? 2 : 4);
+    if (ub > c->f_U_bytes) {
+      if (c->d_f_U) cudaFree(c->d_f_U);
+      c->d_f_U = nullptr;
+      c->f_U_bytes = 0;
+      cudaError_t e = cudaMalloc(&c->d_f_U, ub);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->d_f_U = nullptr;
+        set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return SB_ERR_OOM;
+      }
+      c->f_U_bytes = ub;
+      c->graph.reset();
+    }
+  }
+  if (fac) {
+    fs.gseg = c->d_f_gseg;
+    fs.gmem = c->d_f_gmem;
+    fs.gout = c->d_f_gout;
+    fs.ng = c->fac_ng;
+    fs.K = c->fac_K;
+    fs.couple = c->fac_couple;
+    fs.U = c->d_f_U;
+    fs.R = c->R;
+    fs.G = fG;
+    fs.NCH = fNCH;
+    fs.tiles = ftiles;
+    fa.uidx = c->d_f_uidx;
+    fa.K = c->fac_K;
+    fa.jf = c->fac_jf;
+    fa.U = c->d_f_U;
+    fa.rrowptr = c->d_f_rrowptr;
+    fa.rcol = c->d_f_rcol;
+    fa.rJ = c->d_f_rJ;
+    fa.h = c->d_h32;
+    fa.row_event = c->d_row_event;
+    fa.c0_ev = c->d_c0ev;
+    fa.sched = sched;
+    fa.a0 = (float)a0;
+    fa.dt = (float)dt;
+    fa.dta0 = (float)(dt * a0);
+    fa.y = c->d_y;
+    fa.n = c->n;
+    fa.R = c->R;
+    fa.G = fG;
+    fa.NCH = fNCH;
+    fa.tiles = ftiles;
+  }
   // streamed kernel: chosen, tables valid, a supported replica count, and a ring that fits
   sbd::StreamArgs sa{};
   size_t s_smem = 0;
-  if (c->use_stream && c->stream_ok && c->groups == 1) {
+  if (!fac && c->use_stream && c->stream_ok && c->groups == 1) {
     sa.W = sbd::stream_tile_width(c->R);
     if (sa.W) s_smem = sbd::stream_smem(sa.W, c->stream_jbuf, &sa.nst);
   }
@@ -1149,7 +1706,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   // dSB keeps its sign-byte kernel (fewer instructions per neighbour)
   const int rw_want = c->rw_rows < 0 ? (variant == SB_DSB ? 0 : 2) : c->rw_rows;
   const bool rw_auto_ok = c->rw_rows >= 0 || (!c->use_tiled && c->step_rt == 0);
-  if (!streamed && rw_want && rw_auto_ok && c->groups == 1 && c->R % 128 == 0) {
+  if (!fac && !streamed && rw_want && rw_auto_ok && c->groups == 1 && c->R % 128 == 0) {
     sb_status st0 = ensure_rw(c, rw_want);
     if (st0) return st0;
     if (c->rw_built == rw_want) {
@@ -1181,6 +1738,29 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
       }
     }
   }
+  if (frw) {
+    rw = 2;
+    rw_nch = c->R % 256 == 0 ? 2 : 1;
+    ra.gptr = c->d_frw_gptr;
+    ra.grows = c->d_frw_rows;
+    ra.ent = c->d_frw_ent;
+    ra.ejv = c->d_frw_ejv;
+    ra.h = c->d_h32;
+    ra.row_event = c->d_row_event;
+    ra.c0_ev = c->d_c0ev;
+    ra.sched = sched;
+    ra.a0 = (float)a0;
+    ra.dt = (float)dt;
+    ra.dta0 = (float)(dt * a0);
+    ra.y = c->d_y;
+    ra.n = c->n;
+    ra.R = c->R;
+    ra.ngroups = c->frw_ngroups;
+    ra.gpc = std::max(sbd::kRwBlock / 32, c->step_rpc > 0 ? c->step_rpc / 2 : 0);
+    ra.cta_order = nullptr;
+    ra.sgn_in = nullptr;
+    ra.sgn_out = nullptr;
+  }
   if (streamed) {
     sa.rowptr = c->d_rowptr;
     sa.J = c->d_J;
@@ -1208,7 +1788,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   }
   // the 16-replica dSB kernel exists only with sign bytes: its tiling and the
   // byte condition below must agree
-  const bool dsb16 = !streamed && !rw && variant == SB_DSB && c->dsb_signs && c->j_small &&
+  const bool dsb16 = !fac && !streamed && !rw && variant == SB_DSB && c->dsb_signs && c->j_small &&
                      c->step_rt == 0 &&
                      c->groups == 1 && sbd::dsb16_ok(c->R) &&
                      !(c->tiled_ok && c->use_tiled && c->R % sbd::kTileRT == 0);
@@ -1254,7 +1834,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     }
   }
   const int tiled =
-      (!streamed && !rw && c->tiled_ok && c->use_tiled && c->R % sbd::kTileRT == 0) ? 1 : 0;
+      (!fac && !streamed && !rw && c->tiled_ok && c->use_tiled && c->R % sbd::kTileRT == 0) ? 1 : 0;
   sbd::TiledArgs ta;
   ta.blk_row0 = c->d_blk_row0;
   ta.blk_u0 = c->d_blk_u0;
@@ -1306,6 +1886,25 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
       a.sgn_in = c->d_sgn[cur];
       a.sgn_out = c->d_sgn[cur ^ 1];
     }
+    if (fac) {
+      fs.xin = c->d_x[cur];
+      fs.sgn_in = sgn ? c->d_sgn[cur] : nullptr;
+      if (frw) fs.U = c->d_x[cur] + (size_t)c->n * c->R;
+      cudaError_t ef = sbd::launch_fac_sum(variant, fs, st);
+      if (ef != cudaSuccess || frw) {
+        if (ef != cudaSuccess) return ef;
+        ra.k = k;
+        ra.xin = c->d_x[cur];
+        ra.xout = c->d_x[cur ^ 1];
+        return sbd::launch_step_rw(variant, c->jbf16, 2, rw_nch, ra, st);
+      }
+      fa.k = k;
+      fa.xin = c->d_x[cur];
+      fa.xout = c->d_x[cur ^ 1];
+      fa.sgn_in = sgn ? c->d_sgn[cur] : nullptr;
+      fa.sgn_out = sgn ? c->d_sgn[cur ^ 1] : nullptr;
+      return sbd::launch_step_fac(variant, c->jbf16, fa, st);
+    }
     if (streamed) {
       sa.k = k;
       sa.xin = c->d_x[cur];
@@ -1333,7 +1932,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   };
   const size_t NR = (size_t)c->n * c->R;
   const int ngroups =
-      (!streamed && !rw && !tiled && !dsb16 && c->groups > 1 && t.tiles == c->groups) ? c->groups : 1;
+      (!fac && !streamed && !rw && !tiled && !dsb16 && c->groups > 1 && t.tiles == c->groups) ? c->groups : 1;
   sbd::Tiling tg = t;
   if (ngroups > 1) tg.tiles = 1;
   // all steps for replica group g (tiles g), then the next group: each group's
@@ -1366,7 +1965,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     memcpy(&dtb, &a.dt, 4);
     key = {variant, steps, c->R, c->cur, a0b, dtb, (int64_t)(intptr_t)sched, t.G, tiled, a.rpc,
            t.tiles, a.unroll, sgn, ngroups, streamed, rw, rw_nch, ra.cta_order != nullptr,
-           a.cta_order != nullptr, a.r1_lanes};
+           a.cta_order != nullptr, a.r1_lanes, fac, frw};
   }
   GraphCache& gc = c->graph;
   const bool replay = !key.empty() && gc.exec && gc.key == key;
@@ -1557,6 +2156,36 @@ sb_status sb_step_info(const sb_ctx* ctx, int32_t* rows_per_warp, int64_t* union
   }
   if (rows_per_warp) *rows_per_warp = ctx->rw_built;
   if (union_entries) *union_entries = ctx->rw_built ? ctx->rw_E : 0;
+  return SB_OK;
+}
+
+sb_status sb_set_factor(sb_ctx* ctx, int32_t n_ids, int32_t k, const int32_t* member,
+                        const uint8_t* couple, double w) {
+  return sbh::guarded("sb_set_factor", [&]() -> sb_status {
+    if (!ctx) {
+      set_error("sb_set_factor: null context");
+      return SB_ERR_ARG;
+    }
+    if (!member && !couple && n_ids == 0) {  // remove the factor
+      free_factor(ctx);
+      return SB_OK;
+    }
+    return set_factor(ctx, n_ids, k, member, couple, w);
+  });
+}
+
+sb_status sb_factor_info(const sb_ctx* ctx, int64_t* out) {
+  if (!ctx || !out) {
+    set_error("sb_factor_info: null argument");
+    return SB_ERR_ARG;
+  }
+  out[0] = ctx->fac_set ? 1 : 0;
+  out[1] = ctx->fac_rows;
+  out[2] = ctx->fac_rnnz;
+  out[3] = ctx->fac_urows;
+  out[4] = ctx->fac_ng;
+  out[5] = ctx->fac_members;
+  out[6] = ctx->fac_maxcount;
   return SB_OK;
 }
 
@@ -1882,6 +2511,8 @@ sb_status sb_set_weights(sb_ctx* ctx, const int8_t* cls, const double* quality, 
     if (ctx->tiles_built && (st = setup_tiles(ctx, rp, col))) return st;
     // the row-group kernel's entries carry J too
     if ((st = refill_rw(ctx))) return st;
+    // the factored form's weight and residual were formed for the old couplings
+    free_factor(ctx);
     ctx->have_classes = true;
     return SB_OK;
   });
@@ -2103,16 +2734,24 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
     cudaStream_t s = (cudaStream_t)stream;
     // candidates: (tiled, replica-tile width, rows per CTA); invalid ones are skipped
     struct Cand {
-      int tiled, rt, rpc, unroll, groups, l2, rw;
+      int tiled, rt, rpc, unroll, groups, l2, rw, fac;
     };
     std::vector<Cand> cands = {
-        {0, 0, 0, 4, 1, 0, 0},  {0, 0, 32, 4, 1, 0, 0},  {0, 0, 0, 4, 1, 1, 0},
-        {0, 0, 32, 4, 1, 1, 0}, {0, 128, 0, 4, 1, 0, 0}, {0, 128, 32, 4, 1, 0, 0},
-        {0, 64, 0, 4, 1, 0, 0}, {0, 32, 0, 4, 1, 0, 0},  {0, 0, 0, 4, 2, 0, 0},
-        {0, 0, 32, 4, 2, 0, 0}, {0, 0, 0, 4, 4, 0, 0},   {1, 0, 0, 4, 1, 0, 0},
-        {0, 0, 0, 4, 1, 0, 2},  {0, 0, 32, 4, 1, 0, 2},  {0, 0, 64, 4, 1, 0, 2},
-        {0, 128, 0, 4, 1, 0, 2}, {0, 0, 0, 4, 1, 0, 4},  {0, 0, 64, 4, 1, 0, 4},
-        {0, 128, 0, 4, 1, 0, 4}};
+        {0, 0, 0, 4, 1, 0, 0, 0},  {0, 0, 32, 4, 1, 0, 0, 0},  {0, 0, 0, 4, 1, 1, 0, 0},
+        {0, 0, 32, 4, 1, 1, 0, 0}, {0, 128, 0, 4, 1, 0, 0, 0}, {0, 128, 32, 4, 1, 0, 0, 0},
+        {0, 64, 0, 4, 1, 0, 0, 0}, {0, 32, 0, 4, 1, 0, 0, 0},  {0, 0, 0, 4, 2, 0, 0, 0},
+        {0, 0, 32, 4, 2, 0, 0, 0}, {0, 0, 0, 4, 4, 0, 0, 0},   {1, 0, 0, 4, 1, 0, 0, 0},
+        {0, 0, 0, 4, 1, 0, 2, 0},  {0, 0, 32, 4, 1, 0, 2, 0},  {0, 0, 64, 4, 1, 0, 2, 0},
+        {0, 128, 0, 4, 1, 0, 2, 0}, {0, 0, 0, 4, 1, 0, 4, 0},  {0, 0, 64, 4, 1, 0, 4, 0},
+        {0, 128, 0, 4, 1, 0, 4, 0}};
+    // the factored product (when set and not switched off) is one more candidate
+    const int fac_allowed = ctx->fac_set && ctx->fac_use != 0;
+    // (aSB / bSB: through the row-group kernel when rows per warp are left
+    // automatic, or the dedicated factored kernel with rows per warp off)
+    if (fac_allowed) {
+      cands.insert(cands.begin(), Cand{0, 0, 0, 4, 1, 0, 0, 1});
+      cands.insert(cands.begin(), Cand{0, 0, 0, 4, 1, 0, -1, 1});
+    }
     const int keep_graph = ctx->use_graph;
     ctx->use_graph = 0;
     if ((st = ensure_state(ctx, replicas))) return st;
@@ -2132,7 +2771,7 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
         if (!ctx->tiled_ok) continue;
       }
       if (c.rt && (replicas % c.rt != 0)) continue;
-      if (c.rw && replicas % 128 != 0) continue;
+      if (c.rw > 0 && replicas % 128 != 0) continue;
       if (c.groups > 1) {
         const int rt = replicas / c.groups;
         if (replicas % (4 * c.groups) != 0 || rt > 128 || ((rt / 4) & (rt / 4 - 1)) != 0) continue;
@@ -2143,6 +2782,7 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
       ctx->step_unroll = c.unroll;
       ctx->groups = c.groups;
       ctx->rw_rows = c.rw;
+      ctx->fac_use = c.fac ? -1 : 0;
       if ((st = c.l2 ? l2_persist_on(ctx) : l2_persist_off(ctx))) break;
       ctx->l2_persist = c.l2;
       ctx->graph.reset();
@@ -2176,6 +2816,7 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
     ctx->l2_persist = cands[best].l2;
     if ((st = ctx->l2_persist ? l2_persist_on(ctx) : l2_persist_off(ctx))) return st;
     ctx->rw_rows = cands[best].rw;
+    ctx->fac_use = cands[best].fac ? -1 : (fac_allowed ? 0 : ctx->fac_use);
     ctx->graph.reset();
     if (out_cfg) {
       out_cfg[0] = cands[best].tiled;
@@ -2185,6 +2826,7 @@ sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t
       out_cfg[4] = cands[best].groups;
       out_cfg[5] = cands[best].l2;
       out_cfg[6] = cands[best].rw;
+      out_cfg[7] = cands[best].fac;
     }
     if (out_us_per_step) *out_us_per_step = best_us;
     return SB_OK;
@@ -2268,6 +2910,14 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value) {
         return SB_OK;
       case 8:  // SB_OPT_STREAM
         ctx->use_stream = value != 0;
+        ctx->graph.reset();
+        return SB_OK;
+      case 14:  // SB_OPT_FACTOR
+        if (value < -1 || value > 1) {
+          set_error("sb_set_option: SB_OPT_FACTOR must be -1, 0 or 1");
+          return SB_ERR_ARG;
+        }
+        ctx->fac_use = (int)value;
         ctx->graph.reset();
         return SB_OK;
       case 12:  // SB_OPT_WAIT_NS

@@ -712,6 +712,8 @@ extern "C" sb_status sb_qubo_build_device(const sb_event* ev, const sb_build_par
     sb_qubo* q = new (std::nothrow) sb_qubo;
     if (!q) return fail(cudaErrorMemoryAllocation);
     q->n = (int32_t)n;
+    q->w_c = bp->w_c;
+    q->n_hits = (int32_t)ev->layer.size();
     q->rowptr.resize(n + 1);
     q->col.resize(nnz);
     q->val.resize(nnz);

@@ -1,0 +1,458 @@
+// Factored coupling product of the SB step (Eq. 2 / 6 / 10) for QUBOs whose
+// couplings are mostly one weight shared by whole groups of rows.
+//
+// In the triplet QUBO of Eq. 13 every pair of triplets that share a hit and
+// start on the same or adjacent layers is a conflict with the one weight w_c.
+// Triplets holding hit h at position p form a group (h, p); triplets of groups
+// (h, p) and (h, p') conflict exactly when |p - p'| <= 1. So the conflict part
+// of J x is w (M^T W M) x with M the group incidence (three groups per
+// triplet) and W the small position-coupling pattern, and the rest -- double
+// counts of pairs sharing two hits, the consistent pairs (-1 instead of w_c)
+// and the diagonal -- is an exact sparse residual formed on the host.
+//
+// One step is two launches:
+//   k_fac_sum:  for each group block g (one hit), T_s = sum of x (or, for
+//               dSB, of sgn x) over the block's members in slot s, then
+//               U_s = sum_{s'} W[s][s'] T_{s'} for every slot whose U row a
+//               factored row reads;
+//   k_step_fac: for each row, f = jf * sum of its U rows + residual row . x,
+//               then the fused symplectic-Euler update and wall.
+// A row that the host found cheaper in its plain CSR form has no U rows and
+// its whole CSR row as residual, so one kernel serves both kinds of rows.
+//
+// Layout: lane l of a G-lane row group covers, for FP32 state, the replicas
+// tile0 + 4 l + 4 G j + v (j < NCH, v < 4), i.e. 16-byte chunks strided by the
+// group; for dSB sign bytes the 16 replicas tile0 + 16 l + v. U rows use the
+// same replica layout: FP32 for aSB / bSB; for dSB BF16 sums of 2^-7 sgn
+// (exact: the host checks that no U element can exceed 256 in magnitude).
+//
+// Every sum is formed in a fixed order (members by slot and row, residual in
+// column order), so results are reproducible. For dSB with weights that are
+// multiples of 1/4 every partial sum is exact and the step equals the
+// CSR-order kernels bit for bit; for aSB / bSB the rounding order differs from
+// the CSR order (per-step agreement to ~1e-6 relative).
+#include <cuda_bf16.h>
+
+#include "kernels.cuh"
+#include "signs.cuh"
+
+namespace sbd {
+namespace {
+
+constexpr int kFacBlock = 128;
+
+__device__ __forceinline__ unsigned lane_group_mask(int G) {
+  const int lane = threadIdx.x & 31;
+  return G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+}
+
+// One member's values at this lane's replicas, as loaded: FP32 chunks
+// (MODE 0) or 16 sign bytes (MODE 1, unpacked to 2^-7 sgn only when added).
+template <int MODE, int NCH>
+struct Chunk;
+template <int NCH>
+struct Chunk<0, NCH> {
+  static constexpr int P = 4 * NCH;
+  float4 t[NCH];
+  __device__ __forceinline__ void load(const FacSumArgs& a, size_t off, int G, int row) {
+#pragma unroll
+    for (int j = 0; j < NCH; ++j)
+      t[j] = __ldg(reinterpret_cast<const float4*>(a.xin + (size_t)row * a.R + off) + G * j);
+  }
+  __device__ __forceinline__ void add_to(float (&u)[P]) const {
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+      u[4 * j] += t[j].x;
+      u[4 * j + 1] += t[j].y;
+      u[4 * j + 2] += t[j].z;
+      u[4 * j + 3] += t[j].w;
+    }
+  }
+};
+template <int NCH>
+struct Chunk<1, NCH> {
+  static constexpr int P = 16;
+  uint4 t;
+  __device__ __forceinline__ void load(const FacSumArgs& a, size_t off, int, int row) {
+    t = __ldg(reinterpret_cast<const uint4*>(a.sgn_in + (size_t)row * a.R + off));
+  }
+  __device__ __forceinline__ void add_to(float (&u)[16]) const {
+    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int k = 0; k < 16; ++k) u[k] += scaled_sign_of_byte(w[k >> 2], k & 3);
+  }
+};
+
+// Adds a member in slot s2 to every U_s it couples to (s2 is the same for the
+// whole lane group, so the branches do not diverge inside it).
+template <int K, typename CH>
+__device__ __forceinline__ void add_member(float (&U)[K][CH::P], const CH& v, int s2,
+                                           uint32_t couple) {
+#pragma unroll
+  for (int s = 0; s < K; ++s)
+    if ((couple >> (4 * s + s2)) & 1u) v.add_to(U[s]);
+}
+
+template <int MODE, int NCH, int K>
+__global__ void __launch_bounds__(kFacBlock) k_fac_sum(const FacSumArgs a) {
+  using C = Chunk<MODE, NCH>;
+  constexpr int P = C::P;
+  const int G = a.G;
+  const int gq = threadIdx.x / G;
+  const int l = threadIdx.x - gq * G;
+  const int g = blockIdx.x * (kFacBlock / G) + gq;
+  if (g >= a.ng) return;  // the whole lane group leaves together
+  const unsigned mask = lane_group_mask(G);
+  const size_t off = MODE == 0 ? (size_t)blockIdx.y * (4 * G * NCH) + 4 * l
+                               : (size_t)blockIdx.y * (16 * G) + 16 * l;
+  // slot boundaries of the block's members (members grouped by slot)
+  int bnd[K + 1];
+#pragma unroll
+  for (int s = 0; s <= K; ++s) bnd[s] = __ldg(a.gseg + (size_t)g * K + s);
+  float U[K][P];
+#pragma unroll
+  for (int s = 0; s < K; ++s)
+#pragma unroll
+    for (int v = 0; v < P; ++v) U[s][v] = 0.f;
+  // all members of the block in one pass, G entries per load, four rows in flight;
+  // each lane's entry carries its row and slot, broadcast by shuffles
+  for (int mb = bnd[0]; mb < bnd[K]; mb += G) {
+    const int cnt = min(G, bnd[K] - mb);
+    int mr = 0, ms = 0;
+    if (l < cnt) {
+      const int t = mb + l;
+      mr = __ldg(a.gmem + t);
+#pragma unroll
+      for (int s = 1; s < K; ++s) ms += t >= bnd[s] ? 1 : 0;
+    }
+    int q = 0;
+    for (; q + 4 <= cnt; q += 4) {
+      int r[4], sl[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        r[u] = __shfl_sync(mask, mr, q + u, G);
+        sl[u] = __shfl_sync(mask, ms, q + u, G);
+      }
+      C v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u].load(a, off, G, r[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) add_member<K, C>(U, v[u], sl[u], a.couple);
+    }
+    for (; q < cnt; ++q) {
+      const int r0 = __shfl_sync(mask, mr, q, G), s0 = __shfl_sync(mask, ms, q, G);
+      C v0;
+      v0.load(a, off, G, r0);
+      add_member<K, C>(U, v0, s0, a.couple);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const int u = __ldg(a.gout + (size_t)g * K + s);
+    if (u < 0) continue;
+    if (MODE == 0) {
+      float4* p = reinterpret_cast<float4*>(static_cast<float*>(a.U) + (size_t)u * a.R + off);
+#pragma unroll
+      for (int j = 0; j < NCH; ++j)
+        p[G * j] = make_float4(U[s][4 * j], U[s][4 * j + 1], U[s][4 * j + 2], U[s][4 * j + 3]);
+    } else {
+      // sums of 2^-7 sgn of at most 256 members: exact in BF16 (the top half of the FP32 word)
+      uint32_t w[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        w[k] = (__float_as_uint(U[s][2 * k]) >> 16) | (__float_as_uint(U[s][2 * k + 1]) & 0xffff0000u);
+      uint4* p = reinterpret_cast<uint4*>(static_cast<uint16_t*>(a.U) + (size_t)u * a.R + off);
+      p[0] = make_uint4(w[0], w[1], w[2], w[3]);
+      p[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+  }
+}
+
+__device__ __forceinline__ float jv(const float* J, int p) { return __ldg(J + p); }
+__device__ __forceinline__ float jv(const __nv_bfloat16* J, int p) {
+  return __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(J) + p) << 16);
+}
+
+// One U row of this lane: FP32 (NCH float4) or BF16 sums of 2^-7 sgn (two uint4)
+template <int MODE, int NCH>
+struct URow;
+template <int NCH>
+struct URow<0, NCH> {
+  float4 t[NCH];
+  __device__ __forceinline__ void load(const void* U, size_t base, int G) {
+#pragma unroll
+    for (int j = 0; j < NCH; ++j)
+      t[j] = __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(U) + base) + G * j);
+  }
+  __device__ __forceinline__ void add_to(float (&fu)[4 * NCH]) const {
+#pragma unroll
+    for (int j = 0; j < NCH; ++j) {
+      fu[4 * j] += t[j].x;
+      fu[4 * j + 1] += t[j].y;
+      fu[4 * j + 2] += t[j].z;
+      fu[4 * j + 3] += t[j].w;
+    }
+  }
+};
+template <int NCH>
+struct URow<1, NCH> {
+  uint4 t0, t1;
+  __device__ __forceinline__ void load(const void* U, size_t base, int) {
+    const uint4* p = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(U) + base);
+    t0 = __ldg(p);
+    t1 = __ldg(p + 1);
+  }
+  __device__ __forceinline__ void add_to(float (&fu)[16]) const {
+    const uint32_t w[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      fu[2 * k] += __uint_as_float(w[k] << 16);
+      fu[2 * k + 1] += __uint_as_float(w[k] & 0xffff0000u);
+    }
+  }
+};
+
+// VARIANT 0 aSB, 1 bSB (MODE 0: FP32 x), 2 dSB (MODE 1: sign bytes)
+template <int VARIANT, int MODE, int NCH, int K, typename JT>
+__global__ void __launch_bounds__(kFacBlock) k_step_fac(const FacStepArgs a) {
+  constexpr int P = MODE == 0 ? 4 * NCH : 16;
+  constexpr int NV = MODE == 0 ? NCH : 4;  // float4 of own x (and y) per lane
+  const int G = a.G;
+  const int gq = threadIdx.x / G;
+  const int l = threadIdx.x - gq * G;
+  const int row = blockIdx.x * (kFacBlock / G) + gq;
+  if (row >= a.n) return;
+  const unsigned mask = lane_group_mask(G);
+  const int R = a.R;
+  const size_t off = MODE == 0 ? (size_t)blockIdx.y * (4 * G * NCH) + 4 * l
+                               : (size_t)blockIdx.y * (16 * G) + 16 * l;
+  const JT* J = static_cast<const JT*>(a.rJ);
+  const int p0 = __ldg(a.rrowptr + row), p1 = __ldg(a.rrowptr + row + 1);
+  // residual row, in column order
+  float acc[P];
+#pragma unroll
+  for (int v = 0; v < P; ++v) acc[v] = 0.f;
+  for (int pb = p0; pb < p1; pb += G) {
+    const int cnt = min(G, p1 - pb);
+    int mc = 0;
+    float mw = 0.f;
+    if (l < cnt) {
+      mc = __ldg(a.rcol + pb + l);
+      mw = jv(J, pb + l);
+      if (MODE == 1) mw *= kSignScale;  // 2^7 J: sign bytes read as 2^-7 sgn
+    }
+    int q = 0;
+    for (; q + 4 <= cnt; q += 4) {
+      int c[4];
+      float w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c[u] = __shfl_sync(mask, mc, q + u, G);
+        w[u] = __shfl_sync(mask, mw, q + u, G);
+      }
+      if (MODE == 0) {
+        float4 t[4][NCH];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int j = 0; j < NCH; ++j)
+            t[u][j] = __ldg(reinterpret_cast<const float4*>(a.xin + (size_t)c[u] * R + off) + G * j);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int j = 0; j < NCH; ++j) {
+            acc[4 * j] = fmaf(w[u], t[u][j].x, acc[4 * j]);
+            acc[4 * j + 1] = fmaf(w[u], t[u][j].y, acc[4 * j + 1]);
+            acc[4 * j + 2] = fmaf(w[u], t[u][j].z, acc[4 * j + 2]);
+            acc[4 * j + 3] = fmaf(w[u], t[u][j].w, acc[4 * j + 3]);
+          }
+      } else {
+        uint4 t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          t[u] = __ldg(reinterpret_cast<const uint4*>(a.sgn_in + (size_t)c[u] * R + off));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t ww[4] = {t[u].x, t[u].y, t[u].z, t[u].w};
+#pragma unroll
+          for (int v = 0; v < 16; ++v) acc[v] = fmaf(w[u], scaled_sign_of_byte(ww[v >> 2], v & 3), acc[v]);
+        }
+      }
+    }
+    for (; q < cnt; ++q) {
+      const int c = __shfl_sync(mask, mc, q, G);
+      const float w = __shfl_sync(mask, mw, q, G);
+      if (MODE == 0) {
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+          const float4 t = __ldg(reinterpret_cast<const float4*>(a.xin + (size_t)c * R + off) + G * j);
+          acc[4 * j] = fmaf(w, t.x, acc[4 * j]);
+          acc[4 * j + 1] = fmaf(w, t.y, acc[4 * j + 1]);
+          acc[4 * j + 2] = fmaf(w, t.z, acc[4 * j + 2]);
+          acc[4 * j + 3] = fmaf(w, t.w, acc[4 * j + 3]);
+        }
+      } else {
+        const uint4 t = __ldg(reinterpret_cast<const uint4*>(a.sgn_in + (size_t)c * R + off));
+        const uint32_t ww[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int v = 0; v < 16; ++v) acc[v] = fmaf(w, scaled_sign_of_byte(ww[v >> 2], v & 3), acc[v]);
+      }
+    }
+  }
+  // the factored part: sum of this row's U rows (none for a plain row)
+  bool any = false;
+  float fu[P];
+#pragma unroll
+  for (int v = 0; v < P; ++v) fu[v] = 0.f;
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const int u = __ldg(a.uidx + (size_t)row * K + s);
+    if (u < 0) continue;
+    any = true;
+    URow<MODE, NCH> ur;
+    ur.load(a.U, (size_t)u * R + off, G);
+    ur.add_to(fu);
+  }
+  // dSB: U holds sums of 2^-7 sgn, so the scale is 2^7 jf (exact)
+  const float jf = MODE == 1 ? a.jf * kSignScale : a.jf;
+  if (any) {
+#pragma unroll
+    for (int v = 0; v < P; ++v) acc[v] = fmaf(jf, fu[v], acc[v]);
+  }
+
+  // symplectic Euler: momentum with the old position, then position, then wall
+  const float pa = a.a0 - __ldg(a.sched + a.k);
+  const int ev = a.row_event ? __ldg(a.row_event + row) : 0;
+  const float c0 = __ldg(a.c0_ev + ev);
+  const float hi = __ldg(a.h + row);
+  const size_t idx = (size_t)row * R + off;
+  uint32_t sw[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const size_t o = MODE == 0 ? idx + 4 * G * j : idx + 4 * j;
+    const float4 xv = __ldg(reinterpret_cast<const float4*>(a.xin + o));
+    const float4 yv = *reinterpret_cast<const float4*>(a.y + o);
+    float xs[4] = {xv.x, xv.y, xv.z, xv.w}, ys[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      float x = xs[v], y = ys[v];
+      float force = -pa * x + c0 * (acc[4 * j + v] + hi);
+      if (VARIANT == 0) force -= x * x * x;
+      y = y + a.dt * force;
+      x = x + a.dta0 * y;
+      if (VARIANT != 0 && fabsf(x) > 1.f) {
+        x = copysignf(1.f, x);
+        y = 0.f;
+      }
+      xs[v] = x;
+      ys[v] = y;
+      if (MODE == 1) sw[j] |= sign_byte(x) << (8 * v);
+    }
+    *reinterpret_cast<float4*>(a.xout + o) = make_float4(xs[0], xs[1], xs[2], xs[3]);
+    *reinterpret_cast<float4*>(a.y + o) = make_float4(ys[0], ys[1], ys[2], ys[3]);
+  }
+  if (MODE == 1) *reinterpret_cast<uint4*>(a.sgn_out + idx) = make_uint4(sw[0], sw[1], sw[2], sw[3]);
+}
+
+template <int MODE, int NCH, int K>
+cudaError_t launch_sum_k(const FacSumArgs& a, cudaStream_t s) {
+  if (a.ng <= 0) return cudaSuccess;
+  const int per = kFacBlock / a.G;
+  dim3 grid((a.ng + per - 1) / per, a.tiles);
+  k_fac_sum<MODE, NCH, K><<<grid, kFacBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE, int NCH>
+cudaError_t launch_sum_n(const FacSumArgs& a, cudaStream_t s) {
+  switch (a.K) {
+    case 1: return launch_sum_k<MODE, NCH, 1>(a, s);
+    case 2: return launch_sum_k<MODE, NCH, 2>(a, s);
+    case 3: return launch_sum_k<MODE, NCH, 3>(a, s);
+    case 4: return launch_sum_k<MODE, NCH, 4>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int VARIANT, int MODE, int NCH, int K, typename JT>
+cudaError_t launch_step_k(const FacStepArgs& a, cudaStream_t s) {
+  const int per = kFacBlock / a.G;
+  dim3 grid((a.n + per - 1) / per, a.tiles);
+  k_step_fac<VARIANT, MODE, NCH, K, JT><<<grid, kFacBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int VARIANT, int MODE, int NCH, typename JT>
+cudaError_t launch_step_n(const FacStepArgs& a, cudaStream_t s) {
+  switch (a.K) {
+    case 1: return launch_step_k<VARIANT, MODE, NCH, 1, JT>(a, s);
+    case 2: return launch_step_k<VARIANT, MODE, NCH, 2, JT>(a, s);
+    case 3: return launch_step_k<VARIANT, MODE, NCH, 3, JT>(a, s);
+    case 4: return launch_step_k<VARIANT, MODE, NCH, 4, JT>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename JT>
+cudaError_t launch_step_j(int variant, const FacStepArgs& a, cudaStream_t s) {
+  if (variant == 2) return launch_step_n<2, 1, 1, JT>(a, s);
+  if (a.NCH == 2)
+    return variant == 0 ? launch_step_n<0, 0, 2, JT>(a, s) : launch_step_n<1, 0, 2, JT>(a, s);
+  return variant == 0 ? launch_step_n<0, 0, 1, JT>(a, s) : launch_step_n<1, 0, 1, JT>(a, s);
+}
+
+}  // namespace
+
+bool fac_tiling(int variant, int R, int* G, int* NCH, int* tiles) {
+  if (R < 1) return false;
+  if (variant == 2) {
+    if (R % 16) return false;
+    const int C = R / 16;
+    if (C <= 32 && (C & (C - 1)) == 0) {
+      *G = C;
+      *NCH = 1;
+      *tiles = 1;
+      return true;
+    }
+    if (C % 32 == 0) {
+      *G = 32;
+      *NCH = 1;
+      *tiles = C / 32;
+      return true;
+    }
+    return false;
+  }
+  if (R % 4) return false;
+  const int C = R / 4;
+  if (C <= 32 && (C & (C - 1)) == 0) {
+    *G = C;
+    *NCH = 1;
+    *tiles = 1;
+    return true;
+  }
+  if (C % 64 == 0) {
+    *G = 32;
+    *NCH = 2;
+    *tiles = C / 64;
+    return true;
+  }
+  if (C % 32 == 0) {
+    *G = 32;
+    *NCH = 1;
+    *tiles = C / 32;
+    return true;
+  }
+  return false;
+}
+
+cudaError_t launch_fac_sum(int variant, const FacSumArgs& a, cudaStream_t s) {
+  if (variant == 2) return launch_sum_n<1, 1>(a, s);
+  return a.NCH == 2 ? launch_sum_n<0, 2>(a, s) : launch_sum_n<0, 1>(a, s);
+}
+
+cudaError_t launch_step_fac(int variant, int jbf16, const FacStepArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  return jbf16 ? launch_step_j<__nv_bfloat16>(variant, a, s) : launch_step_j<float>(variant, a, s);
+}
+
+}  // namespace sbd

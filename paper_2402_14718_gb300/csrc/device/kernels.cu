@@ -97,16 +97,16 @@ struct Vec<1> {
   __device__ __forceinline__ void st(float* p) const { *p = v[0]; }
 };
 
-// V sign bytes of one chunk as the floats sgn / 2
+// V sign bytes of one chunk as the floats 2^-7 sgn
 template <int V>
 __device__ __forceinline__ void ld_signs(const uint8_t* p, float (&out)[V]) {
   if (V == 4) {
     const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(p));
 #pragma unroll
-    for (int v = 0; v < V; ++v) out[v] = half_sign_of_byte(w, v);
+    for (int v = 0; v < V; ++v) out[v] = scaled_sign_of_byte(w, v);
   } else {
 #pragma unroll
-    for (int v = 0; v < V; ++v) out[v] = half_sign_of_byte(__ldg(p + v), 0);
+    for (int v = 0; v < V; ++v) out[v] = scaled_sign_of_byte(__ldg(p + v), 0);
   }
 }
 
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kBlock, StepMinBlocks<NCH>::value) k_step(cons
     if (g < cnt) {
       mc = __ldg(a.col + pb + g);
       mv = jval(J, pb + g);
-      if (use_sgn) mv += mv;  // 2 J: sign bytes read as sgn / 2
+      if (use_sgn) mv *= kSignScale;  // 2^7 J: sign bytes read as 2^-7 sgn
     }
     int q = 0;
     for (; q + U <= cnt; q += U) {
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(kDsbBlock, SB_DSB_MINB) k_step_dsb16(const Ste
       if (g < cnt) {
         mc = __ldg(a.col + pb + g);
         mv = jval(J, pb + g);
-        mv += mv;  // 2 J: sign bytes read as sgn / 2
+        mv *= kSignScale;  // 2^7 J: sign bytes read as 2^-7 sgn
       }
       int q = 0;
       for (; q + 4 <= cnt; q += 4) {
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(kDsbBlock, SB_DSB_MINB) k_step_dsb16(const Ste
           const unsigned ww[4] = {sv[u].x, sv[u].y, sv[u].z, sv[u].w};
 #pragma unroll
           for (int v = 0; v < 16; ++v)
-            acc[v] = fmaf(w[u], half_sign_of_byte(ww[v >> 2], v & 3), acc[v]);
+            acc[v] = fmaf(w[u], scaled_sign_of_byte(ww[v >> 2], v & 3), acc[v]);
         }
       }
       for (; q < cnt; ++q) {
@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(kDsbBlock, SB_DSB_MINB) k_step_dsb16(const Ste
         const uint4 s4 = __ldg(reinterpret_cast<const uint4*>(a.sgn_in + (size_t)c * R + 16 * g));
         const unsigned ww[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-        for (int v = 0; v < 16; ++v) acc[v] = fmaf(w, half_sign_of_byte(ww[v >> 2], v & 3), acc[v]);
+        for (int v = 0; v < 16; ++v) acc[v] = fmaf(w, scaled_sign_of_byte(ww[v >> 2], v & 3), acc[v]);
       }
     }
     const float pa = a.a0 - __ldg(a.sched + a.k);
@@ -1041,7 +1041,7 @@ __global__ void k_linear_schedule(float* sched, int32_t steps, double a0) {
 
 __global__ void k_set_c0(float* c0_ev, const double* c0_auto, double c0, int32_t E) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
-    c0_ev[e] = (float)(c0 > 0.0 ? c0 : c0_auto[e]);
+    c0_ev[e] = (float)(c0 > 0.0 ? c0 : (c0 < 0.0 ? -c0 * c0_auto[e] : c0_auto[e]));
 }
 
 // ---------------------------------------------------------------- QUBO -> Ising (FP64)

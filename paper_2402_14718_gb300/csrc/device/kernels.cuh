@@ -91,7 +91,7 @@ cudaError_t launch_pack_tz(const void* J, int jbf16, const uint16_t* lidx, int64
 
 cudaError_t launch_init(float* x, float* y, const int32_t* row_event, const int32_t* ev_row0,
                         int32_t n, int32_t R, uint64_t seed, cudaStream_t s);
-// s[i] = sign byte of x[i]: 0x3F, 0xBF, 0x00 for x > 0, x < 0, x = 0 (signs.cuh)
+// s[i] = sign byte of x[i]: 0x3C, 0xBC, 0x00 for x > 0, x < 0, x = 0 (signs.cuh)
 cudaError_t launch_signs(const float* x, uint8_t* s, size_t count, cudaStream_t st);
 // blocks of the untiled step kernel resident per SM for this tiling and unroll
 int step_blocks_per_sm(int variant, int jbf16, const Tiling& t, int unroll);
@@ -214,6 +214,50 @@ struct StreamArgs {
   // copy), so the consumers' wait for it runs out; -1: off
   int32_t skip_stage;
 };
+
+// ---------------------------------------------------------------- factored step
+// Coupling product split as jf * (M^T W M) x + residual x (factor.cu): group
+// blocks g (e.g. one hit each) with K slots; U rows hold sum_{s'} W[s][s']
+// T_{g,s'}, T_{g,s} the sum of x (dSB: of 2^-7 sgn) over the members of slot s.
+struct FacSumArgs {
+  const int32_t* gseg;   // [ng * K + 1] members of block g, slot s: gmem[gseg[gK+s] .. gseg[gK+s+1])
+  const int32_t* gmem;   // member rows, ascending within a slot
+  const int32_t* gout;   // [ng * K] U row written for (g, s); -1: not needed
+  int32_t ng, K;
+  uint32_t couple;       // bit 4 s + s': W[s][s'] = 1
+  const float* xin;      // aSB / bSB: positions x_k [n x R]
+  const uint8_t* sgn_in; // dSB: sign bytes of x_k [n x R]
+  void* U;               // [U rows x R]: FP32 (aSB / bSB) or BF16 (dSB)
+  int32_t R, G, NCH, tiles;
+};
+
+struct FacStepArgs {
+  const int32_t* uidx;   // [n * K] U rows of each row (-1: none; a plain row has none)
+  int32_t K;
+  float jf;              // factor weight in J units (-w / 4), exact in FP32
+  const void* U;
+  const int32_t* rrowptr;  // residual CSR [n + 1] (may hold the diagonal)
+  const int32_t* rcol;
+  const void* rJ;          // residual values, float or __nv_bfloat16 (exact)
+  const float* h;
+  const int32_t* row_event;
+  const float* c0_ev;
+  const float* sched;
+  int32_t k;
+  float a0, dt, dta0;
+  const float* xin;
+  float* xout;
+  float* y;
+  const uint8_t* sgn_in;   // dSB
+  uint8_t* sgn_out;        // dSB
+  int32_t n, R, G, NCH, tiles;
+};
+
+// Lane-group shape of the factored kernels for R replicas (false: R not supported):
+// G lanes per row, NCH 16-byte chunks per lane (aSB / bSB), tiles replica tiles.
+bool fac_tiling(int variant, int R, int* G, int* NCH, int* tiles);
+cudaError_t launch_fac_sum(int variant, const FacSumArgs& a, cudaStream_t s);
+cudaError_t launch_step_fac(int variant, int jbf16, const FacStepArgs& a, cudaStream_t s);
 
 // Replica-tile width of the streamed kernel for R replicas (0: not supported).
 int stream_tile_width(int R);

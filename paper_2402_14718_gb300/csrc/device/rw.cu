@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a
             for (int j = 0; j < NCH; ++j) {
               const uint32_t t = __ldg(ps + 32 * j);
 #pragma unroll
-              for (int k = 0; k < 4; ++k) xv[u][j][k] = half_sign_of_byte(t, k);
+              for (int k = 0; k < 4; ++k) xv[u][j][k] = scaled_sign_of_byte(t, k);
             }
           } else {
             const float4* px = reinterpret_cast<const float4*>(xl + (size_t)(v >> 4) * rb);
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a
           for (int q = 0; q < RW; ++q)
             if (m[u] & (1u << q)) {
               float wq = w[u].get(q);
-              if (use_sgn) wq += wq;  // 2 J: sign bytes read as sgn / 2
+              if (use_sgn) wq *= kSignScale;  // 2^7 J: sign bytes read as 2^-7 sgn
 #pragma unroll
               for (int j = 0; j < NCH; ++j)
 #pragma unroll

@@ -8,18 +8,22 @@ namespace sbd {
 // sgn(x) with sgn(0) = 0, as a float, in compares and selects only.
 __device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
 
-// A sign stored as one byte: the top byte of the float +0.5 (0x3F), -0.5
-// (0xBF) or +0 (0x00), for x > 0, x < 0 and x = 0.
+// A sign stored as one byte: 0x3C, 0xBC or 0x00 for x > 0, x < 0 and x = 0.
+// Placed as the top byte of an FP32 word (the other bytes zero) it reads
+// +-2^-7 (or +0).
 __device__ __forceinline__ uint32_t sign_byte(float x) {
-  return x > 0.f ? 0x3Fu : (x < 0.f ? 0xBFu : 0u);
+  return x > 0.f ? 0x3Cu : (x < 0.f ? 0xBCu : 0u);
 }
 
-// Byte k of w as the float sgn / 2 (+0.5, -0.5 or +0) in one byte permute: the
-// byte goes to the top of a word whose other bytes are zero. A coupling
-// product takes it with the doubled weight: fma(2 J, sgn / 2, acc) equals
-// fma(J, sgn, acc) bit for bit, since 2 J is exact (|J| < 2^127) and the
-// product 2 J * sgn / 2 = J sgn is exact, leaving the one rounding of the sum.
-__device__ __forceinline__ float half_sign_of_byte(uint32_t w, int k) {
+// The FP32 reading of a sign byte is sgn * 2^-7, so an FP32 coupling product
+// takes it with the weight scaled by 2^7: fma(2^7 J, 2^-7 sgn, acc) equals
+// fma(J, sgn, acc) bit for bit (2^7 J is exact for |J| < 2^120, and the
+// product is exactly J sgn, leaving the one rounding of the sum).
+constexpr float kSignScale = 128.f;
+
+// Byte k of w as the float sgn * 2^-7, in one byte permute: the byte goes to
+// the top of a word whose other bytes are zero.
+__device__ __forceinline__ float scaled_sign_of_byte(uint32_t w, int k) {
   return __int_as_float((int)__byte_perm(w, 0u, 0x0444u | ((uint32_t)k << 12)));
 }
 

@@ -20,6 +20,8 @@ struct sb_qubo {
   std::vector<double> val, lin, quality, kappa, dtheta;
   std::vector<int8_t> cls;
   std::vector<int32_t> trip;  // 3 per triplet
+  double w_c = 1.0;           // conflict weight the couplings were built with
+  int32_t n_hits = 0;         // hits of the event (hit ids lie in [0, n_hits))
 };
 
 namespace sbh {

@@ -214,6 +214,8 @@ extern "C" sb_status sb_qubo_build(const sb_event* ev, const sb_build_params* p,
   sb_qubo* q = new (std::nothrow) sb_qubo;
   if (!q) return SB_ERR_OOM;
   q->n = n;
+  q->w_c = p->w_c;
+  q->n_hits = nh;
   q->rowptr.assign(n + 1, 0);
   for (const Pair& pr : pairs) {
     const int32_t ni = new_index[pr.i], nj = new_index[pr.j];
@@ -288,6 +290,25 @@ extern "C" sb_status sb_qubo_arrays(const sb_qubo* q, int32_t* rowptr, int32_t* 
   if (trip) std::copy(q->trip.begin(), q->trip.end(), trip);
   if (kappa) std::copy(q->kappa.begin(), q->kappa.end(), kappa);
   if (dtheta) std::copy(q->dtheta.begin(), q->dtheta.end(), dtheta);
+  return SB_OK;
+}
+
+// The conflict part of Eq. 13 in factored form (reading of "any conflict": two
+// triplets sharing a hit conflict when they start on the same or adjacent
+// layers). A triplet holding hit h at position p starts on layer(h) - p, so
+// two triplets sharing h at positions p, p' start |p - p'| layers apart: the
+// group of (h, p) couples to the groups (h, p') with |p - p'| <= 1, weight w_c.
+extern "C" sb_status sb_qubo_factor(const sb_qubo* q, int32_t* member, uint8_t* couple, double* w,
+                                    int32_t* n_ids) {
+  if (!q || !member || !couple || !w || !n_ids) {
+    sbh::set_error("sb_qubo_factor: null argument");
+    return SB_ERR_ARG;
+  }
+  std::copy(q->trip.begin(), q->trip.end(), member);
+  for (int p = 0; p < 3; ++p)
+    for (int p2 = 0; p2 < 3; ++p2) couple[3 * p + p2] = (p - p2 <= 1 && p2 - p <= 1) ? 1 : 0;
+  *w = q->w_c;
+  *n_ids = std::max<int32_t>(q->n_hits, 1);
   return SB_OK;
 }
 

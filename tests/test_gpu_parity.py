@@ -13,7 +13,8 @@ torch = pytest.importorskip("torch")
 import paper_2402_14718_gb300 as sb
 from oracle import ising, sb as osb, tracks as otr
 from tests import inputs
-from tests.gpu_common import compare_step, max_rel, workload_qubos, oracle_c0
+from tests.gpu_common import (compare_step, compare_step_elementwise, max_rel, oracle_c0,
+                              workload_qubos)
 
 pytestmark = pytest.mark.gpu
 VARIANTS = [osb.ASB, osb.BSB, osb.DSB]
@@ -106,6 +107,7 @@ def _one_step_case(q, qo, prec, variant, R, seed, a_k, scale, graph=False):
     a32 = float(np.float32(a_k))
     xo, yo = osb.step(J, h, x0.astype(np.float64), y0.astype(np.float64), a32, 1.0, c0, 0.5, variant)
     xpre = osb.prewall_x(J, h, x0.astype(np.float64), y0.astype(np.float64), a32, 1.0, c0, 0.5, variant)
+    compare_step_elementwise(J, h, x0, y0, a32, 1.0, c0, 0.5, variant, xg, yg, xo, yo, xpre)
     return compare_step(xg, yg, xo, yo, xpre)
 
 
