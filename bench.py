@@ -65,6 +65,9 @@ def parse(argv=None):
                     help="experiments (not bench lines)")
     ap.add_argument("--record", default="",
                     help="with --study: also write the JSON lines, with the command, to this file")
+    ap.add_argument("--events", type=int, default=0,
+                    help="batch workloads: every (E / K)-th event only, K events (profiling "
+                         "captures of a few GB on the device); 0: all")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling driver: set up the workload, run this many SB steps with "
                          "one direct launch each (no graph, no timing), exit")
@@ -100,7 +103,7 @@ def job_value(units_per_rank, world_size, ms):
 
 
 # ---------------------------------------------------------------- workloads
-def workload(name, sb_steps=0, variant=""):
+def workload(name, sb_steps=0, variant="", events=0):
     """Run shape and the event recipes (seed, tracks, noise, cuts) of a named
     workload; numbers only (the tables live in the package's workloads module,
     which loads nothing)."""
@@ -123,6 +126,10 @@ def workload(name, sb_steps=0, variant=""):
     if variant:
         w["variant"] = variant
     w["name"] = name
+    if events and events < len(w["events"]):
+        stride = len(w["events"]) // events
+        w["events"] = w["events"][::stride][:events]
+        w["name"] = f"{name}[{events} events]"
     return w
 
 
@@ -399,7 +406,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    w = workload(args.workload, args.sb_steps, args.variant)
+    w = workload(args.workload, args.sb_steps, args.variant, args.events)
     vals = []
     for _ in range(args.warmup + args.steps):
         vals.append(oracle_sample(w, target_s=4.0))
@@ -434,23 +441,27 @@ def _ttt_at(t, p):
 
 
 def time_to_target(sb, w, pairs, ctx, stream, dev, plain_events, plain_runs=64, every=50,
-                   c0_scale=2.0, ref_scale=3.0):
+                   c0_scale=2.0, ref_scale=3.0, targets=(0.001, 0.005)):
     """Time-to-target (section "Results", Table 1): the time to reach 99.9 % of
     the lowest energy found, with 99 % probability, for every event of the
     workload.
 
-    Target of event e: E_best,e + 0.001 |E_best,e| (QUBO energies are
-    negative), E_best,e the lowest energy any run of this study found for it:
-    the batched runs, the plain runs and a reference run (2 S steps, c0 = 3
-    c0_auto). Both timed forms use c0 = 2 c0_auto (a fixed c0, as in the
+    Target of event e: E_low,e + f |E_low,e| (QUBO energies are negative),
+    E_low,e the lowest energy any run of this study found for it (the batched
+    runs, the plain runs and a reference run of 2 S steps with c0 = 3
+    c0_auto), for f = 0.001 (the paper's 99.9 %) and a loosened f = 0.005 (the
+    paper also loosens its target for dSB); where a form never reaches a
+    target it is reported as "did not reach", as in Table 1. Both timed forms use c0 = 2 c0_auto (a fixed c0, as in the
     paper; the factor 2 is where the configured c0 of the workloads reaches
     the lowest energies in the c0 scan).
 
     Batched BF16 form: one run of all events and R replicas with an FP64
     readout every `every` steps (timed). p_e(k) = fraction of event e's
-    replicas at or below its target at checkpoint k; the run succeeds for the
-    whole workload with P(k) = prod_e (1 - (1 - p_e(k))^R), and TTT = min_k
-    t(k) max(1, ln 0.01 / ln(1 - P(k))).
+    replicas at or below its target at checkpoint k; one batched run succeeds
+    for event e with P_e(k) = 1 - (1 - p_e(k))^R, whole-batch runs are repeated
+    until every event has succeeded, with per-event probability q = 0.99^(1/E)
+    so that all E events succeed with 99 %: TTT = min_k t(k) max_e max(1,
+    ln(1 - q) / ln(1 - P_e(k))).
 
     Plain FP32 form (FP32 J, one replica, one event, one kernel launch per
     step, no graph): `plain_runs` runs of each sampled event with checkpoints
@@ -529,35 +540,52 @@ def time_to_target(sb, w, pairs, ctx, stream, dev, plain_events, plain_runs=64, 
         T_p, _, _ = sb.sb_best(cp)
         plain.append(dict(e=e, t_run=t_run, Ep=Ep, T=T_p))
         sb.sb_destroy(cp)
-    # ---- targets
-    E_best = np.minimum(Eb.min(axis=(0, 2)), E_ref)
+    # ---- targets: the paper's (0.1 % above the lowest energy) and a loosened one
+    E_low = np.minimum(Eb.min(axis=(0, 2)), E_ref)
     for p in plain:
-        E_best[p["e"]] = min(E_best[p["e"]], float(p["Ep"].min()))
-    target = E_best + 0.001 * np.abs(E_best)
-    p_rep = (Eb <= target[None, :, None]).mean(axis=2)            # [checkpoint, event]
-    P_all = np.prod(1.0 - (1.0 - p_rep) ** R, axis=1)            # [checkpoint]
-    ttt_b, kb = math.inf, None
-    for k in range(n_ck):
-        v = _ttt_at(times[k], float(P_all[k]))
-        if v < ttt_b:
-            ttt_b, kb = v, k
+        E_low[p["e"]] = min(E_low[p["e"]], float(p["Ep"].min()))
     q_ev = 0.99 ** (1.0 / E)
-    per_event, ttt_sum = [], 0.0
-    for p in plain:
-        pk = (p["Ep"] <= target[p["e"]]).mean(axis=0)
-        best, kk = math.inf, None
+    results = []
+    for frac in targets:
+        target = E_low + frac * np.abs(E_low)
+        p_rep = (Eb <= target[None, :, None]).mean(axis=2)        # [checkpoint, event]
+        P_ev = 1.0 - (1.0 - p_rep) ** R                           # one batched run, per event
+        # batched: whole-batch runs repeated until every event has succeeded
+        ttt_b, kb = math.inf, None
         for k in range(n_ck):
-            tk = p["t_run"] * min(S, (k + 1) * every) / S
-            if pk[k] <= 0.0:
+            if np.any(P_ev[k] <= 0.0):
                 continue
-            v = tk if pk[k] >= q_ev else tk * math.log(1.0 - q_ev) / math.log(1.0 - pk[k])
-            if v < best:
-                best, kk = v, k
-        ttt_sum += best
-        per_event.append({"event": p["e"], "N": qs[p["e"]].n, "run_seconds": p["t_run"],
-                          "p_final": float(pk[-1]), "ttt_seconds": best,
-                          "at_step": None if kk is None else min(S, (kk + 1) * every)})
-    ttt_p = E * ttt_sum / max(len(plain), 1)
+            runs = max(1.0, float(np.max(np.where(P_ev[k] >= q_ev, 1.0,
+                                                  np.log(1.0 - q_ev) / np.log(1.0 - np.minimum(P_ev[k], 1 - 1e-16))))))
+            v = times[k] * runs
+            if v < ttt_b:
+                ttt_b, kb = v, k
+        per_event, ttt_sum = [], 0.0
+        for p in plain:
+            pk = (p["Ep"] <= target[p["e"]]).mean(axis=0)
+            best, kk = math.inf, None
+            for k in range(n_ck):
+                tk = p["t_run"] * min(S, (k + 1) * every) / S
+                if pk[k] <= 0.0:
+                    continue
+                v = tk if pk[k] >= q_ev else tk * math.log(1.0 - q_ev) / math.log(1.0 - pk[k])
+                if v < best:
+                    best, kk = v, k
+            ttt_sum += best
+            per_event.append({"event": p["e"], "N": qs[p["e"]].n, "run_seconds": p["t_run"],
+                              "p_final": float(pk[-1]), "ttt_seconds": best if best < math.inf else None,
+                              "at_step": None if kk is None else min(S, (kk + 1) * every)})
+        ttt_p = E * ttt_sum / max(len(plain), 1)
+        results.append({
+            "target": f"E_low + {frac:g} |E_low|",
+            "batched_bf16": {"seconds": ttt_b if ttt_b < math.inf else "did not reach",
+                             "at_step": None if kb is None else min(S, (kb + 1) * every),
+                             "events_never_reached": int(np.sum(P_ev[-1] <= 0.0)),
+                             "p_rep_final_median": float(np.median(p_rep[-1]))},
+            "plain_fp32": {"seconds": ttt_p if ttt_p < math.inf else "did not reach",
+                           "per_event": per_event},
+            "speedup_batched_vs_plain": (ttt_p / ttt_b) if (ttt_b < math.inf and ttt_p < math.inf)
+            else None})
     # ---- efficiency / purity and the truth energy on the sampled events
     row0 = np.cumsum([0] + [q.n for q in qs])
     eff_b, pur_b, eff_p, pur_p, gaps = [], [], [], [], []
@@ -576,25 +604,25 @@ def time_to_target(sb, w, pairs, ctx, stream, dev, plain_events, plain_runs=64, 
         c1 = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_FP32)
         E_truth = float(sb.sb_energy(c1, np.where(truth > 0, 1, -1).astype(np.int8)[:, None])[0, 0])
         sb.sb_destroy(c1)
-        gaps.append((E_best[e] - E_truth) / abs(E_truth))
+        gaps.append((E_low[e] - E_truth) / abs(E_truth))
     return {
-        "definition": "time to reach 99.9 % of the lowest energy found (E_best + 0.001 |E_best|) "
-                      "with 99 % probability for every event of the workload",
+        "definition": "time to reach the target energy with 99 % probability for every event "
+                      "of the workload; targets: the paper's 99.9 % of the lowest energy found "
+                      "(E_low + 0.001 |E_low|), and a loosened one",
         "c0_scale": c0_scale, "checkpoint_every": every,
         "reference_run": {"steps": 2 * S, "c0_scale": ref_scale, "replicas": R},
-        "batched_bf16": {"seconds": ttt_b, "at_step": None if kb is None else min(S, (kb + 1) * every),
-                         "run_seconds": times[-1], "replicas": R, "events": E,
-                         "P_all_final": float(P_all[-1]),
-                         "p_rep_final_median": float(np.median(p_rep[-1]))},
-        "plain_fp32": {"seconds": ttt_p, "events_sampled": len(plain), "runs_per_event": plain_runs,
-                       "per_event_probability": q_ev, "per_event": per_event,
-                       "scaling": f"{E} x mean over the sampled events"},
-        "speedup_batched_vs_plain": (ttt_p / ttt_b) if (ttt_b < math.inf and ttt_p < math.inf) else None,
+        "batched_run_seconds": times[-1], "replicas": R, "events": E,
+        "plain_runs": {"events_sampled": len(plain), "runs_per_event": plain_runs,
+                       "per_event_probability": q_ev,
+                       "scaling": f"{E} x mean over the sampled events",
+                       "run_seconds": [p["t_run"] for p in plain]},
+        "targets": results,
+        "speedup_batched_vs_plain": results[0]["speedup_batched_vs_plain"],
         "efficiency": {"batched": float(np.mean(eff_b)), "plain": float(np.mean(eff_p))},
         "purity": {"batched": float(np.mean(pur_b)), "plain": float(np.mean(pur_p))},
         "best_over_truth_energy": {"median": float(np.median(gaps)), "min": float(np.min(gaps)),
                                    "max": float(np.max(gaps)),
-                                   "note": "(E_best - E_truth) / |E_truth| on the sampled events; "
+                                   "note": "(E_low - E_truth) / |E_truth| on the sampled events; "
                                            "negative: SB found energies below the true triplets'"},
     }
 
@@ -645,7 +673,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    w = workload(args.workload, args.sb_steps, args.variant)
+    w = workload(args.workload, args.sb_steps, args.variant, args.events)
     R, S, a0, dt, variant = w["R"], w["S"], w["a0"], w["dt"], w["variant"]
     prec = sb.SB_J_BF16 if w["jprec"] == "bf16" else sb.SB_J_FP32
 

@@ -209,6 +209,15 @@ struct sb_ctx {
   int32_t* d_f_gseg = nullptr;
   int32_t* d_f_gmem = nullptr;
   int32_t* d_f_gout = nullptr;
+  int4* d_f_item = nullptr;     // group-sum work items (block, member range, scratch slot)
+  int4* d_f_item1 = nullptr;    // the same with one item per block (the dSB form)
+  int32_t* d_f_gnc = nullptr;   // chunks per block
+  int32_t* d_f_gscr0 = nullptr; // first scratch slot per block (-1: one chunk)
+  int32_t fac_nitems = 0, fac_nslots = 0;
+  int32_t* d_f_cnt = nullptr;   // finished chunks per (block, replica tile); zero between steps
+  size_t f_cnt_count = 0;
+  float* d_f_scr = nullptr;     // chunk sums [slots x K x R]
+  size_t f_scr_count = 0;
   int32_t* d_f_uidx = nullptr;
   int32_t* d_f_rrowptr = nullptr;
   int32_t* d_f_rcol = nullptr;
@@ -404,6 +413,16 @@ void free_factor(sb_ctx* c) {
   dfree(c->d_f_gseg);
   dfree(c->d_f_gmem);
   dfree(c->d_f_gout);
+  if (c->d_f_item) cudaFree(c->d_f_item);
+  c->d_f_item = nullptr;
+  if (c->d_f_item1) cudaFree(c->d_f_item1);
+  c->d_f_item1 = nullptr;
+  dfree(c->d_f_gnc);
+  dfree(c->d_f_gscr0);
+  dfree(c->d_f_cnt);
+  dfree(c->d_f_scr);
+  c->f_cnt_count = c->f_scr_count = 0;
+  c->fac_nitems = c->fac_nslots = 0;
   dfree(c->d_f_uidx);
   dfree(c->d_f_rrowptr);
   dfree(c->d_f_rcol);
@@ -1401,6 +1420,32 @@ sb_status set_factor(sb_ctx* c, int32_t n_ids, int32_t K, const int32_t* member,
     }
   }
   const int32_t ng = (int32_t)gout.size() / K;
+  // work items of the group sums. aSB / bSB (one block per warp): blocks of
+  // more than kChunk members are cut into near-equal chunks (a warp walks its
+  // members one after another, so the largest block would otherwise set the
+  // kernel's time). dSB (eight blocks per warp, advancing together): whole
+  // blocks (measured faster there: the chunk sums' fences cost more than the
+  // split saves).
+  constexpr int64_t kChunk = 16;
+  std::vector<int4> items, items1;
+  for (int32_t ga = 0; ga < ng; ++ga)
+    items1.push_back(make_int4(ga, gseg[(size_t)ga * K], gseg[(size_t)ga * K + K], -1));
+  std::vector<int32_t> gnc(ng), gscr0(ng, -1);
+  int32_t nslots = 0;
+  for (int32_t ga = 0; ga < ng; ++ga) {
+    const int64_t m0 = gseg[(size_t)ga * K], m1 = gseg[(size_t)ga * K + K], cnt = m1 - m0;
+    const int32_t nc = (int32_t)std::max<int64_t>(1, (cnt + kChunk - 1) / kChunk);
+    gnc[ga] = nc;
+    if (nc == 1) {
+      items.push_back(make_int4(ga, (int)m0, (int)m1, -1));
+      continue;
+    }
+    gscr0[ga] = nslots;
+    for (int32_t ci = 0; ci < nc; ++ci)
+      items.push_back(make_int4(ga, (int)(m0 + ci * cnt / nc), (int)(m0 + (ci + 1) * cnt / nc),
+                                nslots + ci));
+    nslots += nc;
+  }
   if ((int64_t)n + nu >= (1 << 27)) {
     set_error("sb_set_factor: rows plus U rows must stay below 2^27");
     return SB_ERR_ARG;
@@ -1481,6 +1526,41 @@ sb_status set_factor(sb_ctx* c, int32_t n_ids, int32_t K, const int32_t* member,
       rj_all.insert(rj_all.end(), t, t + esz);  // little-endian: the low esz bytes
     }
   }
+  {
+    cudaError_t e = cudaMalloc(&c->d_f_item, std::max<size_t>(items.size(), 1) * sizeof(int4));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->d_f_item = nullptr;
+      free_factor(c);
+      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      return SB_ERR_OOM;
+    }
+  }
+  if ((st = dalloc(&c->d_f_gnc, std::max<size_t>(gnc.size(), 1))) ||
+      (st = dalloc(&c->d_f_gscr0, std::max<size_t>(gscr0.size(), 1)))) {
+    free_factor(c);
+    return st;
+  }
+  {
+    cudaError_t e = cudaMalloc(&c->d_f_item1, std::max<size_t>(items1.size(), 1) * sizeof(int4));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->d_f_item1 = nullptr;
+      free_factor(c);
+      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      return SB_ERR_OOM;
+    }
+  }
+  if (!items.empty())
+    SB_CUDA(cudaMemcpy(c->d_f_item, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  if (!items1.empty())
+    SB_CUDA(cudaMemcpy(c->d_f_item1, items1.data(), items1.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  if (ng) {
+    SB_CUDA(cudaMemcpy(c->d_f_gnc, gnc.data(), gnc.size() * 4, cudaMemcpyHostToDevice));
+    SB_CUDA(cudaMemcpy(c->d_f_gscr0, gscr0.data(), gscr0.size() * 4, cudaMemcpyHostToDevice));
+  }
+  c->fac_nitems = (int32_t)items.size();
+  c->fac_nslots = nslots;
   SB_CUDA(cudaMemcpy(c->d_f_gseg, gseg.data(), gseg.size() * 4, cudaMemcpyHostToDevice));
   if (!gmem.empty())
     SB_CUDA(cudaMemcpy(c->d_f_gmem, gmem.data(), gmem.size() * 4, cudaMemcpyHostToDevice));
@@ -1659,6 +1739,32 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     }
   }
   if (fac) {
+    // chunk counters (zeroed once: every launch leaves them at zero) and chunk sums
+    const size_t cnt_need = (size_t)std::max(c->fac_ng, 1) * ftiles;
+    if (cnt_need > c->f_cnt_count) {
+      dfree(c->d_f_cnt);
+      c->f_cnt_count = 0;
+      sb_status st0 = dalloc(&c->d_f_cnt, cnt_need);
+      if (st0) return st0;
+      SB_CUDA(cudaMemset(c->d_f_cnt, 0, cnt_need * 4));
+      c->f_cnt_count = cnt_need;
+      c->graph.reset();
+    }
+    const size_t scr_need = (size_t)std::max(c->fac_nslots, 1) * c->fac_K * c->R;
+    if (scr_need > c->f_scr_count) {
+      dfree(c->d_f_scr);
+      c->f_scr_count = 0;
+      sb_status st0 = dalloc(&c->d_f_scr, scr_need);
+      if (st0) return st0;
+      c->f_scr_count = scr_need;
+      c->graph.reset();
+    }
+    fs.item = variant == SB_DSB ? c->d_f_item1 : c->d_f_item;
+    fs.nitems = variant == SB_DSB ? c->fac_ng : c->fac_nitems;
+    fs.gnc = c->d_f_gnc;
+    fs.gscr0 = c->d_f_gscr0;
+    fs.cnt = c->d_f_cnt;
+    fs.scratch = c->d_f_scr;
     fs.gseg = c->d_f_gseg;
     fs.gmem = c->d_f_gmem;
     fs.gout = c->d_f_gout;

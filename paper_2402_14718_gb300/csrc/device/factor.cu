@@ -22,9 +22,10 @@
 //
 // Layout: lane l of a G-lane row group covers, for FP32 state, the replicas
 // tile0 + 4 l + 4 G j + v (j < NCH, v < 4), i.e. 16-byte chunks strided by the
-// group; for dSB sign bytes the 16 replicas tile0 + 16 l + v. U rows use the
-// same replica layout: FP32 for aSB / bSB; for dSB BF16 sums of 2^-7 sgn
-// (exact: the host checks that no U element can exceed 256 in magnitude).
+// group; for dSB sign bytes the 8 replicas tile0 + 8 l + v (one 8-byte load
+// per neighbour). U rows use the same replica layout: FP32 for aSB / bSB; for
+// dSB BF16 sums of 2^-7 sgn (exact: the host checks that no U element can
+// exceed 256 members).
 //
 // Every sum is formed in a fixed order (members by slot and row, residual in
 // column order), so results are reproducible. For dSB with weights that are
@@ -40,6 +41,40 @@ namespace sbd {
 namespace {
 
 constexpr int kFacBlock = 128;
+// dSB: replicas per lane (measured on the 512-event batch against 16 per lane,
+// and against requesting the U rows and own x, y before the residual walk:
+// both cost occupancy and were slower)
+constexpr int kSgnPer = 8;
+
+// N 32-bit words loaded or stored as one vector (N = 2 or 4)
+template <int N>
+struct Words;
+template <>
+struct Words<2> {
+  uint32_t w[2];
+  __device__ __forceinline__ void ldg(const void* p) {
+    const uint2 t = __ldg(static_cast<const uint2*>(p));
+    w[0] = t.x;
+    w[1] = t.y;
+  }
+  __device__ __forceinline__ void st(void* p) const {
+    *static_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+  }
+};
+template <>
+struct Words<4> {
+  uint32_t w[4];
+  __device__ __forceinline__ void ldg(const void* p) {
+    const uint4 t = __ldg(static_cast<const uint4*>(p));
+    w[0] = t.x;
+    w[1] = t.y;
+    w[2] = t.z;
+    w[3] = t.w;
+  }
+  __device__ __forceinline__ void st(void* p) const {
+    *static_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+};
 
 __device__ __forceinline__ unsigned lane_group_mask(int G) {
   const int lane = threadIdx.x & 31;
@@ -71,15 +106,14 @@ struct Chunk<0, NCH> {
 };
 template <int NCH>
 struct Chunk<1, NCH> {
-  static constexpr int P = 16;
-  uint4 t;
+  static constexpr int P = kSgnPer;
+  Words<P / 4> t;
   __device__ __forceinline__ void load(const FacSumArgs& a, size_t off, int, int row) {
-    t = __ldg(reinterpret_cast<const uint4*>(a.sgn_in + (size_t)row * a.R + off));
+    t.ldg(a.sgn_in + (size_t)row * a.R + off);
   }
-  __device__ __forceinline__ void add_to(float (&u)[16]) const {
-    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+  __device__ __forceinline__ void add_to(float (&u)[P]) const {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) u[k] += scaled_sign_of_byte(w[k >> 2], k & 3);
+    for (int k = 0; k < P; ++k) u[k] += scaled_sign_of_byte(t.w[k >> 2], k & 3);
   }
 };
 
@@ -93,6 +127,43 @@ __device__ __forceinline__ void add_member(float (&U)[K][CH::P], const CH& v, in
     if ((couple >> (4 * s + s2)) & 1u) v.add_to(U[s]);
 }
 
+// Write the K U rows of block g from the sums U (for every slot in use).
+template <int MODE, int NCH, int K, int P>
+__device__ __forceinline__ void store_u(const FacSumArgs& a, int g, size_t off, int G,
+                                        const float (&U)[K][P]) {
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const int u = __ldg(a.gout + (size_t)g * K + s);
+    if (u < 0) continue;
+    if (MODE == 0) {
+      float4* p = reinterpret_cast<float4*>(static_cast<float*>(a.U) + (size_t)u * a.R + off);
+#pragma unroll
+      for (int j = 0; j < NCH; ++j)
+        p[G * j] = make_float4(U[s][4 * j], U[s][4 * j + 1], U[s][4 * j + 2], U[s][4 * j + 3]);
+    } else {
+      // sums of 2^-7 sgn of at most 256 members: exact in BF16 (the top half of the FP32 word)
+      uint16_t* p = static_cast<uint16_t*>(a.U) + (size_t)u * a.R + off;
+#pragma unroll
+      for (int h = 0; h < P / 8; ++h) {
+        Words<4> w;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          w.w[k] = (__float_as_uint(U[s][8 * h + 2 * k]) >> 16) |
+                   (__float_as_uint(U[s][8 * h + 2 * k + 1]) & 0xffff0000u);
+        w.st(p + 8 * h);
+      }
+    }
+  }
+}
+
+// Lane l's P values of slot s of scratch slot c (the lane's own replicas).
+template <int MODE, int NCH, int P>
+__device__ __forceinline__ size_t scr_index(const FacSumArgs& a, int c, int s, size_t off, int G,
+                                            int v) {
+  const size_t base = ((size_t)c * a.K + s) * a.R + off;
+  return MODE == 0 ? base + 4 * G * (v >> 2) + (v & 3) : base + v;
+}
+
 template <int MODE, int NCH, int K>
 __global__ void __launch_bounds__(kFacBlock) k_fac_sum(const FacSumArgs a) {
   using C = Chunk<MODE, NCH>;
@@ -100,11 +171,13 @@ __global__ void __launch_bounds__(kFacBlock) k_fac_sum(const FacSumArgs a) {
   const int G = a.G;
   const int gq = threadIdx.x / G;
   const int l = threadIdx.x - gq * G;
-  const int g = blockIdx.x * (kFacBlock / G) + gq;
-  if (g >= a.ng) return;  // the whole lane group leaves together
+  const int it = blockIdx.x * (kFacBlock / G) + gq;
+  if (it >= a.nitems) return;  // the whole lane group leaves together
   const unsigned mask = lane_group_mask(G);
   const size_t off = MODE == 0 ? (size_t)blockIdx.y * (4 * G * NCH) + 4 * l
-                               : (size_t)blockIdx.y * (16 * G) + 16 * l;
+                               : (size_t)blockIdx.y * (kSgnPer * G) + kSgnPer * l;
+  const int4 item = __ldg(a.item + it);
+  const int g = item.x;
   // slot boundaries of the block's members (members grouped by slot)
   int bnd[K + 1];
 #pragma unroll
@@ -114,10 +187,10 @@ __global__ void __launch_bounds__(kFacBlock) k_fac_sum(const FacSumArgs a) {
   for (int s = 0; s < K; ++s)
 #pragma unroll
     for (int v = 0; v < P; ++v) U[s][v] = 0.f;
-  // all members of the block in one pass, G entries per load, four rows in flight;
+  // this item's members in one pass, G entries per load, four rows in flight;
   // each lane's entry carries its row and slot, broadcast by shuffles
-  for (int mb = bnd[0]; mb < bnd[K]; mb += G) {
-    const int cnt = min(G, bnd[K] - mb);
+  for (int mb = item.y; mb < item.z; mb += G) {
+    const int cnt = min(G, item.z - mb);
     int mr = 0, ms = 0;
     if (l < cnt) {
       const int t = mb + l;
@@ -146,26 +219,38 @@ __global__ void __launch_bounds__(kFacBlock) k_fac_sum(const FacSumArgs a) {
       add_member<K, C>(U, v0, s0, a.couple);
     }
   }
-#pragma unroll
-  for (int s = 0; s < K; ++s) {
-    const int u = __ldg(a.gout + (size_t)g * K + s);
-    if (u < 0) continue;
-    if (MODE == 0) {
-      float4* p = reinterpret_cast<float4*>(static_cast<float*>(a.U) + (size_t)u * a.R + off);
-#pragma unroll
-      for (int j = 0; j < NCH; ++j)
-        p[G * j] = make_float4(U[s][4 * j], U[s][4 * j + 1], U[s][4 * j + 2], U[s][4 * j + 3]);
-    } else {
-      // sums of 2^-7 sgn of at most 256 members: exact in BF16 (the top half of the FP32 word)
-      uint32_t w[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        w[k] = (__float_as_uint(U[s][2 * k]) >> 16) | (__float_as_uint(U[s][2 * k + 1]) & 0xffff0000u);
-      uint4* p = reinterpret_cast<uint4*>(static_cast<uint16_t*>(a.U) + (size_t)u * a.R + off);
-      p[0] = make_uint4(w[0], w[1], w[2], w[3]);
-      p[1] = make_uint4(w[4], w[5], w[6], w[7]);
-    }
+  if (item.w < 0) {  // the whole block in one item
+    store_u<MODE, NCH, K, P>(a, g, off, G, U);
+    return;
   }
+  // one chunk of a split block: its sums to the scratch slot; the chunk that
+  // finishes last adds every chunk's slot in chunk order (a fixed order, so
+  // the result does not depend on which chunk finishes last)
+#pragma unroll
+  for (int s = 0; s < K; ++s)
+#pragma unroll
+    for (int v = 0; v < P; ++v) a.scratch[scr_index<MODE, NCH, P>(a, item.w, s, off, G, v)] = U[s][v];
+  __threadfence();
+  __syncwarp(mask);
+  int last = 0;
+  const int nc = __ldg(a.gnc + g);
+  int* const cnt = a.cnt + (size_t)g * a.tiles + blockIdx.y;  // one counter per replica tile
+  if (l == 0) last = atomicAdd(cnt, 1) == nc - 1;
+  last = __shfl_sync(mask, last, 0, G);
+  if (!last) return;
+  __threadfence();
+  const int c0 = __ldg(a.gscr0 + g);
+#pragma unroll
+  for (int s = 0; s < K; ++s)
+#pragma unroll
+    for (int v = 0; v < P; ++v) U[s][v] = 0.f;
+  for (int c = 0; c < nc; ++c)
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+#pragma unroll
+      for (int v = 0; v < P; ++v) U[s][v] += __ldcg(a.scratch + scr_index<MODE, NCH, P>(a, c0 + c, s, off, G, v));
+  store_u<MODE, NCH, K, P>(a, g, off, G, U);
+  if (l == 0) *cnt = 0;  // ready for the next launch
 }
 
 __device__ __forceinline__ float jv(const float* J, int p) { return __ldg(J + p); }
@@ -196,27 +281,28 @@ struct URow<0, NCH> {
 };
 template <int NCH>
 struct URow<1, NCH> {
-  uint4 t0, t1;
+  Words<4> t[kSgnPer / 8];  // kSgnPer BF16 sums
   __device__ __forceinline__ void load(const void* U, size_t base, int) {
-    const uint4* p = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(U) + base);
-    t0 = __ldg(p);
-    t1 = __ldg(p + 1);
-  }
-  __device__ __forceinline__ void add_to(float (&fu)[16]) const {
-    const uint32_t w[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+    const uint16_t* p = static_cast<const uint16_t*>(U) + base;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      fu[2 * k] += __uint_as_float(w[k] << 16);
-      fu[2 * k + 1] += __uint_as_float(w[k] & 0xffff0000u);
-    }
+    for (int h = 0; h < kSgnPer / 8; ++h) t[h].ldg(p + 8 * h);
+  }
+  __device__ __forceinline__ void add_to(float (&fu)[kSgnPer]) const {
+#pragma unroll
+    for (int h = 0; h < kSgnPer / 8; ++h)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        fu[8 * h + 2 * k] += __uint_as_float(t[h].w[k] << 16);
+        fu[8 * h + 2 * k + 1] += __uint_as_float(t[h].w[k] & 0xffff0000u);
+      }
   }
 };
 
 // VARIANT 0 aSB, 1 bSB (MODE 0: FP32 x), 2 dSB (MODE 1: sign bytes)
 template <int VARIANT, int MODE, int NCH, int K, typename JT>
 __global__ void __launch_bounds__(kFacBlock) k_step_fac(const FacStepArgs a) {
-  constexpr int P = MODE == 0 ? 4 * NCH : 16;
-  constexpr int NV = MODE == 0 ? NCH : 4;  // float4 of own x (and y) per lane
+  constexpr int P = MODE == 0 ? 4 * NCH : kSgnPer;
+  constexpr int NV = P / 4;  // float4 of own x (and y) per lane
   const int G = a.G;
   const int gq = threadIdx.x / G;
   const int l = threadIdx.x - gq * G;
@@ -225,9 +311,26 @@ __global__ void __launch_bounds__(kFacBlock) k_step_fac(const FacStepArgs a) {
   const unsigned mask = lane_group_mask(G);
   const int R = a.R;
   const size_t off = MODE == 0 ? (size_t)blockIdx.y * (4 * G * NCH) + 4 * l
-                               : (size_t)blockIdx.y * (16 * G) + 16 * l;
+                               : (size_t)blockIdx.y * (kSgnPer * G) + kSgnPer * l;
+  const size_t idx = (size_t)row * R + off;
   const JT* J = static_cast<const JT*>(a.rJ);
+  // the row's own x and y and its U rows are read after the residual walk:
+  // ask for them in L2 now, so that those loads do not wait on HBM
+#pragma unroll
+  for (int j = 0; j < P / 4; ++j) {
+    const size_t o = MODE == 0 ? idx + 4 * G * j : idx + 4 * j;
+    prefetch_l2(a.xin + o);
+    prefetch_l2(a.y + o);
+  }
+  int us[K];
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    us[s] = __ldg(a.uidx + (size_t)row * K + s);
+    if (us[s] >= 0)
+      prefetch_l2(static_cast<const char*>(a.U) + ((size_t)us[s] * R + off) * (MODE == 0 ? 4 : 2));
+  }
   const int p0 = __ldg(a.rrowptr + row), p1 = __ldg(a.rrowptr + row + 1);
+
   // residual row, in column order
   float acc[P];
 #pragma unroll
@@ -267,16 +370,14 @@ __global__ void __launch_bounds__(kFacBlock) k_step_fac(const FacStepArgs a) {
             acc[4 * j + 3] = fmaf(w[u], t[u][j].w, acc[4 * j + 3]);
           }
       } else {
-        uint4 t[4];
+        Words<kSgnPer / 4> t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[u].ldg(a.sgn_in + (size_t)c[u] * R + off);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          t[u] = __ldg(reinterpret_cast<const uint4*>(a.sgn_in + (size_t)c[u] * R + off));
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const uint32_t ww[4] = {t[u].x, t[u].y, t[u].z, t[u].w};
-#pragma unroll
-          for (int v = 0; v < 16; ++v) acc[v] = fmaf(w[u], scaled_sign_of_byte(ww[v >> 2], v & 3), acc[v]);
-        }
+          for (int v = 0; v < kSgnPer && v < P; ++v)
+            acc[v] = fmaf(w[u], scaled_sign_of_byte(t[u].w[v >> 2], v & 3), acc[v]);
       }
     }
     for (; q < cnt; ++q) {
@@ -292,10 +393,11 @@ __global__ void __launch_bounds__(kFacBlock) k_step_fac(const FacStepArgs a) {
           acc[4 * j + 3] = fmaf(w, t.w, acc[4 * j + 3]);
         }
       } else {
-        const uint4 t = __ldg(reinterpret_cast<const uint4*>(a.sgn_in + (size_t)c * R + off));
-        const uint32_t ww[4] = {t.x, t.y, t.z, t.w};
+        Words<kSgnPer / 4> t;
+        t.ldg(a.sgn_in + (size_t)c * R + off);
 #pragma unroll
-        for (int v = 0; v < 16; ++v) acc[v] = fmaf(w, scaled_sign_of_byte(ww[v >> 2], v & 3), acc[v]);
+        for (int v = 0; v < kSgnPer && v < P; ++v)
+          acc[v] = fmaf(w, scaled_sign_of_byte(t.w[v >> 2], v & 3), acc[v]);
       }
     }
   }
@@ -306,11 +408,10 @@ __global__ void __launch_bounds__(kFacBlock) k_step_fac(const FacStepArgs a) {
   for (int v = 0; v < P; ++v) fu[v] = 0.f;
 #pragma unroll
   for (int s = 0; s < K; ++s) {
-    const int u = __ldg(a.uidx + (size_t)row * K + s);
-    if (u < 0) continue;
+    if (us[s] < 0) continue;
     any = true;
     URow<MODE, NCH> ur;
-    ur.load(a.U, (size_t)u * R + off, G);
+    ur.load(a.U, (size_t)us[s] * R + off, G);
     ur.add_to(fu);
   }
   // dSB: U holds sums of 2^-7 sgn, so the scale is 2^7 jf (exact)
@@ -325,14 +426,15 @@ __global__ void __launch_bounds__(kFacBlock) k_step_fac(const FacStepArgs a) {
   const int ev = a.row_event ? __ldg(a.row_event + row) : 0;
   const float c0 = __ldg(a.c0_ev + ev);
   const float hi = __ldg(a.h + row);
-  const size_t idx = (size_t)row * R + off;
-  uint32_t sw[4] = {0u, 0u, 0u, 0u};
+  Words<kSgnPer / 4> sw;  // dSB: the new sign bytes
+#pragma unroll
+  for (int k = 0; k < kSgnPer / 4; ++k) sw.w[k] = 0u;
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
     const size_t o = MODE == 0 ? idx + 4 * G * j : idx + 4 * j;
-    const float4 xv = __ldg(reinterpret_cast<const float4*>(a.xin + o));
-    const float4 yv = *reinterpret_cast<const float4*>(a.y + o);
-    float xs[4] = {xv.x, xv.y, xv.z, xv.w}, ys[4] = {yv.x, yv.y, yv.z, yv.w};
+    const float4 xo = __ldg(reinterpret_cast<const float4*>(a.xin + o));
+    const float4 yo = *reinterpret_cast<const float4*>(a.y + o);
+    float xs[4] = {xo.x, xo.y, xo.z, xo.w}, ys[4] = {yo.x, yo.y, yo.z, yo.w};
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       float x = xs[v], y = ys[v];
@@ -346,19 +448,19 @@ __global__ void __launch_bounds__(kFacBlock) k_step_fac(const FacStepArgs a) {
       }
       xs[v] = x;
       ys[v] = y;
-      if (MODE == 1) sw[j] |= sign_byte(x) << (8 * v);
+      if (MODE == 1 && j < kSgnPer / 4) sw.w[j] |= sign_byte(x) << (8 * v);
     }
     *reinterpret_cast<float4*>(a.xout + o) = make_float4(xs[0], xs[1], xs[2], xs[3]);
     *reinterpret_cast<float4*>(a.y + o) = make_float4(ys[0], ys[1], ys[2], ys[3]);
   }
-  if (MODE == 1) *reinterpret_cast<uint4*>(a.sgn_out + idx) = make_uint4(sw[0], sw[1], sw[2], sw[3]);
+  if (MODE == 1) sw.st(a.sgn_out + idx);
 }
 
 template <int MODE, int NCH, int K>
 cudaError_t launch_sum_k(const FacSumArgs& a, cudaStream_t s) {
-  if (a.ng <= 0) return cudaSuccess;
+  if (a.nitems <= 0) return cudaSuccess;
   const int per = kFacBlock / a.G;
-  dim3 grid((a.ng + per - 1) / per, a.tiles);
+  dim3 grid((a.nitems + per - 1) / per, a.tiles);
   k_fac_sum<MODE, NCH, K><<<grid, kFacBlock, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -406,8 +508,8 @@ cudaError_t launch_step_j(int variant, const FacStepArgs& a, cudaStream_t s) {
 bool fac_tiling(int variant, int R, int* G, int* NCH, int* tiles) {
   if (R < 1) return false;
   if (variant == 2) {
-    if (R % 16) return false;
-    const int C = R / 16;
+    if (R % kSgnPer) return false;
+    const int C = R / kSgnPer;
     if (C <= 32 && (C & (C - 1)) == 0) {
       *G = C;
       *NCH = 1;

@@ -223,6 +223,16 @@ struct FacSumArgs {
   const int32_t* gseg;   // [ng * K + 1] members of block g, slot s: gmem[gseg[gK+s] .. gseg[gK+s+1])
   const int32_t* gmem;   // member rows, ascending within a slot
   const int32_t* gout;   // [ng * K] U row written for (g, s); -1: not needed
+  // work items: (block, first member, end member, scratch slot or -1); a block
+  // of more than one chunk of members is split over several items, each adding
+  // its chunk into a scratch slot, and the item that finishes last (counter
+  // cnt[block]) sums the block's slots in chunk order and writes the U rows
+  const int4* item;
+  int32_t nitems;
+  const int32_t* gnc;    // [ng] chunks of each block
+  const int32_t* gscr0;  // [ng] first scratch slot of each block (-1: one chunk)
+  int32_t* cnt;          // [ng x tiles] finished chunks per replica tile (zero between launches)
+  float* scratch;        // [slots x K x R] chunk sums
   int32_t ng, K;
   uint32_t couple;       // bit 4 s + s': W[s][s'] = 1
   const float* xin;      // aSB / bSB: positions x_k [n x R]

@@ -27,4 +27,10 @@ __device__ __forceinline__ float scaled_sign_of_byte(uint32_t w, int k) {
   return __int_as_float((int)__byte_perm(w, 0u, 0x0444u | ((uint32_t)k << 12)));
 }
 
+// Ask for the 128-byte line holding p to be brought into L2 (no register is
+// written; a later load of it then hits L2 instead of waiting on HBM).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 }  // namespace sbd

@@ -29,6 +29,10 @@ CUTS_PAPER = _cuts(4e-4, 0.5, 50.0, 8e-4, 0.1, 1e-4)
 # triplet is < 0.003 rad at 0.1 mm smear); 10k tracks -> N ~ 0.47M, ~21M couplings
 CUTS_DENSE = _cuts(3.5e-4, 0.3, 25.0, 8e-4, 0.04)
 
+# the pile-up event at N ~ 1M: windows between the dense preset and the printed
+# cuts; 10k tracks + 20 % noise -> N = 1.03M, 109M couplings (106 per row)
+CUTS_PILEUP_1M = _cuts(4.4e-4, 0.44, 34.0, 8e-4, 0.057)
+
 WORKLOADS = {
     # plain bSB / dSB on one small event, FP32 J, one replica
     "event100": dict(n_tracks=100, noise_frac=0.1, seed=0, cuts=CUTS_S8,
@@ -42,6 +46,9 @@ WORKLOADS = {
     # high pile-up event
     "event10k": dict(n_tracks=10000, noise_frac=0.2, seed=4000, cuts=CUTS_DENSE,
                      replicas=128, steps=5000, dt=0.5, a0=1.0, jprec="bf16"),
+    # the same event at the stated N ~ 1M (looser cuts)
+    "event10k_1m": dict(n_tracks=10000, noise_frac=0.2, seed=4000, cuts=CUTS_PILEUP_1M,
+                        replicas=128, steps=5000, dt=0.5, a0=1.0, jprec="bf16"),
 }
 
 # 512 uneven events in one context: event e has BATCH512_TRACKS[e] tracks
