@@ -113,8 +113,7 @@ def run_study(args):
                  ("factored", True, []),
                  ("factored, dedicated kernel", True, [(sb.SB_OPT_ROWS_PER_WARP, 0)])]
         if w["variant"] == "dsb":
-            forms = [("plain, sign bytes, FP32 sums", False, [(sb.SB_OPT_DSB_HALF, 0)]),
-                     ("plain, sign bytes, FP16 sums", False, []),
+            forms = [("plain, sign bytes", False, []),
                      ("plain, FP32 positions", False, [(sb.SB_OPT_DSB_SIGNS, 0)]),
                      ("factored, sign bytes", True, [])]
         ref = None

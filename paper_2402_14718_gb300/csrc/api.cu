@@ -1985,15 +1985,23 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
     return cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &v);
   };
+  const int ngroups =
+      (!fac && !streamed && !rw && !tiled && !dsb16 && c->groups > 1 && t.tiles == c->groups) ? c->groups : 1;
+  // factored dSB with sign bytes: neighbours read only the sign bytes
+  // (ping-pong), so each row updates its own x in place and the kernel skips
+  // writing back values that did not change; the other paths ping-pong x
+  const bool x_inplace = fac && sgn && ngroups == 1;
   auto launch = [&](int32_t k, int cur, cudaStream_t st) -> cudaError_t {
-    cudaError_t ew = set_window(c->d_x[cur], st);
+    float* const xi = x_inplace ? c->d_x[c->cur] : c->d_x[cur];
+    float* const xo = x_inplace ? xi : c->d_x[cur ^ 1];
+    cudaError_t ew = set_window(xi, st);
     if (ew != cudaSuccess) return ew;
     if (sgn) {
       a.sgn_in = c->d_sgn[cur];
       a.sgn_out = c->d_sgn[cur ^ 1];
     }
     if (fac) {
-      fs.xin = c->d_x[cur];
+      fs.xin = xi;
       fs.sgn_in = sgn ? c->d_sgn[cur] : nullptr;
       if (frw) fs.U = c->d_x[cur] + (size_t)c->n * c->R;
       cudaError_t ef = sbd::launch_fac_sum(variant, fs, st);
@@ -2005,8 +2013,8 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
         return sbd::launch_step_rw(variant, c->jbf16, 2, rw_nch, ra, st);
       }
       fa.k = k;
-      fa.xin = c->d_x[cur];
-      fa.xout = c->d_x[cur ^ 1];
+      fa.xin = xi;
+      fa.xout = xo;
       fa.sgn_in = sgn ? c->d_sgn[cur] : nullptr;
       fa.sgn_out = sgn ? c->d_sgn[cur ^ 1] : nullptr;
       return sbd::launch_step_fac(variant, c->jbf16, fa, st);
@@ -2019,8 +2027,8 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     }
     if (rw) {
       ra.k = k;
-      ra.xin = c->d_x[cur];
-      ra.xout = c->d_x[cur ^ 1];
+      ra.xin = xi;
+      ra.xout = xo;
       ra.sgn_in = sgn ? c->d_sgn[cur] : nullptr;
       ra.sgn_out = sgn ? c->d_sgn[cur ^ 1] : nullptr;
       return sbd::launch_step_rw(variant, c->jbf16, rw, rw_nch, ra, st);
@@ -2032,13 +2040,11 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
       return sbd::launch_step_tiled(variant, c->jbf16, ta, st);
     }
     a.k = k;
-    a.xin = c->d_x[cur];
-    a.xout = c->d_x[cur ^ 1];
+    a.xin = xi;
+    a.xout = xo;
     return sbd::launch_step(variant, c->jbf16, t, a, st);
   };
   const size_t NR = (size_t)c->n * c->R;
-  const int ngroups =
-      (!fac && !streamed && !rw && !tiled && !dsb16 && c->groups > 1 && t.tiles == c->groups) ? c->groups : 1;
   sbd::Tiling tg = t;
   if (ngroups > 1) tg.tiles = 1;
   // all steps for replica group g (tiles g), then the next group: each group's
@@ -2079,7 +2085,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   if (!replay && !capture) {
     if (!key.empty()) gc.seen = key;
     SB_CUDA(launch_all(c->cur, stream));
-    if (steps & 1) c->cur ^= 1;
+    if ((steps & 1) && !x_inplace) c->cur ^= 1;
     if (c->l2_persist && win_max) {  // leave the caller's stream without our window
       cudaStreamAttrValue v = {};
       v.accessPolicyWindow.num_bytes = 0;
@@ -2101,7 +2107,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     gc.key = key;
   }
   SB_CUDA(cudaGraphLaunch(gc.exec, stream));
-  if (steps & 1) c->cur ^= 1;
+  if ((steps & 1) && !x_inplace) c->cur ^= 1;
   return SB_OK;
 }
 

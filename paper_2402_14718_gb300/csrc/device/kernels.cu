@@ -466,9 +466,6 @@ __global__ void __launch_bounds__(kDsbBlock, SB_DSB_MINB) k_step_dsb16(const Ste
     float acc[16];
 #pragma unroll
     for (int v = 0; v < 16; ++v) acc[v] = 0.f;
-    // the row's own x and y are read after the neighbour walk: into L2 now
-    prefetch_l2(a.xin + (size_t)row * R + 16 * g);
-    prefetch_l2(a.y + (size_t)row * R + 16 * g);
     const int p0 = __ldg(a.rowptr + row), p1 = __ldg(a.rowptr + row + 1);
     for (int pb = p0; pb < p1; pb += G) {
       const int cnt = min(G, p1 - pb);

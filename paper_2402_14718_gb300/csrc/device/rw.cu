@@ -134,20 +134,6 @@ __global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a
       for (int j = 0; j < NCH; ++j)
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[q][j][v] = 0.f;
-    // the group rows' own x and y are read after the union walk: ask for them
-    // in L2 now, so that those loads do not wait on HBM
-    int grow[RW];
-#pragma unroll
-    for (int q = 0; q < RW; ++q) {
-      grow[q] = __ldg(a.grows + (size_t)grp * RW + q);
-      if (grow[q] >= 0) {
-#pragma unroll
-        for (int j = 0; j < NCH; ++j) {
-          prefetch_l2(a.xin + (size_t)grow[q] * R + rep0 + 128 * j);
-          prefetch_l2(a.y + (size_t)grow[q] * R + rep0 + 128 * j);
-        }
-      }
-    }
     const int e0 = __ldg(a.gptr + grp), e1 = __ldg(a.gptr + grp + 1);
     // union entries 32 at a time, one per lane (lanes past the end hold column
     // 0 with an empty mask); the next 32 are loaded ahead
@@ -223,7 +209,7 @@ __global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a
     // symplectic Euler: momentum with the old position, then position, then wall
 #pragma unroll
     for (int q = 0; q < RW; ++q) {
-      const int row = grow[q];
+      const int row = __ldg(a.grows + (size_t)grp * RW + q);
       if (row < 0) continue;
       const int ev = a.row_event ? __ldg(a.row_event + row) : 0;
       const float c0 = __ldg(a.c0_ev + ev);

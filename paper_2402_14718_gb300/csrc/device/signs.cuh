@@ -33,4 +33,11 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// True when the two float4 differ in any bit (a state value that did not
+// change need not be written back where it is updated in place).
+__device__ __forceinline__ bool bits_differ(const float4& a, const float4& b) {
+  return (__float_as_uint(a.x) ^ __float_as_uint(b.x)) | (__float_as_uint(a.y) ^ __float_as_uint(b.y)) |
+         (__float_as_uint(a.z) ^ __float_as_uint(b.z)) | (__float_as_uint(a.w) ^ __float_as_uint(b.w));
+}
+
 }  // namespace sbd

@@ -97,3 +97,62 @@ def test_full_size_batch512_sampled_events():
         xpre = osb.prewall_x(J, h, xp, yp, a_k, B["a0"], c0, B["dt"], osb.DSB)
         compare_step(x[sl], y[sl], xo, yo, xpre)
     sb.sb_destroy(ctx)
+
+
+def test_full_size_batch512_factored_dsb_step():
+    """The bench's configuration: the 512-event batch with the shared-hit factor
+    (hit ids offset per event), R = 64, dSB with sign bytes. One step from a
+    random full-size state equals the plain sign-byte kernel's bit for bit over
+    every event (all partial sums are exact multiples of 1/4), and sampled
+    events, up to a 1000-track one, match the oracle run of that event alone."""
+    B = BATCH512
+    tracks = batch512_tracks()
+    p = sb.build_params(**B["cuts"])
+
+    def build(e):
+        ev = sb.sb_event_generate(B["seed0"] + e, sb.event_params(n_tracks=tracks[e],
+                                                                  noise_frac=B["noise_frac"]))
+        return sb.sb_qubo_build(ev, p)
+
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        qs = list(ex.map(build, range(B["n_events"])))
+    R = B["replicas"]
+    NS = sum(q.n for q in qs)
+    off, mems = 0, []
+    for q in qs:
+        m, couple, wc, n_ids = sb.sb_qubo_factor(q)
+        mems.append(np.where(m >= 0, m + off, -1))
+        off += n_ids
+    x0, y0 = inputs.random_state(NS, R, 97, 0.9)
+    outs = []
+    for factor in (True, False):
+        ctx = sb.sb_create_batch([(q.rowptr, q.col, q.val, q.lin) for q in qs], sb.SB_J_BF16)
+        if factor:
+            sb.sb_set_factor(ctx, off, np.concatenate(mems), couple, wc)
+            assert sb.sb_factor_info(ctx)["rows"] > NS // 2
+        sb.sb_set_state(ctx, x0, y0)
+        sb.sb_advance(ctx, "dsb", B["a0"], 0.0, B["dt"], 1, _sched([0.45]))
+        outs.append(sb.sb_get_state(ctx))
+        if factor:
+            infos = [sb.sb_info(ctx, e) for e in range(len(qs))]
+        sb.sb_destroy(ctx)
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    x, y = outs[0]
+    a_k = float(np.float32(0.45))
+    row0 = np.concatenate([[0], np.cumsum([q.n for q in qs])])
+    order = np.argsort(tracks, kind="stable")
+    picks = [int(order[50]), int(order[256]), int(np.argmin(np.abs(np.asarray(tracks) - 1000)))]
+    for e in picks:
+        ev_o = oev.generate(B["seed0"] + e, oev.EventParams(n_tracks=tracks[e],
+                                                           noise_frac=B["noise_frac"]))
+        qo = oq.build_qubo(ev_o, oracle_params(B["cuts"]))
+        assert np.array_equal(qs[e].col, qo.col) and np.array_equal(qs[e].val, qo.val)
+        J, h, _ = _oracle_J(qo, sb.SB_J_BF16)
+        c0 = ising.c0_auto(ising.to_ising(qo)[0], qo.n)
+        assert infos[e]["c0_auto"] == pytest.approx(c0, rel=1e-12)
+        c0 = float(np.float32(c0))
+        sl = slice(int(row0[e]), int(row0[e + 1]))
+        xp, yp = x0[sl].astype(np.float64), y0[sl].astype(np.float64)
+        xo, yo = osb.step(J, h, xp, yp, a_k, B["a0"], c0, B["dt"], osb.DSB)
+        xpre = osb.prewall_x(J, h, xp, yp, a_k, B["a0"], c0, B["dt"], osb.DSB)
+        compare_step(x[sl], y[sl], xo, yo, xpre)
