@@ -784,23 +784,37 @@ def run_ours(args):
     h2d = sum(t.numel() * t.element_size() for t in pin.values())
     d2h = N + 12 * E
 
+    parts = {"create": 0.0, "factor": 0.0, "run": 0.0, "best_destroy": 0.0}
+
     def e2e_once(seed):
+        # the calls are synchronous but sb_run, which only enqueues: the split
+        # below waits for its stream once (one extra host wait per step)
+        t = [time.perf_counter()]
         h = ctypes.c_void_p()
         _lib.check(_lib.lib.sb_create_batch(E, pin["ns"].data_ptr(), pin["zs"].data_ptr(),
                                             pin["rowptr"].data_ptr(), pin["col"].data_ptr(),
                                             pin["val"].data_ptr(), pin["lin"].data_ptr(), prec,
                                             ctypes.byref(h)))
         c2 = sb.Ctx(h.value)
+        t.append(time.perf_counter())
         if use_factor:
             _lib.check(_lib.lib.sb_set_factor(h.value, int(n_ids), 3, pin["member"].data_ptr(),
                                               pin["couple"].data_ptr(), float(wc)))
+        t.append(time.perf_counter())
         sb.sb_run(c2, variant, a0, 0.0, dt, S, R, seed)
+        torch.cuda.synchronize(dev)
+        t.append(time.perf_counter())
         _lib.check(_lib.lib.sb_best(h.value, T_host.data_ptr(), E_host.data_ptr(), r_host.data_ptr()))
         sb.sb_destroy(c2)
+        t.append(time.perf_counter())
+        for k, a, b in zip(parts, t, t[1:]):
+            parts[k] += b - a
 
     e2e_once(7)
     torch.cuda.synchronize(dev)
     e2e_steps = max(1, min(args.steps, 3))
+    for k in parts:
+        parts[k] = 0.0
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         e2e_once(100 + i)
@@ -809,6 +823,7 @@ def run_ours(args):
     e2e_s = reduce_step_ms(e2e_s * 1e3, ws, dist if ws > 1 else None, dev) * 1e-3
     e2e = {"value": job_value(units, ws, e2e_s * 1e3), "unit": "spin-updates/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s,
+           "seconds_by_call": {k: v / e2e_steps for k, v in parts.items()},
            "calls": "sb_create_batch + sb_set_factor + sb_run + sb_best + sb_destroy"
            if use_factor else "sb_create_batch + sb_run + sb_best + sb_destroy"}
 

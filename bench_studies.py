@@ -65,7 +65,7 @@ def _event(sb, spec):
     return ev, sb.sb_qubo_build(ev, sb.build_params(**spec["cuts"]))
 
 
-def _us_per_step(sb, ctx, variant, R, S, stream, dev, reps=3):
+def _us_per_step(sb, ctx, variant, R, S, stream, dev, reps=2):
     import torch
     sched = torch.tensor(np.linspace(0, 1, S).astype(np.float32), device=dev)
     sb.sb_run(ctx, variant, 1.0, 0.0, 0.5, 0, R, 7, None, stream)
@@ -94,7 +94,7 @@ def run_study(args):
     rec = Recorder(args.record, sys.argv[1:])
     if args.study == "kernels":
         # every step form on one workload: microseconds per step (graph replay,
-        # CUDA events, best of 3 x S steps), the HBM roofline fraction of the
+        # CUDA events, best of 2 runs of the S-step schedule), the HBM roofline fraction of the
         # method's bytes, and whether the state equals the first form's
         w = bench.workload(args.workload, 0, args.variant)
         pairs = bench.build_events(sb, w)
@@ -103,7 +103,7 @@ def run_study(args):
         N = sum(q.n for q in qs)
         nnz = sum(q.nnz for q in qs)
         prec = sb.SB_J_BF16 if w["jprec"] == "bf16" else sb.SB_J_FP32
-        S = 200 if len(qs) == 1 else 40
+        S = w["S"]   # the workload's whole schedule: the spins' wall occupancy changes the cost
         hbm, _ = bench.peaks()
         alg = 16 * N * R + nnz * (6 if prec == sb.SB_J_BF16 else 8) + 8 * N
         forms = [("plain, untiled", False, [(sb.SB_OPT_ROWS_PER_WARP, 0)]),

@@ -243,8 +243,9 @@ sb_status sb_step_info(const sb_ctx* ctx, int32_t* rows_per_warp, int64_t* union
  *   sum_j J_ij x_j = jf sum_s U_{member[i][s], s} + sum_j Rs_ij x_j,
  *   U_{g,s} = sum_{s'} W[s][s'] T_{g,s'},   jf = -w / 4 (J = -b / 4),
  * where the residual Rs = J - jf M^T W M (M: the row-to-(block, slot)
- * incidence; diagonal included) is formed here from the context's QUBO in
- * exact FP64 arithmetic. Each step then forms the U rows (one pass over the
+ * incidence; diagonal included) is formed here, exactly, from the context's
+ * J values (so a factored row uses the same couplings as its CSR row, J
+ * rounded to the context's precision included). Each step then forms the U rows (one pass over the
  * members of the blocks in use) and, per row, reads its K U rows and its
  * residual row instead of its whole CSR row. A row stays in plain CSR form
  * when its residual is not exactly representable in the context's J
@@ -253,7 +254,7 @@ sb_status sb_step_info(const sb_ctx* ctx, int32_t* rows_per_warp, int64_t* union
  * order of the FP32 coupling sums (for dSB with weights that are multiples of
  * 1/4 every partial sum is exact and the states equal the plain kernels' bit
  * for bit). Used by aSB / bSB when R / 4 is a power of two <= 32 or a
- * multiple of 32, and by dSB with sign bytes when R / 16 is a power of two
+ * multiple of 32, and by dSB with sign bytes when R / 8 is a power of two
  * <= 32 or a multiple of 32 and no U element can exceed 256 members; other
  * runs use the plain kernels. SB_OPT_FACTOR switches it off.
  * Inputs (host, copied): n_ids (ids lie in [0, n_ids)); k slots, 1 <= k <= 4;

@@ -49,7 +49,7 @@ struct GraphCache {
 // small counts or when a thread cannot be started). Returns false if f threw
 // (e.g. a failed allocation) in any part; the remaining parts still run.
 template <typename F>
-bool parallel_parts(int64_t count, int parts, F f) {
+bool parallel_parts(int64_t count, int parts, F f, int64_t min_parallel = 8192) {
   std::atomic<bool> ok{true};
   auto run = [&](int p) {
     const int64_t b = count * p / parts, e = count * (p + 1) / parts;
@@ -61,7 +61,7 @@ bool parallel_parts(int64_t count, int parts, F f) {
   };
   const unsigned hw = std::thread::hardware_concurrency();
   const int T = std::min(parts, (int)std::max(1u, std::min(hw, 16u)));
-  if (T <= 1 || count < 8192) {
+  if (T <= 1 || count < min_parallel) {
     for (int p = 0; p < parts; ++p) run(p);
     return ok;
   }
@@ -200,6 +200,7 @@ struct sb_ctx {
   int32_t fac_K = 0;
   uint32_t fac_couple = 0;   // bit 4 s + s': slots s and s' couple
   float fac_jf = 0.f;        // factor weight in J units (-w / 4)
+  uint32_t fac_jf_bits = 0;  // the same in the context precision
   int32_t fac_ng = 0;        // group blocks with a U row in use
   int32_t fac_urows = 0;
   int32_t fac_rows = 0;      // rows in factored form
@@ -218,7 +219,8 @@ struct sb_ctx {
   size_t f_cnt_count = 0;
   float* d_f_scr = nullptr;     // chunk sums [slots x K x R]
   size_t f_scr_count = 0;
-  int32_t* d_f_uidx = nullptr;
+  int32_t* d_f_uidx = nullptr;   // U rows of each row [n x K] (copied into the heads)
+  uint32_t* d_f_head = nullptr;  // row heads of the factored step (sbd::fac_head_words per row)
   int32_t* d_f_rrowptr = nullptr;
   int32_t* d_f_rcol = nullptr;
   void* d_f_rJ = nullptr;
@@ -282,7 +284,8 @@ void dfree(T*& p) {
 }
 
 sb_status validate_csr(int32_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
-                       const double* val, const double* lin) {
+                       const double* val, const double* lin, bool threads = true) {
+  const int64_t min_par = threads ? 8192 : INT64_MAX;
   if (rowptr[0] != 0 || (int64_t)rowptr[n] != nnz) {
     set_error("CSR: rowptr[0] must be 0 and rowptr[n] must equal nnz");
     return SB_ERR_CSR;
@@ -340,7 +343,7 @@ sb_status validate_csr(int32_t n, int64_t nnz, const int32_t* rowptr, const int3
         }
       }
     }
-  });
+  }, min_par);
   sb_status st = first_failure();
   if (st) return st;
   if (!done) {
@@ -364,7 +367,7 @@ sb_status validate_csr(int32_t n, int64_t nnz, const int32_t* rowptr, const int3
           break;
         }
       }
-  });
+  }, min_par);
   st = first_failure();
   if (!st && !done) {
     set_error("CSR check: host allocation failed");
@@ -424,6 +427,8 @@ void free_factor(sb_ctx* c) {
   c->f_cnt_count = c->f_scr_count = 0;
   c->fac_nitems = c->fac_nslots = 0;
   dfree(c->d_f_uidx);
+  if (c->d_f_head) cudaFree(c->d_f_head);
+  c->d_f_head = nullptr;
   dfree(c->d_f_rrowptr);
   dfree(c->d_f_rcol);
   if (c->d_f_rJ) cudaFree(c->d_f_rJ);
@@ -1203,8 +1208,8 @@ sb_status create_common(sb_ctx* c, const int32_t* rowptr, const int32_t* col, co
 // ---------------------------------------------------------------- factored coupling product
 // J x = jf (M^T W M) x + Rs x with M the row -> (block, slot) incidence given by
 // the caller, W the K x K slot-coupling pattern, jf = -w / 4, and the residual
-// Rs = J - jf M^T W M formed here, exactly, from the context's QUBO (diagonal
-// included). A row is kept in factored form when its residual is exactly
+// Rs = J - jf M^T W M formed here, exactly, from the context's J values
+// (diagonal included; J_ii = 0). A row is kept in factored form when its residual is exactly
 // representable in the context's J precision and its factored cost (U rows
 // read + its share of the group sums + residual entries) is below its CSR
 // length; other rows carry their plain CSR row as residual and read no U row.
@@ -1253,22 +1258,23 @@ sb_status set_factor(sb_ctx* c, int32_t n_ids, int32_t K, const int32_t* member,
         if (g >= 0) mem[(size_t)cur[(size_t)g * K + s]++] = i;
       }
   }
-  std::vector<int32_t> row_ev;
-  if (c->E > 1) {
-    row_ev.resize(n);
-    for (int32_t e = 0; e < c->E; ++e)
-      for (int32_t i = c->ev_row0[e]; i < c->ev_row0[e + 1]; ++i) row_ev[i] = e;
-  }
-  // the QUBO's b values and the context's J values (the plain rows keep them)
+  // the context's J values (the plain rows keep them; the residual is formed
+  // from them, so a factored row uses the same couplings as its CSR row)
   const size_t nnz = (size_t)c->nnz, esz = c->jbf16 ? 2 : 4;
-  std::vector<double> qv(nnz);
   std::vector<unsigned char> jraw(nnz * esz);
-  if (nnz) {
-    SB_CUDA(cudaMemcpy(qv.data(), c->d_qval, nnz * 8, cudaMemcpyDeviceToHost));
-    SB_CUDA(cudaMemcpy(jraw.data(), c->d_J, nnz * esz, cudaMemcpyDeviceToHost));
-  }
+  if (nnz) SB_CUDA(cudaMemcpy(jraw.data(), c->d_J, nnz * esz, cudaMemcpyDeviceToHost));
+  auto jval = [&](size_t t) -> double {
+    uint32_t u = 0;
+    memcpy(&u, jraw.data() + t * esz, esz);
+    float f;
+    u = esz == 2 ? u << 16 : u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+  };
   const int32_t* rp = c->h_rowptr.data();
   const int32_t* col = c->h_col.data();
+  int32_t emax = 0;
+  for (int32_t e = 0; e < c->E; ++e) emax = std::max(emax, c->ev_row0[e + 1] - c->ev_row0[e]);
   // rows in parallel parts: residual entries and the form of each row
   const int parts = 64;
   struct Part {
@@ -1280,12 +1286,19 @@ sb_status set_factor(sb_ctx* c, int32_t n_ids, int32_t K, const int32_t* member,
   std::vector<int32_t> rcount(n);
   std::vector<uint8_t> isfac(n);
   const bool ok = parallel_parts(n, parts, [&](int p, int64_t b, int64_t e) {
+    if (b >= e) return;
     Part& P = pt[p];
-    std::vector<int32_t> cand;
+    // coupling counts m_ij of row i against the rows j of its event (dense,
+    // zero between rows), the columns touched, and entries outside the CSR row
+    std::vector<int32_t> cnt((size_t)emax, 0), touched, extra;
     std::vector<int32_t> rc;
     std::vector<uint32_t> rb;
+    int32_t ev = (int32_t)(std::upper_bound(c->ev_row0.begin(), c->ev_row0.end(), (int32_t)b) -
+                           c->ev_row0.begin()) - 1;
     for (int64_t i = b; i < e; ++i) {
-      cand.clear();
+      while (i >= c->ev_row0[ev + 1]) ++ev;
+      const int32_t r0 = c->ev_row0[ev], r1 = c->ev_row0[ev + 1];
+      touched.clear();
       int ns = 0;
       for (int s = 0; s < K; ++s) {
         const int32_t g = member[(size_t)i * K + s];
@@ -1293,49 +1306,58 @@ sb_status set_factor(sb_ctx* c, int32_t n_ids, int32_t K, const int32_t* member,
         ++ns;
         for (int s2 = 0; s2 < K; ++s2)
           if ((cm >> (4 * s + s2)) & 1u)
-            for (int64_t t = seg[(size_t)g * K + s2]; t < seg[(size_t)g * K + s2 + 1]; ++t)
-              cand.push_back(mem[(size_t)t]);
+            for (int64_t t = seg[(size_t)g * K + s2]; t < seg[(size_t)g * K + s2 + 1]; ++t) {
+              const int32_t j = mem[(size_t)t];
+              if (j < r0 || j >= r1) {
+                P.cross_event = true;
+                continue;
+              }
+              if (cnt[(size_t)(j - r0)]++ == 0) touched.push_back(j);
+            }
       }
-      std::sort(cand.begin(), cand.end());
-      if (!row_ev.empty())
-        for (int32_t j : cand)
-          if (row_ev[j] != row_ev[i]) P.cross_event = true;
-      // residual in column order: b_ij - w m_ij (b_ii = 0), as J = -r / 4
+      // residual J_ij - jf m_ij in column order: the CSR row merged with the
+      // coupled rows outside it (the diagonal among them: J_ii = 0)
       rc.clear();
       rb.clear();
       bool exact = true;
-      size_t a = 0;
-      int32_t q = rp[i];
-      const int32_t q1 = rp[i + 1];
-      while (a < cand.size() || q < q1) {
-        int32_t j;
-        double bij = 0.0;
-        int64_t m = 0;
-        const int32_t ja = a < cand.size() ? cand[a] : INT32_MAX;
-        const int32_t jq = q < q1 ? col[q] : INT32_MAX;
-        j = std::min(ja, jq);
-        while (a < cand.size() && cand[a] == j) {
-          ++m;
-          ++a;
-        }
-        if (jq == j) bij = qv[(size_t)q++];
-        const double r = bij - w * (double)m;
-        if (r == 0.0) continue;
+      const int32_t q0 = rp[i], q1 = rp[i + 1];
+      auto emit = [&](int32_t j, double r) {
+        if (r == 0.0) return;
         uint32_t bits = 0;
-        if (!exact_in(-r / 4.0, c->jbf16, &bits)) exact = false;
+        if (!exact_in(r, c->jbf16, &bits)) exact = false;
         rc.push_back(j);
         rb.push_back(bits);
+      };
+      for (int32_t q = q0; q < q1; ++q) {
+        const int32_t j = col[q];
+        int32_t& m = cnt[(size_t)(j - r0)];
+        if (m > 0) m = -m;  // seen in the CSR row
       }
+      extra.clear();
+      for (int32_t j : touched)
+        if (cnt[(size_t)(j - r0)] > 0) extra.push_back(j);
+      std::sort(extra.begin(), extra.end());
+      size_t xa = 0;
+      for (int32_t q = q0; q < q1; ++q) {
+        const int32_t j = col[q];
+        for (; xa < extra.size() && extra[xa] < j; ++xa)
+          emit(extra[xa], -jf * (double)cnt[(size_t)(extra[xa] - r0)]);
+        const int32_t m = cnt[(size_t)(j - r0)];
+        emit(j, jval((size_t)q) - jf * (double)(m < 0 ? -m : m));
+      }
+      for (; xa < extra.size(); ++xa) emit(extra[xa], -jf * (double)cnt[(size_t)(extra[xa] - r0)]);
+      for (int32_t j : touched) cnt[(size_t)(j - r0)] = 0;
+      for (int32_t q = q0; q < q1; ++q) cnt[(size_t)(col[q] - r0)] = 0;
       const int64_t fac_cost = 2 * (int64_t)ns + (int64_t)rc.size();
-      if (ns > 0 && exact && fac_cost < (int64_t)(q1 - rp[i])) {
+      if (ns > 0 && exact && fac_cost < (int64_t)(q1 - q0)) {
         isfac[i] = 1;
         rcount[i] = (int32_t)rc.size();
         P.rcol.insert(P.rcol.end(), rc.begin(), rc.end());
         P.rbits.insert(P.rbits.end(), rb.begin(), rb.end());
       } else {
         isfac[i] = 0;
-        rcount[i] = q1 - rp[i];
-        for (int32_t t = rp[i]; t < q1; ++t) {
+        rcount[i] = q1 - q0;
+        for (int32_t t = q0; t < q1; ++t) {
           uint32_t bits = 0;
           memcpy(&bits, jraw.data() + (size_t)t * esz, esz);
           P.rcol.push_back(col[t]);
@@ -1353,6 +1375,7 @@ sb_status set_factor(sb_ctx* c, int32_t n_ids, int32_t K, const int32_t* member,
       set_error("sb_set_factor: a group id has members in more than one event");
       return SB_ERR_ARG;
     }
+  std::vector<unsigned char>().swap(jraw);
   std::vector<int32_t> rrowptr((size_t)n + 1, 0);
   for (int32_t i = 0; i < n; ++i) {
     if ((int64_t)rrowptr[i] + rcount[i] > INT32_MAX) {
@@ -1390,25 +1413,42 @@ sb_status set_factor(sb_ctx* c, int32_t n_ids, int32_t K, const int32_t* member,
   // blocks with a U row in use: their members (all slots) and U outputs, the
   // blocks with most members first (a lane group's time follows its block's
   // size; the large blocks then start in the first wave, not at the end)
-  std::vector<int32_t> gseg(1, 0), gmem, gout;
-  int32_t maxcount = 0;
   std::vector<int32_t> act;
   for (int32_t g = 0; g < n_ids; ++g) {
     bool used = false;
     for (int s = 0; s < K; ++s) used = used || urow[(size_t)g * K + s] >= 0;
     if (used) act.push_back(g);
   }
-  std::stable_sort(act.begin(), act.end(), [&](int32_t x, int32_t y) {
-    return seg[(size_t)x * K + K] - seg[(size_t)x * K] > seg[(size_t)y * K + K] - seg[(size_t)y * K];
-  });
+  {
+    // stable counting sort by member count, descending
+    std::vector<int64_t> sz(act.size());
+    int64_t smax = 0;
+    for (size_t t = 0; t < act.size(); ++t) {
+      sz[t] = seg[(size_t)act[t] * K + K] - seg[(size_t)act[t] * K];
+      smax = std::max(smax, sz[t]);
+    }
+    std::vector<int64_t> start((size_t)smax + 2, 0);
+    for (int64_t v : sz) ++start[(size_t)(smax - v) + 1];
+    for (size_t t = 0; t + 1 < start.size(); ++t) start[t + 1] += start[t];
+    std::vector<int32_t> sorted(act.size());
+    for (size_t t = 0; t < act.size(); ++t) sorted[(size_t)start[(size_t)(smax - sz[t])]++] = act[t];
+    act.swap(sorted);
+  }
+  int64_t total_mem = 0;
+  for (int32_t g : act) total_mem += seg[(size_t)g * K + K] - seg[(size_t)g * K];
+  if (total_mem > INT32_MAX) {
+    set_error("sb_set_factor: too many member entries");
+    return SB_ERR_ARG;
+  }
+  std::vector<int32_t> gseg(1, 0), gmem, gout;
+  gseg.reserve(act.size() * K + 1);
+  gout.reserve(act.size() * K);
+  gmem.reserve((size_t)total_mem);
+  int32_t maxcount = 0;
   for (int32_t g : act) {
     for (int s = 0; s < K; ++s) {
       const int64_t a0 = seg[(size_t)g * K + s], a1 = seg[(size_t)g * K + s + 1];
       gmem.insert(gmem.end(), mem.begin() + a0, mem.begin() + a1);
-      if ((int64_t)gmem.size() > INT32_MAX) {
-        set_error("sb_set_factor: too many member entries");
-        return SB_ERR_ARG;
-      }
       gseg.push_back((int32_t)gmem.size());
       gout.push_back(urow[(size_t)g * K + s]);
       if (urow[(size_t)g * K + s] >= 0) {
@@ -1428,6 +1468,7 @@ sb_status set_factor(sb_ctx* c, int32_t n_ids, int32_t K, const int32_t* member,
   // split saves).
   constexpr int64_t kChunk = 16;
   std::vector<int4> items, items1;
+  items1.reserve((size_t)ng);
   for (int32_t ga = 0; ga < ng; ++ga)
     items1.push_back(make_int4(ga, gseg[(size_t)ga * K], gseg[(size_t)ga * K + K], -1));
   std::vector<int32_t> gnc(ng), gscr0(ng, -1);
@@ -1450,48 +1491,23 @@ sb_status set_factor(sb_ctx* c, int32_t n_ids, int32_t K, const int32_t* member,
     set_error("sb_set_factor: rows plus U rows must stay below 2^27");
     return SB_ERR_ARG;
   }
-  // extended CSR for the row-group kernel: each row's residual, then its U
-  // rows as columns n + u (ascending) with the value jf
-  std::vector<int32_t> xrp((size_t)n + 1, 0);
-  for (int32_t i = 0; i < n; ++i) {
-    int32_t k = rcount[i];
-    if (isfac[i])
-      for (int s = 0; s < K; ++s) k += uidx[(size_t)i * K + s] >= 0 ? 1 : 0;
-    if ((int64_t)xrp[i] + k > INT32_MAX) {
-      set_error("sb_set_factor: extended CSR too large");
-      return SB_ERR_ARG;
-    }
-    xrp[i + 1] = xrp[i] + k;
-  }
-  std::vector<int32_t> xcol((size_t)xrp[n]);
-  std::vector<unsigned char> xj((size_t)xrp[n] * esz);
+  // the residual of all parts, in row order (each part copies its own range)
+  std::vector<int32_t> rcol_all((size_t)rnnz);
+  std::vector<unsigned char> rj_all((size_t)rnnz * esz);
   {
-    int64_t src = 0;  // running position in the concatenated residual
-    int64_t dst = 0;
-    std::vector<int32_t> rc_all;
-    std::vector<uint32_t> rb_all;
-    rc_all.reserve((size_t)rnnz);
-    rb_all.reserve((size_t)rnnz);
-    for (const Part& P : pt) {
-      rc_all.insert(rc_all.end(), P.rcol.begin(), P.rcol.end());
-      rb_all.insert(rb_all.end(), P.rbits.begin(), P.rbits.end());
-    }
-    for (int32_t i = 0; i < n; ++i) {
-      for (int32_t t = 0; t < rcount[i]; ++t, ++src, ++dst) {
-        xcol[(size_t)dst] = rc_all[(size_t)src];
-        memcpy(xj.data() + (size_t)dst * esz, &rb_all[(size_t)src], esz);
+    std::vector<int64_t> pofs(parts + 1, 0);
+    for (int p = 0; p < parts; ++p) pofs[p + 1] = pofs[p] + (int64_t)pt[p].rcol.size();
+    parallel_parts(parts, parts, [&](int, int64_t b, int64_t e) {
+      for (int64_t p = b; p < e; ++p) {
+        Part& P = pt[(size_t)p];
+        if (!P.rcol.empty())
+          memcpy(rcol_all.data() + pofs[p], P.rcol.data(), P.rcol.size() * 4);
+        unsigned char* d = rj_all.data() + (size_t)pofs[p] * esz;
+        for (size_t t = 0; t < P.rbits.size(); ++t) memcpy(d + t * esz, &P.rbits[t], esz);  // low esz bytes (little-endian)
+        std::vector<int32_t>().swap(P.rcol);
+        std::vector<uint32_t>().swap(P.rbits);
       }
-      if (!isfac[i]) continue;
-      int32_t uu[4];
-      int m = 0;
-      for (int s = 0; s < K; ++s)
-        if (uidx[(size_t)i * K + s] >= 0) uu[m++] = uidx[(size_t)i * K + s];
-      std::sort(uu, uu + m);
-      for (int t = 0; t < m; ++t, ++dst) {
-        xcol[(size_t)dst] = n + uu[t];
-        memcpy(xj.data() + (size_t)dst * esz, &jf_bits, esz);
-      }
-    }
+    }, 1);
   }
   // upload (replacing an earlier factor)
   SB_CUDA(cudaDeviceSynchronize());
@@ -1504,52 +1520,27 @@ sb_status set_factor(sb_ctx* c, int32_t n_ids, int32_t K, const int32_t* member,
     free_factor(c);
     return st;
   }
-  {
-    cudaError_t e = cudaMalloc(&c->d_f_rJ, std::max<int64_t>(rnnz, 1) * esz);
+  auto raw_alloc = [&](void** p, size_t bytes) -> sb_status {
+    cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      c->d_f_rJ = nullptr;
+      *p = nullptr;
       free_factor(c);
       set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
       return SB_ERR_OOM;
     }
-  }
-  std::vector<int32_t> rcol_all;
-  std::vector<unsigned char> rj_all;
-  rcol_all.reserve((size_t)rnnz);
-  rj_all.reserve((size_t)rnnz * esz);
-  for (const Part& P : pt) {
-    rcol_all.insert(rcol_all.end(), P.rcol.begin(), P.rcol.end());
-    for (uint32_t b : P.rbits) {
-      unsigned char t[4];
-      memcpy(t, &b, 4);
-      rj_all.insert(rj_all.end(), t, t + esz);  // little-endian: the low esz bytes
-    }
-  }
-  {
-    cudaError_t e = cudaMalloc(&c->d_f_item, std::max<size_t>(items.size(), 1) * sizeof(int4));
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      c->d_f_item = nullptr;
-      free_factor(c);
-      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
-      return SB_ERR_OOM;
-    }
-  }
+    return SB_OK;
+  };
+  if ((st = raw_alloc(&c->d_f_rJ, std::max<int64_t>(rnnz, 1) * esz)) ||
+      (st = raw_alloc(reinterpret_cast<void**>(&c->d_f_item), std::max<size_t>(items.size(), 1) * sizeof(int4))) ||
+      (st = raw_alloc(reinterpret_cast<void**>(&c->d_f_item1), std::max<size_t>(items1.size(), 1) * sizeof(int4))) ||
+      (st = raw_alloc(reinterpret_cast<void**>(&c->d_f_head),
+                      std::max<size_t>((size_t)n * sbd::fac_head_words((int)esz) * 4, 16))))
+    return st;
   if ((st = dalloc(&c->d_f_gnc, std::max<size_t>(gnc.size(), 1))) ||
       (st = dalloc(&c->d_f_gscr0, std::max<size_t>(gscr0.size(), 1)))) {
     free_factor(c);
     return st;
-  }
-  {
-    cudaError_t e = cudaMalloc(&c->d_f_item1, std::max<size_t>(items1.size(), 1) * sizeof(int4));
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      c->d_f_item1 = nullptr;
-      free_factor(c);
-      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
-      return SB_ERR_OOM;
-    }
   }
   if (!items.empty())
     SB_CUDA(cudaMemcpy(c->d_f_item, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
@@ -1573,21 +1564,23 @@ sb_status set_factor(sb_ctx* c, int32_t n_ids, int32_t K, const int32_t* member,
     SB_CUDA(cudaMemcpy(c->d_f_rJ, rj_all.data(), (size_t)rnnz * esz, cudaMemcpyHostToDevice));
   }
   {
-    cudaError_t e = cudaMalloc(&c->d_f_xJ, std::max<size_t>(xj.size(), 16));
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      c->d_f_xJ = nullptr;
-      free_factor(c);
-      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
-      return SB_ERR_OOM;
-    }
-    if (!xj.empty()) SB_CUDA(cudaMemcpy(c->d_f_xJ, xj.data(), xj.size(), cudaMemcpyHostToDevice));
+    // row heads, formed on the device from the uploaded residual and U rows
+    sbd::FacHeadArgs ha{};
+    ha.uidx = c->d_f_uidx;
+    ha.rrowptr = c->d_f_rrowptr;
+    ha.rcol = c->d_f_rcol;
+    ha.rJ = c->d_f_rJ;
+    ha.head = c->d_f_head;
+    ha.n = n;
+    ha.K = K;
+    ha.jbytes = (int)esz;
+    SB_CUDA(sbd::launch_fac_head(ha, 0));
+    SB_CUDA(cudaDeviceSynchronize());
   }
-  c->h_fx_rowptr.swap(xrp);
-  c->h_fx_col.swap(xcol);
   c->fac_K = K;
   c->fac_couple = cm;
   c->fac_jf = (float)jf;
+  c->fac_jf_bits = jf_bits;
   c->fac_ng = ng;
   c->fac_urows = (int32_t)nu;
   c->fac_rows = nfac;
@@ -1599,9 +1592,69 @@ sb_status set_factor(sb_ctx* c, int32_t n_ids, int32_t K, const int32_t* member,
   return SB_OK;
 }
 
-// Row-group tables of the extended CSR (factored aSB / bSB), built on first use.
+// The extended CSR of the row-group kernel (aSB / bSB with a factor): each
+// row's residual, then its U rows as columns n + u (ascending) with the value
+// jf. Formed on first use from the uploaded residual and U rows.
+sb_status ensure_fx(sb_ctx* c) {
+  if (c->d_f_xJ) return SB_OK;
+  const int32_t n = c->n, K = c->fac_K;
+  const size_t esz = c->jbf16 ? 2 : 4;
+  const int64_t rnnz = c->fac_rnnz;
+  std::vector<int32_t> rrowptr((size_t)n + 1), rcol((size_t)rnnz), uidx((size_t)n * K);
+  std::vector<unsigned char> rj((size_t)rnnz * esz);
+  SB_CUDA(cudaDeviceSynchronize());
+  SB_CUDA(cudaMemcpy(rrowptr.data(), c->d_f_rrowptr, rrowptr.size() * 4, cudaMemcpyDeviceToHost));
+  SB_CUDA(cudaMemcpy(uidx.data(), c->d_f_uidx, uidx.size() * 4, cudaMemcpyDeviceToHost));
+  if (rnnz) {
+    SB_CUDA(cudaMemcpy(rcol.data(), c->d_f_rcol, rcol.size() * 4, cudaMemcpyDeviceToHost));
+    SB_CUDA(cudaMemcpy(rj.data(), c->d_f_rJ, rj.size(), cudaMemcpyDeviceToHost));
+  }
+  std::vector<int32_t> xrp((size_t)n + 1, 0);
+  for (int32_t i = 0; i < n; ++i) {
+    int64_t k = rrowptr[i + 1] - rrowptr[i];
+    for (int s = 0; s < K; ++s) k += uidx[(size_t)i * K + s] >= 0 ? 1 : 0;
+    if ((int64_t)xrp[i] + k > INT32_MAX) {
+      set_error("sb_set_factor: extended CSR too large");
+      return SB_ERR_ARG;
+    }
+    xrp[i + 1] = xrp[i] + (int32_t)k;
+  }
+  std::vector<int32_t> xcol((size_t)xrp[n]);
+  std::vector<unsigned char> xj((size_t)xrp[n] * esz);
+  for (int32_t i = 0; i < n; ++i) {
+    int64_t dst = xrp[i];
+    const int32_t r0 = rrowptr[i], r1 = rrowptr[i + 1];
+    if (r1 > r0) {
+      memcpy(xcol.data() + dst, rcol.data() + r0, (size_t)(r1 - r0) * 4);
+      memcpy(xj.data() + (size_t)dst * esz, rj.data() + (size_t)r0 * esz, (size_t)(r1 - r0) * esz);
+      dst += r1 - r0;
+    }
+    int32_t uu[4];
+    int m = 0;
+    for (int s = 0; s < K; ++s)
+      if (uidx[(size_t)i * K + s] >= 0) uu[m++] = uidx[(size_t)i * K + s];
+    std::sort(uu, uu + m);
+    for (int t = 0; t < m; ++t, ++dst) {
+      xcol[(size_t)dst] = n + uu[t];
+      memcpy(xj.data() + (size_t)dst * esz, &c->fac_jf_bits, esz);
+    }
+  }
+  cudaError_t e = cudaMalloc(&c->d_f_xJ, std::max<size_t>(xj.size(), 16));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->d_f_xJ = nullptr;
+    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return SB_ERR_OOM;
+  }
+  if (!xj.empty()) SB_CUDA(cudaMemcpy(c->d_f_xJ, xj.data(), xj.size(), cudaMemcpyHostToDevice));
+  c->h_fx_rowptr.swap(xrp);
+  c->h_fx_col.swap(xcol);
+  return SB_OK;
+}
+
 sb_status ensure_frw(sb_ctx* c, int RW) {
   if (c->frw_built == RW) return SB_OK;
+  if (sb_status st0 = ensure_fx(c)) return st0;
   dfree(c->d_frw_gptr);
   dfree(c->d_frw_rows);
   dfree(c->d_frw_ent);
@@ -1776,7 +1829,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     fs.G = fG;
     fs.NCH = fNCH;
     fs.tiles = ftiles;
-    fa.uidx = c->d_f_uidx;
+    fa.head = c->d_f_head;
     fa.K = c->fac_K;
     fa.jf = c->fac_jf;
     fa.U = c->d_f_U;
@@ -2186,28 +2239,45 @@ sb_status sb_create_batch(int32_t n_events, const int32_t* n_per_event,
       set_error("sb_create: null CSR arrays");
       return SB_ERR_ARG;
     }
-    // validate each event and build the global CSR (global column indices)
+    // validate each event and build the global CSR (global column indices);
+    // several events: one event per task, tasks on the host threads
     std::vector<int32_t> grp((size_t)ntot + 1), gcol((size_t)ztot);
     std::vector<int32_t> ev_row0(n_events + 1);
-    int64_t rp_off = 0, z_off = 0, r_off = 0;
+    std::vector<int64_t> rp_off(n_events + 1, 0), z_off(n_events + 1, 0);
     for (int32_t e = 0; e < n_events; ++e) {
-      const int32_t ne = n_per_event[e];
-      const int64_t ze = nnz_per_event[e];
-      const int32_t* rp = rowptr + rp_off;
-      sb_status st = validate_csr(ne, ze, rp, col + z_off, qval + z_off, qlin + r_off);
-      if (st) {
-        if (n_events > 1) set_error("event " + std::to_string(e) + ": " + sbh::g_err);
-        return st;
-      }
-      ev_row0[e] = (int32_t)r_off;
-      for (int32_t i = 0; i < ne; ++i) grp[r_off + i] = (int32_t)(z_off + rp[i]);
-      for (int64_t p = 0; p < ze; ++p) gcol[z_off + p] = (int32_t)(col[z_off + p] + r_off);
-      rp_off += ne + 1;
-      z_off += ze;
-      r_off += ne;
+      ev_row0[e + 1] = ev_row0[e] + n_per_event[e];
+      rp_off[e + 1] = rp_off[e] + n_per_event[e] + 1;
+      z_off[e + 1] = z_off[e] + nnz_per_event[e];
     }
+    std::vector<sb_status> est(n_events, SB_OK);
+    std::vector<std::string> emsg(n_events);
+    auto one_event = [&](int32_t e, bool threads) {
+      const int32_t ne = n_per_event[e];
+      const int64_t ze = nnz_per_event[e], zo = z_off[e];
+      const int32_t r0 = ev_row0[e];
+      const int32_t* rp = rowptr + rp_off[e];
+      est[e] = validate_csr(ne, ze, rp, col + zo, qval + zo, qlin + r0, threads);
+      if (est[e]) {
+        emsg[e] = sbh::g_err;
+        return;
+      }
+      for (int32_t i = 0; i < ne; ++i) grp[(size_t)r0 + i] = (int32_t)(zo + rp[i]);
+      for (int64_t p = 0; p < ze; ++p) gcol[(size_t)(zo + p)] = (int32_t)(col[zo + p] + r0);
+    };
+    if (n_events == 1) {
+      one_event(0, true);
+    } else if (!parallel_parts(n_events, std::min(n_events, 256), [&](int, int64_t b, int64_t e) {
+                 for (int64_t t = b; t < e; ++t) one_event((int32_t)t, false);
+               }, 2)) {
+      set_error("sb_create: host allocation failed");
+      return SB_ERR_OOM;
+    }
+    for (int32_t e = 0; e < n_events; ++e)
+      if (est[e]) {
+        set_error(n_events > 1 ? "event " + std::to_string(e) + ": " + emsg[e] : emsg[e]);
+        return est[e];
+      }
     grp[ntot] = (int32_t)ztot;
-    ev_row0[n_events] = (int32_t)ntot;
     sb_ctx* c = new (std::nothrow) sb_ctx;
     if (!c) {
       set_error("sb_create: host allocation failed");

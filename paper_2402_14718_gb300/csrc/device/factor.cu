@@ -272,6 +272,101 @@ __device__ __forceinline__ float jv(const float* J, int p) { return __ldg(J + p)
 __device__ __forceinline__ float jv(const __nv_bfloat16* J, int p) {
   return __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(J) + p) << 16);
 }
+// value t of a row head's J part (words from kFacHead + kFacHeadU on)
+template <typename JT>
+__device__ __forceinline__ float head_j(const uint32_t* hd, int t) {
+  const uint32_t* p = hd + kFacHead + kFacHeadU;
+  if (sizeof(JT) == 4) return __uint_as_float(__ldg(p + t));
+  return __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p) + t) << 16);
+}
+
+__global__ void k_fac_head(const FacHeadArgs a) {
+  const int HW = fac_head_words(a.jbytes);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)a.n * HW) return;
+  const int64_t row = t / HW;
+  const int w = (int)(t - row * HW);
+  const int p0 = a.rrowptr[row], L = a.rrowptr[row + 1] - p0;
+  uint32_t v = 0;
+  if (w < kFacHead) {
+    v = w < L ? (uint32_t)a.rcol[p0 + w] : 0u;
+  } else if (w < kFacHead + kFacHeadU) {
+    const int s = w - kFacHead;
+    v = s < a.K ? (uint32_t)a.uidx[row * a.K + s] : 0xffffffffu;
+  } else if (a.jbytes == 4) {
+    const int e = w - kFacHead - kFacHeadU;
+    v = e < L ? static_cast<const uint32_t*>(a.rJ)[p0 + e] : 0u;
+  } else {
+    const int e = 2 * (w - kFacHead - kFacHeadU);
+    const uint16_t* J = static_cast<const uint16_t*>(a.rJ);
+    v = (e < L ? J[p0 + e] : 0u) | (e + 1 < L ? (uint32_t)J[p0 + e + 1] << 16 : 0u);
+  }
+  a.head[t] = v;
+}
+
+// Adds cnt residual entries (lane q of the lane group holds column mc and
+// weight mw of entry q) to this lane's replicas, four neighbour rows in flight.
+template <int MODE, int NCH, int P>
+__device__ __forceinline__ void walk_entries(float (&acc)[P], int cnt, int mc, float mw,
+                                             unsigned mask, int G, const float* xin,
+                                             const uint8_t* sgn_in, size_t off, int R) {
+  int q = 0;
+  for (; q + 4 <= cnt; q += 4) {
+    int c[4];
+    float w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      c[u] = __shfl_sync(mask, mc, q + u, G);
+      w[u] = __shfl_sync(mask, mw, q + u, G);
+    }
+    if (MODE == 0) {
+      float4 t[4][NCH];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < NCH; ++j)
+          t[u][j] = __ldg(reinterpret_cast<const float4*>(xin + (size_t)c[u] * R + off) + G * j);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+          acc[4 * j] = fmaf(w[u], t[u][j].x, acc[4 * j]);
+          acc[4 * j + 1] = fmaf(w[u], t[u][j].y, acc[4 * j + 1]);
+          acc[4 * j + 2] = fmaf(w[u], t[u][j].z, acc[4 * j + 2]);
+          acc[4 * j + 3] = fmaf(w[u], t[u][j].w, acc[4 * j + 3]);
+        }
+    } else {
+      Words<kSgnPer / 4> t[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) t[u].ldg(sgn_in + (size_t)c[u] * R + off);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < kSgnPer && v < P; ++v)
+          acc[v] = fmaf(w[u], scaled_sign_of_byte(t[u].w[v >> 2], v & 3), acc[v]);
+    }
+  }
+  for (; q < cnt; ++q) {
+    const int c = __shfl_sync(mask, mc, q, G);
+    const float w = __shfl_sync(mask, mw, q, G);
+    if (MODE == 0) {
+#pragma unroll
+      for (int j = 0; j < NCH; ++j) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(xin + (size_t)c * R + off) + G * j);
+        acc[4 * j] = fmaf(w, t.x, acc[4 * j]);
+        acc[4 * j + 1] = fmaf(w, t.y, acc[4 * j + 1]);
+        acc[4 * j + 2] = fmaf(w, t.z, acc[4 * j + 2]);
+        acc[4 * j + 3] = fmaf(w, t.w, acc[4 * j + 3]);
+      }
+    } else {
+      Words<kSgnPer / 4> t;
+      t.ldg(sgn_in + (size_t)c * R + off);
+#pragma unroll
+      for (int v = 0; v < kSgnPer && v < P; ++v)
+        acc[v] = fmaf(w, scaled_sign_of_byte(t.w[v >> 2], v & 3), acc[v]);
+    }
+  }
+}
 
 // One U row of this lane: FP32 (NCH float4) or BF16 sums of 2^-7 sgn (two uint4)
 template <int MODE, int NCH>
@@ -337,84 +432,44 @@ __global__ void __launch_bounds__(kFacBlock, (FacMinBlocks<MODE, NCH>::step)) k_
     prefetch_l2(a.xin + o);
     prefetch_l2(a.y + o);
   }
+  constexpr int HW = fac_head_words(sizeof(JT));
+  const uint32_t* hd = a.head + (size_t)row * HW;
   int us[K];
 #pragma unroll
   for (int s = 0; s < K; ++s) {
-    us[s] = __ldg(a.uidx + (size_t)row * K + s);
+    us[s] = (int)__ldg(hd + kFacHead + s);
     if (us[s] >= 0)
       prefetch_l2(static_cast<const char*>(a.U) + ((size_t)us[s] * R + off) * (MODE == 0 ? 4 : 2));
   }
   const int p0 = __ldg(a.rrowptr + row), p1 = __ldg(a.rrowptr + row + 1);
 
-  // residual row, in column order
+  // residual row, in column order: its first kFacHead entries from the head,
+  // the rest from the residual CSR
   float acc[P];
 #pragma unroll
   for (int v = 0; v < P; ++v) acc[v] = 0.f;
-  for (int pb = p0; pb < p1; pb += G) {
+  const int nh = min(p1 - p0, kFacHead);
+  for (int hb = 0; hb < nh; hb += G) {
+    const int cnt = min(G, nh - hb);
+    int mc = 0;
+    float mw = 0.f;
+    if (l < cnt) {
+      mc = (int)__ldg(hd + hb + l);
+      mw = head_j<JT>(hd, hb + l);
+      if (MODE == 1) mw *= kSignScale;  // 2^7 J: sign bytes read as 2^-7 sgn
+    }
+    walk_entries<MODE, NCH, P>(acc, cnt, mc, mw, mask, G, a.xin, a.sgn_in, off, R);
+  }
+  for (int pb = p0 + kFacHead; pb < p1; pb += G) {
     const int cnt = min(G, p1 - pb);
     int mc = 0;
     float mw = 0.f;
     if (l < cnt) {
       mc = __ldg(a.rcol + pb + l);
       mw = jv(J, pb + l);
-      if (MODE == 1) mw *= kSignScale;  // 2^7 J: sign bytes read as 2^-7 sgn
+      if (MODE == 1) mw *= kSignScale;
     }
-    int q = 0;
-    for (; q + 4 <= cnt; q += 4) {
-      int c[4];
-      float w[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        c[u] = __shfl_sync(mask, mc, q + u, G);
-        w[u] = __shfl_sync(mask, mw, q + u, G);
-      }
-      if (MODE == 0) {
-        float4 t[4][NCH];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int j = 0; j < NCH; ++j)
-            t[u][j] = __ldg(reinterpret_cast<const float4*>(a.xin + (size_t)c[u] * R + off) + G * j);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int j = 0; j < NCH; ++j) {
-            acc[4 * j] = fmaf(w[u], t[u][j].x, acc[4 * j]);
-            acc[4 * j + 1] = fmaf(w[u], t[u][j].y, acc[4 * j + 1]);
-            acc[4 * j + 2] = fmaf(w[u], t[u][j].z, acc[4 * j + 2]);
-            acc[4 * j + 3] = fmaf(w[u], t[u][j].w, acc[4 * j + 3]);
-          }
-      } else {
-        Words<kSgnPer / 4> t[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) t[u].ldg(a.sgn_in + (size_t)c[u] * R + off);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < kSgnPer && v < P; ++v)
-            acc[v] = fmaf(w[u], scaled_sign_of_byte(t[u].w[v >> 2], v & 3), acc[v]);
-      }
-    }
-    for (; q < cnt; ++q) {
-      const int c = __shfl_sync(mask, mc, q, G);
-      const float w = __shfl_sync(mask, mw, q, G);
-      if (MODE == 0) {
-#pragma unroll
-        for (int j = 0; j < NCH; ++j) {
-          const float4 t = __ldg(reinterpret_cast<const float4*>(a.xin + (size_t)c * R + off) + G * j);
-          acc[4 * j] = fmaf(w, t.x, acc[4 * j]);
-          acc[4 * j + 1] = fmaf(w, t.y, acc[4 * j + 1]);
-          acc[4 * j + 2] = fmaf(w, t.z, acc[4 * j + 2]);
-          acc[4 * j + 3] = fmaf(w, t.w, acc[4 * j + 3]);
-        }
-      } else {
-        Words<kSgnPer / 4> t;
-        t.ldg(a.sgn_in + (size_t)c * R + off);
-#pragma unroll
-        for (int v = 0; v < kSgnPer && v < P; ++v)
-          acc[v] = fmaf(w, scaled_sign_of_byte(t.w[v >> 2], v & 3), acc[v]);
-      }
-    }
+    walk_entries<MODE, NCH, P>(acc, cnt, mc, mw, mask, G, a.xin, a.sgn_in, off, R);
   }
   // the factored part: sum of this row's U rows (none for a plain row)
   bool any = false;
@@ -565,6 +620,13 @@ bool fac_tiling(int variant, int R, int* G, int* NCH, int* tiles) {
     return true;
   }
   return false;
+}
+
+cudaError_t launch_fac_head(const FacHeadArgs& a, cudaStream_t s) {
+  const int64_t total = (int64_t)a.n * fac_head_words(a.jbytes);
+  if (total <= 0) return cudaSuccess;
+  k_fac_head<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fac_sum(int variant, const FacSumArgs& a, cudaStream_t s) {

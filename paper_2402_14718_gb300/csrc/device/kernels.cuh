@@ -241,8 +241,27 @@ struct FacSumArgs {
   int32_t R, G, NCH, tiles;
 };
 
+// Row head of the factored step (fac_head_words() 32-bit words per row): the
+// first kFacHead residual columns (0 past the row's end), the U rows
+// (kFacHeadU words, -1 where none) and the first kFacHead residual values in
+// the context precision. One line per row holds everything a row's first
+// loads need, so they do not wait on the residual row pointer.
+constexpr int kFacHead = 8, kFacHeadU = 4;
+__host__ __device__ constexpr int fac_head_words(int jbytes) {
+  return kFacHead + kFacHeadU + kFacHead * jbytes / 4;
+}
+struct FacHeadArgs {
+  const int32_t* uidx;     // [n * K] U rows of each row (-1: none)
+  const int32_t* rrowptr;  // residual CSR
+  const int32_t* rcol;
+  const void* rJ;
+  uint32_t* head;          // [n * fac_head_words(jbytes)]
+  int32_t n, K, jbytes;
+};
+cudaError_t launch_fac_head(const FacHeadArgs& a, cudaStream_t s);
+
 struct FacStepArgs {
-  const int32_t* uidx;   // [n * K] U rows of each row (-1: none; a plain row has none)
+  const uint32_t* head;  // [n * fac_head_words(J bytes)] row heads
   int32_t K;
   float jf;              // factor weight in J units (-w / 4), exact in FP32
   const void* U;
