@@ -114,6 +114,33 @@ def test_factor_dsb_equals_plain_kernel_bit_for_bit(R):
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
+@pytest.mark.parametrize("R", [64, 512])
+def test_factor_dsb_whole_run_equals_plain_kernel_bit_for_bit(R):
+    """Over a whole 1000-step dSB schedule (the bifurcation, then spins pinned on
+    the walls, where the factored step writes back only what changed and x is
+    updated in place), in one piece and enqueued as two halves, the factored
+    states equal the plain sign-byte kernel's bit for bit; R = 512 runs two
+    replica tiles."""
+    _, qc, _, _ = workload_qubos("event1000")
+    S = 1000
+    a = np.linspace(0.0, 1.0, S)
+    out = []
+    for factor, halves in ((False, False), (True, False), (True, True)):
+        ctx = _fctx(qc, sb.SB_J_BF16, factor)
+        sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 1)
+        sb.sb_run(ctx, "dsb", 1.0, 0.0, 0.5, 0, R, seed=31)
+        if halves:
+            sb.sb_advance(ctx, "dsb", 1.0, 0.0, 0.5, S // 2, _sched(a[:S // 2]))
+            sb.sb_advance(ctx, "dsb", 1.0, 0.0, 0.5, S - S // 2, _sched(a[S // 2:]))
+        else:
+            sb.sb_advance(ctx, "dsb", 1.0, 0.0, 0.5, S, _sched(a))
+        out.append(sb.sb_get_state(ctx))
+    x, _ = out[0]
+    assert np.mean(np.abs(x) == 1.0) > 0.5   # the run reaches the pinned phase
+    for o in out[1:]:
+        assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])
+
+
 def test_factor_rows_left_plain_equal_plain_kernel():
     """Couplings that BF16 cannot hold exactly leave every residual inexact: all
     rows stay in plain form, and the factored kernel then runs the CSR-order FMA
