@@ -255,7 +255,8 @@ sb_status sb_step_info(const sb_ctx* ctx, int32_t* rows_per_warp, int64_t* union
  * 1/4 every partial sum is exact and the states equal the plain kernels' bit
  * for bit). Used by aSB / bSB when R / 4 is a power of two <= 32 or a
  * multiple of 32, and by dSB with sign bytes when R / 8 is a power of two
- * <= 32 or a multiple of 32 and no U element can exceed 256 members; other
+ * <= 32 or a multiple of 32 (U rows in BF16 while no U element sums more
+ * than 256 members, else in FP32; both exact); other
  * runs use the plain kernels. SB_OPT_FACTOR switches it off.
  * Inputs (host, copied): n_ids (ids lie in [0, n_ids)); k slots, 1 <= k <= 4;
  * member[n k] (block id of row i's slot s at k i + s, -1 for none); couple[k

@@ -1759,8 +1759,11 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   int fG = 0, fNCH = 0, ftiles = 0;
   const int fac = (c->fac_set && c->fac_use != 0 && c->groups == 1 &&
                    sbd::fac_tiling(variant, c->R, &fG, &fNCH, &ftiles) &&
-                   (variant != SB_DSB || (c->dsb_signs && c->j_small && c->fac_maxcount <= 256)))
+                   (variant != SB_DSB || (c->dsb_signs && c->j_small)))
                       ? 1 : 0;
+  // dSB: BF16 U rows hold sums of at most 256 members exactly; larger blocks
+  // take FP32 U rows (the dSB kernels' NCH = 2 instances)
+  if (fac && variant == SB_DSB && c->fac_maxcount > 256) fNCH = 2;
   sbd::FacSumArgs fs{};
   sbd::FacStepArgs fa{};
   // aSB / bSB with R a multiple of 128: the row-group kernel over the extended
@@ -1775,7 +1778,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     }
   }
   if (fac && !frw) {
-    const size_t ub = (size_t)std::max(c->fac_urows, 1) * c->R * (variant == SB_DSB ? 2 : 4);
+    const size_t ub = (size_t)std::max(c->fac_urows, 1) * c->R * (variant == SB_DSB && fNCH == 1 ? 2 : 4);
     if (ub > c->f_U_bytes) {
       if (c->d_f_U) cudaFree(c->d_f_U);
       c->d_f_U = nullptr;

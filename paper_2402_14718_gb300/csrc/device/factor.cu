@@ -24,8 +24,9 @@
 // tile0 + 4 l + 4 G j + v (j < NCH, v < 4), i.e. 16-byte chunks strided by the
 // group; for dSB sign bytes the 8 replicas tile0 + 8 l + v (one 8-byte load
 // per neighbour). U rows use the same replica layout: FP32 for aSB / bSB; for
-// dSB BF16 sums of 2^-7 sgn (exact: the host checks that no U element can
-// exceed 256 members).
+// dSB BF16 sums of 2^-7 sgn (exact while no U element sums more than 256
+// members), else FP32 sums (the dSB kernels' NCH = 2 instances; NCH has no
+// other meaning there).
 //
 // Every sum is formed in a fixed order (members by slot and row, residual in
 // column order), so results are reproducible. For dSB with weights that are
@@ -140,6 +141,12 @@ __device__ __forceinline__ void store_u(const FacSumArgs& a, int g, size_t off, 
 #pragma unroll
       for (int j = 0; j < NCH; ++j)
         p[G * j] = make_float4(U[s][4 * j], U[s][4 * j + 1], U[s][4 * j + 2], U[s][4 * j + 3]);
+    } else if (NCH == 2) {
+      // dSB, blocks of more than 256 members: FP32 sums of 2^-7 sgn (exact)
+      float4* p = reinterpret_cast<float4*>(static_cast<float*>(a.U) + (size_t)u * a.R + off);
+#pragma unroll
+      for (int h = 0; h < P / 4; ++h)
+        p[h] = make_float4(U[s][4 * h], U[s][4 * h + 1], U[s][4 * h + 2], U[s][4 * h + 3]);
     } else {
       // sums of 2^-7 sgn of at most 256 members: exact in BF16 (the top half of the FP32 word)
       uint16_t* p = static_cast<uint16_t*>(a.U) + (size_t)u * a.R + off;
@@ -389,6 +396,24 @@ struct URow<0, NCH> {
     }
   }
 };
+template <>
+struct URow<1, 2> {  // dSB with FP32 U rows
+  float4 t[kSgnPer / 4];
+  __device__ __forceinline__ void load(const void* U, size_t base, int) {
+#pragma unroll
+    for (int h = 0; h < kSgnPer / 4; ++h)
+      t[h] = __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(U) + base) + h);
+  }
+  __device__ __forceinline__ void add_to(float (&fu)[kSgnPer]) const {
+#pragma unroll
+    for (int h = 0; h < kSgnPer / 4; ++h) {
+      fu[4 * h] += t[h].x;
+      fu[4 * h + 1] += t[h].y;
+      fu[4 * h + 2] += t[h].z;
+      fu[4 * h + 3] += t[h].w;
+    }
+  }
+};
 template <int NCH>
 struct URow<1, NCH> {
   Words<4> t[kSgnPer / 8];  // kSgnPer BF16 sums
@@ -439,7 +464,7 @@ __global__ void __launch_bounds__(kFacBlock, (FacMinBlocks<MODE, NCH>::step)) k_
   for (int s = 0; s < K; ++s) {
     us[s] = (int)__ldg(hd + kFacHead + s);
     if (us[s] >= 0)
-      prefetch_l2(static_cast<const char*>(a.U) + ((size_t)us[s] * R + off) * (MODE == 0 ? 4 : 2));
+      prefetch_l2(static_cast<const char*>(a.U) + ((size_t)us[s] * R + off) * (MODE == 0 || NCH == 2 ? 4 : 2));
   }
   const int p0 = __ldg(a.rrowptr + row), p1 = __ldg(a.rrowptr + row + 1);
 
@@ -572,7 +597,7 @@ cudaError_t launch_step_n(const FacStepArgs& a, cudaStream_t s) {
 
 template <typename JT>
 cudaError_t launch_step_j(int variant, const FacStepArgs& a, cudaStream_t s) {
-  if (variant == 2) return launch_step_n<2, 1, 1, JT>(a, s);
+  if (variant == 2) return a.NCH == 2 ? launch_step_n<2, 1, 2, JT>(a, s) : launch_step_n<2, 1, 1, JT>(a, s);
   if (a.NCH == 2)
     return variant == 0 ? launch_step_n<0, 0, 2, JT>(a, s) : launch_step_n<1, 0, 2, JT>(a, s);
   return variant == 0 ? launch_step_n<0, 0, 1, JT>(a, s) : launch_step_n<1, 0, 1, JT>(a, s);
@@ -630,7 +655,7 @@ cudaError_t launch_fac_head(const FacHeadArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_fac_sum(int variant, const FacSumArgs& a, cudaStream_t s) {
-  if (variant == 2) return launch_sum_n<1, 1>(a, s);
+  if (variant == 2) return a.NCH == 2 ? launch_sum_n<1, 2>(a, s) : launch_sum_n<1, 1>(a, s);
   return a.NCH == 2 ? launch_sum_n<0, 2>(a, s) : launch_sum_n<0, 1>(a, s);
 }
 

@@ -141,6 +141,25 @@ def test_factor_dsb_whole_run_equals_plain_kernel_bit_for_bit(R):
         assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])
 
 
+def test_factor_dsb_large_blocks_fp32_u_rows_bit_for_bit():
+    """Blocks of more than 256 members: BF16 cannot hold their U sums, so dSB
+    takes FP32 U rows (still exact); 60 steps equal the plain sign-byte
+    kernel's state bit for bit."""
+    couple = np.array([[1, 1], [1, 0]], np.uint8)
+    q, member = inputs.grouped_qubo(1200, 2, 4, couple, 1.0, 6, seed=12)
+    out = []
+    for factor in (True, False):
+        ctx = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_BF16)
+        sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 1)
+        if factor:
+            sb.sb_set_factor(ctx, 4, member, couple, 1.0)
+            info = sb.sb_factor_info(ctx)
+            assert info["max_count"] > 256 and info["rows"] > q.n // 2
+        sb.sb_run(ctx, "dsb", 1.0, 0.0, 0.5, 60, 64, seed=5)
+        out.append(sb.sb_get_state(ctx))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 def test_factor_rows_left_plain_equal_plain_kernel():
     """Couplings that BF16 cannot hold exactly leave every residual inexact: all
     rows stay in plain form, and the factored kernel then runs the CSR-order FMA
