@@ -190,10 +190,23 @@ def step_kernels(cfg, variant, R, info):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one SB step (all
 # its launches) from an ncu capture of the step's kernels, keyed by workload,
 # variant, kernels and those kernels' sources (sha256 prefix, kernel_source_hash);
-# any other combination reports null. Captures larger than a few GB on the
-# device are not taken: the batch's figure is a smaller event's capture
-# scaled by the spin-updates, and says so.
-MEASURED_TRAFFIC = {}
+# any other combination reports null. Each capture is one ncu pass of the
+# third step of the profiling driver (`--profile-steps 4`, the workload's own
+# size), early in the schedule where no spin is pinned yet, so the writes are
+# at their largest.
+_CAPTURE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
+            "-k regex:\"k_fac_sum|{step}\" -s 2 -c 2 python bench.py{args} --profile-steps 4")
+MEASURED_TRAFFIC = {
+    ("batch512", "dsb", ("k_fac_sum", "k_step_fac"), "4fda71d6f28a04a0"): {
+        "bytes_per_step": 679649792 + 7449627392,
+        "source": _CAPTURE.format(step="k_step_fac", args="")},
+    ("event10k", "dsb", ("k_fac_sum", "k_step_fac"), "4fda71d6f28a04a0"): {
+        "bytes_per_step": 101213184 + 1215277568,
+        "source": _CAPTURE.format(step="k_step_fac", args=" --workload event10k --variant dsb")},
+    ("event1000", "bsb", ("k_fac_sum", "k_step_rw"), "7bf9b71bcf8d0102"): {
+        "bytes_per_step": 41916928 + 134077696,
+        "source": _CAPTURE.format(step="k_step_rw", args=" --workload event1000")},
+}
 
 KERNEL_SOURCES = {"k_step_rw": ("rw.cu", "kernels.cuh", "signs.cuh"),
                   "k_step_stream": ("stream.cu", "kernels.cuh", "signs.cuh"),

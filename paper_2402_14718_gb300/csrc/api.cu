@@ -1410,9 +1410,10 @@ sb_status set_factor(sb_ctx* c, int32_t n_ids, int32_t K, const int32_t* member,
       if (g >= 0) uidx[(size_t)i * K + s] = urow[(size_t)g * K + s];
     }
   }
-  // blocks with a U row in use: their members (all slots) and U outputs, the
-  // blocks with most members first (a lane group's time follows its block's
-  // size; the large blocks then start in the first wave, not at the end)
+  // blocks with a U row in use: their members (all slots) and U outputs, by
+  // event and, within an event, the blocks with most members first (a lane
+  // group's time follows its block's size; the large blocks then start early,
+  // not at the end)
   std::vector<int32_t> act;
   for (int32_t g = 0; g < n_ids; ++g) {
     bool used = false;
@@ -1433,6 +1434,28 @@ sb_status set_factor(sb_ctx* c, int32_t n_ids, int32_t K, const int32_t* member,
     std::vector<int32_t> sorted(act.size());
     for (size_t t = 0; t < act.size(); ++t) sorted[(size_t)start[(size_t)(smax - sz[t])]++] = act[t];
     act.swap(sorted);
+    // then, stably, by event: the blocks summed at the same time read the
+    // sign bytes or x rows of a few events, which stay in L2 (sorted by size
+    // over the whole batch they spread over every event's rows)
+    if (c->E > 1) {
+      std::vector<int32_t> bev(act.size());
+      std::vector<int64_t> es((size_t)c->E + 1, 0);
+      for (size_t t = 0; t < act.size(); ++t) {
+        const int32_t g = act[t];
+        int32_t row = 0;
+        for (int s = 0; s < K; ++s)
+          if (seg[(size_t)g * K + s + 1] > seg[(size_t)g * K + s]) {
+            row = mem[(size_t)seg[(size_t)g * K + s]];
+            break;
+          }
+        bev[t] = (int32_t)(std::upper_bound(c->ev_row0.begin(), c->ev_row0.end(), row) -
+                           c->ev_row0.begin()) - 1;
+        ++es[(size_t)bev[t] + 1];
+      }
+      for (size_t e = 0; e + 1 < es.size(); ++e) es[e + 1] += es[e];
+      for (size_t t = 0; t < act.size(); ++t) sorted[(size_t)es[(size_t)bev[t]]++] = act[t];
+      act.swap(sorted);
+    }
   }
   int64_t total_mem = 0;
   for (int32_t g : act) total_mem += seg[(size_t)g * K + K] - seg[(size_t)g * K];
