@@ -102,6 +102,34 @@ def job_value(units_per_rank, world_size, ms):
     return units_per_rank * world_size / (ms * 1e-3)
 
 
+def best_across_ranks(E_best, T_best, ev_row0, dist=None, device=None):
+    """Job-wide best of every event when each rank ran its own replicas: the
+    lowest energy over the ranks (ties to the lowest rank) and that rank's
+    selection for the event's rows. One all-gather of the per-event energies
+    and one of the selections, after the run (no data-path collective).
+    Returns (energies [E], winning rank [E], selection [N] uint8)."""
+    import torch
+    E = np.asarray(E_best, np.float64)
+    T = np.asarray(T_best, np.uint8)
+    if dist is None or dist.get_world_size() <= 1:
+        return E.copy(), np.zeros(len(E), np.int32), T.copy()
+    ws = dist.get_world_size()
+    te = torch.from_numpy(E.copy()).to(device)
+    tt = torch.from_numpy(T.copy()).to(device)
+    Es = [torch.empty_like(te) for _ in range(ws)]
+    Ts = [torch.empty_like(tt) for _ in range(ws)]
+    dist.all_gather(Es, te)
+    dist.all_gather(Ts, tt)
+    Em = np.stack([x.cpu().numpy() for x in Es])
+    Tm = [x.cpu().numpy() for x in Ts]
+    win = np.argmin(Em, axis=0).astype(np.int32)   # first minimum: the lowest rank
+    out = np.empty_like(T)
+    for e in range(len(E)):
+        a, b = int(ev_row0[e]), int(ev_row0[e + 1])
+        out[a:b] = Tm[win[e]][a:b]
+    return Em[win, np.arange(len(E))], win, out
+
+
 # ---------------------------------------------------------------- workloads
 def workload(name, sb_steps=0, variant="", events=0):
     """Run shape and the event recipes (seed, tracks, noise, cuts) of a named
@@ -859,6 +887,13 @@ def run_ours(args):
             "roofline": roofline, "e2e": e2e,
             "gpu_launches": (3 + (1 if variant == "dsb" else 0) + S * len(knames) + 4) * args.steps,
             "clocks": clk, "wall_s_timed": t_wall}
+    if ws > 1:
+        # the job's best of every event over all ranks' replicas
+        T_r, E_r, _ = sb.sb_best(ctx)
+        row0 = np.cumsum([0] + [q.n for q in qs])
+        E_job, win, _ = best_across_ranks(E_r, T_r, row0, dist, dev)
+        line["best_over_ranks"] = {"sum_E": float(np.sum(E_job)),
+                                   "events_won_by_rank": np.bincount(win, minlength=ws).tolist()}
     small = E > 1 or N <= 100000   # the oracle's pure-Python builder must finish in seconds
     if rank == 0 and not args.no_energy_check and small:
         sb.sb_run(ctx, variant, a0, 0.0, dt, S, R, 31, None, stream)
