@@ -39,7 +39,8 @@ typedef enum {
   SB_ERR_CUDA = 3,     /* a CUDA runtime call failed; see sb_last_error() */
   SB_ERR_OOM = 4,      /* device or host allocation failed (no C++ exception crosses this API) */
   SB_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up */
-  SB_ERR_STATE = 6     /* call out of order (e.g. readout before any run) */
+  SB_ERR_STATE = 6,    /* call out of order (e.g. readout before any run) */
+  SB_ERR_BOUNDS = 7    /* bounds-checked build: a kernel met an index outside its array */
 } sb_status;
 
 typedef enum { SB_ASB = 0, SB_BSB = 1, SB_DSB = 2 } sb_variant;
@@ -517,6 +518,13 @@ sb_status sb_energy_noalloc(int32_t n, const int32_t* rowptr, const int32_t* col
  * whenever sb_set_factor has set one and the run is supported; 0 runs the
  * plain kernels. sb_autotune times both and sets this option. */
 #define SB_OPT_FACTOR 14
+/* SB_OPT_TEST_BAD_COL (15): test hook of the bounds-checked build only
+ * (sb_checked_build() == 1; SB_ERR_ARG in the release build). Value p in
+ * [0, nnz) overwrites the context's device copy of CSR column p with n + 7,
+ * an index outside the state, so that the next step or energy kernel that
+ * reads it records it (sb_check_bounds) and reads row 0 instead. The host
+ * copies and the context's other tables are not changed. */
+#define SB_OPT_TEST_BAD_COL 15
 sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
 
 /*
@@ -530,6 +538,35 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value);
  */
 sb_status sb_autotune(sb_ctx* ctx, sb_variant variant, int32_t replicas, int32_t trial_steps,
                       int32_t* out_cfg, float* out_us_per_step, void* stream);
+
+/*
+ * Bounds-checked build -- the device-side stand-in for a memory checker
+ * (no counterpart in the paper). The library built with SB_CHECKED=1
+ * (libsbtrack_checked.so) tests, in the step kernels (plain, sign-byte,
+ * one-replica, row-group, factored: CSR columns, row-pointer pairs, U rows,
+ * group members) and the energy kernel, every index it reads before using
+ * it. An index outside its array is recorded -- the first one per kernel
+ * module -- and replaced by 0, so the access stays inside the array and
+ * nothing traps; a row-pointer pair outside [0, nnz] reads as an empty row.
+ * Results are then wrong but the device stays usable. Not covered: the
+ * tiled and streamed step options, the adjoint kernels and the device QUBO
+ * builder. The release build compiles the tests away.
+ *
+ * sb_checked_build: 1 in the bounds-checked build, 0 in the release build.
+ *
+ * sb_check_bounds: synchronises the current device, then reads and clears
+ * the recorded index of every kernel module. Returns SB_OK with *first = 0
+ * when none was recorded (always so in the release build); otherwise
+ * SB_ERR_BOUNDS, *first = module << 48 | site << 32 | index (module 1: plain,
+ * sign-byte, one-replica and energy kernels; 2: factored kernels; 3:
+ * row-group kernel; site 1: CSR column, 2: row-pointer pair (its end), 3: U
+ * row, 4: group member, 5: row-group union column; index: the offending
+ * value, as 32 bits) for the first module that recorded one, and
+ * sb_last_error() names it. SB_ERR_ARG when first is NULL, SB_ERR_CUDA when a
+ * copy fails.
+ */
+int32_t sb_checked_build(void);
+sb_status sb_check_bounds(uint64_t* first);
 
 #ifdef __cplusplus
 }

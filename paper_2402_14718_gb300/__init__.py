@@ -15,13 +15,14 @@ from ._lib import (SB_ASB, SB_BSB, SB_DSB, SB_J_BF16, SB_J_FP32, SB_OPT_DSB_SIGN
                    SB_OPT_HEAVY_FIRST, SB_OPT_L2_PERSIST, SB_OPT_R1_LANES, SB_OPT_REPLICA_GROUPS,
                    SB_OPT_ROWS_PER_WARP, SB_OPT_STEP_RPC, SB_OPT_STEP_RT, SB_OPT_STEP_UNROLL,
                    SB_OPT_STREAM, SB_OPT_TEST_SKIP_STAGE, SB_OPT_TILED, SB_OPT_WAIT_NS,
-                   SB_OPT_FACTOR, SbError, check, lib)
+                   SB_OPT_FACTOR, SB_OPT_TEST_BAD_COL, SB_ERR_BOUNDS, SbError, check, lib)
 
 __all__ = [
     "SB_ASB", "SB_BSB", "SB_DSB", "SB_J_FP32", "SB_J_BF16", "SB_OPT_GRAPH", "SB_OPT_TILED",
     "SB_OPT_STREAM", "SB_OPT_ROWS_PER_WARP", "SB_OPT_HEAVY_FIRST", "SB_OPT_R1_LANES", "SB_OPT_STEP_RT", "SB_OPT_STEP_RPC",
     "SB_OPT_STEP_UNROLL", "SB_OPT_DSB_SIGNS", "SB_OPT_REPLICA_GROUPS", "SB_OPT_L2_PERSIST",
-    "SB_OPT_WAIT_NS", "SB_OPT_TEST_SKIP_STAGE", "SB_OPT_FACTOR", "SbError",
+    "SB_OPT_WAIT_NS", "SB_OPT_TEST_SKIP_STAGE", "SB_OPT_FACTOR", "SB_OPT_TEST_BAD_COL",
+    "SB_ERR_BOUNDS", "SbError", "sb_checked_build", "sb_check_bounds", "decode_bounds",
     "event_params", "build_params", "sb_event_generate", "sb_qubo_build", "sb_tracks",
     "sb_qubo_build_device", "sb_qubo_factor", "sb_set_factor", "sb_factor_info",
     "sb_create", "sb_create_batch", "sb_destroy", "sb_info", "sb_step_info", "sb_gather_probe",
@@ -281,6 +282,39 @@ def sb_factor_info(ctx):
     check(lib.sb_factor_info(ctx.handle, out.ctypes.data_as(ctypes.c_void_p)))
     keys = ("set", "rows", "residual_nnz", "u_rows", "blocks", "members", "max_count")
     return {k: int(v) for k, v in zip(keys, out)}
+
+
+def sb_checked_build():
+    """True when the loaded library is the bounds-checked build."""
+    return bool(lib.sb_checked_build())
+
+
+BOUNDS_MODULES = {1: "step / energy kernels", 2: "factored kernels", 3: "row-group kernel"}
+BOUNDS_SITES = {1: "CSR column", 2: "row-pointer pair", 3: "U row", 4: "group member",
+                5: "row-group union column"}
+
+
+def decode_bounds(word):
+    """(module, site, index) of a word from sb_check_bounds (see include/sb.h);
+    None for 0."""
+    if not word:
+        return None
+    idx = word & 0xFFFFFFFF
+    if idx >= 1 << 31:
+        idx -= 1 << 32
+    return (BOUNDS_MODULES.get(word >> 48, "?"), BOUNDS_SITES.get((word >> 32) & 0xFFFF, "?"), idx)
+
+
+def sb_check_bounds():
+    """Synchronise and read / clear the recorded out-of-range indices: None if
+    none, else (status SB_ERR_BOUNDS, decoded word, message); raises on other
+    errors."""
+    w = ctypes.c_uint64()
+    st = lib.sb_check_bounds(ctypes.byref(w))
+    if st == SB_ERR_BOUNDS:
+        return st, decode_bounds(w.value), lib.sb_last_error().decode(errors="replace")
+    check(st)
+    return None
 
 
 def sb_step_info(ctx):

@@ -4,7 +4,8 @@ The library is loaded on the first call through ``lib`` (importing the package
 alone loads nothing, so the numbers-only module ``workloads`` can be imported
 without it). Loading builds the in-tree library first if it is missing or
 older than its sources; if that fails the call raises: there is no fallback
-path.
+path. With SB_LIBRARY=checked in the environment the bounds-checked build
+(libsbtrack_checked.so, same entry points) is loaded instead.
 """
 import ctypes
 import os
@@ -15,7 +16,8 @@ c_int32, c_int64, c_uint64, c_double = ctypes.c_int32, ctypes.c_int64, ctypes.c_
 c_void_p, c_char_p = ctypes.c_void_p, ctypes.c_char_p
 P = ctypes.POINTER
 
-SB_OK, SB_ERR_ARG, SB_ERR_CSR, SB_ERR_CUDA, SB_ERR_OOM, SB_ERR_TIMEOUT, SB_ERR_STATE = range(7)
+(SB_OK, SB_ERR_ARG, SB_ERR_CSR, SB_ERR_CUDA, SB_ERR_OOM, SB_ERR_TIMEOUT, SB_ERR_STATE,
+ SB_ERR_BOUNDS) = range(8)
 SB_ASB, SB_BSB, SB_DSB = 0, 1, 2
 SB_J_FP32, SB_J_BF16 = 0, 1
 SB_OPT_GRAPH = 0
@@ -33,6 +35,8 @@ SB_OPT_R1_LANES = 11
 SB_OPT_WAIT_NS = 12
 SB_OPT_TEST_SKIP_STAGE = 13
 SB_OPT_FACTOR = 14
+SB_OPT_TEST_BAD_COL = 15
+CHECKED = os.environ.get("SB_LIBRARY", "") == "checked"
 
 
 class SbEventParams(ctypes.Structure):
@@ -106,16 +110,19 @@ _SIGS = {
     "sb_autotune": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p]),
     "sb_energy_noalloc": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                     c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "sb_checked_build": (c_int32, []),
+    "sb_check_bounds": (c_int32, [P(c_uint64)]),
 }
 
 
 def _load():
-    path = _build.LIB
+    path = _build.LIB_CHECKED if CHECKED else _build.LIB
     try:
-        _build.build()
+        _build.build(checked=CHECKED)
     except Exception as exc:  # a missing toolchain with a present library is fine
         if not os.path.exists(path):
-            raise ImportError(f"libsbtrack.so is missing and could not be built: {exc}") from exc
+            raise ImportError(f"{os.path.basename(path)} is missing and could not be built: "
+                              f"{exc}") from exc
     lib = ctypes.CDLL(path)
     for name, (res, args) in _SIGS.items():
         fn = getattr(lib, name)
@@ -145,7 +152,7 @@ class _Lib:
 
 
 lib = _Lib()
-LIB_PATH = _build.LIB
+LIB_PATH = _build.LIB_CHECKED if CHECKED else _build.LIB
 
 
 def check(status):

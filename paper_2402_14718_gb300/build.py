@@ -1,5 +1,9 @@
 """Build the in-tree shared library ``libsbtrack.so`` (CUDA kernels for
 sm_103a + host C++) with nvcc and g++; objects go to ``_build/``.
+``build(checked=True)`` builds the bounds-checked library
+``libsbtrack_checked.so`` instead (every kernel source compiled with
+-DSB_CHECKED=1; objects in ``_build/checked/``; the host C++ objects are
+shared).
 
 Host C++ is compiled with -ffp-contract=off -fno-builtin: the event generator
 and the QUBO builder must evaluate each double expression exactly as written
@@ -16,6 +20,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsbtrack.so")
+LIB_CHECKED = os.path.join(PKG, "libsbtrack_checked.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 CU = ["api.cu", "device/kernels.cu", "device/stream.cu", "device/rw.cu", "device/noalloc.cu", "device/build.cu",
@@ -55,17 +60,19 @@ def _deps():
     return out
 
 
-def build(verbose=False, force=False, ptxas_verbose=False):
+def build(verbose=False, force=False, ptxas_verbose=False, checked=False):
     """Compile what is stale; SB_EXTRA_NVCC (environment) appends nvcc flags."""
-    os.makedirs(BUILD, exist_ok=True)
-    extra = os.environ.get("SB_EXTRA_NVCC", "").split()
+    cu_dir = os.path.join(BUILD, "checked") if checked else BUILD
+    lib_path = LIB_CHECKED if checked else LIB
+    os.makedirs(cu_dir, exist_ok=True)
+    extra = os.environ.get("SB_EXTRA_NVCC", "").split() + (["-DSB_CHECKED=1"] if checked else [])
     deps = _deps()
     nvcc = _nvcc()
     jobs = []
     objs = []
     for f in CU:
         src = os.path.join(CSRC, f)
-        obj = os.path.join(BUILD, f.replace("/", "_") + ".o")
+        obj = os.path.join(cu_dir, f.replace("/", "_") + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + deps):
             cmd = [nvcc, ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -86,13 +93,14 @@ def build(verbose=False, force=False, ptxas_verbose=False):
         for o in outs:
             if o.strip():
                 print(o)
-    if jobs or not os.path.exists(LIB) or _stale(LIB, objs):
+    if jobs or not os.path.exists(lib_path) or _stale(lib_path, objs):
         lib64 = os.path.join(_cuda_home(), "lib64")
-        _run([nvcc, ARCH, "-shared", "-cudart", "shared", "-o", LIB + ".tmp"] + objs +
+        _run([nvcc, ARCH, "-shared", "-cudart", "shared", "-o", lib_path + ".tmp"] + objs +
              ["-Xlinker", "-rpath," + lib64])
-        os.replace(LIB + ".tmp", LIB)
-    return LIB
+        os.replace(lib_path + ".tmp", lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, force="--force" in sys.argv, ptxas_verbose="--ptxas" in sys.argv))
+    print(build(verbose=True, force="--force" in sys.argv, ptxas_verbose="--ptxas" in sys.argv,
+                checked="--checked" in sys.argv))

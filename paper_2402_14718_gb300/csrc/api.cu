@@ -1855,6 +1855,10 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     fs.G = fG;
     fs.NCH = fNCH;
     fs.tiles = ftiles;
+    fs.n = c->n;
+    fs.urows = c->fac_urows;
+    fa.urows = c->fac_urows;
+    fa.rnnz = c->fac_rnnz;
     fa.head = c->d_f_head;
     fa.K = c->fac_K;
     fa.jf = c->fac_jf;
@@ -1940,6 +1944,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
     ra.y = c->d_y;
     ra.n = c->n;
     ra.R = c->R;
+    ra.xrows = c->n + c->fac_urows;  // the extended CSR's columns n + u are U rows
     ra.ngroups = c->frw_ngroups;
     ra.gpc = std::max(sbd::kRwBlock / 32, c->step_rpc > 0 ? c->step_rpc / 2 : 0);
     ra.cta_order = nullptr;
@@ -1995,6 +2000,7 @@ sb_status enqueue_steps(sb_ctx* c, int variant, double a0, double dt, int32_t st
   a.G = t.G;
   a.unroll = c->step_unroll;
   a.tile0 = 0;
+  a.nnz = c->nnz;
   a.rpc = std::max(256 / t.G, c->step_rpc);
   a.frec = nullptr;
   if (c->step_rpc < 0) {  // one wave: every resident CTA walks one contiguous row chunk
@@ -2209,6 +2215,7 @@ sb_status readout(sb_ctx* c, const int8_t* d_spins, int32_t R, cudaStream_t s) {
   a.R = R;
   a.G = t.G;
   a.partial = c->d_partial;
+  a.nnz = c->nnz;
   SB_CUDA(sbd::launch_energy_partial(t, a, s));
   SB_CUDA(sbd::launch_energy_reduce(c->d_partial, c->d_ev_blk0, c->E, R, c->d_Eall, s));
   SB_CUDA(sbd::launch_argmin(c->d_Eall, c->E, R, c->d_bestE, c->d_bestr, s));
@@ -2355,6 +2362,38 @@ sb_status sb_info(const sb_ctx* ctx, int32_t e, int32_t* n, int64_t* nnz, double
   if (sigma_j) *sigma_j = ctx->sigma[e];
   if (c0_auto) *c0_auto = ctx->c0_auto[e];
   return SB_OK;
+}
+
+int32_t sb_checked_build(void) { return SB_CHECKED ? 1 : 0; }
+
+sb_status sb_check_bounds(uint64_t* first) {
+  return sbh::guarded("sb_check_bounds", [&]() -> sb_status {
+    if (!first) {
+      set_error("sb_check_bounds: first must not be NULL");
+      return SB_ERR_ARG;
+    }
+    *first = 0;
+    if (!SB_CHECKED) return SB_OK;
+    SB_CUDA(cudaDeviceSynchronize());
+    unsigned long long w[3] = {0, 0, 0};
+    SB_CUDA(sbd::chk_read_kernels(&w[0]));
+    SB_CUDA(sbd::chk_read_factor(&w[1]));
+    SB_CUDA(sbd::chk_read_rw(&w[2]));
+    static const char* const kModule[3] = {"step / energy kernels", "factored kernels",
+                                            "row-group kernel"};
+    static const char* const kSite[6] = {"?", "CSR column", "row-pointer pair", "U row",
+                                         "group member", "row-group union column"};
+    for (int m = 0; m < 3; ++m) {
+      if (!w[m]) continue;
+      const uint32_t site = (uint32_t)(w[m] >> 32), idx = (uint32_t)w[m];
+      *first = ((uint64_t)(m + 1) << 48) | ((uint64_t)(site & 0xffff) << 32) | idx;
+      set_error(std::string("sb_check_bounds: ") + kModule[m] + ": " +
+                (site < 6 ? kSite[site] : "?") + " " + std::to_string((int32_t)idx) +
+                " outside its array");
+      return SB_ERR_BOUNDS;
+    }
+    return SB_OK;
+  });
 }
 
 sb_status sb_step_info(const sb_ctx* ctx, int32_t* rows_per_warp, int64_t* union_entries) {
@@ -2808,6 +2847,7 @@ sb_status sb_backward(sb_ctx* ctx, double a0, double c0, double dt, int32_t step
     a.rpc = 256 / t.G;
     a.unroll = 4;
     a.tile0 = 0;
+    a.nnz = ctx->nnz;
     a.ytil = nullptr;
     a.mask = nullptr;
     a.frec = nullptr;
@@ -3118,6 +3158,21 @@ sb_status sb_set_option(sb_ctx* ctx, int32_t key, int64_t value) {
         return SB_OK;
       case 8:  // SB_OPT_STREAM
         ctx->use_stream = value != 0;
+        ctx->graph.reset();
+        return SB_OK;
+      case 15:  // SB_OPT_TEST_BAD_COL (bounds-checked build only)
+        if (!SB_CHECKED) {
+          set_error("sb_set_option: SB_OPT_TEST_BAD_COL needs the bounds-checked build");
+          return SB_ERR_ARG;
+        }
+        if (value < 0 || value >= ctx->nnz) {
+          set_error("sb_set_option: SB_OPT_TEST_BAD_COL must be a CSR entry in [0, nnz)");
+          return SB_ERR_ARG;
+        }
+        {
+          const int32_t bad = ctx->n + 7;
+          SB_CUDA(cudaMemcpy(ctx->d_col + value, &bad, sizeof(bad), cudaMemcpyHostToDevice));
+        }
         ctx->graph.reset();
         return SB_OK;
       case 14:  // SB_OPT_FACTOR

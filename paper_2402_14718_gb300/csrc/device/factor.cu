@@ -134,8 +134,9 @@ __device__ __forceinline__ void store_u(const FacSumArgs& a, int g, size_t off, 
                                         const float (&U)[K][P]) {
 #pragma unroll
   for (int s = 0; s < K; ++s) {
-    const int u = __ldg(a.gout + (size_t)g * K + s);
+    int u = __ldg(a.gout + (size_t)g * K + s);
     if (u < 0) continue;
+    u = chk_idx(u, a.urows, kChkURow);
     if (MODE == 0) {
       float4* p = reinterpret_cast<float4*>(static_cast<float*>(a.U) + (size_t)u * a.R + off);
 #pragma unroll
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(kFacBlock, (FacMinBlocks<MODE, NCH>::sum)) k_f
     int mr = 0, ms = 0;
     if (l < cnt) {
       const int t = mb + l;
-      mr = __ldg(a.gmem + t);
+      mr = chk_idx(__ldg(a.gmem + t), a.n, kChkMember);
 #pragma unroll
       for (int s = 1; s < K; ++s) ms += t >= bnd[s] ? 1 : 0;
     }
@@ -463,10 +464,12 @@ __global__ void __launch_bounds__(kFacBlock, (FacMinBlocks<MODE, NCH>::step)) k_
 #pragma unroll
   for (int s = 0; s < K; ++s) {
     us[s] = (int)__ldg(hd + kFacHead + s);
+    if (us[s] >= 0) us[s] = chk_idx(us[s], a.urows, kChkURow);
     if (us[s] >= 0)
       prefetch_l2(static_cast<const char*>(a.U) + ((size_t)us[s] * R + off) * (MODE == 0 || NCH == 2 ? 4 : 2));
   }
-  const int p0 = __ldg(a.rrowptr + row), p1 = __ldg(a.rrowptr + row + 1);
+  int p0 = __ldg(a.rrowptr + row), p1 = __ldg(a.rrowptr + row + 1);
+  chk_rows(p0, p1, a.rnnz);
 
   // residual row, in column order: its first kFacHead entries from the head,
   // the rest from the residual CSR
@@ -479,7 +482,7 @@ __global__ void __launch_bounds__(kFacBlock, (FacMinBlocks<MODE, NCH>::step)) k_
     int mc = 0;
     float mw = 0.f;
     if (l < cnt) {
-      mc = (int)__ldg(hd + hb + l);
+      mc = chk_idx((int)__ldg(hd + hb + l), a.n, kChkCol);
       mw = head_j<JT>(hd, hb + l);
       if (MODE == 1) mw *= kSignScale;  // 2^7 J: sign bytes read as 2^-7 sgn
     }
@@ -490,7 +493,7 @@ __global__ void __launch_bounds__(kFacBlock, (FacMinBlocks<MODE, NCH>::step)) k_
     int mc = 0;
     float mw = 0.f;
     if (l < cnt) {
-      mc = __ldg(a.rcol + pb + l);
+      mc = chk_idx(__ldg(a.rcol + pb + l), a.n, kChkCol);
       mw = jv(J, pb + l);
       if (MODE == 1) mw *= kSignScale;
     }
@@ -663,5 +666,7 @@ cudaError_t launch_step_fac(int variant, int jbf16, const FacStepArgs& a, cudaSt
   if (a.n <= 0) return cudaSuccess;
   return jbf16 ? launch_step_j<__nv_bfloat16>(variant, a, s) : launch_step_j<float>(variant, a, s);
 }
+
+SB_CHECK_READER(chk_read_factor)
 
 }  // namespace sbd

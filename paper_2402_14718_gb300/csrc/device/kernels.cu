@@ -161,13 +161,14 @@ __global__ void __launch_bounds__(kBlock, StepMinBlocks<NCH>::value) k_step(cons
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[j][v] = 0.f;
 
-  const int p0 = __ldg(a.rowptr + row), p1 = __ldg(a.rowptr + row + 1);
+  int p0 = __ldg(a.rowptr + row), p1 = __ldg(a.rowptr + row + 1);
+  chk_rows(p0, p1, a.nnz);
   for (int pb = p0; pb < p1; pb += G) {
     const int cnt = min(G, p1 - pb);
     int mc = 0;
     float mv = 0.f;
     if (g < cnt) {
-      mc = __ldg(a.col + pb + g);
+      mc = chk_idx(__ldg(a.col + pb + g), a.n, kChkCol);
       mv = jval(J, pb + g);
       if (use_sgn) mv *= kSignScale;  // 2^7 J: sign bytes read as 2^-7 sgn
     }
@@ -332,7 +333,8 @@ __global__ void __launch_bounds__(kBlock) k_step_r1(const StepArgs a) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= a.n) return;
   const JT* J = static_cast<const JT*>(a.J);
-  const int p0 = __ldg(a.rowptr + row), p1 = __ldg(a.rowptr + row + 1);
+  int p0 = __ldg(a.rowptr + row), p1 = __ldg(a.rowptr + row + 1);
+  chk_rows(p0, p1, a.nnz);
   float acc = 0.f;
   int p = p0;
   for (; p + 8 <= p1; p += 8) {
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(kBlock) k_step_r1(const StepArgs a) {
     float w[8], xv[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      c[u] = __ldg(a.col + p + u);
+      c[u] = chk_idx(__ldg(a.col + p + u), a.n, kChkCol);
       w[u] = jval(J, p + u);
     }
 #pragma unroll
@@ -349,7 +351,7 @@ __global__ void __launch_bounds__(kBlock) k_step_r1(const StepArgs a) {
     for (int u = 0; u < 8; ++u) acc = fmaf(w[u], VARIANT == 2 ? sgnf(xv[u]) : xv[u], acc);
   }
   for (; p < p1; ++p) {
-    const float xv = __ldg(a.xin + __ldg(a.col + p));
+    const float xv = __ldg(a.xin + chk_idx(__ldg(a.col + p), a.n, kChkCol));
     acc = fmaf(jval(J, p), VARIANT == 2 ? sgnf(xv) : xv, acc);
   }
   const float pa = a.a0 - __ldg(a.sched + a.k);
@@ -389,7 +391,8 @@ __global__ void __launch_bounds__(kBlock) k_step_r1g(const StepArgs a) {
   if (row >= a.n) return;  // the whole group leaves together
   const unsigned mask = group_mask(G);
   const JT* J = static_cast<const JT*>(a.J);
-  const int p0 = __ldg(a.rowptr + row), p1 = __ldg(a.rowptr + row + 1);
+  int p0 = __ldg(a.rowptr + row), p1 = __ldg(a.rowptr + row + 1);
+  chk_rows(p0, p1, a.nnz);
   float acc = 0.f;
   for (int pb = p0; pb < p1; pb += G * U) {
     float w[U], xv[U];
@@ -399,7 +402,7 @@ __global__ void __launch_bounds__(kBlock) k_step_r1g(const StepArgs a) {
       int c = row;
       w[u] = 0.f;
       if (p < p1) {
-        c = __ldg(a.col + p);
+        c = chk_idx(__ldg(a.col + p), a.n, kChkCol);
         w[u] = jval(J, p);
       }
       xv[u] = __ldg(a.xin + c);
@@ -466,13 +469,14 @@ __global__ void __launch_bounds__(kDsbBlock, SB_DSB_MINB) k_step_dsb16(const Ste
     float acc[16];
 #pragma unroll
     for (int v = 0; v < 16; ++v) acc[v] = 0.f;
-    const int p0 = __ldg(a.rowptr + row), p1 = __ldg(a.rowptr + row + 1);
+    int p0 = __ldg(a.rowptr + row), p1 = __ldg(a.rowptr + row + 1);
+    chk_rows(p0, p1, a.nnz);
     for (int pb = p0; pb < p1; pb += G) {
       const int cnt = min(G, p1 - pb);
       int mc = 0;
       float mv = 0.f;
       if (g < cnt) {
-        mc = __ldg(a.col + pb + g);
+        mc = chk_idx(__ldg(a.col + pb + g), a.n, kChkCol);
         mv = jval(J, pb + g);
         mv *= kSignScale;  // 2^7 J: sign bytes read as 2^-7 sgn
       }
@@ -1144,13 +1148,14 @@ __global__ void __launch_bounds__(kBlock) k_energy_partial(const EnergyArgs a) {
     for (int j = 0; j < NCH; ++j)
 #pragma unroll
       for (int v = 0; v < V; ++v) inner[j][v] = 0.0;
-    const int p0 = a.rowptr[row], p1 = a.rowptr[row + 1];
+    int p0 = a.rowptr[row], p1 = a.rowptr[row + 1];
+    chk_rows(p0, p1, a.nnz);
     for (int pb = p0; pb < p1; pb += G) {
       const int cnt = min(G, p1 - pb);
       int mc = 0;
       double mv = 0.0;
       if (g < cnt) {
-        mc = a.col[pb + g];
+        mc = chk_idx(a.col[pb + g], a.n, kChkCol);
         mv = a.qval[pb + g];
       }
       for (int q = 0; q < cnt; ++q) {
@@ -1498,5 +1503,7 @@ cudaError_t launch_best_T(const float* x, const int32_t* row_event, const int32_
   k_best_T<<<grid_for(n, kBlock), kBlock, 0, s>>>(x, row_event, best_r, n, R, T);
   return cudaGetLastError();
 }
+
+SB_CHECK_READER(chk_read_kernels)
 
 }  // namespace sbd

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "checks.cuh"
+
 namespace sbd {
 
 // Replica tiling of the N x R state: each row is handled by a group of G
@@ -52,6 +54,7 @@ struct StepArgs {
   const int32_t* cta_order = nullptr;
   int32_t unroll;         // neighbours in flight per thread (4)
   int32_t tile0;          // first replica tile of this launch (sequential replica groups)
+  int64_t nnz = INT64_MAX;  // CSR entries (the bounds-checked build tests rowptr against it)
 };
 
 cudaError_t launch_step(int variant, int jbf16, const Tiling& t, const StepArgs& a,
@@ -120,6 +123,7 @@ struct EnergyArgs {
   int32_t nblk;
   int32_t n, R, G;
   double* partial;         // [nblk x R] scratch
+  int64_t nnz = INT64_MAX; // CSR entries, where known (bounds-checked build)
 };
 cudaError_t launch_energy_partial(const Tiling& t, const EnergyArgs& a, cudaStream_t s);
 // E[e*R + r] = sum of the event's block partials, in block order.
@@ -239,6 +243,7 @@ struct FacSumArgs {
   const uint8_t* sgn_in; // dSB: sign bytes of x_k [n x R]
   void* U;               // [U rows x R]: FP32 (aSB / bSB) or BF16 (dSB)
   int32_t R, G, NCH, tiles;
+  int32_t n, urows;      // state rows and U rows (bounds-checked build)
 };
 
 // Row head of the factored step (fac_head_words() 32-bit words per row): the
@@ -280,6 +285,8 @@ struct FacStepArgs {
   const uint8_t* sgn_in;   // dSB
   uint8_t* sgn_out;        // dSB
   int32_t n, R, G, NCH, tiles;
+  int32_t urows;       // U rows (bounds-checked build)
+  int64_t rnnz;        // residual entries (bounds-checked build)
 };
 
 // Lane-group shape of the factored kernels for R replicas (false: R not supported):
@@ -328,6 +335,7 @@ struct RwArgs {
   // CTA b works on chunk cta_order[b] (chunks of gpc groups, heaviest first,
   // so that the last CTAs of a step are light); NULL: chunk b
   const int32_t* cta_order = nullptr;
+  int32_t xrows = 0;         // rows of xin (state rows + U rows of the extended CSR; bounds-checked build)
 };
 constexpr int kRwMaxRows = 4;  // RW is 2 or 4 (the mask has 4 bits)
 #ifndef SB_RW_BLOCK

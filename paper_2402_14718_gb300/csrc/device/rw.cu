@@ -162,8 +162,9 @@ __global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a
           const unsigned v = (unsigned)__shfl_sync(0xffffffffu, pk, q0 + u);
           w[u] = jp.shfl(q0 + u);
           m[u] = v & 15u;
+          const unsigned cu = (unsigned)chk_idx((int)(v >> 4), a.xrows > 0 ? a.xrows : a.n, kChkEntry);
           if (use_sgn) {
-            const uint32_t* ps = reinterpret_cast<const uint32_t*>(xl + (size_t)(v >> 4) * rb);
+            const uint32_t* ps = reinterpret_cast<const uint32_t*>(xl + (size_t)cu * rb);
 #pragma unroll
             for (int j = 0; j < NCH; ++j) {
               const uint32_t t = __ldg(ps + 32 * j);
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(kRwBlock, SB_RW_MINB) k_step_rw(const RwArgs a
               for (int k = 0; k < 4; ++k) xv[u][j][k] = scaled_sign_of_byte(t, k);
             }
           } else {
-            const float4* px = reinterpret_cast<const float4*>(xl + (size_t)(v >> 4) * rb);
+            const float4* px = reinterpret_cast<const float4*>(xl + (size_t)cu * rb);
 #pragma unroll
             for (int j = 0; j < NCH; ++j) {
               const float4 t = __ldg(px + 32 * j);
@@ -297,5 +298,7 @@ cudaError_t launch_fill_ejv(const void* J, int jbf16, const int32_t* pos, int64_
                                            static_cast<float*>(ejv));
   return cudaGetLastError();
 }
+
+SB_CHECK_READER(chk_read_rw)
 
 }  // namespace sbd
