@@ -225,14 +225,21 @@ def step_kernels(cfg, variant, R, info):
 _CAPTURE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
             "-k regex:\"k_fac_sum|{step}\" -s 2 -c 2 python bench.py{args} --profile-steps 4")
 MEASURED_TRAFFIC = {
-    ("batch512", "dsb", ("k_fac_sum", "k_step_fac"), "4fda71d6f28a04a0"): {
-        "bytes_per_step": 679649792 + 7449627392,
-        "source": _CAPTURE.format(step="k_step_fac", args="")},
-    ("event10k", "dsb", ("k_fac_sum", "k_step_fac"), "4fda71d6f28a04a0"): {
-        "bytes_per_step": 101213184 + 1215277568,
+    # the full batch holds ~8 GB on the device: counters are taken on every 4th
+    # event (128 events, sum N = 1,120,853; 1,531,240,704 B per step) and scaled
+    # by the spin-updates (x 5,677,517 / 1,120,853). Per spin-update the traffic
+    # rises with the working set (20.7 / 21.3 B at 64 / 128 events; 22.4 B in an
+    # earlier capture of the whole batch with the same kernel code), so this is
+    # a lower bound by about 5 %.
+    ("batch512", "dsb", ("k_fac_sum", "k_step_fac"), "9ffffff132286b78"): {
+        "bytes_per_step": 7756275915,
+        "source": _CAPTURE.format(step="k_step_fac", args=" --events 128") +
+        " (every 4th event; scaled to the 512 events by the spin-updates)"},
+    ("event10k", "dsb", ("k_fac_sum", "k_step_fac"), "9ffffff132286b78"): {
+        "bytes_per_step": 78817024 + 22779136 + 717631232 + 497986304,
         "source": _CAPTURE.format(step="k_step_fac", args=" --workload event10k --variant dsb")},
-    ("event1000", "bsb", ("k_fac_sum", "k_step_rw"), "7bf9b71bcf8d0102"): {
-        "bytes_per_step": 41916928 + 134077696,
+    ("event1000", "bsb", ("k_fac_sum", "k_step_rw"), "b5333c45d2b32b72"): {
+        "bytes_per_step": 40304896 + 1613056 + 101010688 + 33296128,
         "source": _CAPTURE.format(step="k_step_rw", args=" --workload event1000")},
 }
 
@@ -481,150 +488,227 @@ def _ttt_at(t, p):
     return t * math.log(0.01) / math.log(1.0 - p)
 
 
+def ttt_rounds(P, q):
+    """Rounds of a solver needed for every event (last axis) to have succeeded
+    with probability q, given one round's per-event success probability P:
+    max_e max(1, ln(1 - q) / ln(1 - P_e)), inf where some P_e = 0."""
+    with np.errstate(divide="ignore"):
+        need = np.where(P >= q, 1.0, np.log(1.0 - q) / np.log(1.0 - np.minimum(P, 1 - 1e-16)))
+    need = np.where(P <= 0.0, np.inf, np.maximum(need, 1.0))
+    return need.max(axis=-1)
+
+
+def ttt_strategy(t_list, P_list, q):
+    """Best round over two run configurations: run configuration c up to its
+    checkpoint k_c, or not at all (k_c = -1). A round costs t_1(k_1) + t_2(k_2)
+    and succeeds for an event with 1 - (1 - P_1(k_1)) (1 - P_2(k_2)); rounds
+    are repeated until every event has succeeded with probability q. t_c:
+    [checkpoints] seconds; P_c: [checkpoints, events]. Returns (seconds,
+    (k_1, k_2)); seconds = inf when no round reaches every event."""
+    (t1, t2), (P1, P2) = t_list, P_list
+    t1 = np.concatenate([[0.0], t1])
+    t2 = np.concatenate([[0.0], t2])
+    P1 = np.concatenate([np.zeros((1,) + P1.shape[1:]), P1])
+    P2 = np.concatenate([np.zeros((1,) + P2.shape[1:]), P2])
+    P = 1.0 - (1.0 - P1[:, None]) * (1.0 - P2[None, :])          # [k1 + 1, k2 + 1, events]
+    with np.errstate(invalid="ignore"):                             # 0 x inf where neither runs
+        T = (t1[:, None] + t2[None, :]) * ttt_rounds(P, q)
+    T[0, 0] = np.inf
+    i = np.unravel_index(int(np.argmin(T)), T.shape)
+    return float(T[i]), (int(i[0]) - 1, int(i[1]) - 1)
+
+
 def time_to_target(sb, w, pairs, ctx, stream, dev, plain_events, plain_runs=64, every=50,
-                   c0_scale=2.0, ref_scale=3.0, targets=(0.001, 0.005)):
+                   configs=((1, 2.0), (2, 3.0)), targets=(0.001, 0.005)):
     """Time-to-target (section "Results", Table 1): the time to reach 99.9 % of
     the lowest energy found, with 99 % probability, for every event of the
     workload.
 
-    Target of event e: E_low,e + f |E_low,e| (QUBO energies are negative),
-    E_low,e the lowest energy any run of this study found for it (the batched
-    runs, the plain runs and a reference run of 2 S steps with c0 = 3
-    c0_auto), for f = 0.001 (the paper's 99.9 %) and a loosened f = 0.005 (the
-    paper also loosens its target for dSB); where a form never reaches a
-    target it is reported as "did not reach", as in Table 1. Both timed forms use c0 = 2 c0_auto (a fixed c0, as in the
-    paper; the factor 2 is where the configured c0 of the workloads reaches
-    the lowest energies in the c0 scan).
+    Two run configurations (`configs`: run length m S and a fixed c0 = s
+    c0_auto; the paper fixes c0 and picks the run length): S steps at c0 = 2
+    c0_auto (where the c0 scan finds the lowest energies of the configured
+    c0) and 2 S steps at c0 = 3 c0_auto (better on some events, worse on
+    most). Every run of the study is timed with checkpoints. Target of event
+    e: E_low,e + f |E_low,e| (QUBO energies are negative), E_low,e the lowest
+    energy any run of this study found for it, for f = 0.001 (the paper's
+    99.9 %) and a loosened f = 0.005 (the paper also loosens its target for
+    dSB); where a form never reaches a target it is reported as "did not
+    reach", as in Table 1.
 
-    Batched BF16 form: one run of all events and R replicas with an FP64
-    readout every `every` steps (timed). p_e(k) = fraction of event e's
-    replicas at or below its target at checkpoint k; one batched run succeeds
-    for event e with P_e(k) = 1 - (1 - p_e(k))^R, whole-batch runs are repeated
-    until every event has succeeded, with per-event probability q = 0.99^(1/E)
-    so that all E events succeed with 99 %: TTT = min_k t(k) max_e max(1,
-    ln(1 - q) / ln(1 - P_e(k))).
+    A round of a form runs each configuration up to a checkpoint of its own
+    choosing, or not at all, and succeeds for an event when any of its runs
+    reaches the event's target; rounds are repeated until every event has
+    succeeded, with per-event probability q = 0.99^(1/E) so that all E events
+    succeed with 99 % (ttt_strategy). Each form's TTT is its best round.
+
+    Batched BF16 form: one graph-replayed run of all events per configuration,
+    with an FP64 readout every `every` steps (timed), at the workload's R
+    replicas and, where R is a multiple of 64, at R / 8 (the form keeps the
+    replica count of its best round: where one replica often reaches the
+    target, a round of fewer replicas is shorter). p_e(k) = fraction of event
+    e's replicas at or below its target at checkpoint k; one batched run of
+    R_b replicas succeeds for event e with P_e(k) = 1 - (1 - p_e(k))^R_b.
 
     Plain FP32 form (FP32 J, one replica, one event, one kernel launch per
-    step, no graph): `plain_runs` runs of each sampled event with checkpoints
-    give its own p_e(k); a plain run is timed without checkpoints and t_e(k)
-    = t_run,e k / S. Events are solved one after another, each repeated until
-    it succeeds, with per-event probability q = 0.99^(1/E) so that all E events
-    succeed with 99 %: TTT_e = min_k t_e(k) max(1, ln(1 - q) / ln(1 - p_e(k))),
-    and the workload's plain TTT is E times the mean of TTT_e over the
-    sampled events. Efficiency and purity (Eq. 18-19) of each form's best
-    selection are reported on the sampled events."""
+    step, no graph): `plain_runs` runs of each sampled event and configuration
+    with checkpoints give its own p_e(k); a plain run is timed without
+    checkpoints and t_e(k) = t_run,e k / (m S). Events are solved one after
+    another, each with its own best round; the workload's plain TTT is E times
+    the mean of TTT_e over the sampled events. Efficiency and purity (Eq.
+    18-19) of each form's best selection (first configuration) are reported on
+    the sampled events."""
     import torch
     qs = [q for _, q in pairs]
     E = len(qs)
     R, S, a0, dt, variant = w["R"], w["S"], w["a0"], w["dt"], w["variant"]
-    n_ck = (S + every - 1) // every
-    sched = torch.tensor(np.array([a0 * k / (S - 1) for k in range(S)], np.float32), device=dev)
-    d_E = torch.empty(E * R, dtype=torch.float64, device=dev)
-    # ---- batched run with checkpoints
-    sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 1)
-    sb.sb_run(ctx, variant, a0, -c0_scale, dt, 0, R, 4242, None, stream)
-    start = torch.cuda.Event(enable_timing=True)
-    start.record(stream)
-    marks, Es = [], []
-    for k0 in range(0, S, every):
-        n = min(every, S - k0)
-        sb.sb_advance(ctx, variant, a0, -c0_scale, dt, n, sched[k0:k0 + n], stream)
-        sb.sb_readout_device(ctx, d_E, None, None, None, stream)
-        e = torch.cuda.Event(enable_timing=True)
-        e.record(stream)
-        marks.append(e)
-        Es.append(d_E.clone())
-    torch.cuda.synchronize(dev)
-    times = [start.elapsed_time(m) * 1e-3 for m in marks]
-    Eb = np.stack([e.cpu().numpy().reshape(E, R) for e in Es])   # [checkpoint, event, replica]
-    T_b, _, _ = sb.sb_best(ctx)
-    # ---- reference run: 2 S steps, c0 = 3 c0_auto
-    sched2 = torch.tensor(np.array([a0 * k / (2 * S - 1) for k in range(2 * S)], np.float32),
-                          device=dev)
-    sb.sb_run(ctx, variant, a0, -ref_scale, dt, 2 * S, R, 5151, sched2, stream)
-    sb.sb_readout_device(ctx, d_E, None, None, None, stream)
-    torch.cuda.synchronize(dev)
-    E_ref = d_E.cpu().numpy().reshape(E, R).min(axis=1)
-    # ---- plain FP32 form on the sampled events
-    plain = []
     d1 = torch.empty(1, dtype=torch.float64, device=dev)
-    for e in plain_events:
-        q = qs[e]
-        cp = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_FP32)
-        sb.sb_set_option(cp, sb.SB_OPT_GRAPH, 0)
-        c0e = c0_scale * sb.sb_info(cp)["c0_auto"]
-        sb.sb_run(cp, variant, a0, c0e, dt, 20, 1, 1, None, stream)   # warm-up
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for i in range(4):
-            sb.sb_run(cp, variant, a0, c0e, dt, S, 1, 9000 + i, None, stream)
-            sb.sb_readout_device(cp, d1, None, None, None, stream)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        t_run = e0.elapsed_time(e1) * 1e-3 / 4
-        ck = []
-        for i in range(plain_runs):
-            sb.sb_run(cp, variant, a0, c0e, dt, 0, 1, 7000 + i, None, stream)
-            row = []
-            for k0 in range(0, S, every):
-                n = min(every, S - k0)
-                sb.sb_advance(cp, variant, a0, c0e, dt, n, sched[k0:k0 + n], stream)
+    # replica counts of the batched form: the workload's R, and R / 8 (a round
+    # of fewer replicas is shorter where one replica often reaches the target)
+    batched_R = [R] + ([R // 8] if R % 64 == 0 else [])
+    shapes = []
+    for mult, c0_scale in configs:
+        Sc = mult * S
+        sched = torch.tensor(np.array([a0 * k / (Sc - 1) for k in range(Sc)], np.float32),
+                             device=dev)
+        shapes.append(dict(steps=Sc, c0_scale=c0_scale, n_ck=(Sc + every - 1) // every,
+                           sched=sched, batched=[]))
+    # ---- batched runs with checkpoints, at each replica count of the form (with
+    # the autotuner's kernel choice for that count; the workload's R is tuned already)
+    for j, Rb in enumerate(batched_R):
+        if Rb != R:
+            sb.sb_autotune(ctx, variant, Rb, 20, stream)
+        d_E = torch.empty(E * Rb, dtype=torch.float64, device=dev)
+        for ci, r in enumerate(shapes):
+            Sc, c0_scale, sched = r["steps"], r["c0_scale"], r["sched"]
+            sb.sb_set_option(ctx, sb.SB_OPT_GRAPH, 1)
+            sb.sb_run(ctx, variant, a0, -c0_scale, dt, 0, Rb, 4242 + 10 * j + ci, None, stream)
+            # the run's own time to each checkpoint: the readouts between
+            # (events before and after each) are left out, as the plain form's
+            # run time is taken without them
+            start = torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            pre, post, Es = [], [start], []
+            for k0 in range(0, Sc, every):
+                n = min(every, Sc - k0)
+                sb.sb_advance(ctx, variant, a0, -c0_scale, dt, n, sched[k0:k0 + n], stream)
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                pre.append(e)
+                sb.sb_readout_device(ctx, d_E, None, None, None, stream)
+                Es.append(d_E.clone())
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                post.append(e)
+            torch.cuda.synchronize(dev)
+            times = np.cumsum([post[i].elapsed_time(pre[i]) * 1e-3 for i in range(len(pre))]).tolist()
+            Eb = np.stack([e.cpu().numpy().reshape(E, Rb) for e in Es])   # [checkpoint, event, replica]
+            T_b = sb.sb_best(ctx)[0] if ci == 0 and Rb == R else None
+            r["batched"].append(dict(R=Rb, times=times, Eb=Eb, T_b=T_b))
+    runs = []
+    for ci, r in enumerate(shapes):
+        Sc, c0_scale, sched = r["steps"], r["c0_scale"], r["sched"]
+        # ---- plain FP32 form on the sampled events
+        plain = []
+        for e in plain_events:
+            q = qs[e]
+            cp = sb.sb_create(q.n, q.rowptr, q.col, q.val, q.lin, sb.SB_J_FP32)
+            sb.sb_set_option(cp, sb.SB_OPT_GRAPH, 0)
+            c0e = c0_scale * sb.sb_info(cp)["c0_auto"]
+            sb.sb_run(cp, variant, a0, c0e, dt, 20, 1, 1, None, stream)   # warm-up
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(4):
+                sb.sb_run(cp, variant, a0, c0e, dt, Sc, 1, 9000 + i, None, stream)
                 sb.sb_readout_device(cp, d1, None, None, None, stream)
-                row.append(d1.clone())
-            ck.append(row)
-            if i == plain_runs - 1:
-                torch.cuda.synchronize(dev)
-        Ep = np.array([[float(v.item()) for v in row] for row in ck])   # [run, checkpoint]
-        best_run = int(np.argmin(Ep[:, -1]))
-        sb.sb_run(cp, variant, a0, c0e, dt, S, 1, 7000 + best_run, None, stream)
-        T_p, _, _ = sb.sb_best(cp)
-        plain.append(dict(e=e, t_run=t_run, Ep=Ep, T=T_p))
-        sb.sb_destroy(cp)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t_run = e0.elapsed_time(e1) * 1e-3 / 4
+            ck = []
+            for i in range(plain_runs):
+                sb.sb_run(cp, variant, a0, c0e, dt, 0, 1, 7000 + i, None, stream)
+                row = []
+                for k0 in range(0, Sc, every):
+                    n = min(every, Sc - k0)
+                    sb.sb_advance(cp, variant, a0, c0e, dt, n, sched[k0:k0 + n], stream)
+                    sb.sb_readout_device(cp, d1, None, None, None, stream)
+                    row.append(d1.clone())
+                ck.append(row)
+                if i == plain_runs - 1:
+                    torch.cuda.synchronize(dev)
+            Ep = np.array([[float(v.item()) for v in row] for row in ck])   # [run, checkpoint]
+            T_p = None
+            if ci == 0:
+                best_run = int(np.argmin(Ep[:, -1]))
+                sb.sb_run(cp, variant, a0, c0e, dt, Sc, 1, 7000 + best_run, None, stream)
+                T_p = sb.sb_best(cp)[0]
+            plain.append(dict(e=e, t_run=t_run, Ep=Ep, T=T_p))
+            sb.sb_destroy(cp)
+        r["plain"] = plain
+        runs.append(r)
+    T_b = runs[0]["batched"][0]["T_b"]
+    plain = runs[0]["plain"]
     # ---- targets: the paper's (0.1 % above the lowest energy) and a loosened one
-    E_low = np.minimum(Eb.min(axis=(0, 2)), E_ref)
-    for p in plain:
-        E_low[p["e"]] = min(E_low[p["e"]], float(p["Ep"].min()))
+    E_low = np.min([b["Eb"].min(axis=(0, 2)) for r in runs for b in r["batched"]], axis=0)
+    for r in runs:
+        for p in r["plain"]:
+            E_low[p["e"]] = min(E_low[p["e"]], float(p["Ep"].min()))
     q_ev = 0.99 ** (1.0 / E)
+
+    def at_step(r, k):
+        return None if k < 0 else min(r["steps"], (k + 1) * every)
+
+    def batched_ttt(target):
+        alone, best, pick = [], math.inf, None
+        for j, Rb in enumerate(batched_R):
+            P_list = []
+            for r in runs:
+                b = r["batched"][j]
+                p_rep = (b["Eb"] <= target[None, :, None]).mean(axis=2)    # [checkpoint, event]
+                P_list.append(1.0 - (1.0 - p_rep) ** Rb)                    # one batched run, per event
+                v = np.array(b["times"]) * ttt_rounds(P_list[-1], q_ev)
+                k = int(np.argmin(v))
+                alone.append({"replicas": Rb, "steps": r["steps"], "c0_scale": r["c0_scale"],
+                              "seconds": float(v[k]) if v[k] < math.inf else "did not reach",
+                              "at_step": at_step(r, k) if v[k] < math.inf else None,
+                              "run_seconds": b["times"][-1],
+                              "events_never_reached": int(np.sum(P_list[-1][-1] <= 0.0)),
+                              "p_rep_final_median": float(np.median(p_rep[-1]))})
+            t, ks = ttt_strategy([np.array(r["batched"][j]["times"]) for r in runs], P_list, q_ev)
+            if t < best:
+                best, pick = t, (Rb, ks)
+        return {"seconds": best if best < math.inf else "did not reach",
+                "replicas": pick[0] if pick else None,
+                "round": [{"steps": r["steps"], "c0_scale": r["c0_scale"], "to_step": at_step(r, k)}
+                          for r, k in zip(runs, pick[1])] if pick else None,
+                "configurations": alone}, best
+
+    def plain_ttt(target):
+        per_event, ttt_sum = [], 0.0
+        for j, e in enumerate(r0["e"] for r0 in runs[0]["plain"]):
+            t_list, P_list = [], []
+            for r in runs:
+                p = r["plain"][j]
+                t_list.append(p["t_run"] * np.minimum(r["steps"], (np.arange(r["n_ck"]) + 1) * every)
+                              / r["steps"])
+                P_list.append((p["Ep"] <= target[e]).mean(axis=0)[:, None])   # [checkpoint, 1]
+            best, ks = ttt_strategy(t_list, P_list, q_ev)
+            ttt_sum += best
+            per_event.append({"event": e, "N": qs[e].n,
+                              "run_seconds": [r["plain"][j]["t_run"] for r in runs],
+                              "p_final": [float(P[-1, 0]) for P in P_list],
+                              "ttt_seconds": best if best < math.inf else None,
+                              "round": [at_step(r, k) for r, k in zip(runs, ks)]})
+        ttt = E * ttt_sum / max(len(runs[0]["plain"]), 1)
+        return {"seconds": ttt if ttt < math.inf else "did not reach", "per_event": per_event}, ttt
+
     results = []
     for frac in targets:
         target = E_low + frac * np.abs(E_low)
-        p_rep = (Eb <= target[None, :, None]).mean(axis=2)        # [checkpoint, event]
-        P_ev = 1.0 - (1.0 - p_rep) ** R                           # one batched run, per event
-        # batched: whole-batch runs repeated until every event has succeeded
-        ttt_b, kb = math.inf, None
-        for k in range(n_ck):
-            if np.any(P_ev[k] <= 0.0):
-                continue
-            runs = max(1.0, float(np.max(np.where(P_ev[k] >= q_ev, 1.0,
-                                                  np.log(1.0 - q_ev) / np.log(1.0 - np.minimum(P_ev[k], 1 - 1e-16))))))
-            v = times[k] * runs
-            if v < ttt_b:
-                ttt_b, kb = v, k
-        per_event, ttt_sum = [], 0.0
-        for p in plain:
-            pk = (p["Ep"] <= target[p["e"]]).mean(axis=0)
-            best, kk = math.inf, None
-            for k in range(n_ck):
-                tk = p["t_run"] * min(S, (k + 1) * every) / S
-                if pk[k] <= 0.0:
-                    continue
-                v = tk if pk[k] >= q_ev else tk * math.log(1.0 - q_ev) / math.log(1.0 - pk[k])
-                if v < best:
-                    best, kk = v, k
-            ttt_sum += best
-            per_event.append({"event": p["e"], "N": qs[p["e"]].n, "run_seconds": p["t_run"],
-                              "p_final": float(pk[-1]), "ttt_seconds": best if best < math.inf else None,
-                              "at_step": None if kk is None else min(S, (kk + 1) * every)})
-        ttt_p = E * ttt_sum / max(len(plain), 1)
+        b, ttt_b = batched_ttt(target)
+        p, ttt_p = plain_ttt(target)
         results.append({
-            "target": f"E_low + {frac:g} |E_low|",
-            "batched_bf16": {"seconds": ttt_b if ttt_b < math.inf else "did not reach",
-                             "at_step": None if kb is None else min(S, (kb + 1) * every),
-                             "events_never_reached": int(np.sum(P_ev[-1] <= 0.0)),
-                             "p_rep_final_median": float(np.median(p_rep[-1]))},
-            "plain_fp32": {"seconds": ttt_p if ttt_p < math.inf else "did not reach",
-                           "per_event": per_event},
+            "target": f"E_low + {frac:g} |E_low|", "batched_bf16": b, "plain_fp32": p,
             "speedup_batched_vs_plain": (ttt_p / ttt_b) if (ttt_b < math.inf and ttt_p < math.inf)
             else None})
     # ---- efficiency / purity and the truth energy on the sampled events
@@ -650,9 +734,9 @@ def time_to_target(sb, w, pairs, ctx, stream, dev, plain_events, plain_runs=64, 
         "definition": "time to reach the target energy with 99 % probability for every event "
                       "of the workload; targets: the paper's 99.9 % of the lowest energy found "
                       "(E_low + 0.001 |E_low|), and a loosened one",
-        "c0_scale": c0_scale, "checkpoint_every": every,
-        "reference_run": {"steps": 2 * S, "c0_scale": ref_scale, "replicas": R},
-        "batched_run_seconds": times[-1], "replicas": R, "events": E,
+        "configurations": [{"steps": r["steps"], "c0_scale": r["c0_scale"]} for r in runs],
+        "batched_replicas": batched_R,
+        "checkpoint_every": every, "replicas": R, "events": E,
         "plain_runs": {"events_sampled": len(plain), "runs_per_event": plain_runs,
                        "per_event_probability": q_ev,
                        "scaling": f"{E} x mean over the sampled events",

@@ -182,9 +182,12 @@ template <int MODE, int NCH>
 struct FacMinBlocks {
   static constexpr int sum = NCH == 2 ? 7 : 9, step = NCH == 2 ? 8 : 9;
 };
+#ifndef SB_FAC_DSB_STEP_MINB
+#define SB_FAC_DSB_STEP_MINB 12
+#endif
 template <int NCH>
 struct FacMinBlocks<1, NCH> {
-  static constexpr int sum = 10, step = 12;
+  static constexpr int sum = 10, step = SB_FAC_DSB_STEP_MINB;
 };
 
 template <int MODE, int NCH, int K>
