@@ -530,7 +530,8 @@ def time_to_target(sb, w, pairs, ctx, stream, dev, plain_events, plain_runs=64, 
     c0) and 2 S steps at c0 = 3 c0_auto (better on some events, worse on
     most). Every run of the study is timed with checkpoints. Target of event
     e: E_low,e + f |E_low,e| (QUBO energies are negative), E_low,e the lowest
-    energy any run of this study found for it, for f = 0.001 (the paper's
+    energy any run of this study at the workload's replica count (batched)
+    or of the plain form found for it, for f = 0.001 (the paper's
     99.9 %) and a loosened f = 0.005 (the paper also loosens its target for
     dSB); where a form never reaches a target it is reported as "did not
     reach", as in Table 1.
@@ -649,7 +650,9 @@ def time_to_target(sb, w, pairs, ctx, stream, dev, plain_events, plain_runs=64, 
     T_b = runs[0]["batched"][0]["T_b"]
     plain = runs[0]["plain"]
     # ---- targets: the paper's (0.1 % above the lowest energy) and a loosened one
-    E_low = np.min([b["Eb"].min(axis=(0, 2)) for r in runs for b in r["batched"]], axis=0)
+    # (the runs at R / 8 are another round shape of the batched form, not more
+    # samples of the study: they are scored against the same targets)
+    E_low = np.min([r["batched"][0]["Eb"].min(axis=(0, 2)) for r in runs], axis=0)
     for r in runs:
         for p in r["plain"]:
             E_low[p["e"]] = min(E_low[p["e"]], float(p["Ep"].min()))
