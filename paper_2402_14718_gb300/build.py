@@ -2,8 +2,8 @@
 sm_103a + host C++) with nvcc and g++; objects go to ``_build/``.
 ``build(checked=True)`` builds the bounds-checked library
 ``libsbtrack_checked.so`` instead (every kernel source compiled with
--DSB_CHECKED=1; objects in ``_build/checked/``; the host C++ objects are
-shared).
+-DSB_CHECKED=1; all its objects in ``_build/checked/``, so the two builds
+can run at the same time).
 
 Host C++ is compiled with -ffp-contract=off -fno-builtin: the event generator
 and the QUBO builder must evaluate each double expression exactly as written
@@ -82,7 +82,7 @@ def build(verbose=False, force=False, ptxas_verbose=False, checked=False):
             jobs.append(cmd)
     for f in CPP:
         src = os.path.join(CSRC, f)
-        obj = os.path.join(BUILD, f.replace("/", "_") + ".o")
+        obj = os.path.join(cu_dir, f.replace("/", "_") + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + deps):
             jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-builtin",
