@@ -447,6 +447,22 @@ def test_conflicting_doublets_are_removed_and_short_tracks_dropped():
     assert tracks.chain({(0, 1), (1, 2), (2, 3)}) == [[0, 1, 2, 3]]
 
 
+def test_efficiency_and_purity_by_hand():
+    """Eq. 18-19 on a hand-built event: efficiency = TP / (TP + FN) over the
+    true doublets (hits of one particle on adjacent layers), purity = TP /
+    (TP + FP) over the selected ones; the two differ, so a swap is caught."""
+    from types import SimpleNamespace
+    # particle 0 on layers 0-3, particle 1 on layers 0-3, particle 2 on layers
+    # 0 and 2 (no adjacent pair), two noise hits
+    ev = SimpleNamespace(particle=[0, 0, 0, 0, 1, 1, 1, 1, 2, 2, -1, -1],
+                         layer=[0, 1, 2, 3, 0, 1, 2, 3, 0, 2, 1, 2])
+    assert tracks.true_doublets(ev) == {(0, 1), (1, 2), (2, 3), (4, 5), (5, 6), (6, 7)}
+    reco = {(0, 1), (1, 2), (2, 3), (10, 11)}
+    assert tracks.score(ev, reco) == (3, 1, 3, 0.5, 0.75)
+    reco = {(4, 5), (5, 6), (6, 7), (0, 1), (1, 2), (2, 3), (8, 9), (10, 11)}
+    assert tracks.score(ev, reco) == (6, 2, 0, 1.0, 0.75)
+
+
 # ---------------------------------------------------------------- TTT
 def test_ttt_closed_forms():
     assert ttt.ttt_at(2.0, 1.0) == 2.0
