@@ -77,3 +77,26 @@ def test_single_rank_has_no_collective():
     import numpy as np
     E, win, T = bench.best_across_ranks([-1.0, -2.0], np.ones(4, np.uint8), [0, 2, 4])
     assert E.tolist() == [-1.0, -2.0] and win.tolist() == [0, 0] and T.tolist() == [1, 1, 1, 1]
+
+
+def test_reference_arm_under_torchrun_prints_one_line():
+    """The reference arm launched as the driver launches N > 1 (torchrun, two
+    ranks on 127.0.0.1): rank 0 alone times the oracle and prints one JSON
+    line; the other rank exits 0 without work. Loads no part of the library."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py",
+           "--impl", "reference", "--gpus", "2", "--workload", "event100", "--steps", "1",
+           "--warmup", "0"]
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run(cmd, cwd=root, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
