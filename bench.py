@@ -238,6 +238,9 @@ MEASURED_TRAFFIC = {
     ("event10k", "dsb", ("k_fac_sum", "k_step_fac"), "9ffffff132286b78"): {
         "bytes_per_step": 78817024 + 22779136 + 717631232 + 497986304,
         "source": _CAPTURE.format(step="k_step_fac", args=" --workload event10k --variant dsb")},
+    ("event10k_1m", "dsb", ("k_fac_sum", "k_step_fac"), "9ffffff132286b78"): {
+        "bytes_per_step": 255639040 + 96422912 + 1643463936 + 1169588992,
+        "source": _CAPTURE.format(step="k_step_fac", args=" --workload event10k_1m --variant dsb")},
     ("event1000", "bsb", ("k_fac_sum", "k_step_rw"), "b5333c45d2b32b72"): {
         "bytes_per_step": 40304896 + 1613056 + 101010688 + 33296128,
         "source": _CAPTURE.format(step="k_step_rw", args=" --workload event1000")},
